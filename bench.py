@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the TileGS forward path on GB300.
+
+A step is one whole frame of the hot path -- projection, tile intersection,
+ordering (binned: depth range, bin count/scan/scatter, repair; baseline: global
+radix sort) and rasterisation -- of the 1M-Gaussian mixture scene at
+1920x1080 (fx = fy = 1100), inputs resident in HBM.  The headline `value` is
+the binned (EXACT) path's frame throughput in Mpix/s; the plain global-sort
+path is timed beside it on the same GPU, with per-stage and raster-kernel
+times for both.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Timing: W untimed warm-up frames, then K frames, each preceded by an L2 flush
+(a 256 MiB write outside the timed events) and bracketed by CUDA events on
+the stream the library launches on; barrier + synchronize around the loop,
+max over ranks.  Multi-GPU: independent replicas, one frame per rank per step
+(no data-path collective; the method does not shard a frame).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "raster ms/frame & Mpix/s at 1080p: binned vs global-sort, same GB300, err≤1e-5"
+WORKLOAD = "mid"
+WORKLOAD_DESC = ("1M Gaussians (90% 64-component anisotropic mixture + 10% background shell, "
+                 "log-scales N(-5,1), SH degree 3 N(0,0.3), opacity sigmoid(N(0,1.5)), seed 1); "
+                 "camera (0,0,3) -> origin, 1920x1080, fx=fy=1100")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- dist
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def dist_init(backend):
+    import torch.distributed as dist
+    ws, rank, _ = dist_env()
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist if ws > 1 else None
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------------- oracle timing (cpu_baseline / reference arm)
+def oracle_frame_estimate(scene, cam, n_sample_tiles=48, seed=7):
+    """Time the CPU oracle on a bounded sample of the frame.
+
+    The per-frame setup (projection of every Gaussian, emission, the per-tile
+    sorted lists) is timed once in full; the compositing is timed on a seeded
+    sample of tiles with all host cores (OpenMP over tiles).  The frame
+    estimate is setup + composite_time * (tiles / sampled tiles)."""
+    import numpy as np
+
+    import oracle as O
+    ncores = len(os.sched_getaffinity(0))
+    O.set_threads(ncores)
+    t0 = time.perf_counter()
+    proj = O.project(scene, cam)
+    ent = O.emit(proj, cam.width, cam.height)
+    tx, ty = O.tiles_xy(cam.width, cam.height)
+    off, stream = O.sort_tiles(ent, tx * ty)
+    t_setup = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    tiles = rng.choice(tx * ty, size=min(n_sample_tiles, tx * ty), replace=False).astype(np.int32)
+    t1 = time.perf_counter()
+    O.composite(proj, off, stream, cam.width, cam.height, tiles=tiles)
+    t_comp = time.perf_counter() - t1
+    frame_s = t_setup + t_comp * (tx * ty) / len(tiles)
+    return dict(frame_s=frame_s, t_setup=t_setup, t_comp=t_comp, n_tiles=int(len(tiles)),
+                total_tiles=int(tx * ty), cores=ncores, entries=int(ent[0].shape[0]))
+
+
+def cpu_baseline_block(scene, cam):
+    est = oracle_frame_estimate(scene, cam)
+    P = cam.width * cam.height
+    return {"value": round(P / est["frame_s"] / 1e6, 6), "unit": "Mpix/s", "cores": est["cores"],
+            "kind": "oracle",
+            "sample": (f"full projection+emission+per-tile sort of the frame ({est['t_setup']:.2f} s, 1 thread) "
+                       f"+ compositing of {est['n_tiles']} seeded tiles of {est['total_tiles']} "
+                       f"({est['t_comp']:.2f} s, {est['cores']} threads), extrapolated to the frame"),
+            "frame_s_est": round(est["frame_s"], 3)}
+
+
+def run_reference(args):
+    """The oracle as the reference arm (rank 0 only)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2609_03613_gb300 import scenes
+    scene, cam = scenes.workload(WORKLOAD)
+    P = cam.width * cam.height
+    times = []
+    blocks = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        est = oracle_frame_estimate(scene, cam, n_sample_tiles=16, seed=100 + i)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(est["frame_s"])
+            blocks.append((dt, est))
+    frame_s = sum(times) / len(times)
+    value = P / frame_s / 1e6
+    est = blocks[-1][1]
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Mpix/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(frame_s * 1e3, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD_DESC, "path": "CPU oracle (plain C, float32 spec order)"},
+           "cpu_baseline": {"value": round(value, 6), "unit": "Mpix/s", "cores": est["cores"], "kind": "oracle",
+                            "sample": ("each step: full projection+emission+per-tile sort, compositing of 16 "
+                                       "seeded tiles on all cores, extrapolated to the frame")},
+           "e2e": {"value": round(value, 6), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------- ours
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("raster.cu", "internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2609_03613_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    """ncu DRAM traffic of the binned raster kernel for this workload, if the
+    profile was taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "raster_binned_mid.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None, None
+    if d.get("kernel_hash") != kernel_hash():
+        return None, d
+    return d.get("dram_bytes_per_launch"), d
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2609_03613_gb300 import scenes, tilegs as G
+
+    ws, rank, local = dist_env()
+    dist = dist_init("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    scene, cam = scenes.workload(WORKLOAD)
+    P = cam.width * cam.height
+    ds = G.DeviceScene.from_numpy(scene, dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    bg = (0.0, 0.0, 0.0)
+    H, W = cam.height, cam.width
+
+    def make(mode):
+        ctx = G.Context(mode)
+        out = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
+               torch.empty((H, W), dtype=torch.int32, device=dev))
+        ctx.render(ds, cam, bg, out)  # sizes the scratch (one read of M)
+        torch.cuda.synchronize()
+        m = ctx.last_entry_count()
+        ctx.reserve(ds.n, int(m * 1.25) + 1024, W, H)
+        ctx.enable_timing(True)
+        return ctx, out, m
+
+    def timed(ctx, out, steps, warmup, sampler=None):
+        for _ in range(warmup):
+            ctx.render(ds, cam, bg, out, flags=G.RENDER_NO_SYNC)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        stage = {s: [] for s in G.STAGES}
+        l0 = ctx.launch_count()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record()
+            ctx.render(ds, cam, bg, out, flags=G.RENDER_NO_SYNC)
+            ev[i][1].record()
+            st = ctx.stage_times()  # events on the library's stream; synchronises
+            for s in G.STAGES:
+                stage[s].append(st[s])
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        wall = time.perf_counter() - w0
+        ms = [a.elapsed_time(b) for a, b in ev]
+        launches = ctx.launch_count() - l0
+        return ms, stage, wall, launches
+
+    ctx_b, out_b, m_b = make("exact")
+    ctx_g, out_g, m_g = make("global")
+    assert ctx_b.error() == 0 and ctx_g.error() == 0
+
+    with ClockSampler(local) as clk:
+        ms_b, st_b, wall_b, launches = timed(ctx_b, out_b, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_g, st_g, wall_g, _ = timed(ctx_g, out_g, args.steps, args.warmup)
+
+    frame_b = sum(ms_b) / len(ms_b)
+    frame_g = sum(ms_g) / len(ms_g)
+    frame_b = max_over_ranks(frame_b, dist, dev)
+    frame_g = max_over_ranks(frame_g, dist, dev)
+    mean = lambda v: sum(v) / len(v)
+    raster_b = mean(st_b["raster"])
+    raster_g = mean(st_g["raster"])
+
+    # images of both paths must agree (EXACT reproduces the global order)
+    ctx_b.render(ds, cam, bg, out_b)
+    ctx_g.render(ds, cam, bg, out_g)
+    torch.cuda.synchronize()
+    err_vs_global = float((out_b[0] - out_g[0]).abs().max().item())
+    last_equal = bool(torch.equal(out_b[2], out_g[2]))
+
+    # the paper's approximate policy, for the repair ablation
+    ctx_p = G.Context("paper")
+    out_p = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
+             torch.empty((H, W), dtype=torch.int32, device=dev))
+    ctx_p.render(ds, cam, bg, out_p)
+    ctx_p.enable_timing(True)
+    ms_p, st_p, _, _ = timed(ctx_p, out_p, max(3, args.steps // 4), 2)
+    ctx_p.render(ds, cam, bg, out_p)
+    torch.cuda.synchronize()
+    err_paper = float((out_p[0] - out_b[0]).abs().max().item())
+
+    # roofline of the dominant kernel (binned raster): float32 ops of the
+    # compositing definition it executed, counted by its instrumented twin
+    ops = None
+    try:
+        proj = ctx_b.project(ds, cam)
+        isect, m_cap, m_dev, m = ctx_b.tile_intersect(proj, ds.n, cam)
+        words, offsets, _ = ctx_b.sort_or_bin(proj, ds.scales, ds.n, cam, isect, m_cap, m_dev)
+        _, _, _, nt = ctx_b.rasterize_fwd(proj, ds.n, cam, words, offsets, count_tests=True)
+        ops = ctx_b.last_raster_ops()
+        tests = int(nt.sum().item())
+        del proj, isect, words, offsets, nt
+    except Exception as e:  # pragma: no cover
+        tests = None
+        print(f"op count failed: {e}", file=sys.stderr)
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = n_sm * 128 * sm_mhz * 1e6  # fp32 lanes x clock: instructions / s
+    achieved = ops / (raster_b * 1e-3) if ops else None
+    traffic, prof = load_traffic()
+    roofline = {"kernel": "k_raster<16,binned>", "bound": "alu",
+                "achieved": round(achieved / 1e12, 4) if achieved else None,
+                "peak": round(peak_ops / 1e12, 4), "unit": "Tinst/s",
+                "frac": round(achieved / peak_ops, 4) if achieved else None,
+                "traffic": traffic,
+                "peak_source": (f"{n_sm} SMs x 128 fp32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled "
+                                "during the timed region)"),
+                "ops_per_launch": ops, "tests_per_launch": tests}
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
+        hs = G.DeviceScene(pin(scene.means), pin(scene.scales), pin(scene.quats), pin(scene.opacities),
+                           pin(scene.sh), scene.sh_degree)
+        hout = (torch.empty((H, W, 3)).pin_memory(), torch.empty((H, W)).pin_memory(),
+                torch.empty((H, W), dtype=torch.int32).pin_memory())
+        ctx_e = G.Context("exact")
+        flags = G.RENDER_HOST_INPUTS | G.RENDER_HOST_OUTPUTS
+        for _ in range(args.warmup):
+            ctx_e.render(hs, cam, bg, hout, flags=flags)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx_e.render(hs, cam, bg, hout, flags=flags)  # returns after the outputs landed
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, dev)
+        h2d = sum(int(t.numel()) * 4 for t in (hs.means, hs.scales, hs.quats, hs.opacities, hs.sh))
+        d2h = sum(int(t.numel()) * 4 for t in hout)
+        e2e = {"value": round(ws * P / e2e_s / 1e6, 4), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3, 3)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_block(scene, cam)
+
+    if rank != 0:
+        return
+    value = ws * P / (frame_b * 1e-3) / 1e6
+    res = {
+        "metric": METRIC, "value": round(value, 4), "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(frame_b, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "path": "binned EXACT, K=64, 16x16 tiles",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "entries_per_frame": m_b},
+        "raster_ms": round(raster_b, 4),
+        "raster_mpix_s": round(P / (raster_b * 1e-3) / 1e6, 3),
+        "stages_ms": {s: round(mean(v), 4) for s, v in st_b.items() if mean(v) > 0},
+        "global_sort": {"frame_ms": round(frame_g, 4), "raster_ms": round(raster_g, 4),
+                        "value": round(ws * P / (frame_g * 1e-3) / 1e6, 4),
+                        "stages_ms": {s: round(mean(v), 4) for s, v in st_g.items() if mean(v) > 0}},
+        "speedup_raster_vs_global": round(raster_g / raster_b, 4),
+        "speedup_frame_vs_global": round(frame_g / frame_b, 4),
+        "max_abs_err_vs_global": err_vs_global, "last_id_equal_vs_global": last_equal,
+        "paper_policy": {"frame_ms": round(mean(ms_p), 4), "raster_ms": round(mean(st_p["raster"]), 4),
+                         "max_abs_err_vs_exact": err_paper},
+        "frame_ms_min": round(min(ms_b), 4), "frame_ms_median": round(statistics.median(ms_b), 4),
+        "wall_s_timed": round(wall_b, 3),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": int(launches),
+    }
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    try:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+    except Exception:
+        pass
+
+
+if __name__ == "__main__":
+    main()

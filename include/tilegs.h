@@ -1,0 +1,288 @@
+/*
+ * tilegs.h -- C ABI of libtilegs.so, the GB300 (sm_103a) TileGS forward path.
+ *
+ * The method is "TileGS: Tile-Local Depth Binning for Gaussian Splatting
+ * Rasterization".  A frame runs:
+ *   gs_project        -> per-Gaussian 2D mean / conic / depth / tile rect / colour
+ *                        (Sec. 3.1, "projected Gaussian inputs")
+ *   gs_tile_intersect -> one entry per (Gaussian, covered tile)       (Sec. 3.1)
+ *   gs_sort_or_bin    -> either the baseline global (tile, depth) sort (Sec. 3.1)
+ *                        or depth-range estimation + tile-local bin construction
+ *                        + selective repair (Sec. 3.2, 3.3, 3.5; supplement
+ *                        algorithms 2-4), both producing a tile-major stream
+ *   gs_rasterize_fwd  -> front-to-back compositing over each tile's span
+ *                        (Sec. 3.4; supplement algorithm 5)
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers on the current CUDA device unless
+ *     the name or comment says "host".  The caller owns them; the library never
+ *     frees or retains them past the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is enqueued asynchronously on it; nothing blocks the
+ *     host unless the comment says so.
+ *   - Return value: GS_OK or a GS_ERR_* code.  Argument errors are detected on
+ *     the host before anything is enqueued.  Errors detected on the device
+ *     (capacity overflow, a bounded wait that ran out) set the context's sticky
+ *     error word, read by gs_get_error() after the stream has been synchronised.
+ *   - A context is used by one host thread at a time; calls that share a
+ *     context and overlap on different streams race on its scratch memory.
+ *   - Floating point: float32 in a fixed operation order (no fast-math), so the
+ *     integer decisions (tile rectangles, alpha skips, transmittance stops, bin
+ *     indices) are reproducible bit for bit.
+ */
+#ifndef TILEGS_H
+#define TILEGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+enum {
+    GS_OK = 0,
+    GS_ERR_INVALID_ARG = 1, /* bad size, null pointer, unsupported option      */
+    GS_ERR_CAPACITY = 2,    /* more entries than the caller's capacity; the
+                               needed count is still written to the M output */
+    GS_ERR_CUDA = 3,        /* a CUDA runtime call failed                     */
+    GS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up             */
+    GS_ERR_NO_MEMORY = 5,   /* scratch allocation failed                      */
+    GS_ERR_NUMERIC = 6      /* non-finite input where a finite one is needed  */
+};
+const char* gs_status_string(int status);
+
+/* ---------------------------------------------------------------- modes */
+enum {
+    /* Baseline: global stable radix sort of (tile, depth) keys, one
+     * contiguous range per tile (Sec. 3.1, "globally sorted tile-depth
+     * stream").  Offsets stride K = 1. */
+    GS_MODE_GLOBAL_SORT = 0,
+    /* Tile-local depth bins with a monotone split map (bin order never
+     * inverts depth order) and every segment of length >= 2 put in (depth,
+     * gid) order: the stream is identical to GS_MODE_GLOBAL_SORT's. */
+    GS_MODE_BINNED_EXACT = 1,
+    /* The paper's default policy: near-depth-shifted log-space bins and the
+     * five selection rules with the floor(0.25 M) entry budget (Sec. 3.5,
+     * table of exact-repair selection rules).  Approximate by design. */
+    GS_MODE_BINNED_PAPER = 2,
+    /* Bins as in PAPER mode, no repair (the "No repair" row of the paper's
+     * repair ablation). */
+    GS_MODE_BINNED_NOREPAIR = 3
+};
+
+/* ---------------------------------------------------------------- camera */
+typedef struct gs_camera {
+    float viewmat[16];  /* row-major world-to-camera, OpenCV axes (x right, y down, z forward) */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_plane, far_plane; /* Gaussians with depth outside (near, far) are culled */
+} gs_camera;
+
+/* ---------------------------------------------------------------- config */
+#define GS_MAX_K 128
+typedef struct gs_config {
+    int32_t mode;          /* GS_MODE_* */
+    int32_t tile_size;     /* 8, 16 or 32 pixels (16 = the paper's) */
+    int32_t K;             /* bins per tile, 1..GS_MAX_K (64 = paper default) */
+    int32_t sample_count;  /* S, depth-range samples (8192) */
+    float p_lo, p_hi;      /* percentiles of the depth range (1, 99) */
+    float pad;             /* padding fraction of the clipped span (0.05) */
+    float near_alpha, near_gamma; /* near-depth shift (1.0, 0.25) */
+    float eps;             /* numerical floor (1e-4) */
+    float repair_budget_frac; /* B_rep = floor(frac * M) (0.25) */
+    int32_t near_shift;    /* 1: bin on z - min(alpha s_max, gamma z) (PAPER default) */
+    int32_t tile_cull;     /* 1: conservative tile-level alpha cull in the binned raster */
+    int32_t persistent;    /* 1: binned raster runs persistent CTAs over tiles in
+                              descending span order */
+} gs_config;
+
+/* Fill *cfg with the paper's defaults (supplement, default No-GW configuration
+ * and default repair-threshold tables) for the given mode.  EXACT mode turns
+ * the near-depth shift off (it would make the bin map non-monotone). */
+void gs_config_default(gs_config* cfg, int32_t mode);
+
+/* ---------------------------------------------------------------- context */
+typedef struct gs_ctx gs_ctx;
+
+/* Create a context on the current CUDA device.  Owns scratch memory (grown on
+ * demand with cudaMalloc, so never grow it inside a stream capture: call
+ * gs_reserve first), a device error word and timing events.
+ * Errors: GS_ERR_INVALID_ARG (cfg out of range), GS_ERR_NO_MEMORY. */
+int gs_create(gs_ctx** out, const gs_config* cfg);
+int gs_destroy(gs_ctx* ctx);
+int gs_set_config(gs_ctx* ctx, const gs_config* cfg);
+int gs_get_config(const gs_ctx* ctx, gs_config* cfg);
+
+/* Pre-grow scratch for up to n Gaussians, m_cap entries and an image of
+ * width x height (synchronous; allocates). */
+int gs_reserve(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t width, int32_t height);
+
+/* Sticky device error word (synchronises `stream` first; host).  Returns the
+ * first GS_ERR_* raised on the device since the last gs_clear_error. */
+int gs_get_error(gs_ctx* ctx, void* stream);
+int gs_clear_error(gs_ctx* ctx, void* stream);
+
+/* Per-stage device times of the last gs_render / gs_sort_or_bin call when
+ * timing is enabled (host; synchronises).  ms[] receives GS_STAGE_COUNT values. */
+enum { GS_STAGE_PROJECT = 0, GS_STAGE_INTERSECT, GS_STAGE_DEPTH_RANGE, GS_STAGE_BIN,
+       GS_STAGE_REPAIR, GS_STAGE_SORT, GS_STAGE_RASTER, GS_STAGE_COUNT };
+int gs_enable_timing(gs_ctx* ctx, int32_t on);
+int gs_get_stage_times(gs_ctx* ctx, float* ms);
+
+/* ---------------------------------------------------------------- layouts */
+/*
+ * Projected buffer (caller-owned, gs_projected_bytes(n) bytes, 256-byte
+ * aligned base).  Structure of arrays, each field 256-byte aligned at the
+ * offset gs_projected_offset(n, field):
+ *   GS_P_XY_AB   float4[n]  {mean_x, mean_y, conic_a, conic_b}
+ *   GS_P_C_O_Z   float4[n]  {conic_c, opacity, depth, cull_tau}
+ *   GS_P_RGB     float4[n]  {r, g, b, cull_margin}
+ *   GS_P_RECT    uint2[n]   {tx0 | ty0 << 16, tx1 | ty1 << 16} (tiles tx0 <= tx < tx1)
+ *   GS_P_RADIUS  int32[n]   pixel radius, 0 = culled
+ * conic (a, b, c) is the upper triangle of the inverse 2D covariance;
+ * cull_tau / cull_margin feed the conservative tile cull (ln(255 o) and a
+ * rounding margin); a culled Gaussian has an empty rect.
+ */
+enum { GS_P_XY_AB = 0, GS_P_C_O_Z, GS_P_RGB, GS_P_RECT, GS_P_RADIUS, GS_P_NFIELDS };
+size_t gs_projected_bytes(int64_t n);
+size_t gs_projected_offset(int64_t n, int32_t field);
+
+/*
+ * Intersection buffer (caller-owned, gs_isect_bytes(m_cap) bytes): three
+ * uint32 arrays of m_cap entries at offsets 0, m_cap*4 and m_cap*8 (rounded to
+ * 256 bytes by gs_isect_bytes): tile id (ty * tiles_x + tx), depth bits
+ * (float bits of the positive depth, so integer order is depth order) and
+ * Gaussian id.  Emission order: gid ascending, then ty, then tx.
+ */
+size_t gs_isect_bytes(int64_t m_cap);
+size_t gs_isect_offset(int64_t m_cap, int32_t field); /* field 0 tile, 1 zbits, 2 gid */
+
+/* Tiles of an image: ceil(width / tile) * ceil(height / tile). */
+int32_t gs_num_tiles(int32_t width, int32_t height, int32_t tile_size);
+
+/* ---------------------------------------------------------------- stages */
+
+/*
+ * Project n Gaussians (Sec. 3.1; the projection is the 3DGS/EWA one, which
+ * the paper leaves unchanged).
+ *   means [n,3], scales [n,3] (linear, already activated), quats [n,4]
+ *   (w,x,y,z, any non-zero norm), opacities [n] (in [0,1]), sh [n,(d+1)^2,3]
+ *   with d = sh_degree in 0..3; cam is a HOST struct.
+ * Writes the projected buffer.  Errors: GS_ERR_INVALID_ARG.
+ */
+int gs_project(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
+               const float* opacities, const float* sh, int32_t sh_degree, int64_t n,
+               const gs_camera* cam, void* projected, void* stream);
+
+/*
+ * Tile intersection (Sec. 3.1: "emits one tile-intersection record per
+ * covered tile").  Counts the tiles of every projected Gaussian, scans them
+ * and emits entries into `isect` (capacity m_cap).
+ *   m_dev: device int64 receiving M (always written, even past capacity).
+ *   m_host: optional HOST pointer; when non-NULL the call synchronises the
+ *           stream and writes M there.
+ * When M > m_cap nothing past m_cap is written and GS_ERR_CAPACITY is raised
+ * (returned directly when m_host is given, else via gs_get_error).
+ */
+int gs_tile_intersect(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
+                      void* isect, int64_t m_cap, int64_t* m_dev, int64_t* m_host,
+                      void* stream);
+
+/*
+ * Order the entries into a tile-major stream, per the context's mode.
+ *   stream_words [m_cap] uint64: (depth_bits << 32) | gid.
+ *   offsets [T*K' + 1] int32 with K' = 1 in GLOBAL mode, K' = cfg.K otherwise:
+ *     tile t's span is [offsets[t*K'], offsets[(t+1)*K']), bin b of tile t is
+ *     [offsets[t*K'+b], offsets[t*K'+b+1]).
+ * GLOBAL: stable LSD radix sort on (tile, depth bits); ties keep gid order.
+ * BINNED_*: depth range (supplement algorithm 2) -> count / scan / scatter
+ *   (algorithm 3) -> repair (algorithm 4; EXACT sorts every segment).
+ * `scales` [n,3] is read only when the near-depth shift is on.
+ * zrange_out: optional device float[2] receiving [zmin, zmax] (binned modes).
+ */
+int gs_sort_or_bin(gs_ctx* ctx, const void* projected, const float* scales, int64_t n,
+                   const gs_camera* cam, const void* isect, int64_t m_cap, const int64_t* m_dev,
+                   uint64_t* stream_words, int32_t* offsets, float* zrange_out, void* stream);
+
+/*
+ * The binned path's steps one at a time (for inspection and tests).
+ * gs_depth_range: writes zrange[2] = [zmin, zmax] (supplement algorithm 2).
+ * gs_bin_build: count / exclusive scan / atomic scatter into bins (algorithm
+ *   3) given zrange; the order inside a segment is unspecified.
+ * gs_repair: selected_out (optional device uint8 [T*K]) receives the segments
+ *   sorted: all with length >= 2 (EXACT) or the rule/budget selection (PAPER,
+ *   algorithm 4); NOREPAIR sorts nothing.
+ */
+int gs_depth_range(gs_ctx* ctx, const void* projected, const float* scales, int64_t n,
+                   const gs_camera* cam, const void* isect, int64_t m_cap, const int64_t* m_dev,
+                   float* zrange, void* stream);
+int gs_bin_build(gs_ctx* ctx, const void* projected, const float* scales, int64_t n,
+                 const gs_camera* cam, const void* isect, int64_t m_cap, const int64_t* m_dev,
+                 const float* zrange, uint64_t* stream_words, int32_t* offsets, void* stream);
+int gs_repair(gs_ctx* ctx, const gs_camera* cam, const int64_t* m_dev, uint64_t* stream_words,
+              const int32_t* offsets, uint8_t* selected_out, void* stream);
+
+/*
+ * Front-to-back compositing of each tile's span (Sec. 3.4; supplement
+ * algorithm 5).  Per pixel centre (x + 0.5, y + 0.5) and entry g in stream
+ * order: q = 1/2 d^T conic d, alpha = min(0.99, o exp(-q)), skip alpha < 1/255,
+ * stop before applying when T (1 - alpha) < 1e-4, C += c alpha T, T *= 1 - alpha.
+ *   n: the Gaussian count the projected buffer was laid out for.
+ *   offsets_stride: 1 for a GLOBAL stream, cfg.K for a binned one.
+ *   bg: HOST float[3].  rgb [H,W,3], alpha [H,W] (= 1 - T), last [H,W] (stream
+ *   index of the last applied entry, -1 if none); ntests [H,W] optional:
+ *   entries each pixel visited, the stopping one included.
+ * The GLOBAL kernel is the plain baseline (gsplat-style batch staging); the
+ * binned kernel adds the conservative tile-alpha cull and colour staging of
+ * the paper's default configuration.  Both give identical images.
+ */
+int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
+                     const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
+                     const float* bg, float* rgb, float* alpha, int32_t* last, int32_t* ntests,
+                     void* stream);
+
+/* ---------------------------------------------------------------- whole frame */
+typedef struct gs_scene {
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opacities;
+    const float* sh;
+    int32_t sh_degree;
+    int64_t n;
+} gs_scene;
+
+enum {
+    GS_RENDER_HOST_INPUTS = 1,  /* scene arrays are HOST memory (pinned for async copies) */
+    GS_RENDER_HOST_OUTPUTS = 2, /* rgb/alpha/last are HOST memory */
+    GS_RENDER_NO_SYNC = 4       /* do not read M back: use reserved capacity only */
+};
+
+/*
+ * One whole frame: project -> intersect -> sort_or_bin -> rasterize, with all
+ * intermediates in context scratch.  With GS_RENDER_HOST_* the copies run on
+ * `stream` inside the call and the call returns after the outputs landed.
+ * Without GS_RENDER_NO_SYNC the entry count is read back once to grow scratch.
+ * last may be NULL.  Errors: as the stages.
+ */
+int gs_render(gs_ctx* ctx, const gs_scene* scene, const gs_camera* cam, const float* bg,
+              float* rgb, float* alpha, int32_t* last, int32_t flags, void* stream);
+
+/* Entry count of the last gs_render (host; valid after the stream synchronises). */
+int64_t gs_last_entry_count(gs_ctx* ctx);
+
+/* Number of CUDA kernels this context has launched so far (host counter). */
+int64_t gs_launch_count(const gs_ctx* ctx);
+
+/* Float32 operations of the compositing definition executed by the last
+ * gs_rasterize_fwd call that passed an ntests buffer (host; synchronises):
+ * 8 per visit, +17 when exp is evaluated, +3 when alpha passes, +4 when the
+ * entry is applied.  -1 on error. */
+int64_t gs_last_raster_ops(gs_ctx* ctx, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TILEGS_H */

@@ -490,7 +490,7 @@ int64_t orc_depth_range(int64_t m, const uint32_t* entry_gid, const float* depth
 /* Shared set-up: z'min = max(zmin, eps), z'max = max(zmax, z'min + 1e-6),
  * lmin = ln z'min, lmax = ln z'max.  splits[k-1] for k = 1..K-1 are the
  * log-spaced depths exp(lmin + (lmax - lmin) * (k/K)) used by the monotone
- * map. */
+ * map, as a running maximum. */
 void orc_bin_params(float zmin, float zmax, int K, float eps, float* lmin_out, float* lmax_out,
                     float* splits)
 {
@@ -503,6 +503,10 @@ void orc_bin_params(float zmin, float zmax, int K, float eps, float* lmin_out, f
         const float t = (float)k / (float)K;
         splits[k - 1] = orc_expf(lmin + (lmax - lmin) * t);
     }
+    /* keep the list non-decreasing (a no-op unless exp rounding ever broke
+     * monotonicity), so "number of splits <= z" is also a binary search */
+    for (int k = 1; k < K - 1; ++k)
+        if (splits[k] < splits[k - 1]) splits[k] = splits[k - 1];
 }
 
 /* The paper's map: u = clamp((ln max(z, eps) - lmin) / (lmax - lmin), 0,

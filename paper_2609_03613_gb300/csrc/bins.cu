@@ -1,0 +1,617 @@
+// bins.cu -- the TileGS ordering path:
+//   K7  robust depth range      (supplement, "Robust depth-range estimation")
+//   K8  depth-to-bin maps       (supplement, the log-depth-bin formula; and the
+//                                monotone split map of EXACT mode)
+//   K9-K11 count / scan / scatter into the tile-bin-major stream
+//                               (Sec. 3.3; supplement "Tile-local bin construction")
+//   K13 repair selection        (Sec. 3.5 rule table; supplement "Selective
+//                                repair selection and local exact sorting")
+//   K14 segment sorts by the baseline key (depth bits, gid)
+#include "internal.cuh"
+
+namespace gs {
+
+// ------------------------------------------------------------------ depth range
+constexpr int kDrThreads = 1024;
+constexpr int kDrMaxS = 8192;
+
+struct DrArgs {
+    float near_plane, far_plane;
+    int S;
+    int near_shift;
+    float near_alpha, near_gamma;
+    float p_lo, p_hi, pad, eps;
+    int K;
+};
+
+__device__ __forceinline__ float zkey_of(float z, const float* __restrict__ scales, uint32_t g, float a, float gm)
+{
+    const float s0 = __ldg(scales + 3 * (size_t)g), s1 = __ldg(scales + 3 * (size_t)g + 1),
+                s2 = __ldg(scales + 3 * (size_t)g + 2);
+    const float smax = fmaxf(fmaxf(s0, s1), s2);
+    return z - fminf(a * smax, gm * z);
+}
+
+__device__ __forceinline__ int64_t rank_of(float p, int64_t n)
+{
+    int64_t k = (int64_t)ceil((double)p / 100.0 * (double)n);
+    if (k < 1) k = 1;
+    if (k > n) k = n;
+    return k;
+}
+
+// Bin parameters from [zmin, zmax]: z'min = max(zmin, eps),
+// z'max = max(zmax, z'min + 1e-6), lmin/lmax their logs, and K-1 log-spaced
+// split depths exp(lmin + (lmax - lmin) k/K), kept non-decreasing.
+__device__ void write_bin_params(BinParams* bp, float zmin, float zmax, int K, float eps, int nsamples)
+{
+    __shared__ float s_l[2];
+    if (threadIdx.x == 0) {
+        const float zmn = fmaxf(zmin, eps);
+        const float zmx = fmaxf(zmax, zmn + 1e-6f);
+        s_l[0] = spec_log(zmn);
+        s_l[1] = spec_log(zmx);
+        bp->zmin = zmin;
+        bp->zmax = zmax;
+        bp->lmin = s_l[0];
+        bp->lmax = s_l[1];
+        bp->K = K;
+        bp->nsamples = nsamples;
+    }
+    __syncthreads();
+    __shared__ float s_split[GS_MAX_K];
+    const float lmin = s_l[0], lmax = s_l[1];
+    for (int k = 1 + threadIdx.x; k < K; k += blockDim.x) {
+        const float t = (float)k / (float)K;
+        s_split[k - 1] = spec_exp(lmin + (lmax - lmin) * t);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 1; k < K - 1; ++k)
+            if (s_split[k] < s_split[k - 1]) s_split[k] = s_split[k - 1];
+    __syncthreads();
+    for (int k = threadIdx.x; k < K - 1; k += blockDim.x) bp->splits[k] = s_split[k];
+}
+
+__global__ void __launch_bounds__(kDrThreads)
+k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales, IsectView is,
+              const int64_t* __restrict__ m_dev, int64_t m_cap, DrArgs a, BinParams* bp)
+{
+    __shared__ uint32_t s_v[kDrMaxS];
+    __shared__ int s_n;
+    __shared__ uint32_t s_h[2][256];
+    __shared__ uint32_t s_pref[2];
+    __shared__ int64_t s_k[2];
+    if (threadIdx.x == 0) s_n = 0;
+    __syncthreads();
+    const int64_t M = live_count(m_dev, m_cap);
+    const int64_t ns = M < (int64_t)a.S ? M : (int64_t)a.S;
+    const float lo_clamp = fmaxf(a.near_plane, a.eps);
+    for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
+        const int64_t j = (i * M) / ns;
+        const uint32_t g = is.gid[j];
+        float z = c_o_z[g].z;
+        if (a.near_shift) z = zkey_of(z, scales, g, a.near_alpha, a.near_gamma);
+        if (!(z > 0.0f)) continue;
+        z = fminf(fmaxf(z, lo_clamp), a.far_plane);
+        s_v[atomicAdd(&s_n, 1)] = __float_as_uint(z);
+    }
+    __syncthreads();
+    const int n = s_n;
+    float zmin, zmax;
+    if (n == 0) {
+        zmin = lo_clamp;
+        zmax = a.far_plane;
+    } else {
+        if (threadIdx.x == 0) {
+            s_k[0] = rank_of(a.p_lo, n);
+            s_k[1] = rank_of(a.p_hi, n);
+            s_pref[0] = s_pref[1] = 0u;
+        }
+        __syncthreads();
+        // radix select (positive floats: bit order = value order), 8 bits at a time
+        uint32_t mask = 0u;
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int d = threadIdx.x; d < 512; d += blockDim.x) s_h[d >> 8][d & 255] = 0u;
+            __syncthreads();
+            const uint32_t p0 = s_pref[0], p1 = s_pref[1];
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const uint32_t v = s_v[i];
+                const uint32_t dg = (v >> shift) & 255u;
+                if ((v & mask) == p0) atomicAdd(&s_h[0][dg], 1u);
+                if ((v & mask) == p1) atomicAdd(&s_h[1][dg], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x < 2) {
+                const int t = threadIdx.x;
+                int64_t k = s_k[t];
+                uint32_t dsel = 255u;
+                for (uint32_t d = 0; d < 256; ++d) {
+                    const uint32_t c = s_h[t][d];
+                    if ((int64_t)c >= k) { dsel = d; break; }
+                    k -= c;
+                }
+                s_k[t] = k;
+                s_pref[t] |= dsel << shift;
+            }
+            mask |= 255u << shift;
+            __syncthreads();
+        }
+        const float zlo = __uint_as_float(s_pref[0]);
+        const float zhi = __uint_as_float(s_pref[1]);
+        const float span = fmaxf(zhi - zlo, 1e-6f);
+        zmin = fmaxf(a.near_plane, zlo - a.pad * span);
+        zmax = fminf(a.far_plane, zhi + a.pad * span);
+    }
+    write_bin_params(bp, zmin, zmax, a.K, a.eps, n);
+}
+
+__global__ void k_bin_params_from(const float* __restrict__ zrange, int K, float eps, BinParams* bp)
+{
+    write_bin_params(bp, zrange[0], zrange[1], K, eps, -1);
+}
+
+int depth_range(gs_ctx* ctx, const ProjView& pv, const float* scales, const IsectView& is, int64_t m_cap,
+                const int64_t* m_dev, const gs_camera* cam, cudaStream_t st)
+{
+    const gs_config& c = ctx->cfg;
+    DrArgs a;
+    a.near_plane = cam->near_plane;
+    a.far_plane = cam->far_plane;
+    a.S = c.sample_count;
+    a.near_shift = c.near_shift;
+    a.near_alpha = c.near_alpha;
+    a.near_gamma = c.near_gamma;
+    a.p_lo = c.p_lo;
+    a.p_hi = c.p_hi;
+    a.pad = c.pad;
+    a.eps = c.eps;
+    a.K = c.K;
+    k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, is, m_dev, m_cap, a, ctx->d_bp);
+    ctx->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int set_zrange(gs_ctx* ctx, const float* zrange, cudaStream_t st)
+{
+    k_bin_params_from<<<1, 128, 0, st>>>(zrange, ctx->cfg.K, ctx->cfg.eps, ctx->d_bp);
+    ctx->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------ bin maps
+// Monotone map: the number of split depths <= z (binary search over the
+// non-decreasing split list).
+__device__ __forceinline__ int bin_split(float z, const float* s_split, int K)
+{
+    int lo = 0, hi = K - 1;  // answer in [0, K-1]
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_split[mid] <= z) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// The paper's clamped log map.
+__device__ __forceinline__ int bin_log(float z, float lmin, float lmax, int K, float eps)
+{
+    float u = (spec_log(fmaxf(z, eps)) - lmin) / (lmax - lmin);
+    u = fminf(fmaxf(u, 0.0f), 1.0f - 1e-6f);
+    int b = (int)floorf((float)K * u);
+    b = b < 0 ? 0 : b;
+    b = b > K - 1 ? K - 1 : b;
+    return b;
+}
+
+struct BinArgs {
+    int K;
+    int map_log;  // 1: paper log map on the near-shifted key
+    int near_shift;
+    float near_alpha, near_gamma, eps;
+};
+
+__global__ void __launch_bounds__(256)
+k_bin_count(IsectView is, const float4* __restrict__ c_o_z, const float* __restrict__ scales,
+            const int64_t* __restrict__ m_dev, int64_t m_cap, const BinParams* __restrict__ bp, BinArgs a,
+            int32_t* __restrict__ count, uint8_t* __restrict__ bin_of)
+{
+    __shared__ float s_split[GS_MAX_K];
+    for (int k = threadIdx.x; k < a.K - 1; k += blockDim.x) s_split[k] = bp->splits[k];
+    __syncthreads();
+    const float lmin = bp->lmin, lmax = bp->lmax;
+    const int64_t M = live_count(m_dev, m_cap);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < M; e += stride) {
+        const uint32_t t = is.tile[e];
+        int b;
+        if (a.map_log) {
+            const uint32_t g = is.gid[e];
+            float z = __uint_as_float(is.zbits[e]);
+            if (a.near_shift) z = zkey_of(z, scales, g, a.near_alpha, a.near_gamma);
+            b = bin_log(z, lmin, lmax, a.K, a.eps);
+        } else {
+            b = bin_split(__uint_as_float(is.zbits[e]), s_split, a.K);
+        }
+        bin_of[e] = (uint8_t)b;
+        atomicAdd(&count[(int64_t)t * a.K + b], 1);
+    }
+}
+
+// Fill each (tile, bin) segment from its end: the counter returns to zero.
+__global__ void __launch_bounds__(256)
+k_bin_scatter(IsectView is, const int64_t* __restrict__ m_dev, int64_t m_cap, int K,
+              const uint8_t* __restrict__ bin_of, const int32_t* __restrict__ offsets,
+              int32_t* __restrict__ count, uint64_t* __restrict__ words)
+{
+    const int64_t M = live_count(m_dev, m_cap);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < M; e += stride) {
+        const int64_t seg = (int64_t)is.tile[e] * K + bin_of[e];
+        const int32_t p = offsets[seg] + atomicSub(&count[seg], 1) - 1;
+        words[p] = ((uint64_t)is.zbits[e] << 32) | is.gid[e];
+    }
+}
+
+constexpr int32_t kTailCap = 1 << 16;
+
+int bins_reserve(gs_ctx* ctx, int64_t m_cap, int64_t nseg)
+{
+    int r;
+    void* p = ctx->d_count;
+    if ((r = ensure(&p, &ctx->count_cap, (size_t)(nseg + 1) * 4)) != GS_OK) return r;
+    ctx->d_count = (int32_t*)p;
+    p = ctx->d_bin;
+    if ((r = ensure(&p, &ctx->bin_cap, (size_t)(m_cap > 0 ? m_cap : 1))) != GS_OK) return r;
+    ctx->d_bin = (uint8_t*)p;
+    p = ctx->d_sel;
+    if ((r = ensure(&p, &ctx->sel_cap, align256((size_t)nseg) + (size_t)(nseg + 1) * 8 + 256)) != GS_OK) return r;
+    ctx->d_sel = (uint8_t*)p;
+    p = ctx->d_tail;
+    if ((r = ensure(&p, &ctx->tail_cap, (size_t)(kTailCap + 1) * 4)) != GS_OK) return r;
+    ctx->d_tail = (int32_t*)p;
+    return GS_OK;
+}
+
+int bin_build(gs_ctx* ctx, const ProjView& pv, const float* scales, const IsectView& is, int64_t m_cap,
+              const int64_t* m_dev, int32_t n_tiles, uint64_t* stream_words, int32_t* offsets,
+              cudaStream_t st)
+{
+    const gs_config& c = ctx->cfg;
+    const int64_t nseg = (int64_t)n_tiles * c.K;
+    int r;
+    if ((r = bins_reserve(ctx, m_cap, nseg)) != GS_OK) return r;
+    GS_CUDA_TRY(cudaMemsetAsync(ctx->d_count, 0, (size_t)nseg * 4, st));
+    BinArgs a;
+    a.K = c.K;
+    a.map_log = (c.mode == GS_MODE_BINNED_EXACT) ? 0 : 1;
+    a.near_shift = c.near_shift;
+    a.near_alpha = c.near_alpha;
+    a.near_gamma = c.near_gamma;
+    a.eps = c.eps;
+    const unsigned grid = (unsigned)ctx->num_sms * 8;
+    k_bin_count<<<grid, 256, 0, st>>>(is, pv.c_o_z, scales, m_dev, m_cap, ctx->d_bp, a, ctx->d_count, ctx->d_bin);
+    ctx->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    if ((r = exclusive_scan_i32(ctx, ctx->d_count, nseg, offsets, nullptr, st)) != GS_OK) return r;
+    k_bin_scatter<<<grid, 256, 0, st>>>(is, m_dev, m_cap, c.K, ctx->d_bin, offsets, ctx->d_count, stream_words);
+    ctx->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------ repair selection
+// The rules of the paper's selection table in exact integer form.
+__device__ __forceinline__ int keep_len(int64_t l, int64_t ltile, int b)
+{
+    if (l <= 1) return 0;
+    bool keep = false;
+    if (l >= 320) keep = true;
+    if (l > 512) keep = true;
+    if (100 * l >= 45 * ltile) keep = true;
+    if (l >= 129 && l <= 256 && 100 * l >= 10 * ltile) keep = true;
+    if (b < 2 && l >= 16) keep = true;
+    return keep ? (int)l : 0;
+}
+
+__global__ void k_keep_lengths(const int32_t* __restrict__ off, int64_t nseg, int K, int32_t* __restrict__ klen)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseg; q += stride) {
+        const int64_t t = q / K;
+        const int b = (int)(q - t * K);
+        const int64_t l = (int64_t)off[q + 1] - off[q];
+        const int64_t ltile = (int64_t)off[(t + 1) * K] - off[t * K];
+        klen[q] = keep_len(l, ltile, b);
+    }
+}
+
+// Budget B = floor(frac * M).  Segments whose inclusive prefix of kept lengths
+// stays within B are selected (the greedy accepts all of them); the first one
+// that overflows and everything after it go to the one-block greedy below.
+__global__ void k_select_prefix(const int32_t* __restrict__ klen, const int32_t* __restrict__ pre, int64_t nseg,
+                                const int64_t* __restrict__ m_dev, double frac, uint8_t* __restrict__ sel)
+{
+    const int64_t B = (int64_t)floor(frac * (double)(*m_dev));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseg; q += stride)
+        sel[q] = (klen[q] > 0 && (int64_t)pre[q] + klen[q] <= B) ? 1 : 0;
+}
+
+// Exact sequential greedy from the first overflow: keep if used + l <= B.
+// Chunks of 1024 segments; inside a chunk, candidates longer than the room
+// left are rejected at once (used only grows), the rest accepted up to the
+// first that overflows, which is rejected; repeat.
+__global__ void __launch_bounds__(1024)
+k_select_greedy(const int32_t* __restrict__ klen, const int32_t* __restrict__ pre, int64_t nseg,
+                const int64_t* __restrict__ m_dev, double frac, uint8_t* __restrict__ sel)
+{
+    __shared__ int64_t s_warp[32];
+    __shared__ int64_t s_used;
+    __shared__ int64_t s_first;
+    const int64_t B = (int64_t)floor(frac * (double)(*m_dev));
+    // first q whose inclusive prefix exceeds B (pre is non-decreasing)
+    if (threadIdx.x == 0) {
+        int64_t lo = 0, hi = nseg;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)pre[mid] + klen[mid] > B) hi = mid;
+            else lo = mid + 1;
+        }
+        s_first = lo;
+        s_used = lo < nseg ? (int64_t)pre[lo] : 0;
+    }
+    __syncthreads();
+    const int64_t q0 = s_first;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t c0 = q0; c0 < nseg; c0 += blockDim.x) {
+        const int64_t q = c0 + threadIdx.x;
+        int64_t len = q < nseg ? klen[q] : 0;
+        bool undecided = len > 0;
+        bool accept = false;
+        while (true) {
+            const int64_t room = B - s_used;
+            if (undecided && len > room) undecided = false;  // can never fit
+            const int64_t v = undecided ? len : 0;
+            // inclusive block prefix of v
+            int64_t incl = v;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t t = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += t;
+            }
+            if (lane == 31) s_warp[warp] = incl;
+            __syncthreads();
+            int64_t wp = 0;
+            for (int w = 0; w < warp; ++w) wp += s_warp[w];
+            incl += wp;
+            // candidates whose prefix overflows: the earliest is rejected
+            const bool over = undecided && incl > room;
+            const unsigned ball = __ballot_sync(0xffffffffu, over);
+            __shared__ int s_firstover;
+            if (threadIdx.x == 0) s_firstover = 1 << 30;
+            __syncthreads();
+            if (ball && lane == __ffs(ball) - 1) atomicMin(&s_firstover, (int)threadIdx.x);
+            __syncthreads();
+            const int fo = s_firstover;
+            if (fo == (1 << 30)) {
+                if (undecided) accept = true;
+                __syncthreads();
+                if (threadIdx.x == blockDim.x - 1) s_used += incl;
+                __syncthreads();
+                break;
+            }
+            if (undecided && (int)threadIdx.x < fo) {
+                accept = true;
+                undecided = false;
+            }
+            if ((int)threadIdx.x == fo) undecided = false;
+            // used grows by the accepted prefix before fo
+            __syncthreads();
+            if ((int)threadIdx.x == fo) s_used += incl - v;
+            __syncthreads();
+        }
+        if (q < nseg) sel[q] = accept ? 1 : 0;
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ segment sorts
+// All sorts order the 64-bit words (depth bits << 32 | gid) ascending.
+// Bitonic networks in the form where every compare-exchange puts the minimum
+// at the lower index (a mirrored compare at the first step of each merge), so
+// positions past the segment end behave as +infinity and can be skipped.
+
+__device__ __forceinline__ void cex(uint64_t* a, int i, int l)
+{
+    const uint64_t x = a[i], y = a[l];
+    if (y < x) {
+        a[i] = y;
+        a[l] = x;
+    }
+}
+
+struct SyncWarp {
+    __device__ void operator()() const { __syncwarp(); }
+};
+struct SyncBlock {
+    __device__ void operator()() const { __syncthreads(); }
+};
+
+// Sort a[0..n) held in (shared or global) memory by `nthreads` cooperating
+// threads with index `tid`; `sync` is called between steps.
+template <class Sync>
+__device__ void bitonic_mem(uint64_t* a, int n, int tid, int nthreads, Sync sync)
+{
+    int P = 1;
+    while (P < n) P <<= 1;
+    for (int k = 2; k <= P; k <<= 1) {
+        const int h = k >> 1;
+        for (int t = tid; t < P / 2; t += nthreads) {
+            const int blk = t / h, r = t - blk * h;
+            const int i = blk * k + r, l = blk * k + (k - 1 - r);
+            if (l < n) cex(a, i, l);
+        }
+        sync();
+        for (int j = k >> 2; j > 0; j >>= 1) {
+            for (int t = tid; t < P / 2; t += nthreads) {
+                const int i = 2 * j * (t / j) + (t % j), l = i + j;
+                if (l < n) cex(a, i, l);
+            }
+            sync();
+        }
+    }
+}
+
+// 32 words, one per lane, sorted ascending across the warp.
+__device__ __forceinline__ uint64_t warp_bitonic32(uint64_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
+            const bool up = ((lane & k) == 0);
+            const bool lower = ((lane & j) == 0);
+            // lower lane of an ascending pair keeps the min, etc.
+            const bool take_min = (lower == up);
+            v = take_min ? (o < v ? o : v) : (o > v ? o : v);
+        }
+    }
+    return v;
+}
+
+constexpr int kRpThreads = 256;
+constexpr int kRpWarps = kRpThreads / 32;
+constexpr int kRpWarpCap = 512;                     // per-warp shared sort
+constexpr int kRpCtaCap = kRpWarps * kRpWarpCap;    // whole-CTA shared sort (4096)
+
+// One block per tile: sort the tile's selected segments (sel == nullptr:
+// every segment with length >= 2).  Longer than kRpCtaCap: queued as a tail.
+__global__ void __launch_bounds__(kRpThreads)
+k_repair_tiles(const int32_t* __restrict__ off, int K, const uint8_t* __restrict__ sel, uint64_t* __restrict__ words,
+               int32_t* __restrict__ tail, int32_t tail_cap, int* err)
+{
+    __shared__ uint64_t s_buf[kRpCtaCap];
+    __shared__ int32_t s_off[GS_MAX_K + 1];
+    __shared__ int s_big[GS_MAX_K];
+    __shared__ int s_nbig;
+    const int64_t t = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b = threadIdx.x; b <= K; b += blockDim.x) s_off[b] = off[t * K + b];
+    if (threadIdx.x == 0) s_nbig = 0;
+    __syncthreads();
+    if (s_off[K] - s_off[0] < 2) return;
+    uint64_t* wbuf = s_buf + warp * kRpWarpCap;
+    for (int b = warp; b < K; b += kRpWarps) {
+        const int l = s_off[b + 1] - s_off[b];
+        if (l < 2) continue;
+        if (sel && !sel[t * K + b]) continue;
+        uint64_t* seg = words + s_off[b];
+        if (l <= 32) {
+            uint64_t v = lane < l ? seg[lane] : ~0ull;
+            v = warp_bitonic32(v);
+            if (lane < l) seg[lane] = v;
+        } else if (l <= kRpWarpCap) {
+            for (int i = lane; i < l; i += 32) wbuf[i] = seg[i];
+            __syncwarp();
+            bitonic_mem(wbuf, l, lane, 32, SyncWarp{});
+            for (int i = lane; i < l; i += 32) seg[i] = wbuf[i];
+            __syncwarp();
+        } else if (lane == 0) {
+            s_big[atomicAdd(&s_nbig, 1)] = b;
+        }
+    }
+    __syncthreads();
+    const int nbig = s_nbig;
+    for (int k = 0; k < nbig; ++k) {
+        const int b = s_big[k];
+        const int l = s_off[b + 1] - s_off[b];
+        uint64_t* seg = words + s_off[b];
+        if (l <= kRpCtaCap) {
+            for (int i = threadIdx.x; i < l; i += blockDim.x) s_buf[i] = seg[i];
+            __syncthreads();
+            bitonic_mem(s_buf, l, threadIdx.x, blockDim.x, SyncBlock{});
+            for (int i = threadIdx.x; i < l; i += blockDim.x) seg[i] = s_buf[i];
+            __syncthreads();
+        } else if (threadIdx.x == 0) {
+            const int slot = atomicAdd(&tail[0], 1);
+            if (slot < tail_cap) tail[1 + slot] = (int32_t)(t * K + b);
+            else raise_error(err, GS_ERR_CAPACITY);
+        }
+    }
+}
+
+// One block per queued long segment: bitonic sort in global memory.
+__global__ void __launch_bounds__(1024)
+k_repair_tail(const int32_t* __restrict__ off, const int32_t* __restrict__ tail, int32_t tail_cap,
+              uint64_t* __restrict__ words)
+{
+    const int ntail = min(tail[0], tail_cap);
+    for (int k = blockIdx.x; k < ntail; k += gridDim.x) {
+        const int32_t q = tail[1 + k];
+        const int l = off[q + 1] - off[q];
+        bitonic_mem(words + off[q], l, threadIdx.x, blockDim.x, SyncBlock{});
+        __syncthreads();
+    }
+}
+
+__global__ void k_fill_selected(const int32_t* __restrict__ off, int64_t nseg, const uint8_t* __restrict__ sel,
+                                int mode, uint8_t* __restrict__ out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseg; q += stride) {
+        const int l = off[q + 1] - off[q];
+        uint8_t v = 0;
+        if (mode == GS_MODE_BINNED_EXACT) v = l >= 2;
+        else if (mode == GS_MODE_BINNED_PAPER) v = sel[q] && l >= 2;
+        out[q] = v;
+    }
+}
+
+int repair(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* words, const int32_t* offsets,
+           uint8_t* selected_out, cudaStream_t st)
+{
+    const gs_config& c = ctx->cfg;
+    const int64_t nseg = (int64_t)n_tiles * c.K;
+    int r;
+    const unsigned grid = (unsigned)ctx->num_sms * 8;
+    if (c.mode == GS_MODE_BINNED_NOREPAIR) {
+        if (selected_out) GS_CUDA_TRY(cudaMemsetAsync(selected_out, 0, (size_t)nseg, st));
+        return GS_OK;
+    }
+    const uint8_t* sel = nullptr;
+    if (c.mode == GS_MODE_BINNED_PAPER) {
+        // kept lengths -> exclusive prefix -> prefix-fitting selection -> exact greedy tail
+        if ((r = bins_reserve(ctx, 1, nseg)) != GS_OK) return r;
+        uint8_t* s = ctx->d_sel;
+        int32_t* klen = reinterpret_cast<int32_t*>(s + align256((size_t)nseg));
+        int32_t* pre = klen + (nseg + 1);
+        k_keep_lengths<<<grid, 256, 0, st>>>(offsets, nseg, c.K, klen);
+        if ((r = exclusive_scan_i32(ctx, klen, nseg, pre, nullptr, st)) != GS_OK) return r;
+        k_select_prefix<<<grid, 256, 0, st>>>(klen, pre, nseg, m_dev, (double)c.repair_budget_frac, s);
+        k_select_greedy<<<1, 1024, 0, st>>>(klen, pre, nseg, m_dev, (double)c.repair_budget_frac, s);
+        ctx->launches += 3;
+        GS_CUDA_TRY(cudaGetLastError());
+        sel = s;
+    }
+    const int32_t tail_cap = kTailCap;
+    if ((r = bins_reserve(ctx, 1, nseg)) != GS_OK) return r;
+    GS_CUDA_TRY(cudaMemsetAsync(ctx->d_tail, 0, 4, st));
+    if (n_tiles > 0)
+        k_repair_tiles<<<(unsigned)n_tiles, kRpThreads, 0, st>>>(offsets, c.K, sel, words, ctx->d_tail, tail_cap,
+                                                                 ctx->d_err);
+    k_repair_tail<<<(unsigned)ctx->num_sms, 1024, 0, st>>>(offsets, ctx->d_tail, tail_cap, words);
+    ctx->launches += (n_tiles > 0 ? 2 : 1);
+    GS_CUDA_TRY(cudaGetLastError());
+    if (selected_out) {
+        k_fill_selected<<<grid, 256, 0, st>>>(offsets, nseg, sel, c.mode, selected_out);
+        ctx->launches += 1;
+        GS_CUDA_TRY(cudaGetLastError());
+    }
+    return GS_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,521 @@
+// ctx.cu -- context, configuration, layouts, error word, stage timing and the
+// C-ABI entry points that sequence the kernels of the other translation units.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+int gs_cuda_fail(cudaError_t e, const char* what)
+{
+    if (getenv("TILEGS_DEBUG")) fprintf(stderr, "tilegs: %s failed: %s\n", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? GS_ERR_NO_MEMORY : GS_ERR_CUDA;
+}
+
+extern "C" const char* gs_status_string(int status)
+{
+    switch (status) {
+        case GS_OK: return "ok";
+        case GS_ERR_INVALID_ARG: return "invalid argument";
+        case GS_ERR_CAPACITY: return "entry capacity exceeded";
+        case GS_ERR_CUDA: return "CUDA runtime error";
+        case GS_ERR_TIMEOUT: return "bounded device wait timed out";
+        case GS_ERR_NO_MEMORY: return "out of device memory";
+        case GS_ERR_NUMERIC: return "non-finite input";
+        default: return "unknown status";
+    }
+}
+
+// Defaults: the paper's supplement tables (default No-GW configuration and
+// default selective-repair thresholds) and Sec. 4.4 (K = 64).
+extern "C" void gs_config_default(gs_config* cfg, int32_t mode)
+{
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->mode = mode;
+    cfg->tile_size = 16;
+    cfg->K = 64;
+    cfg->sample_count = 8192;
+    cfg->p_lo = 1.0f;
+    cfg->p_hi = 99.0f;
+    cfg->pad = 0.05f;
+    cfg->near_alpha = 1.0f;
+    cfg->near_gamma = 0.25f;
+    cfg->eps = 1e-4f;
+    cfg->repair_budget_frac = 0.25f;
+    cfg->near_shift = (mode == GS_MODE_BINNED_PAPER || mode == GS_MODE_BINNED_NOREPAIR) ? 1 : 0;
+    cfg->tile_cull = 1;
+    cfg->persistent = 1;
+}
+
+namespace gs {
+
+int check_config(const gs_config* c)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (c->mode < GS_MODE_GLOBAL_SORT || c->mode > GS_MODE_BINNED_NOREPAIR) return GS_ERR_INVALID_ARG;
+    if (c->tile_size != 8 && c->tile_size != 16 && c->tile_size != 32) return GS_ERR_INVALID_ARG;
+    if (c->K < 1 || c->K > GS_MAX_K) return GS_ERR_INVALID_ARG;
+    if (c->sample_count < 1 || c->sample_count > 8192) return GS_ERR_INVALID_ARG;
+    if (!(c->p_lo >= 0.0f && c->p_lo <= 100.0f && c->p_hi >= c->p_lo && c->p_hi <= 100.0f))
+        return GS_ERR_INVALID_ARG;
+    if (!(c->pad >= 0.0f) || !(c->eps > 0.0f) || !(c->repair_budget_frac >= 0.0f))
+        return GS_ERR_INVALID_ARG;
+    if (c->mode == GS_MODE_BINNED_EXACT && c->near_shift) return GS_ERR_INVALID_ARG;
+    return GS_OK;
+}
+
+int ensure(void** p, size_t* cap, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    if (*p && *cap >= bytes) return GS_OK;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    size_t want = align256(bytes + bytes / 8);
+    cudaError_t e = cudaMalloc(p, want);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return GS_ERR_NO_MEMORY;
+    }
+    *cap = want;
+    return GS_OK;
+}
+
+void stage_begin(gs_ctx* ctx, int stage, cudaStream_t st)
+{
+    if (ctx->timing && ctx->ev_ok) {
+        cudaEventRecord(ctx->ev_b[stage], st);
+        ctx->stage_used[stage] = 1;
+    }
+}
+
+void stage_end(gs_ctx* ctx, int stage, cudaStream_t st)
+{
+    if (ctx->timing && ctx->ev_ok) cudaEventRecord(ctx->ev_e[stage], st);
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int gs_create(gs_ctx** out, const gs_config* cfg)
+{
+    if (!out || check_config(cfg) != GS_OK) return GS_ERR_INVALID_ARG;
+    gs_ctx* c = new gs_ctx();
+    c->cfg = *cfg;
+    cudaGetDevice(&c->device);
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) { delete c; return GS_ERR_NO_MEMORY; }
+    cudaMemset(c->d_err, 0, sizeof(int));
+    if (cudaMalloc(&c->d_bp, sizeof(BinParams)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
+    if (cudaMalloc(&c->d_tile_counter, 64 * sizeof(int32_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
+    if (cudaMalloc(&c->r_m, 2 * sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
+    if (cudaMalloc(&c->d_ops, sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
+    if (cudaMallocHost(&c->h_m, 2 * sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
+    c->ev_ok = 1;
+    for (int s = 0; s < GS_STAGE_COUNT; ++s) {
+        if (cudaEventCreate(&c->ev_b[s]) != cudaSuccess || cudaEventCreate(&c->ev_e[s]) != cudaSuccess)
+            c->ev_ok = 0;
+        c->stage_used[s] = 0;
+        c->stage_ms[s] = 0.0f;
+    }
+    *out = c;
+    return GS_OK;
+}
+
+extern "C" int gs_destroy(gs_ctx* c)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    void* ptrs[] = {c->d_err, c->d_scan, c->d_goff, c->d_keys[0], c->d_keys[1], c->d_vals[0],
+                    c->d_vals[1], c->d_hist, c->d_count, c->d_bin, c->d_bp, c->d_sel, c->d_tail,
+                    c->d_tiles_order, c->d_tile_counter, c->r_proj, c->r_isect, c->r_stream,
+                    c->r_off, c->r_m, c->r_scene, c->r_out, c->d_ops};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_m) cudaFreeHost(c->h_m);
+    if (c->ev_ok)
+        for (int s = 0; s < GS_STAGE_COUNT; ++s) {
+            cudaEventDestroy(c->ev_b[s]);
+            cudaEventDestroy(c->ev_e[s]);
+        }
+    delete c;
+    return GS_OK;
+}
+
+extern "C" int gs_set_config(gs_ctx* c, const gs_config* cfg)
+{
+    if (!c || check_config(cfg) != GS_OK) return GS_ERR_INVALID_ARG;
+    c->cfg = *cfg;
+    return GS_OK;
+}
+
+extern "C" int gs_get_config(const gs_ctx* c, gs_config* cfg)
+{
+    if (!c || !cfg) return GS_ERR_INVALID_ARG;
+    *cfg = c->cfg;
+    return GS_OK;
+}
+
+extern "C" int gs_get_error(gs_ctx* c, void* stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    int h = 0;
+    GS_CUDA_TRY(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    GS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return h;
+}
+
+extern "C" int gs_clear_error(gs_ctx* c, void* stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    GS_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), (cudaStream_t)stream));
+    return GS_OK;
+}
+
+extern "C" int gs_enable_timing(gs_ctx* c, int32_t on)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    c->timing = on ? 1 : 0;
+    return GS_OK;
+}
+
+extern "C" int gs_get_stage_times(gs_ctx* c, float* ms)
+{
+    if (!c || !ms) return GS_ERR_INVALID_ARG;
+    for (int s = 0; s < GS_STAGE_COUNT; ++s) {
+        ms[s] = 0.0f;
+        if (c->timing && c->ev_ok && c->stage_used[s]) {
+            GS_CUDA_TRY(cudaEventSynchronize(c->ev_e[s]));
+            float v = 0.0f;
+            if (cudaEventElapsedTime(&v, c->ev_b[s], c->ev_e[s]) == cudaSuccess) ms[s] = v;
+            else cudaGetLastError();
+        }
+        c->stage_used[s] = 0;
+    }
+    return GS_OK;
+}
+
+// ------------------------------------------------------------------ layouts
+extern "C" size_t gs_projected_offset(int64_t n, int32_t field)
+{
+    const size_t sizes[GS_P_NFIELDS] = {16, 16, 16, 8, 4};
+    size_t off = 0;
+    for (int f = 0; f < field && f < GS_P_NFIELDS; ++f) off += align256(sizes[f] * (size_t)n);
+    return off;
+}
+
+extern "C" size_t gs_projected_bytes(int64_t n) { return gs_projected_offset(n, GS_P_NFIELDS); }
+
+extern "C" size_t gs_isect_offset(int64_t m_cap, int32_t field)
+{
+    return (size_t)field * align256((size_t)m_cap * 4);
+}
+
+extern "C" size_t gs_isect_bytes(int64_t m_cap) { return gs_isect_offset(m_cap, 3); }
+
+extern "C" int32_t gs_num_tiles(int32_t width, int32_t height, int32_t tile)
+{
+    if (tile <= 0 || width <= 0 || height <= 0) return 0;
+    return ((width + tile - 1) / tile) * ((height + tile - 1) / tile);
+}
+
+static bool cam_ok(const gs_camera* cam)
+{
+    if (!cam) return false;
+    if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 * 8 || cam->height > 65535 * 8)
+        return false;
+    if (!(cam->fx > 0.0f) || !(cam->fy > 0.0f)) return false;
+    if (!(cam->near_plane >= 0.0f) || !(cam->far_plane > cam->near_plane)) return false;
+    return true;
+}
+
+// ------------------------------------------------------------------ entry points
+namespace gs {
+int launch_project(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
+                   const float* opac, const float* sh, int32_t sh_degree, int64_t n,
+                   const gs_camera* cam, const ProjView& pv, cudaStream_t st);
+int launch_emit(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
+                const IsectView& is, int64_t m_cap, int64_t* m_dev, cudaStream_t st);
+}  // namespace gs
+
+extern "C" int gs_project(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
+                          const float* opacities, const float* sh, int32_t sh_degree, int64_t n,
+                          const gs_camera* cam, void* projected, void* stream)
+{
+    if (!ctx || !cam_ok(cam) || n < 0 || n > INT32_MAX - 1 || sh_degree < 0 || sh_degree > 3)
+        return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!means || !scales || !quats || !opacities || !sh || !projected))
+        return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    stage_begin(ctx, GS_STAGE_PROJECT, st);
+    int r = launch_project(ctx, means, scales, quats, opacities, sh, sh_degree, n, cam,
+                           proj_view(projected, n), st);
+    stage_end(ctx, GS_STAGE_PROJECT, st);
+    return r;
+}
+
+extern "C" int gs_tile_intersect(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
+                                 void* isect, int64_t m_cap, int64_t* m_dev, int64_t* m_host,
+                                 void* stream)
+{
+    if (!ctx || !cam_ok(cam) || n < 0 || n > INT32_MAX - 1 || m_cap < 0 || m_cap > INT32_MAX - 1 || !m_dev)
+        return GS_ERR_INVALID_ARG;
+    if ((n > 0 && !projected) || (m_cap > 0 && !isect)) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    stage_begin(ctx, GS_STAGE_INTERSECT, st);
+    int r = launch_emit(ctx, proj_view(const_cast<void*>(projected), n), n, cam,
+                        isect_view(isect, m_cap), m_cap, m_dev, st);
+    stage_end(ctx, GS_STAGE_INTERSECT, st);
+    if (r != GS_OK) return r;
+    if (m_host) {
+        GS_CUDA_TRY(cudaMemcpyAsync(ctx->h_m, m_dev, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GS_CUDA_TRY(cudaStreamSynchronize(st));
+        *m_host = ctx->h_m[0];
+        if (ctx->h_m[0] > m_cap) return GS_ERR_CAPACITY;
+    }
+    return GS_OK;
+}
+
+static int sort_args_ok(gs_ctx* ctx, const gs_camera* cam, int64_t n, int64_t m_cap, const int64_t* m_dev)
+{
+    if (!ctx || !cam_ok(cam) || n < 0 || m_cap < 0 || m_cap > INT32_MAX - 1 || !m_dev) return 0;
+    return 1;
+}
+
+extern "C" int gs_depth_range(gs_ctx* ctx, const void* projected, const float* scales, int64_t n,
+                              const gs_camera* cam, const void* isect, int64_t m_cap,
+                              const int64_t* m_dev, float* zrange, void* stream)
+{
+    if (!sort_args_ok(ctx, cam, n, m_cap, m_dev) || !zrange) return GS_ERR_INVALID_ARG;
+    if (ctx->cfg.near_shift && !scales) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = depth_range(ctx, proj_view(const_cast<void*>(projected), n), scales,
+                        isect_view(const_cast<void*>(isect), m_cap), m_cap, m_dev, cam, st);
+    if (r != GS_OK) return r;
+    GS_CUDA_TRY(cudaMemcpyAsync(zrange, ctx->d_bp, 2 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return GS_OK;
+}
+
+extern "C" int gs_bin_build(gs_ctx* ctx, const void* projected, const float* scales, int64_t n,
+                            const gs_camera* cam, const void* isect, int64_t m_cap,
+                            const int64_t* m_dev, const float* zrange, uint64_t* stream_words,
+                            int32_t* offsets, void* stream)
+{
+    if (!sort_args_ok(ctx, cam, n, m_cap, m_dev) || !zrange || !stream_words || !offsets)
+        return GS_ERR_INVALID_ARG;
+    if (ctx->cfg.mode == GS_MODE_GLOBAL_SORT) return GS_ERR_INVALID_ARG;
+    if (ctx->cfg.near_shift && !scales) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = set_zrange(ctx, zrange, st);
+    if (r != GS_OK) return r;
+    const int32_t T = gs_num_tiles(cam->width, cam->height, ctx->cfg.tile_size);
+    return bin_build(ctx, proj_view(const_cast<void*>(projected), n), scales,
+                     isect_view(const_cast<void*>(isect), m_cap), m_cap, m_dev, T, stream_words,
+                     offsets, st);
+}
+
+extern "C" int gs_repair(gs_ctx* ctx, const gs_camera* cam, const int64_t* m_dev, uint64_t* stream_words,
+                         const int32_t* offsets, uint8_t* selected_out, void* stream)
+{
+    if (!ctx || !cam_ok(cam) || !m_dev || !stream_words || !offsets) return GS_ERR_INVALID_ARG;
+    if (ctx->cfg.mode == GS_MODE_GLOBAL_SORT) return GS_ERR_INVALID_ARG;
+    const int32_t T = gs_num_tiles(cam->width, cam->height, ctx->cfg.tile_size);
+    return repair(ctx, T, m_dev, stream_words, offsets, selected_out, (cudaStream_t)stream);
+}
+
+extern "C" int gs_sort_or_bin(gs_ctx* ctx, const void* projected, const float* scales, int64_t n,
+                              const gs_camera* cam, const void* isect, int64_t m_cap,
+                              const int64_t* m_dev, uint64_t* stream_words, int32_t* offsets,
+                              float* zrange_out, void* stream)
+{
+    if (!sort_args_ok(ctx, cam, n, m_cap, m_dev) || !stream_words || !offsets) return GS_ERR_INVALID_ARG;
+    if (m_cap > 0 && !isect) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t T = gs_num_tiles(cam->width, cam->height, ctx->cfg.tile_size);
+    IsectView is = isect_view(const_cast<void*>(isect), m_cap);
+    if (ctx->cfg.mode == GS_MODE_GLOBAL_SORT) {
+        stage_begin(ctx, GS_STAGE_SORT, st);
+        int r = global_sort(ctx, is, m_cap, m_dev, T, stream_words, offsets, st);
+        stage_end(ctx, GS_STAGE_SORT, st);
+        return r;
+    }
+    if (ctx->cfg.near_shift && !scales) return GS_ERR_INVALID_ARG;
+    ProjView pv = proj_view(const_cast<void*>(projected), n);
+    stage_begin(ctx, GS_STAGE_DEPTH_RANGE, st);
+    int r = depth_range(ctx, pv, scales, is, m_cap, m_dev, cam, st);
+    stage_end(ctx, GS_STAGE_DEPTH_RANGE, st);
+    if (r != GS_OK) return r;
+    if (zrange_out)
+        GS_CUDA_TRY(cudaMemcpyAsync(zrange_out, ctx->d_bp, 2 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    stage_begin(ctx, GS_STAGE_BIN, st);
+    r = bin_build(ctx, pv, scales, is, m_cap, m_dev, T, stream_words, offsets, st);
+    stage_end(ctx, GS_STAGE_BIN, st);
+    if (r != GS_OK) return r;
+    stage_begin(ctx, GS_STAGE_REPAIR, st);
+    r = repair(ctx, T, m_dev, stream_words, offsets, nullptr, st);
+    stage_end(ctx, GS_STAGE_REPAIR, st);
+    return r;
+}
+
+extern "C" int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
+                                const uint64_t* stream_words, const int32_t* offsets,
+                                int32_t offsets_stride, const float* bg, float* rgb, float* alpha,
+                                int32_t* last, int32_t* ntests, void* stream)
+{
+    if (!ctx || !cam_ok(cam) || n < 0 || !offsets || !bg || !rgb || !alpha || !last)
+        return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!projected || !stream_words)) return GS_ERR_INVALID_ARG;
+    if (offsets_stride < 1 || offsets_stride > GS_MAX_K) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool baseline = (ctx->cfg.mode == GS_MODE_GLOBAL_SORT);
+    stage_begin(ctx, GS_STAGE_RASTER, st);
+    int r = raster_fwd(ctx, proj_view(const_cast<void*>(projected), n), cam, stream_words, offsets,
+                       offsets_stride, bg, rgb, alpha, last, ntests, baseline, st);
+    stage_end(ctx, GS_STAGE_RASTER, st);
+    return r;
+}
+
+// ------------------------------------------------------------------ whole frame
+static int render_buffers(gs_ctx* c, int64_t n, int64_t m_cap, int32_t T)
+{
+    int r;
+    if ((r = ensure(&c->r_proj, &c->r_proj_cap, gs_projected_bytes(n))) != GS_OK) return r;
+    if (m_cap > c->r_m_cap) {
+        size_t cap_bytes = 0;
+        if (c->r_isect) cudaFree(c->r_isect);
+        if (c->r_stream) cudaFree(c->r_stream);
+        c->r_isect = nullptr;
+        c->r_stream = nullptr;
+        c->r_m_cap = 0;
+        if ((r = ensure(&c->r_isect, &cap_bytes, gs_isect_bytes(m_cap))) != GS_OK) return r;
+        size_t sb = 0;
+        void* sp = nullptr;
+        if ((r = ensure(&sp, &sb, (size_t)m_cap * 8)) != GS_OK) return r;
+        c->r_stream = (uint64_t*)sp;
+        c->r_m_cap = m_cap;
+    }
+    const int32_t kmax = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : c->cfg.K;
+    void* op = c->r_off;
+    if ((r = ensure(&op, &c->r_off_cap, ((size_t)T * kmax + 1) * 4)) != GS_OK) return r;
+    c->r_off = (int32_t*)op;
+    return GS_OK;
+}
+
+extern "C" int gs_reserve(gs_ctx* c, int64_t n, int64_t m_cap, int32_t width, int32_t height)
+{
+    if (!c || n < 0 || m_cap < 0 || m_cap > INT32_MAX - 1 || width <= 0 || height <= 0)
+        return GS_ERR_INVALID_ARG;
+    const int32_t T = gs_num_tiles(width, height, c->cfg.tile_size);
+    int r = render_buffers(c, n, m_cap, T);
+    if (r != GS_OK) return r;
+    // grow the internal scratch of every stage once, outside any capture
+    return gs::reserve_internal(c, n, m_cap, T);
+}
+
+extern "C" int64_t gs_last_entry_count(gs_ctx* c) { return c ? c->last_m : -1; }
+
+extern "C" int64_t gs_launch_count(const gs_ctx* c) { return c ? c->launches : -1; }
+
+extern "C" int64_t gs_last_raster_ops(gs_ctx* c, void* stream)
+{
+    if (!c) return -1;
+    int64_t h = 0;
+    if (cudaMemcpyAsync(&h, c->d_ops, sizeof(int64_t), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return -1;
+    return h;
+}
+
+extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, const float* bg,
+                         float* rgb, float* alpha, int32_t* last, int32_t flags, void* stream)
+{
+    if (!c || !sc || !cam_ok(cam) || !bg || !rgb || !alpha) return GS_ERR_INVALID_ARG;
+    if (sc->n < 0 || sc->n > INT32_MAX - 1 || sc->sh_degree < 0 || sc->sh_degree > 3) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = sc->n;
+    const int32_t W = cam->width, H = cam->height;
+    const int32_t T = gs_num_tiles(W, H, c->cfg.tile_size);
+    const int ncoef = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+    int r;
+    const float *means = sc->means, *scales = sc->scales, *quats = sc->quats, *opac = sc->opacities,
+                *sh = sc->sh;
+    if (flags & GS_RENDER_HOST_INPUTS) {
+        // one device copy of the scene, refreshed every call
+        const size_t fl = (size_t)n * (3 + 3 + 4 + 1 + 3 * ncoef);
+        void* p = c->r_scene;
+        if ((r = ensure(&p, &c->r_scene_cap, fl * 4 + 5 * 256)) != GS_OK) return r;
+        c->r_scene = (float*)p;
+        char* b = (char*)p;
+        const float* src[5] = {means, scales, quats, opac, sh};
+        const size_t cnt[5] = {(size_t)n * 3, (size_t)n * 3, (size_t)n * 4, (size_t)n, (size_t)n * 3 * ncoef};
+        const float* dst[5];
+        for (int k = 0; k < 5; ++k) {
+            dst[k] = (const float*)b;
+            if (cnt[k]) GS_CUDA_TRY(cudaMemcpyAsync(b, src[k], cnt[k] * 4, cudaMemcpyHostToDevice, st));
+            b += align256(cnt[k] * 4);
+        }
+        means = dst[0]; scales = dst[1]; quats = dst[2]; opac = dst[3]; sh = dst[4];
+    }
+    float *d_rgb = rgb, *d_alpha = alpha;
+    int32_t* d_last = last;
+    if ((flags & GS_RENDER_HOST_OUTPUTS) || !last) {
+        const size_t px = (size_t)W * H;
+        void* p = c->r_out;
+        if ((r = ensure(&p, &c->r_out_cap, px * 5 * 4 + 3 * 256)) != GS_OK) return r;
+        c->r_out = (float*)p;
+        char* b = (char*)p;
+        float* o_rgb = (float*)b; b += align256(px * 12);
+        float* o_alpha = (float*)b; b += align256(px * 4);
+        int32_t* o_last = (int32_t*)b;
+        if (flags & GS_RENDER_HOST_OUTPUTS) { d_rgb = o_rgb; d_alpha = o_alpha; d_last = o_last; }
+        else d_last = o_last;
+    }
+    if ((r = render_buffers(c, n, c->r_m_cap > 0 ? c->r_m_cap : 1, T)) != GS_OK) return r;
+    ProjView pv = proj_view(c->r_proj, n);
+    if (n > 0) {
+        stage_begin(c, GS_STAGE_PROJECT, st);
+        r = launch_project(c, means, scales, quats, opac, sh, sc->sh_degree, n, cam, pv, st);
+        stage_end(c, GS_STAGE_PROJECT, st);
+        if (r != GS_OK) return r;
+    }
+    stage_begin(c, GS_STAGE_INTERSECT, st);
+    r = count_scan(c, pv, n, c->r_m, st);
+    if (r != GS_OK) return r;
+    if (!(flags & GS_RENDER_NO_SYNC)) {
+        // size the entry buffers: read M once, grow if needed
+        GS_CUDA_TRY(cudaMemcpyAsync(c->h_m, c->r_m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (c->h_m[0] > c->r_m_cap) {
+            if ((r = render_buffers(c, n, c->h_m[0], T)) != GS_OK) return r;
+        }
+    }
+    r = emit_only(c, pv, n, cam, isect_view(c->r_isect, c->r_m_cap), c->r_m_cap, c->r_m, st);
+    stage_end(c, GS_STAGE_INTERSECT, st);
+    if (r != GS_OK) return r;
+    const int32_t stride = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : c->cfg.K;
+    r = gs_sort_or_bin(c, c->r_proj, scales, n, cam, c->r_isect, c->r_m_cap, c->r_m, c->r_stream,
+                       c->r_off, nullptr, st);
+    if (r != GS_OK) return r;
+    stage_begin(c, GS_STAGE_RASTER, st);
+    r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,
+                   c->cfg.mode == GS_MODE_GLOBAL_SORT, st);
+    stage_end(c, GS_STAGE_RASTER, st);
+    if (r != GS_OK) return r;
+    if (flags & GS_RENDER_HOST_OUTPUTS) {
+        const size_t px = (size_t)W * H;
+        GS_CUDA_TRY(cudaMemcpyAsync(rgb, d_rgb, px * 12, cudaMemcpyDeviceToHost, st));
+        GS_CUDA_TRY(cudaMemcpyAsync(alpha, d_alpha, px * 4, cudaMemcpyDeviceToHost, st));
+        if (last) GS_CUDA_TRY(cudaMemcpyAsync(last, d_last, px * 4, cudaMemcpyDeviceToHost, st));
+    }
+    GS_CUDA_TRY(cudaMemcpyAsync(c->h_m + 1, c->r_m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (flags & (GS_RENDER_HOST_INPUTS | GS_RENDER_HOST_OUTPUTS)) {
+        GS_CUDA_TRY(cudaStreamSynchronize(st));
+        c->last_m = c->h_m[1];
+        if (c->last_m > c->r_m_cap) return GS_ERR_CAPACITY;
+    } else {
+        c->last_m = c->h_m[0];
+    }
+    return GS_OK;
+}

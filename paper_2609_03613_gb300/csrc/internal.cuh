@@ -1,0 +1,256 @@
+// internal.cuh -- shared pieces of libtilegs (not part of the ABI).
+//
+// Built with -fmad=false: no multiply-add is fused unless fmaf() is written,
+// so every float32 value that decides an integer (tile rectangle, alpha skip,
+// transmittance stop, bin index) follows the operation order stated at its
+// definition.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tilegs.h"
+
+#define GS_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t e_ = (expr);                            \
+        if (e_ != cudaSuccess) return gs_cuda_fail(e_, #expr); \
+    } while (0)
+
+int gs_cuda_fail(cudaError_t e, const char* what);
+
+namespace gs {
+
+constexpr int kNumSMs = 152;  // GB300: 2 dies x 76 SMs (queried at runtime where it matters)
+
+// ------------------------------------------------------------------ records
+// Byte offsets of the projected fields (each 256-byte aligned).
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct ProjView {
+    float4* xy_ab;   // {mean_x, mean_y, conic_a, conic_b}
+    float4* c_o_z;   // {conic_c, opacity, depth, cull_tau}
+    float4* rgb;     // {r, g, b, cull_margin}
+    uint2* rect;     // {tx0 | ty0 << 16, tx1 | ty1 << 16}
+    int32_t* radius;
+};
+
+inline ProjView proj_view(void* base, int64_t n)
+{
+    char* b = static_cast<char*>(base);
+    ProjView v;
+    v.xy_ab = reinterpret_cast<float4*>(b + gs_projected_offset(n, GS_P_XY_AB));
+    v.c_o_z = reinterpret_cast<float4*>(b + gs_projected_offset(n, GS_P_C_O_Z));
+    v.rgb = reinterpret_cast<float4*>(b + gs_projected_offset(n, GS_P_RGB));
+    v.rect = reinterpret_cast<uint2*>(b + gs_projected_offset(n, GS_P_RECT));
+    v.radius = reinterpret_cast<int32_t*>(b + gs_projected_offset(n, GS_P_RADIUS));
+    return v;
+}
+
+struct IsectView {
+    uint32_t* tile;
+    uint32_t* zbits;
+    uint32_t* gid;
+};
+
+inline IsectView isect_view(void* base, int64_t m_cap)
+{
+    char* b = static_cast<char*>(base);
+    IsectView v;
+    v.tile = reinterpret_cast<uint32_t*>(b + gs_isect_offset(m_cap, 0));
+    v.zbits = reinterpret_cast<uint32_t*>(b + gs_isect_offset(m_cap, 1));
+    v.gid = reinterpret_cast<uint32_t*>(b + gs_isect_offset(m_cap, 2));
+    return v;
+}
+
+// Live entry count: the device count when it fits the capacity, else 0 (the
+// emitter has raised GS_ERR_CAPACITY and written nothing).
+__device__ __forceinline__ int64_t live_count(const int64_t* m_dev, int64_t m_cap)
+{
+    const int64_t m = *m_dev;
+    return (m >= 0 && m <= m_cap) ? m : 0;
+}
+
+// ------------------------------------------------------------------ device error word
+// Kernels record the first device-side error here (atomicCAS from 0).
+__device__ inline void raise_error(int* err, int code)
+{
+    if (err) atomicCAS(err, 0, code);
+}
+
+// ------------------------------------------------------------------ elementary functions
+// exp by Cody-Waite range reduction and a degree-7 Taylor polynomial (W. J.
+// Cody and W. Waite, "Software Manual for the Elementary Functions", 1980):
+// n = round(x log2 e) via the 1.5 * 2^23 shifter, r = x - n ln2 in two
+// pieces, e^r by Horner over 1/k!, then scaled by 2^n built in the exponent
+// field.  Every step is one correctly rounded float32 operation.  The core
+// requires x in [-87, 88] (so that 2^n is a normal float); spec_exp clamps.
+__device__ __forceinline__ float spec_exp_core(float x)
+{
+    const float kLog2e = 1.44269504088896341f;
+    const float kLn2Hi = 0.693145751953125f;
+    const float kLn2Lo = 1.42860682030941723e-6f;
+    const float kShift = 12582912.0f;  // 1.5 * 2^23
+    const float k = fmaf(x, kLog2e, kShift);
+    const float n = __fsub_rn(k, kShift);
+    float r = fmaf(n, -kLn2Hi, x);
+    r = fmaf(n, -kLn2Lo, r);
+    float p = 1.0f / 5040.0f;
+    p = fmaf(p, r, 1.0f / 720.0f);
+    p = fmaf(p, r, 1.0f / 120.0f);
+    p = fmaf(p, r, 1.0f / 24.0f);
+    p = fmaf(p, r, 1.0f / 6.0f);
+    p = fmaf(p, r, 0.5f);
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    // bits(k) = bits(kShift) + n for |n| < 2^22, so the exponent field of
+    // 2^n is (bits(k) - bits(kShift) + 127) << 23.
+    const int e = (__float_as_int(k) - 0x4B400000 + 127) << 23;
+    return __fmul_rn(p, __int_as_float(e));
+}
+
+// Full-range variant: clamps x to [-87, 88] first.
+__device__ __forceinline__ float spec_exp(float x)
+{
+    x = x < -87.0f ? -87.0f : x;
+    x = x > 88.0f ? 88.0f : x;
+    return spec_exp_core(x);
+}
+
+// ln by exponent split and the atanh series (Abramowitz and Stegun 4.1.27):
+// x = 2^e m, m in (sqrt(1/2), sqrt(2)], s = (m-1)/(m+1),
+// ln m = 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9), ln x = e ln2 + ln m.
+// Defined for normal positive x.
+__device__ __forceinline__ float spec_log(float x)
+{
+    const float kLn2Hi = 0.693145751953125f;
+    const float kLn2Lo = 1.42860682030941723e-6f;
+    const uint32_t u = __float_as_uint(x);
+    int e = int((u >> 23) & 0xffu) - 127;
+    float m = __uint_as_float((u & 0x007fffffu) | 0x3f800000u);
+    if (m > 1.41421356f) {
+        m = __fmul_rn(m, 0.5f);
+        e = e + 1;
+    }
+    const float s = __fdiv_rn(__fsub_rn(m, 1.0f), __fadd_rn(m, 1.0f));
+    const float s2 = __fmul_rn(s, s);
+    float p = 1.0f / 9.0f;
+    p = fmaf(p, s2, 1.0f / 7.0f);
+    p = fmaf(p, s2, 1.0f / 5.0f);
+    p = fmaf(p, s2, 1.0f / 3.0f);
+    p = fmaf(p, s2, 1.0f);
+    const float lnm = __fmul_rn(__fmul_rn(2.0f, s), p);
+    const float fe = float(e);
+    return fmaf(fe, kLn2Hi, fmaf(fe, kLn2Lo, lnm));
+}
+
+// ------------------------------------------------------------------ bins
+struct BinParams {
+    float zmin, zmax;  // robust depth range
+    float lmin, lmax;  // ln z'min, ln z'max
+    int32_t K;
+    int32_t nsamples;  // kept samples
+    float splits[GS_MAX_K];  // K-1 log-spaced split depths (monotone map)
+};
+
+}  // namespace gs
+
+// ------------------------------------------------------------------ context
+struct gs_ctx {
+    gs_config cfg;
+    int device = 0;
+    int num_sms = 152;
+    int* d_err = nullptr;
+    // scan scratch (block sums)
+    void* d_scan = nullptr;
+    size_t scan_bytes = 0;
+    // per-Gaussian emission offsets [n+1]
+    int32_t* d_goff = nullptr;
+    size_t goff_cap = 0;
+    // global radix sort ping-pong + histograms
+    uint64_t* d_keys[2] = {nullptr, nullptr};
+    uint32_t* d_vals[2] = {nullptr, nullptr};
+    size_t sort_cap = 0;
+    uint32_t* d_hist = nullptr;
+    size_t hist_cap = 0;
+    // binning
+    int32_t* d_count = nullptr;  // T*K counters
+    size_t count_cap = 0;
+    uint8_t* d_bin = nullptr;    // per-entry bin id
+    size_t bin_cap = 0;
+    gs::BinParams* d_bp = nullptr;
+    uint8_t* d_sel = nullptr;    // per-segment repair selection
+    size_t sel_cap = 0;
+    int32_t* d_tail = nullptr;   // segments too long for a shared-memory sort
+    size_t tail_cap = 0;
+    int32_t* d_tiles_order = nullptr;  // persistent raster tile order
+    int32_t* d_tile_counter = nullptr;
+    size_t order_cap = 0;
+    // whole-frame buffers (gs_render)
+    void* r_proj = nullptr; size_t r_proj_cap = 0;
+    void* r_isect = nullptr; int64_t r_m_cap = 0;
+    uint64_t* r_stream = nullptr;
+    int32_t* r_off = nullptr; size_t r_off_cap = 0;
+    int64_t* r_m = nullptr;
+    int64_t* h_m = nullptr;  // pinned
+    float* r_scene = nullptr; size_t r_scene_cap = 0;  // device copies of host inputs
+    float* r_out = nullptr; size_t r_out_cap = 0;      // device outputs for host outputs
+    int64_t last_m = 0;
+    int64_t launches = 0;  // kernels this context has launched
+    int64_t* d_ops = nullptr;  // compositing ops counted by the instrumented raster
+    // timing
+    int timing = 0;
+    cudaEvent_t ev_b[GS_STAGE_COUNT];
+    cudaEvent_t ev_e[GS_STAGE_COUNT];
+    int ev_ok = 0;
+    float stage_ms[GS_STAGE_COUNT];
+    int stage_used[GS_STAGE_COUNT];
+};
+
+// ------------------------------------------------------------------ internal launchers
+namespace gs {
+
+int ensure(void** p, size_t* cap, size_t bytes);
+int check_config(const gs_config* cfg);
+
+// scan.cu
+// Exclusive scan of int32 counts[0..n) into out[0..n] (out[n] = total) with
+// the total also stored as int64 at total64 (nullable).  3 kernels.
+int exclusive_scan_i32(gs_ctx* ctx, const int32_t* counts, int64_t n, int32_t* out,
+                       int64_t* total64, cudaStream_t st);
+// Tile counts of the projected rects, scanned into per-Gaussian offsets.
+int scan_tile_counts(gs_ctx* ctx, const uint2* rect, int64_t n, int32_t* out, int64_t* total64,
+                     cudaStream_t st);
+
+// tile counts -> per-Gaussian offsets (ctx->d_goff) and M; then the emission
+int count_scan(gs_ctx* ctx, const ProjView& pv, int64_t n, int64_t* m_dev, cudaStream_t st);
+int emit_only(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, const IsectView& is,
+              int64_t m_cap, const int64_t* m_dev, cudaStream_t st);
+
+// sort.cu
+int global_sort(gs_ctx* ctx, const IsectView& is, int64_t m_cap, const int64_t* m_dev,
+                int32_t n_tiles, uint64_t* stream_words, int32_t* offsets, cudaStream_t st);
+
+// bins.cu
+int depth_range(gs_ctx* ctx, const ProjView& pv, const float* scales, const IsectView& is,
+                int64_t m_cap, const int64_t* m_dev, const gs_camera* cam, cudaStream_t st);
+int bin_build(gs_ctx* ctx, const ProjView& pv, const float* scales, const IsectView& is,
+              int64_t m_cap, const int64_t* m_dev, int32_t n_tiles, uint64_t* stream_words,
+              int32_t* offsets, cudaStream_t st);
+int repair(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* stream_words,
+           const int32_t* offsets, uint8_t* selected_out, cudaStream_t st);
+int set_zrange(gs_ctx* ctx, const float* zrange, cudaStream_t st);
+
+// raster.cu
+int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* stream_words,
+               const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
+               int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st);
+
+// grow every stage's internal scratch for (n, m_cap, T) (synchronous)
+int reserve_internal(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t n_tiles);
+
+// timing helpers
+void stage_begin(gs_ctx* ctx, int stage, cudaStream_t st);
+void stage_end(gs_ctx* ctx, int stage, cudaStream_t st);
+
+}  // namespace gs
