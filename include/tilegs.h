@@ -225,6 +225,30 @@ int gs_repair(gs_ctx* ctx, const gs_camera* cam, const int64_t* m_dev, uint64_t*
               const int32_t* offsets, uint8_t* selected_out, void* stream);
 
 /*
+ * gs_depth_range without a context and without allocating anything (the
+ * paper has no counterpart: this is a deployment variant of gs_depth_range).
+ * For callers that cannot call cudaMalloc -- an application whose device
+ * memory belongs to its own allocator or fixed budget and that passes this
+ * library only pre-allocated buffers, or code that must not set off
+ * cudaMalloc's implicit device synchronisation while other work runs.
+ *   cfg: HOST config (mode-independent fields: sample_count, p_lo, p_hi, pad,
+ *        near_shift / near_alpha / near_gamma, eps, K); other arguments and
+ *        the result zrange[2] as for gs_depth_range.
+ * Scratch: one 536-byte bin-parameter record in a file-scope static
+ * __device__ array, held by every GPU that loads the library until exit.  Its
+ * limit: K <= GS_MAX_K (128) split depths and sample_count <= 8192; larger
+ * values return GS_ERR_INVALID_ARG before anything is enqueued.
+ * The first call on each device resolves the scratch address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Calls cudaMalloc, cudaFree and no allocating routine.  All calls share the
+ * scratch, which keeps the last call's contents (each call rewrites every
+ * field it reads), so calls that overlap on the GPU race.
+ */
+int gs_depth_range_noalloc(const gs_config* cfg, const void* projected, const float* scales, int64_t n,
+                           const gs_camera* cam, const void* isect, int64_t m_cap, const int64_t* m_dev,
+                           float* zrange, void* stream);
+
+/*
  * Front-to-back compositing of each tile's span (Sec. 3.4; supplement
  * algorithm 5).  Per pixel centre (x + 0.5, y + 0.5) and entry g in stream
  * order: q = 1/2 d^T conic d, alpha = min(0.99, o exp(-q)), skip alpha < 1/255,

@@ -173,6 +173,29 @@ int depth_range(gs_ctx* ctx, const ProjView& pv, const float* scales, const Isec
     return GS_OK;
 }
 
+// The same launch with the bin-parameter record placed by the caller (used by
+// the entry point that allocates nothing).
+int launch_depth_range_into(const gs_config& c, const ProjView& pv, const float* scales, const IsectView& is,
+                            int64_t m_cap, const int64_t* m_dev, const gs_camera* cam, BinParams* bp,
+                            cudaStream_t st)
+{
+    DrArgs a;
+    a.near_plane = cam->near_plane;
+    a.far_plane = cam->far_plane;
+    a.S = c.sample_count;
+    a.near_shift = c.near_shift;
+    a.near_alpha = c.near_alpha;
+    a.near_gamma = c.near_gamma;
+    a.p_lo = c.p_lo;
+    a.p_hi = c.p_hi;
+    a.pad = c.pad;
+    a.eps = c.eps;
+    a.K = c.K;
+    k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, is, m_dev, m_cap, a, bp);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
 int set_zrange(gs_ctx* ctx, const float* zrange, cudaStream_t st)
 {
     k_bin_params_from<<<1, 128, 0, st>>>(zrange, ctx->cfg.K, ctx->cfg.eps, ctx->d_bp);

@@ -240,6 +240,9 @@ int bin_build(gs_ctx* ctx, const ProjView& pv, const float* scales, const IsectV
 int repair(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* stream_words,
            const int32_t* offsets, uint8_t* selected_out, cudaStream_t st);
 int set_zrange(gs_ctx* ctx, const float* zrange, cudaStream_t st);
+int launch_depth_range_into(const gs_config& c, const ProjView& pv, const float* scales, const IsectView& is,
+                            int64_t m_cap, const int64_t* m_dev, const gs_camera* cam, BinParams* bp,
+                            cudaStream_t st);
 
 // raster.cu
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* stream_words,

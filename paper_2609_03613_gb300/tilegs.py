@@ -34,7 +34,7 @@ EXPORTS = [
     "gs_get_stage_times", "gs_projected_bytes", "gs_projected_offset", "gs_isect_bytes",
     "gs_isect_offset", "gs_num_tiles", "gs_project", "gs_tile_intersect", "gs_sort_or_bin",
     "gs_depth_range", "gs_bin_build", "gs_repair", "gs_rasterize_fwd", "gs_render",
-    "gs_last_entry_count", "gs_launch_count", "gs_last_raster_ops",
+    "gs_last_entry_count", "gs_launch_count", "gs_last_raster_ops", "gs_depth_range_noalloc",
 ]
 
 
@@ -115,6 +115,8 @@ def lib():
         "gs_last_entry_count": (i64, [vp]),
         "gs_launch_count": (i64, [vp]),
         "gs_last_raster_ops": (i64, [vp, vp]),
+        "gs_depth_range_noalloc": (C.c_int, [C.POINTER(GsConfig), vp, vp, i64, C.POINTER(GsCamera), vp, i64,
+                                             vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -381,3 +383,13 @@ def projected_fields(projected, n):
     rect = projected[o[3]:o[3] + 8 * n].view(torch.int32).view(n, 2)
     radius = projected[o[4]:o[4] + 4 * n].view(torch.int32)
     return dict(xy_ab=xy_ab, c_o_z=c_o_z, rgb=rgb, rect=rect, radius=radius)
+
+
+def depth_range_noalloc(cfg: GsConfig, projected, scales, n, cam, isect, m_cap, m_dev, zrange):
+    """gs_depth_range_noalloc: the depth range with no context and no device
+    allocation (all buffers, zrange included, come from the caller)."""
+    c = gs_camera(cam)
+    check(lib().gs_depth_range_noalloc(C.byref(cfg), _ptr(projected), _ptr(scales), int(n), C.byref(c),
+                                       _ptr(isect), int(m_cap), _ptr(m_dev), _ptr(zrange), _stream()),
+          "gs_depth_range_noalloc")
+    return zrange
