@@ -44,11 +44,14 @@ L2_FLUSH_BYTES = 256 << 20
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-frame", action="store_true",
+                    help="for ncu: two warm-up frames, then one frame of each path, no timing")
+    ap.add_argument("--modes", default="exact,global", help="paths run by --profile-frame")
     return ap.parse_args()
 
 
@@ -216,7 +219,7 @@ def run_reference(args):
 # --------------------------------------------------------------------- ours
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("raster.cu", "internal.cuh"):
+    for f in ("raster.cu", "internal.cuh", "device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2609_03613_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -251,20 +254,27 @@ def run_ours(args):
     bg = (0.0, 0.0, 0.0)
     H, W = cam.height, cam.width
 
+    side = torch.cuda.Stream(device=dev)  # graphs cannot be captured on the legacy stream
+
     def make(mode):
         ctx = G.Context(mode)
         out = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
                torch.empty((H, W), dtype=torch.int32, device=dev))
-        ctx.render(ds, cam, bg, out)  # sizes the scratch (one read of M)
+        with torch.cuda.stream(side):
+            ctx.render(ds, cam, bg, out)  # sizes the scratch (one read of M)
         torch.cuda.synchronize()
         m = ctx.last_entry_count()
         ctx.reserve(ds.n, int(m * 1.25) + 1024, W, H)
-        ctx.enable_timing(True)
         return ctx, out, m
 
-    def timed(ctx, out, steps, warmup, sampler=None):
-        for _ in range(warmup):
-            ctx.render(ds, cam, bg, out, flags=G.RENDER_NO_SYNC)
+    def timed(ctx, out, steps, warmup, flags=G.RENDER_NO_SYNC | G.RENDER_GRAPH):
+        # stage events only outside graphs (their records inside a captured
+        # graph do not time the stages)
+        staged = not (flags & G.RENDER_GRAPH)
+        ctx.enable_timing(staged)
+        with torch.cuda.stream(side):
+            for _ in range(warmup):
+                ctx.render(ds, cam, bg, out, flags=flags)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         stage = {s: [] for s in G.STAGES}
@@ -273,14 +283,16 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         w0 = time.perf_counter()
-        for i in range(steps):
-            flush.zero_()
-            ev[i][0].record()
-            ctx.render(ds, cam, bg, out, flags=G.RENDER_NO_SYNC)
-            ev[i][1].record()
-            st = ctx.stage_times()  # events on the library's stream; synchronises
-            for s in G.STAGES:
-                stage[s].append(st[s])
+        with torch.cuda.stream(side):
+            for i in range(steps):
+                flush.zero_()
+                ev[i][0].record()
+                ctx.render(ds, cam, bg, out, flags=flags)
+                ev[i][1].record()
+                if staged:
+                    st = ctx.stage_times()  # events on the library's stream; synchronises
+                    for s in G.STAGES:
+                        stage[s].append(st[s])
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
@@ -294,9 +306,13 @@ def run_ours(args):
     assert ctx_b.error() == 0 and ctx_g.error() == 0
 
     with ClockSampler(local) as clk:
-        ms_b, st_b, wall_b, launches = timed(ctx_b, out_b, args.steps, args.warmup)
+        ms_b, _, wall_b, launches = timed(ctx_b, out_b, args.steps, args.warmup)
+        ms_g, _, wall_g, _ = timed(ctx_g, out_g, args.steps, args.warmup)
+        # the same frames issued launch by launch (no graph), with per-stage
+        # events on the library's stream: the stage and raster-kernel times
+        ms_b_ng, st_b, _, _ = timed(ctx_b, out_b, max(50, args.steps // 2), 3, flags=G.RENDER_NO_SYNC)
+        ms_g_ng, st_g, _, _ = timed(ctx_g, out_g, max(50, args.steps // 2), 3, flags=G.RENDER_NO_SYNC)
     clocks = clk.summary()
-    ms_g, st_g, wall_g, _ = timed(ctx_g, out_g, args.steps, args.warmup)
 
     frame_b = sum(ms_b) / len(ms_b)
     frame_g = sum(ms_g) / len(ms_g)
@@ -307,8 +323,9 @@ def run_ours(args):
     raster_g = mean(st_g["raster"])
 
     # images of both paths must agree (EXACT reproduces the global order)
-    ctx_b.render(ds, cam, bg, out_b)
-    ctx_g.render(ds, cam, bg, out_g)
+    with torch.cuda.stream(side):
+        ctx_b.render(ds, cam, bg, out_b)
+        ctx_g.render(ds, cam, bg, out_g)
     torch.cuda.synchronize()
     err_vs_global = float((out_b[0] - out_g[0]).abs().max().item())
     last_equal = bool(torch.equal(out_b[2], out_g[2]))
@@ -317,10 +334,11 @@ def run_ours(args):
     ctx_p = G.Context("paper")
     out_p = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
              torch.empty((H, W), dtype=torch.int32, device=dev))
-    ctx_p.render(ds, cam, bg, out_p)
-    ctx_p.enable_timing(True)
-    ms_p, st_p, _, _ = timed(ctx_p, out_p, max(3, args.steps // 4), 2)
-    ctx_p.render(ds, cam, bg, out_p)
+    with torch.cuda.stream(side):
+        ctx_p.render(ds, cam, bg, out_p)
+    ms_p, st_p, _, _ = timed(ctx_p, out_p, max(3, args.steps // 4), 2, flags=G.RENDER_NO_SYNC)
+    with torch.cuda.stream(side):
+        ctx_p.render(ds, cam, bg, out_p)
     torch.cuda.synchronize()
     err_paper = float((out_p[0] - out_b[0]).abs().max().item())
 
@@ -390,11 +408,13 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 4), "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(frame_b, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC, "path": "binned EXACT, K=64, 16x16 tiles",
+        "config": {"workload": WORKLOAD_DESC,
+                   "path": "binned EXACT, K=64, 16x16 tiles, frame replayed as one CUDA graph",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "entries_per_frame": m_b},
         "raster_ms": round(raster_b, 4),
+        "raster_ms_source": "CUDA events around the raster kernel on the library stream, un-captured frames",
         "raster_mpix_s": round(P / (raster_b * 1e-3) / 1e6, 3),
         "stages_ms": {s: round(mean(v), 4) for s, v in st_b.items() if mean(v) > 0},
         "global_sort": {"frame_ms": round(frame_g, 4), "raster_ms": round(raster_g, 4),
@@ -406,6 +426,7 @@ def run_ours(args):
         "paper_policy": {"frame_ms": round(mean(ms_p), 4), "raster_ms": round(mean(st_p["raster"]), 4),
                          "max_abs_err_vs_exact": err_paper},
         "frame_ms_min": round(min(ms_b), 4), "frame_ms_median": round(statistics.median(ms_b), 4),
+        "frame_ms_without_graph": {"binned": round(mean(ms_b_ng), 4), "global_sort": round(mean(ms_g_ng), 4)},
         "wall_s_timed": round(wall_b, 3),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(launches),
@@ -413,8 +434,27 @@ def run_ours(args):
     print(json.dumps(res), flush=True)
 
 
+def run_profile_frame(args):
+    """Minimal frame sequence for Nsight Compute captures."""
+    import torch
+
+    from paper_2609_03613_gb300 import scenes, tilegs as G
+    scene, cam = scenes.workload(WORKLOAD)
+    ds = G.DeviceScene.from_numpy(scene, "cuda")
+    for mode in args.modes.split(","):
+        ctx = G.Context(mode)
+        for _ in range(3):
+            ctx.render(ds, cam)
+        torch.cuda.synchronize()
+        assert ctx.error() == 0
+        print(mode, "entries", ctx.last_entry_count(), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.profile_frame:
+        run_profile_frame(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -96,6 +96,13 @@ typedef struct gs_config {
     int32_t tile_cull;     /* 1: conservative tile-level alpha cull in the binned raster */
     int32_t persistent;    /* 1: binned raster runs persistent CTAs over tiles in
                               descending span order */
+    int32_t repair_in_raster; /* EXACT only, 1 (default): gs_sort_or_bin sorts only
+                              segments longer than 2048 entries and gs_rasterize_fwd
+                              sorts each segment it reaches in shared memory just
+                              before compositing it, so segments past every
+                              pixel's termination are never sorted.  The image is
+                              identical either way; with 0 the stream is fully
+                              sorted by gs_sort_or_bin. */
 } gs_config;
 
 /* Fill *cfg with the paper's defaults (supplement, default No-GW configuration
@@ -255,9 +262,9 @@ int gs_depth_range_noalloc(const gs_config* cfg, const void* projected, const fl
  * stop before applying when T (1 - alpha) < 1e-4, C += c alpha T, T *= 1 - alpha.
  *   n: the Gaussian count the projected buffer was laid out for.
  *   offsets_stride: 1 for a GLOBAL stream, cfg.K for a binned one.
- *   bg: HOST float[3].  rgb [H,W,3], alpha [H,W] (= 1 - T), last [H,W] (stream
- *   index of the last applied entry, -1 if none); ntests [H,W] optional:
- *   entries each pixel visited, the stopping one included.
+ *   bg: HOST float[3].  rgb [H,W,3], alpha [H,W] (= 1 - T), last [H,W] (id of
+ *   the last applied Gaussian, -1 if none); ntests [H,W] optional: entries
+ *   each pixel visited, the stopping one included.
  * The GLOBAL kernel is the plain baseline (gsplat-style batch staging); the
  * binned kernel adds the conservative tile-alpha cull and colour staging of
  * the paper's default configuration.  Both give identical images.
@@ -281,7 +288,14 @@ typedef struct gs_scene {
 enum {
     GS_RENDER_HOST_INPUTS = 1,  /* scene arrays are HOST memory (pinned for async copies) */
     GS_RENDER_HOST_OUTPUTS = 2, /* rgb/alpha/last are HOST memory */
-    GS_RENDER_NO_SYNC = 4       /* do not read M back: use reserved capacity only */
+    GS_RENDER_NO_SYNC = 4,      /* do not read M back: use reserved capacity only */
+    GS_RENDER_GRAPH = 8         /* device buffers only: capture the frame's launches
+                                   into a CUDA graph on the first call and replay it
+                                   on later calls with identical arguments (pointers,
+                                   sizes, camera, background, config); implies
+                                   NO_SYNC, so capacity must be reserved first
+                                   (gs_reserve or one plain gs_render), and
+                                   needs a non-default stream */
 };
 
 /*

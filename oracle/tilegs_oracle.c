@@ -356,7 +356,7 @@ void orc_sort_tiles(int64_t m, const uint32_t* tile, const uint32_t* zbits, cons
  *   q = fmaf(dx, fmaf(a/2, dx, b*dy), ((c/2)*dy)*dy)      (= 1/2 d^T conic d)
  *   skip unless q >= 0;  alpha = min(0.99, o * exp(-q));  skip if alpha < 1/255;
  *   Tn = T (1 - alpha); stop (without applying) if Tn < 1e-4;
- *   C = fmaf(col, alpha*T, C); T = Tn; last = stream index.
+ *   C = fmaf(col, alpha*T, C); T = Tn; last = gid of the applied entry.
  * out_rgb = fmaf(T, bg, C), out_alpha = 1 - T.  out_ntests (nullable) counts
  * the entries a pixel visits, the stopping one included.
  */
@@ -398,7 +398,7 @@ void orc_composite(const float* mean2d, const float* conic, const float* opac, c
                     C1 = fmaf(rgb[3 * g + 1], wgt, C1);
                     C2 = fmaf(rgb[3 * g + 2], wgt, C2);
                     T = Tn;
-                    last = s;
+                    last = (int32_t)g;
                 }
                 const int64_t p = (int64_t)j * width + i;
                 out_rgb[3 * p] = fmaf(T, bg[0], C0);

@@ -7,7 +7,7 @@
 //   K13 repair selection        (Sec. 3.5 rule table; supplement "Selective
 //                                repair selection and local exact sorting")
 //   K14 segment sorts by the baseline key (depth bits, gid)
-#include "internal.cuh"
+#include "device.cuh"
 
 namespace gs {
 
@@ -73,8 +73,41 @@ __device__ void write_bin_params(BinParams* bp, float zmin, float zmax, int K, f
     for (int k = threadIdx.x; k < K - 1; k += blockDim.x) bp->splits[k] = s_split[k];
 }
 
+// Sample j of the emission order -> gid, from the materialised entries ...
+struct GidFromIsect {
+    const uint32_t* gid;
+    __device__ uint32_t operator()(int64_t, int64_t j) const { return gid[j]; }
+};
+// ... or from a per-sample gid array filled by k_sample_gids.
+struct GidFromSamples {
+    const uint32_t* gid;  // indexed by sample number
+    __device__ uint32_t operator()(int64_t i, int64_t) const { return gid[i]; }
+};
+
+// Sample i of S' = min(S, M): entry j = floor(i M / S') of the emission order;
+// its Gaussian is the last one whose first entry is <= j (empty Gaussians
+// share their successor's offset and are skipped).  One thread per sample.
+__global__ void __launch_bounds__(256)
+k_sample_gids(const int32_t* __restrict__ goff, int64_t n, const int64_t* __restrict__ m_dev, int64_t m_cap, int S,
+              uint32_t* __restrict__ out)
+{
+    const int64_t M = live_count(m_dev, m_cap);
+    const int64_t ns = M < (int64_t)S ? M : (int64_t)S;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    const int64_t j = (i * M) / ns;
+    int64_t lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)goff[mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    out[i] = (uint32_t)lo;
+}
+
+template <class GidOf>
 __global__ void __launch_bounds__(kDrThreads)
-k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales, IsectView is,
+k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales, GidOf gid_of,
               const int64_t* __restrict__ m_dev, int64_t m_cap, DrArgs a, BinParams* bp)
 {
     __shared__ uint32_t s_v[kDrMaxS];
@@ -89,7 +122,7 @@ k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales
     const float lo_clamp = fmaxf(a.near_plane, a.eps);
     for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
         const int64_t j = (i * M) / ns;
-        const uint32_t g = is.gid[j];
+        const uint32_t g = gid_of(i, j);
         float z = c_o_z[g].z;
         if (a.near_shift) z = zkey_of(z, scales, g, a.near_alpha, a.near_gamma);
         if (!(z > 0.0f)) continue;
@@ -167,7 +200,7 @@ int depth_range(gs_ctx* ctx, const ProjView& pv, const float* scales, const Isec
     a.pad = c.pad;
     a.eps = c.eps;
     a.K = c.K;
-    k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, is, m_dev, m_cap, a, ctx->d_bp);
+    k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, GidFromIsect{is.gid}, m_dev, m_cap, a, ctx->d_bp);
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -191,7 +224,41 @@ int launch_depth_range_into(const gs_config& c, const ProjView& pv, const float*
     a.pad = c.pad;
     a.eps = c.eps;
     a.K = c.K;
-    k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, is, m_dev, m_cap, a, bp);
+    k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, GidFromIsect{is.gid}, m_dev, m_cap, a, bp);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int samples_reserve(gs_ctx* ctx)
+{
+    void* p = ctx->d_samples;
+    int r = ensure(&p, &ctx->samples_cap, (size_t)kDrMaxS * 4);
+    ctx->d_samples = (uint32_t*)p;
+    return r;
+}
+
+int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64_t n, int64_t m_cap,
+                     const int64_t* m_dev, const gs_camera* cam, cudaStream_t st)
+{
+    const gs_config& c = ctx->cfg;
+    DrArgs a;
+    a.near_plane = cam->near_plane;
+    a.far_plane = cam->far_plane;
+    a.S = c.sample_count;
+    a.near_shift = c.near_shift;
+    a.near_alpha = c.near_alpha;
+    a.near_gamma = c.near_gamma;
+    a.p_lo = c.p_lo;
+    a.p_hi = c.p_hi;
+    a.pad = c.pad;
+    a.eps = c.eps;
+    a.K = c.K;
+    int r = samples_reserve(ctx);
+    if (r != GS_OK) return r;
+    k_sample_gids<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(ctx->d_goff, n, m_dev, m_cap, a.S, ctx->d_samples);
+    k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, GidFromSamples{ctx->d_samples}, m_dev, m_cap, a,
+                                             ctx->d_bp);
+    ctx->launches += 2;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
@@ -202,20 +269,6 @@ int set_zrange(gs_ctx* ctx, const float* zrange, cudaStream_t st)
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
-}
-
-// ------------------------------------------------------------------ bin maps
-// Monotone map: the number of split depths <= z (binary search over the
-// non-decreasing split list).
-__device__ __forceinline__ int bin_split(float z, const float* s_split, int K)
-{
-    int lo = 0, hi = K - 1;  // answer in [0, K-1]
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (s_split[mid] <= z) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
 }
 
 // The paper's clamped log map.
@@ -440,72 +493,6 @@ k_select_greedy(const int32_t* __restrict__ klen, const int32_t* __restrict__ pr
     }
 }
 
-// ------------------------------------------------------------------ segment sorts
-// All sorts order the 64-bit words (depth bits << 32 | gid) ascending.
-// Bitonic networks in the form where every compare-exchange puts the minimum
-// at the lower index (a mirrored compare at the first step of each merge), so
-// positions past the segment end behave as +infinity and can be skipped.
-
-__device__ __forceinline__ void cex(uint64_t* a, int i, int l)
-{
-    const uint64_t x = a[i], y = a[l];
-    if (y < x) {
-        a[i] = y;
-        a[l] = x;
-    }
-}
-
-struct SyncWarp {
-    __device__ void operator()() const { __syncwarp(); }
-};
-struct SyncBlock {
-    __device__ void operator()() const { __syncthreads(); }
-};
-
-// Sort a[0..n) held in (shared or global) memory by `nthreads` cooperating
-// threads with index `tid`; `sync` is called between steps.
-template <class Sync>
-__device__ void bitonic_mem(uint64_t* a, int n, int tid, int nthreads, Sync sync)
-{
-    int P = 1;
-    while (P < n) P <<= 1;
-    for (int k = 2; k <= P; k <<= 1) {
-        const int h = k >> 1;
-        for (int t = tid; t < P / 2; t += nthreads) {
-            const int blk = t / h, r = t - blk * h;
-            const int i = blk * k + r, l = blk * k + (k - 1 - r);
-            if (l < n) cex(a, i, l);
-        }
-        sync();
-        for (int j = k >> 2; j > 0; j >>= 1) {
-            for (int t = tid; t < P / 2; t += nthreads) {
-                const int i = 2 * j * (t / j) + (t % j), l = i + j;
-                if (l < n) cex(a, i, l);
-            }
-            sync();
-        }
-    }
-}
-
-// 32 words, one per lane, sorted ascending across the warp.
-__device__ __forceinline__ uint64_t warp_bitonic32(uint64_t v)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const uint64_t o = __shfl_xor_sync(0xffffffffu, v, j);
-            const bool up = ((lane & k) == 0);
-            const bool lower = ((lane & j) == 0);
-            // lower lane of an ascending pair keeps the min, etc.
-            const bool take_min = (lower == up);
-            v = take_min ? (o < v ? o : v) : (o > v ? o : v);
-        }
-    }
-    return v;
-}
-
 constexpr int kRpThreads = 256;
 constexpr int kRpWarps = kRpThreads / 32;
 constexpr int kRpWarpCap = 512;                     // per-warp shared sort
@@ -515,7 +502,7 @@ constexpr int kRpCtaCap = kRpWarps * kRpWarpCap;    // whole-CTA shared sort (40
 // every segment with length >= 2).  Longer than kRpCtaCap: queued as a tail.
 __global__ void __launch_bounds__(kRpThreads)
 k_repair_tiles(const int32_t* __restrict__ off, int K, const uint8_t* __restrict__ sel, uint64_t* __restrict__ words,
-               int32_t* __restrict__ tail, int32_t tail_cap, int* err)
+               int32_t* __restrict__ tail, int32_t tail_cap, int* err, int min_len)
 {
     __shared__ uint64_t s_buf[kRpCtaCap];
     __shared__ int32_t s_off[GS_MAX_K + 1];
@@ -526,11 +513,11 @@ k_repair_tiles(const int32_t* __restrict__ off, int K, const uint8_t* __restrict
     for (int b = threadIdx.x; b <= K; b += blockDim.x) s_off[b] = off[t * K + b];
     if (threadIdx.x == 0) s_nbig = 0;
     __syncthreads();
-    if (s_off[K] - s_off[0] < 2) return;
+    if (s_off[K] - s_off[0] < min_len) return;
     uint64_t* wbuf = s_buf + warp * kRpWarpCap;
     for (int b = warp; b < K; b += kRpWarps) {
         const int l = s_off[b + 1] - s_off[b];
-        if (l < 2) continue;
+        if (l < 2 || l < min_len) continue;
         if (sel && !sel[t * K + b]) continue;
         uint64_t* seg = words + s_off[b];
         if (l <= 32) {
@@ -582,13 +569,13 @@ k_repair_tail(const int32_t* __restrict__ off, const int32_t* __restrict__ tail,
 }
 
 __global__ void k_fill_selected(const int32_t* __restrict__ off, int64_t nseg, const uint8_t* __restrict__ sel,
-                                int mode, uint8_t* __restrict__ out)
+                                int mode, int min_len, uint8_t* __restrict__ out)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseg; q += stride) {
         const int l = off[q + 1] - off[q];
         uint8_t v = 0;
-        if (mode == GS_MODE_BINNED_EXACT) v = l >= 2;
+        if (mode == GS_MODE_BINNED_EXACT) v = l >= min_len;
         else if (mode == GS_MODE_BINNED_PAPER) v = sel[q] && l >= 2;
         out[q] = v;
     }
@@ -596,6 +583,12 @@ __global__ void k_fill_selected(const int32_t* __restrict__ off, int64_t nseg, c
 
 int repair(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* words, const int32_t* offsets,
            uint8_t* selected_out, cudaStream_t st)
+{
+    return repair_min(ctx, n_tiles, m_dev, words, offsets, selected_out, 2, st);
+}
+
+int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* words, const int32_t* offsets,
+               uint8_t* selected_out, int32_t min_len, cudaStream_t st)
 {
     const gs_config& c = ctx->cfg;
     const int64_t nseg = (int64_t)n_tiles * c.K;
@@ -625,12 +618,12 @@ int repair(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* words, 
     GS_CUDA_TRY(cudaMemsetAsync(ctx->d_tail, 0, 4, st));
     if (n_tiles > 0)
         k_repair_tiles<<<(unsigned)n_tiles, kRpThreads, 0, st>>>(offsets, c.K, sel, words, ctx->d_tail, tail_cap,
-                                                                 ctx->d_err);
+                                                                 ctx->d_err, min_len);
     k_repair_tail<<<(unsigned)ctx->num_sms, 1024, 0, st>>>(offsets, ctx->d_tail, tail_cap, words);
     ctx->launches += (n_tiles > 0 ? 2 : 1);
     GS_CUDA_TRY(cudaGetLastError());
     if (selected_out) {
-        k_fill_selected<<<grid, 256, 0, st>>>(offsets, nseg, sel, c.mode, selected_out);
+        k_fill_selected<<<grid, 256, 0, st>>>(offsets, nseg, sel, c.mode, min_len < 2 ? 2 : min_len, selected_out);
         ctx->launches += 1;
         GS_CUDA_TRY(cudaGetLastError());
     }

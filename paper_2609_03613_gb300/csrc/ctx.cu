@@ -45,6 +45,7 @@ extern "C" void gs_config_default(gs_config* cfg, int32_t mode)
     cfg->near_shift = (mode == GS_MODE_BINNED_PAPER || mode == GS_MODE_BINNED_NOREPAIR) ? 1 : 0;
     cfg->tile_cull = 1;
     cfg->persistent = 1;
+    cfg->repair_in_raster = (mode == GS_MODE_BINNED_EXACT) ? 1 : 0;
 }
 
 namespace gs {
@@ -82,17 +83,25 @@ int ensure(void** p, size_t* cap, size_t bytes)
     return GS_OK;
 }
 
+// Inside a stream capture the records become external event-record nodes,
+// so the graph's replays still time every stage.
+static void record(gs_ctx* ctx, cudaEvent_t ev, cudaStream_t st)
+{
+    if (ctx->capturing) cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+    else cudaEventRecord(ev, st);
+}
+
 void stage_begin(gs_ctx* ctx, int stage, cudaStream_t st)
 {
     if (ctx->timing && ctx->ev_ok) {
-        cudaEventRecord(ctx->ev_b[stage], st);
+        record(ctx, ctx->ev_b[stage], st);
         ctx->stage_used[stage] = 1;
     }
 }
 
 void stage_end(gs_ctx* ctx, int stage, cudaStream_t st)
 {
-    if (ctx->timing && ctx->ev_ok) cudaEventRecord(ctx->ev_e[stage], st);
+    if (ctx->timing && ctx->ev_ok) record(ctx, ctx->ev_e[stage], st);
 }
 
 }  // namespace gs
@@ -130,10 +139,11 @@ extern "C" int gs_destroy(gs_ctx* c)
     void* ptrs[] = {c->d_err, c->d_scan, c->d_goff, c->d_keys[0], c->d_keys[1], c->d_vals[0],
                     c->d_vals[1], c->d_hist, c->d_count, c->d_bin, c->d_bp, c->d_sel, c->d_tail,
                     c->d_tiles_order, c->d_tile_counter, c->r_proj, c->r_isect, c->r_stream,
-                    c->r_off, c->r_m, c->r_scene, c->r_out, c->d_ops};
+                    c->r_off, c->r_m, c->r_scene, c->r_out, c->d_ops, c->d_tiles, c->d_samples};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_m) cudaFreeHost(c->h_m);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
     if (c->ev_ok)
         for (int s = 0; s < GS_STAGE_COUNT; ++s) {
             cudaEventDestroy(c->ev_b[s]);
@@ -349,6 +359,17 @@ extern "C" int gs_sort_or_bin(gs_ctx* ctx, const void* projected, const float* s
     if (r != GS_OK) return r;
     if (zrange_out)
         GS_CUDA_TRY(cudaMemcpyAsync(zrange_out, ctx->d_bp, 2 * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (ctx->cfg.mode == GS_MODE_BINNED_EXACT) {
+        stage_begin(ctx, GS_STAGE_BIN, st);
+        r = exact_bins(ctx, pv, n, cam, false, m_cap, m_dev, stream_words, offsets, st);
+        stage_end(ctx, GS_STAGE_BIN, st);
+        if (r != GS_OK) return r;
+        stage_begin(ctx, GS_STAGE_REPAIR, st);
+        r = repair_min(ctx, T, m_dev, stream_words, offsets, nullptr,
+                       ctx->cfg.repair_in_raster ? kRasterSortCap + 1 : 2, st);
+        stage_end(ctx, GS_STAGE_REPAIR, st);
+        return r;
+    }
     stage_begin(ctx, GS_STAGE_BIN, st);
     r = bin_build(ctx, pv, scales, is, m_cap, m_dev, T, stream_words, offsets, st);
     stage_end(ctx, GS_STAGE_BIN, st);
@@ -411,7 +432,7 @@ extern "C" int gs_reserve(gs_ctx* c, int64_t n, int64_t m_cap, int32_t width, in
     int r = render_buffers(c, n, m_cap, T);
     if (r != GS_OK) return r;
     // grow the internal scratch of every stage once, outside any capture
-    return gs::reserve_internal(c, n, m_cap, T);
+    return gs::reserve_internal(c, n, m_cap, width, height);
 }
 
 extern "C" int64_t gs_last_entry_count(gs_ctx* c) { return c ? c->last_m : -1; }
@@ -428,8 +449,8 @@ extern "C" int64_t gs_last_raster_ops(gs_ctx* c, void* stream)
     return h;
 }
 
-extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, const float* bg,
-                         float* rgb, float* alpha, int32_t* last, int32_t flags, void* stream)
+static int render_impl(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, const float* bg, float* rgb,
+                       float* alpha, int32_t* last, int32_t flags, void* stream)
 {
     if (!c || !sc || !cam_ok(cam) || !bg || !rgb || !alpha) return GS_ERR_INVALID_ARG;
     if (sc->n < 0 || sc->n > INT32_MAX - 1 || sc->sh_degree < 0 || sc->sh_degree > 3) return GS_ERR_INVALID_ARG;
@@ -491,12 +512,30 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
             if ((r = render_buffers(c, n, c->h_m[0], T)) != GS_OK) return r;
         }
     }
-    r = emit_only(c, pv, n, cam, isect_view(c->r_isect, c->r_m_cap), c->r_m_cap, c->r_m, st);
-    stage_end(c, GS_STAGE_INTERSECT, st);
-    if (r != GS_OK) return r;
     const int32_t stride = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : c->cfg.K;
-    r = gs_sort_or_bin(c, c->r_proj, scales, n, cam, c->r_isect, c->r_m_cap, c->r_m, c->r_stream,
-                       c->r_off, nullptr, st);
+    if (c->cfg.mode == GS_MODE_BINNED_EXACT) {
+        // the emission is fused with the bucketing by tile: no emission-order
+        // entries are written; depth samples map to gids through the offsets
+        stage_end(c, GS_STAGE_INTERSECT, st);
+        stage_begin(c, GS_STAGE_DEPTH_RANGE, st);
+        r = depth_range_goff(c, pv, scales, n, c->r_m_cap, c->r_m, cam, st);
+        stage_end(c, GS_STAGE_DEPTH_RANGE, st);
+        if (r != GS_OK) return r;
+        stage_begin(c, GS_STAGE_BIN, st);
+        r = exact_bins(c, pv, n, cam, true, c->r_m_cap, c->r_m, c->r_stream, c->r_off, st);
+        stage_end(c, GS_STAGE_BIN, st);
+        if (r != GS_OK) return r;
+        stage_begin(c, GS_STAGE_REPAIR, st);
+        r = repair_min(c, T, c->r_m, c->r_stream, c->r_off, nullptr,
+                       c->cfg.repair_in_raster ? kRasterSortCap + 1 : 2, st);
+        stage_end(c, GS_STAGE_REPAIR, st);
+    } else {
+        r = emit_only(c, pv, n, cam, isect_view(c->r_isect, c->r_m_cap), c->r_m_cap, c->r_m, st);
+        stage_end(c, GS_STAGE_INTERSECT, st);
+        if (r != GS_OK) return r;
+        r = gs_sort_or_bin(c, c->r_proj, scales, n, cam, c->r_isect, c->r_m_cap, c->r_m, c->r_stream,
+                           c->r_off, nullptr, st);
+    }
     if (r != GS_OK) return r;
     stage_begin(c, GS_STAGE_RASTER, st);
     r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,
@@ -517,5 +556,76 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
     } else {
         c->last_m = c->h_m[0];
     }
+    return GS_OK;
+}
+
+// The frame as a CUDA graph: captured on first use (and whenever any pointer,
+// size, camera, background or configuration value changes), replayed after.
+extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, const float* bg, float* rgb,
+                         float* alpha, int32_t* last, int32_t flags, void* stream)
+{
+    if (!(flags & GS_RENDER_GRAPH)) return render_impl(c, sc, cam, bg, rgb, alpha, last, flags, stream);
+    if (!c || !sc || !cam || !bg || !rgb || !alpha) return GS_ERR_INVALID_ARG;
+    if (flags & (GS_RENDER_HOST_INPUTS | GS_RENDER_HOST_OUTPUTS)) return GS_ERR_INVALID_ARG;
+    if (c->r_m_cap <= 1) return GS_ERR_INVALID_ARG;  // capacity must be reserved first
+    if (!stream) return GS_ERR_INVALID_ARG;          // the legacy stream cannot be captured
+    cudaStream_t st = (cudaStream_t)stream;
+    struct Key {
+        gs_scene sc;
+        gs_camera cam;
+        float bg[3];
+        void *rgb, *alpha, *last, *proj, *isect, *stream, *off, *scene_copy, *out;
+        int64_t m_cap;
+        gs_config cfg;
+        int timing, device;
+    } key;
+    memset(&key, 0, sizeof(key));
+    key.sc = *sc;
+    key.cam = *cam;
+    for (int k = 0; k < 3; ++k) key.bg[k] = bg[k];
+    key.rgb = rgb;
+    key.alpha = alpha;
+    key.last = last;
+    key.proj = c->r_proj;
+    key.isect = c->r_isect;
+    key.stream = c->r_stream;
+    key.off = c->r_off;
+    key.scene_copy = c->r_scene;
+    key.out = c->r_out;
+    key.m_cap = c->r_m_cap;
+    key.cfg = c->cfg;
+    key.timing = c->timing;
+    key.device = c->device;
+    static_assert(sizeof(Key) <= sizeof(c->gkey), "graph key");
+    if (!(c->gexec && c->gkey_len == sizeof(Key) && memcmp(c->gkey, &key, sizeof(Key)) == 0)) {
+        if (c->gexec) {
+            cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+        }
+        const int64_t l0 = c->launches;
+        cudaGraph_t graph = nullptr;
+        GS_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        c->capturing = 1;
+        int r = render_impl(c, sc, cam, bg, rgb, alpha, last, flags | GS_RENDER_NO_SYNC, stream);
+        c->capturing = 0;
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (r != GS_OK || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return r != GS_OK ? r : gs_cuda_fail(e, "cudaStreamEndCapture");
+        }
+        e = cudaGraphInstantiate(&c->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->gexec = nullptr;
+            return gs_cuda_fail(e, "cudaGraphInstantiate");
+        }
+        c->glaunches = c->launches - l0;
+        c->launches = l0;
+        memcpy(c->gkey, &key, sizeof(Key));
+        c->gkey_len = sizeof(Key);
+    }
+    GS_CUDA_TRY(cudaGraphLaunch(c->gexec, st));
+    c->launches += c->glaunches;
     return GS_OK;
 }

@@ -183,6 +183,10 @@ struct gs_ctx {
     size_t sel_cap = 0;
     int32_t* d_tail = nullptr;   // segments too long for a shared-memory sort
     size_t tail_cap = 0;
+    int32_t* d_tiles = nullptr;   // tile-count difference grid, tile offsets, cursors
+    size_t tiles_cap = 0;
+    uint32_t* d_samples = nullptr; // depth-range sample gids
+    size_t samples_cap = 0;
     int32_t* d_tiles_order = nullptr;  // persistent raster tile order
     int32_t* d_tile_counter = nullptr;
     size_t order_cap = 0;
@@ -198,6 +202,12 @@ struct gs_ctx {
     int64_t last_m = 0;
     int64_t launches = 0;  // kernels this context has launched
     int64_t* d_ops = nullptr;  // compositing ops counted by the instrumented raster
+    // whole-frame CUDA graph (GS_RENDER_GRAPH)
+    cudaGraphExec_t gexec = nullptr;
+    unsigned char gkey[512];
+    size_t gkey_len = 0;
+    int64_t glaunches = 0;
+    int capturing = 0;
     // timing
     int timing = 0;
     cudaEvent_t ev_b[GS_STAGE_COUNT];
@@ -244,13 +254,30 @@ int launch_depth_range_into(const gs_config& c, const ProjView& pv, const float*
                             int64_t m_cap, const int64_t* m_dev, const gs_camera* cam, BinParams* bp,
                             cudaStream_t st);
 
+// tiles.cu: EXACT-mode bin construction straight from the projected rects
+// (with the tile cull: per-row culled spans; without: layered difference
+// counts and the expansion, which needs ctx->d_goff -- computed here unless
+// goff_ready).  Segments are left unsorted.
+int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, bool goff_ready, int64_t m_cap,
+               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st);
+// bins.cu: sort segments of length >= min_len (EXACT) or the rule/budget
+// selection (PAPER)
+int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* stream_words, const int32_t* offsets,
+               uint8_t* selected_out, int32_t min_len, cudaStream_t st);
+// segments longer than this are sorted before the raster when the raster
+// sorts the segments it reaches
+constexpr int kRasterSortCap = 2048;
+// depth range with samples mapped to gids through the per-Gaussian offsets
+int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64_t n, int64_t m_cap,
+                     const int64_t* m_dev, const gs_camera* cam, cudaStream_t st);
+
 // raster.cu
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* stream_words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st);
 
 // grow every stage's internal scratch for (n, m_cap, T) (synchronous)
-int reserve_internal(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t n_tiles);
+int reserve_internal(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t width, int32_t height);
 
 // timing helpers
 void stage_begin(gs_ctx* ctx, int stage, cudaStream_t st);

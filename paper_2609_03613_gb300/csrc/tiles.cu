@@ -1,0 +1,470 @@
+// tiles.cu -- bin construction for EXACT mode (Sec. 3.3; supplement Alg. 3),
+// arranged for GB300.  With the monotone split map every entry of a Gaussian
+// falls in the same bin b(z_g), so:
+//
+//   1. count[t, b]: each Gaussian adds its tile rect to layer b of a stack of
+//      K 2D difference arrays over the tile grid (four atomics per Gaussian
+//      instead of one per entry); per-layer 2D prefix sums give the counts;
+//   2. exclusive scan of count in tile-major, bin-minor order -> bin offsets
+//      (the same array Alg. 3's global count/scan produces);
+//   3. scatter: each entry takes a slot in its (t, b) segment from an atomic
+//      cursor -- straight from the Gaussians' rects (warp-cooperative
+//      expansion, the emission-order entries are never written) or from
+//      materialised entries.
+//
+// The order inside a segment is left to the repair (Alg. 4): an eager sort of
+// every segment, or the raster's in-shared-memory sort of each segment it
+// reaches (segments too long for its buffer are sorted here, eagerly).
+#include "device.cuh"
+#include "scan.cuh"
+
+namespace gs {
+
+constexpr int kTbThreads = 512;
+constexpr int kTbWarps = kTbThreads / 32;
+constexpr int kTbCap = 12288;          // entries of a tile sorted in shared memory (96 KB)
+constexpr int kTbWarpSortMax = 512;    // longer bins are sorted by the whole CTA
+
+// ------------------------------------------------------------------ counts
+// Per visible Gaussian: its bin (kept in gbin) and its rect added to layer b.
+__global__ void __launch_bounds__(256)
+k_bin_diff(const uint2* __restrict__ rect, const float4* __restrict__ c_o_z, int64_t n, int tiles_x, int tiles_y,
+           const BinParams* __restrict__ bp, int K, int32_t* __restrict__ D, uint8_t* __restrict__ gbin)
+{
+    __shared__ float s_split[GS_MAX_K];
+    for (int k = threadIdx.x; k < K - 1; k += blockDim.x) s_split[k] = bp->splits[k];
+    __syncthreads();
+    const int W1 = tiles_x + 1;
+    const int64_t layer = (int64_t)(tiles_y + 1) * W1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += stride) {
+        const uint2 r = rect[g];
+        const int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff, ty1 = r.y >> 16;
+        if (tx0 >= tx1 || ty0 >= ty1) continue;
+        const int b = bin_split(c_o_z[g].z, s_split, K);
+        gbin[g] = (uint8_t)b;
+        int32_t* L = D + b * layer;
+        atomicAdd(&L[ty0 * W1 + tx0], 1);
+        atomicAdd(&L[ty0 * W1 + tx1], -1);
+        atomicAdd(&L[ty1 * W1 + tx0], -1);
+        atomicAdd(&L[ty1 * W1 + tx1], 1);
+    }
+}
+
+// One block per layer: 2D inclusive prefix (columns, then rows) in place.
+__global__ void __launch_bounds__(1024)
+k_layer_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y)
+{
+    const int W1 = tiles_x + 1;
+    int32_t* L = D + (int64_t)blockIdx.x * (tiles_y + 1) * W1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int x = threadIdx.x; x < tiles_x; x += blockDim.x) {
+        int32_t run = 0;
+        for (int y = 0; y < tiles_y; ++y) {
+            run += L[y * W1 + x];
+            L[y * W1 + x] = run;
+        }
+    }
+    __syncthreads();
+    for (int y = warp; y < tiles_y; y += blockDim.x / 32) {
+        int32_t carry = 0;
+        for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+            const int x = x0 + lane;
+            int32_t v = x < tiles_x ? L[y * W1 + x] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t u = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d) v += u;
+            }
+            if (x < tiles_x) L[y * W1 + x] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ row spans (tile cull)
+struct CullArgs {
+    const float4* xy_ab;
+    const float4* c_o_z;
+    const float4* rgb;
+    int tile;
+};
+
+// Tiles [*a, *b) of row ty (inside [tx0, tx1)) whose pixel-centre boxes can
+// hold a pixel with alpha >= 1/255.  A contributing pixel p has
+// Q(m - p) <= tau / margin (the tile cull's bound), so it lies in that
+// ellipse; the ellipse meets the row's band of pixel centres in a convex set
+// whose x-projection is one interval, found from the band ends and the
+// ellipse's leftmost/rightmost points.  Every box is widened (5e-3 relative +
+// 0.05 px) to cover float32 rounding; margin 0 (ill-conditioned conic) keeps
+// the whole row.
+__device__ __forceinline__ void row_span(float mx, float my, float ha, float hb, float hc, float tau, float margin,
+                                         int ty, int tile, int tx0, int tx1, int* a, int* b)
+{
+    *a = tx0;
+    *b = tx1;
+    if (!(margin > 0.0f)) return;
+    const float tp = tau / margin;
+    const float D = 4.0f * ha * hc - hb * hb;
+    if (!(D > 0.0f) || !(tp > 0.0f)) return;
+    const float y0 = (float)(ty * tile);
+    float yl = my - (y0 + (float)tile - 0.5f), yh = my - (y0 + 0.5f);
+    yl = yl - (0.05f + 5e-3f * fabsf(yl));
+    yh = yh + (0.05f + 5e-3f * fabsf(yh));
+    const float dymax = sqrtf(4.0f * ha * tp / D) * (1.0f + 5e-3f) + 0.05f;
+    const float ya = fmaxf(yl, -dymax), yb = fminf(yh, dymax);
+    if (ya > yb) {
+        *b = *a;  // the band misses the ellipse
+        return;
+    }
+    const float ext = sqrtf(4.0f * hc * tp / D);
+    const float dy_left = hb * ext / (2.0f * hc);  // dy of the leftmost point (dx = -ext)
+    const float s_a = sqrtf(fmaxf(0.0f, 4.0f * ha * tp - D * ya * ya));
+    const float s_b = sqrtf(fmaxf(0.0f, 4.0f * ha * tp - D * yb * yb));
+    const float La = (-hb * ya - s_a) / (2.0f * ha), Lb = (-hb * yb - s_b) / (2.0f * ha);
+    const float Ra = (-hb * ya + s_a) / (2.0f * ha), Rb = (-hb * yb + s_b) / (2.0f * ha);
+    float dxmin = (dy_left >= ya && dy_left <= yb) ? -ext : fminf(La, Lb);
+    float dxmax = (-dy_left >= ya && -dy_left <= yb) ? ext : fmaxf(Ra, Rb);
+    dxmin = dxmin - (0.05f + 5e-3f * fabsf(dxmin));
+    dxmax = dxmax + (0.05f + 5e-3f * fabsf(dxmax));
+    const float ft = (float)tile;
+    float fa = ceilf((mx - dxmax - (ft - 0.5f)) / ft), fb = floorf((mx - dxmin - 0.5f) / ft) + 1.0f;
+    fa = fminf(fmaxf(fa, (float)tx0), (float)tx1);
+    fb = fminf(fmaxf(fb, (float)tx0), (float)tx1);
+    *a = (int)fa;
+    *b = fb > fa ? (int)fb : (int)fa;
+}
+
+struct LoadRectRows {
+    const uint2* rect;
+    __device__ int64_t operator()(int64_t i) const
+    {
+        const uint2 r = rect[i];
+        const int64_t w = (int64_t)(r.y & 0xffffu) - (int64_t)(r.x & 0xffffu);
+        const int64_t h = (int64_t)(r.y >> 16) - (int64_t)(r.x >> 16);
+        return (w > 0 && h > 0) ? h : 0;
+    }
+};
+
+// Warp-cooperative over (Gaussian, row) pairs: a warp owns 32 consecutive
+// Gaussians, whose rows are consecutive records [roff[g0], roff[g0 + 32)).
+// Each lane holds its Gaussian (record, bin); every row record is computed by
+// one lane from the owner's values (shuffled): the row's culled span, the
+// record (gid, row | start, width), and +1 / -1 at the span ends of layer b's
+// row (a per-row difference array).
+__global__ void __launch_bounds__(256)
+k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict__ roff, CullArgs ca, int tiles_x,
+            const BinParams* __restrict__ bp, int K, const int64_t* __restrict__ m_dev, int64_t m_cap,
+            int32_t* __restrict__ Drow, int64_t layer, uint8_t* __restrict__ gbin, uint32_t* __restrict__ rs_g,
+            uint32_t* __restrict__ rs_ya, uint32_t* __restrict__ rs_w)
+{
+    __shared__ float s_split[GS_MAX_K];
+    for (int k = threadIdx.x; k < K - 1; k += blockDim.x) s_split[k] = bp->splits[k];
+    __syncthreads();
+    if (*m_dev > m_cap) return;
+    const int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+    if (g0 >= n) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t gl = g0 + lane;
+    const bool ok = gl < n;
+    const int32_t my_off = roff[ok ? gl : n];
+    const int32_t base = __shfl_sync(0xffffffffu, my_off, 0);
+    const int32_t end = roff[(g0 + 32) < n ? (g0 + 32) : n];
+    uint2 r = make_uint2(0u, 0u);
+    float4 p = make_float4(0.f, 0.f, 0.f, 0.f), q = p;
+    float margin = 0.0f;
+    uint32_t bin = 0u;
+    if (ok) {
+        r = rect[gl];
+        if ((r.x & 0xffffu) < (r.y & 0xffffu) && (r.x >> 16) < (r.y >> 16)) {
+            p = __ldg(ca.xy_ab + gl);
+            q = __ldg(ca.c_o_z + gl);
+            margin = __ldg(&ca.rgb[gl].w);
+            bin = (uint32_t)bin_split(q.z, s_split, K);
+            gbin[gl] = (uint8_t)bin;
+        }
+    }
+    const int W1 = tiles_x + 1;
+    for (int32_t e0 = base; e0 < end; e0 += 32) {
+        const int32_t e = e0 + lane;
+        int k = 0;
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            const int32_t v = __shfl_sync(0xffffffffu, my_off, (k + s) & 31);
+            if (k + s < 32 && v <= e) k += s;
+        }
+        const uint32_t ra = __shfl_sync(0xffffffffu, r.x, k), rb = __shfl_sync(0xffffffffu, r.y, k);
+        const float mx = __shfl_sync(0xffffffffu, p.x, k), my = __shfl_sync(0xffffffffu, p.y, k);
+        const float ca_ = __shfl_sync(0xffffffffu, p.z, k), cb = __shfl_sync(0xffffffffu, p.w, k);
+        const float cc = __shfl_sync(0xffffffffu, q.x, k), tau = __shfl_sync(0xffffffffu, q.w, k);
+        const float mg = __shfl_sync(0xffffffffu, margin, k);
+        const uint32_t b = __shfl_sync(0xffffffffu, bin, k);
+        const int32_t o = __shfl_sync(0xffffffffu, my_off, k);
+        if (e < end) {
+            const int tx0 = ra & 0xffff, ty0 = ra >> 16, tx1 = rb & 0xffff;
+            const int ty = ty0 + (e - o);
+            int a, x1;
+            row_span(mx, my, 0.5f * ca_, cb, 0.5f * cc, tau, mg, ty, ca.tile, tx0, tx1, &a, &x1);
+            rs_g[e] = (uint32_t)(g0 + k);
+            rs_ya[e] = (uint32_t)ty | ((uint32_t)a << 16);
+            rs_w[e] = (uint32_t)(x1 - a);
+            if (x1 > a) {
+                int32_t* L = Drow + b * layer;
+                atomicAdd(&L[ty * W1 + a], 1);
+                atomicAdd(&L[ty * W1 + x1], -1);
+            }
+        }
+    }
+}
+
+// One block per layer: inclusive prefix along each row.
+__global__ void __launch_bounds__(1024)
+k_layer_rows_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y, int64_t layer)
+{
+    const int W1 = tiles_x + 1;
+    int32_t* L = D + (int64_t)blockIdx.x * layer;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int y = warp; y < tiles_y; y += blockDim.x / 32) {
+        int32_t carry = 0;
+        for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+            const int x = x0 + lane;
+            int32_t v = x < tiles_x ? L[y * W1 + x] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t u = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d) v += u;
+            }
+            if (x < tiles_x) L[y * W1 + x] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+}
+
+// Warp-cooperative over the entries of 32 consecutive row records: a warp
+// scans the records' widths, then each lane takes every 32nd entry, finds its
+// record by a binary search over the prefix and takes a slot in the entry's
+// (tile, bin) segment; two entries per lane are in flight.
+__global__ void __launch_bounds__(256)
+k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ rs_w,
+                   const int32_t* __restrict__ roff, int64_t n, const float4* __restrict__ c_o_z,
+                   const uint8_t* __restrict__ gbin, int tiles_x, int K, const int64_t* __restrict__ m_dev,
+                   int64_t m_cap, const int32_t* __restrict__ off, int32_t* __restrict__ cur,
+                   uint64_t* __restrict__ words)
+{
+    if (*m_dev > m_cap) return;
+    const int64_t R = roff[n];
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (R + 31) / 32;
+    const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += wstride) {
+        const int64_t k = c * 32 + lane;
+        uint32_t w = 0, g = 0, ya = 0, b = 0, z = 0;
+        if (k < R) {
+            w = rs_w[k];
+            if (w) {
+                g = rs_g[k];
+                ya = rs_ya[k];
+                b = gbin[g];
+                z = __float_as_uint(c_o_z[g].z);
+            }
+        }
+        // inclusive prefix of the widths across the warp
+        uint32_t incl = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += u;
+        }
+        const uint32_t excl = incl - w;
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        for (uint32_t e0 = 0; e0 < total; e0 += 64) {
+            int32_t p[2];
+            uint64_t word[2];
+            bool live[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const uint32_t e = e0 + 32 * u + lane;
+                // owner: the last lane whose exclusive prefix is <= e
+                int o = 0;
+#pragma unroll
+                for (int s = 16; s > 0; s >>= 1) {
+                    const uint32_t v = __shfl_sync(0xffffffffu, excl, (o + s) & 31);
+                    if (o + s < 32 && v <= e) o += s;
+                }
+                const uint32_t oex = __shfl_sync(0xffffffffu, excl, o);
+                const uint32_t og = __shfl_sync(0xffffffffu, g, o), oya = __shfl_sync(0xffffffffu, ya, o);
+                const uint32_t ob = __shfl_sync(0xffffffffu, b, o), oz = __shfl_sync(0xffffffffu, z, o);
+                live[u] = e < total;
+                if (live[u]) {
+                    const int ty = (int)(oya & 0xffffu), tx = (int)(oya >> 16) + (int)(e - oex);
+                    const int64_t qi = ((int64_t)ty * tiles_x + tx) * K + ob;
+                    p[u] = off[qi] + atomicAdd(&cur[qi], 1);
+                    word[u] = ((uint64_t)oz << 32) | og;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+                if (live[u]) words[p[u]] = word[u];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ scatter
+// Without the tile cull: straight from the rects with the warp-cooperative
+// expansion, four entries per lane in flight so the returning atomics overlap.
+__global__ void __launch_bounds__(256)
+k_bin_scatter_rects(const uint2* __restrict__ rect, const float4* __restrict__ c_o_z,
+                    const int32_t* __restrict__ goff, const uint8_t* __restrict__ gbin, int64_t n, int tiles_x,
+                    int K, const int64_t* __restrict__ m_dev, int64_t m_cap, const int32_t* __restrict__ off,
+                    int32_t* __restrict__ cur, uint64_t* __restrict__ words)
+{
+    if (*m_dev > m_cap) return;  // capacity error raised by the caller's check
+    const int64_t g0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+    if (g0 >= n) return;
+    const WarpExpand wx(rect, c_o_z, goff, n, g0);
+    const int lane = threadIdx.x & 31;
+    const int64_t gl = g0 + lane;
+    const uint32_t mybin = (gl < n && ((wx.r1 & 0xffffu) > (wx.r0 & 0xffffu))) ? gbin[gl] : 0u;
+    for (int32_t e0 = wx.base; e0 < wx.end; e0 += 128) {
+        uint32_t g[4], t[4], z[4], b[4];
+        int32_t p[4];
+        bool live[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            wx.entry(e0 + 32 * u + lane, tiles_x, &g[u], &t[u], &z[u]);
+            b[u] = __shfl_sync(0xffffffffu, mybin, (int)(g[u] - (uint32_t)g0) & 31);
+            live[u] = e0 + 32 * u + lane < wx.end;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (live[u]) {
+                const int64_t q = (int64_t)t[u] * K + b[u];
+                p[u] = off[q] + atomicAdd(&cur[q], 1);
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (live[u]) words[p[u]] = ((uint64_t)z[u] << 32) | g[u];
+    }
+}
+
+__global__ void k_capacity_check(const int64_t* __restrict__ m_dev, int64_t m_cap, int* err)
+{
+    if (*m_dev > m_cap) raise_error(err, GS_ERR_CAPACITY);
+}
+
+// Count of segment q = t*K + b from the prefixed layers (tile-major order).
+struct LoadLayerCount {
+    const int32_t* D;
+    int K, tiles_x, W1;
+    int64_t layer;
+    __device__ int64_t operator()(int64_t q) const
+    {
+        const int64_t t = q / K;
+        const int b = (int)(q - t * K);
+        const int y = (int)(t / tiles_x), x = (int)(t - (int64_t)y * tiles_x);
+        return D[b * layer + (int64_t)y * W1 + x];
+    }
+};
+
+__global__ void k_zero_if_over(const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ off, int64_t nq)
+{
+    if (*m_dev <= m_cap) return;  // over capacity: empty stream, nothing out of bounds downstream
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x)
+        off[q] = 0;
+}
+
+struct ExactScratch {
+    int32_t* D;      // K layers of (tiles_y + 1) x (tiles_x + 1) difference counts
+    int32_t* cur;    // T*K scatter cursors
+    uint8_t* gbin;   // n per-Gaussian bins
+    int32_t* roff;   // n + 1 row-record offsets
+    uint32_t *rs_g, *rs_ya, *rs_w;  // row records (<= m_cap)
+    int64_t* total;  // scratch count
+};
+
+static size_t exact_scratch(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t tiles_x, int32_t tiles_y, int K,
+                            ExactScratch* v)
+{
+    const size_t layer = (size_t)(tiles_x + 1) * (tiles_y + 1);
+    const size_t T = (size_t)tiles_x * tiles_y;
+    const size_t mc = (size_t)(m_cap > 0 ? m_cap : 1), nn = (size_t)(n > 0 ? n : 1);
+    const size_t sizes[] = {layer * K * 4, T * K * 4, nn, (nn + 1) * 4, mc * 4, mc * 4, mc * 4, 8};
+    size_t total = 0;
+    for (size_t s : sizes) total += align256(s);
+    if (v) {
+        char* b = (char*)ctx->d_tiles;
+        void** dst[] = {(void**)&v->D, (void**)&v->cur, (void**)&v->gbin, (void**)&v->roff, (void**)&v->rs_g,
+                        (void**)&v->rs_ya, (void**)&v->rs_w, (void**)&v->total};
+        for (int k = 0; k < 8; ++k) {
+            *dst[k] = b;
+            b += align256(sizes[k]);
+        }
+    }
+    return total;
+}
+
+int exact_bins_reserve(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t tiles_x, int32_t tiles_y, int K)
+{
+    void* p = ctx->d_tiles;
+    int r = ensure(&p, &ctx->tiles_cap, exact_scratch(ctx, n, m_cap, tiles_x, tiles_y, K, nullptr));
+    ctx->d_tiles = (int32_t*)p;
+    return r;
+}
+
+int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, bool goff_ready, int64_t m_cap,
+               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st)
+{
+    const int tile = ctx->cfg.tile_size, K = ctx->cfg.K;
+    const int32_t tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
+    const int64_t T = (int64_t)tiles_x * tiles_y, nseg = T * K;
+    int r;
+    if ((r = exact_bins_reserve(ctx, n, m_cap, tiles_x, tiles_y, K)) != GS_OK) return r;
+    ExactScratch v;
+    exact_scratch(ctx, n, m_cap, tiles_x, tiles_y, K, &v);
+    const size_t layer = (size_t)(tiles_x + 1) * (tiles_y + 1);
+    GS_CUDA_TRY(cudaMemsetAsync(v.cur, 0, (size_t)nseg * 4, st));
+    GS_CUDA_TRY(cudaMemsetAsync(v.D, 0, layer * K * 4, st));
+    const unsigned g_sm = (unsigned)ctx->num_sms * 8;
+    k_capacity_check<<<1, 1, 0, st>>>(m_dev, m_cap, ctx->d_err);
+    ctx->launches += 1;
+    if (ctx->cfg.tile_cull) {
+        // rows of every rect, each row's culled span, per-row difference counts
+        const int64_t rlayer = (int64_t)tiles_y * (tiles_x + 1);
+        if ((r = scan_impl(ctx, LoadRectRows{pv.rect}, n, v.roff, v.total, st)) != GS_OK) return r;
+        CullArgs ca{pv.xy_ab, pv.c_o_z, pv.rgb, tile};
+        const int64_t warps = (n + 31) / 32;
+        if (warps > 0)
+            k_row_spans<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(pv.rect, n, v.roff, ca, tiles_x, ctx->d_bp, K,
+                                                                     m_dev, m_cap, v.D, rlayer, v.gbin, v.rs_g,
+                                                                     v.rs_ya, v.rs_w);
+        k_layer_rows_prefix<<<(unsigned)K, 1024, 0, st>>>(v.D, tiles_x, tiles_y, rlayer);
+        ctx->launches += 2;
+        if ((r = scan_impl(ctx, LoadLayerCount{v.D, K, tiles_x, tiles_x + 1, rlayer}, nseg, offsets, nullptr, st)) != GS_OK)
+            return r;
+        k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1);
+        if (n > 0)
+            k_bin_scatter_rows<<<g_sm * 2, 256, 0, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.roff, n, pv.c_o_z, v.gbin, tiles_x,
+                                                         K, m_dev, m_cap, offsets, v.cur, words);
+        ctx->launches += 2;
+    } else {
+        // whole rects per bin layer: four atomics per Gaussian, 2D prefix sums
+        if (!goff_ready && (r = count_scan(ctx, pv, n, v.total, st)) != GS_OK) return r;
+        if (n > 0) k_bin_diff<<<g_sm, 256, 0, st>>>(pv.rect, pv.c_o_z, n, tiles_x, tiles_y, ctx->d_bp, K, v.D, v.gbin);
+        k_layer_prefix<<<(unsigned)K, 1024, 0, st>>>(v.D, tiles_x, tiles_y);
+        ctx->launches += 2;
+        if ((r = scan_impl(ctx, LoadLayerCount{v.D, K, tiles_x, tiles_x + 1, (int64_t)layer}, nseg, offsets, nullptr,
+                           st)) != GS_OK)
+            return r;
+        k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1);
+        const int64_t warps = (n + 31) / 32;
+        if (warps > 0)
+            k_bin_scatter_rects<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(pv.rect, pv.c_o_z, ctx->d_goff, v.gbin, n,
+                                                                             tiles_x, K, m_dev, m_cap, offsets, v.cur,
+                                                                             words);
+        ctx->launches += 2;
+    }
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+}  // namespace gs

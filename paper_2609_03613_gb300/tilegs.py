@@ -24,7 +24,7 @@ MODE_GLOBAL_SORT, MODE_BINNED_EXACT, MODE_BINNED_PAPER, MODE_BINNED_NOREPAIR = 0
 MODES = {"global": 0, "exact": 1, "paper": 2, "norepair": 3}
 STAGES = ["project", "intersect", "depth_range", "bin", "repair", "sort", "raster"]
 MAX_K = 128
-RENDER_HOST_INPUTS, RENDER_HOST_OUTPUTS, RENDER_NO_SYNC = 1, 2, 4
+RENDER_HOST_INPUTS, RENDER_HOST_OUTPUTS, RENDER_NO_SYNC, RENDER_GRAPH = 1, 2, 4, 8
 P_XY_AB, P_C_O_Z, P_RGB, P_RECT, P_RADIUS = range(5)
 
 # Every symbol include/tilegs.h declares (checked by the CPU export test).
@@ -53,7 +53,7 @@ class GsConfig(C.Structure):
                 ("sample_count", C.c_int32), ("p_lo", C.c_float), ("p_hi", C.c_float),
                 ("pad", C.c_float), ("near_alpha", C.c_float), ("near_gamma", C.c_float),
                 ("eps", C.c_float), ("repair_budget_frac", C.c_float), ("near_shift", C.c_int32),
-                ("tile_cull", C.c_int32), ("persistent", C.c_int32)]
+                ("tile_cull", C.c_int32), ("persistent", C.c_int32), ("repair_in_raster", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

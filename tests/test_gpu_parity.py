@@ -124,15 +124,55 @@ def test_global_sort_stream_bitexact(tile):
     np.testing.assert_array_equal(r["words"], stream)
 
 
+def assert_lazy_stream(words, offsets, stream, cap=2048):
+    """Stream left for the raster's repair: every segment holds exactly the
+    global order's entries of that range, and segments longer than the
+    raster's sort buffer are already sorted."""
+    for q in range(offsets.shape[0] - 1):
+        a, b = offsets[q], offsets[q + 1]
+        if b - a > cap:
+            np.testing.assert_array_equal(words[a:b], stream[a:b])
+        elif b - a > 0:
+            np.testing.assert_array_equal(np.sort(words[a:b]), stream[a:b])
+
+
+def assert_culled_stream(words, offsets, K, off_o, stream_o, eager):
+    """Stream built with the tile cull: each tile's span holds a subset of
+    the tile's baseline list; with the eager repair it is that subset in the
+    baseline (depth, gid) order."""
+    T = off_o.shape[0] - 1
+    kept = 0
+    for t in range(T):
+        S = words[offsets[t * K]:offsets[(t + 1) * K]]
+        O = stream_o[off_o[t]:off_o[t + 1]]
+        inO = np.isin(S, O)
+        assert inO.all(), t
+        if eager:
+            np.testing.assert_array_equal(S, O[np.isin(O, S)])
+        kept += S.shape[0]
+    return kept
+
+
+@pytest.mark.parametrize("cull", [0, 1])
+@pytest.mark.parametrize("lazy", [0, 1])
 @pytest.mark.parametrize("K", [1, 8, 64, 128])
-def test_binned_exact_stream_equals_global_order(tiny, K):
+def test_binned_exact_stream_equals_global_order(tiny, K, lazy, cull):
     sc, cam, P, ent, off, stream = tiny[:6]
-    r = run_stage_pipeline("exact", sc, cam, K=K)
-    np.testing.assert_array_equal(r["offsets"][::K], off)
-    np.testing.assert_array_equal(r["words"], stream)
-    # bin offsets themselves match the oracle's monotone-map construction
+    r = run_stage_pipeline("exact", sc, cam, K=K, repair_in_raster=lazy, tile_cull=cull)
+    np.testing.assert_array_equal(bits(r["rgb"]), bits(tiny[6][0]))
+    np.testing.assert_array_equal(r["last"], tiny[6][2])
     zr_o, _ = O.depth_range(ent[2], P["depth"], sc.scales, near_shift=False)
     np.testing.assert_array_equal(bits(r["zr"]), bits(zr_o))
+    if cull:
+        kept = assert_culled_stream(r["words"], r["offsets"], K, off, stream, eager=not lazy)
+        assert 0 < kept < stream.shape[0]
+        return
+    np.testing.assert_array_equal(r["offsets"][::K], off)
+    if lazy:
+        assert_lazy_stream(r["words"], r["offsets"], stream)
+    else:
+        np.testing.assert_array_equal(r["words"], stream)
+    # bin offsets themselves match the oracle's monotone-map construction
     off_b, _ = O.bin_build(ent, 256, K, 0, zr_o)
     np.testing.assert_array_equal(r["offsets"], off_b)
 
@@ -226,12 +266,15 @@ def test_paper_selection_budget_binding_matches_greedy():
     assert used < int(np.where(lens >= 320, lens, 0).sum())  # the budget did bind
 
 
-@pytest.mark.parametrize("mode", ["global", "exact"])
+@pytest.mark.parametrize("mode", ["global", "exact", "exact-eager"])
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_raster_matches_oracle(tiny, mode, tile):
     sc, cam = tiny[0], tiny[1]
     proj_o, ent, (off, stream), (rgb_o, a_o, l_o) = O.render(sc, cam, tile, bg=(0.1, 0.2, 0.3))
-    ctx = G.Context(mode, tile_size=tile)
+    if mode == "exact-eager":
+        ctx = G.Context("exact", tile_size=tile, repair_in_raster=0)
+    else:
+        ctx = G.Context(mode, tile_size=tile)
     ds, proj, _ = gpu_project(ctx, sc, cam)
     isect, m_cap, m_dev, m = ctx.tile_intersect(proj, sc.n, cam)
     words, offsets, _ = ctx.sort_or_bin(proj, ds.scales, sc.n, cam, isect, m_cap, m_dev)
@@ -325,13 +368,15 @@ def test_everything_culled_behind_camera():
         assert r["m"] == 0 and np.all(r["alpha"] == 0)
 
 
-@pytest.mark.parametrize("mode,K", [("global", 1), ("exact", 1), ("exact", 4)])
-def test_ragged_image_and_giant_gaussian(mode, K):
+@pytest.mark.parametrize("mode,K,lazy,cull", [("global", 1, 0, 0), ("exact", 1, 0, 0), ("exact", 4, 0, 0),
+                                              ("exact", 1, 1, 0), ("exact", 4, 1, 0), ("exact", 4, 1, 1),
+                                              ("exact", 1, 0, 1)])
+def test_ragged_image_and_giant_gaussian(mode, K, lazy, cull):
     """Odd image size (ragged edge tiles) plus one Gaussian covering every
     tile and deep ranges: bins longer than the shared-memory sort go through
     the global-memory tail sort."""
     rng = np.random.default_rng(61)
-    n = 20000
+    n = 40000
     base = scenes.tiny_scene(n, 61)
     means = base.means.copy()
     means[:, 2] = rng.uniform(-0.05, 0.05, n)  # a thin slab: long per-tile lists
@@ -340,9 +385,14 @@ def test_ragged_image_and_giant_gaussian(mode, K):
     sc = scenes.Scene(means, scales, base.quats, base.opacities * 0.3, base.sh, 0)
     cam = scenes.Camera(scenes.look_at((0, 0, 3.0)), 300.0, 300.0, 125.0, 65.5, 250, 131)
     proj_o, ent, (off, stream), (rgb_o, a_o, l_o) = O.render(sc, cam)
-    assert np.diff(off).max() > 5000
-    r = run_stage_pipeline(mode, sc, cam, K=K)
-    np.testing.assert_array_equal(r["words"], stream)
+    assert np.diff(off).max() > 12288  # longer than the tile kernel's shared buffer
+    r = run_stage_pipeline(mode, sc, cam, K=K, repair_in_raster=lazy, tile_cull=cull)
+    if cull:
+        assert_culled_stream(r["words"], r["offsets"], K, off, stream, eager=not lazy)
+    elif lazy:
+        assert_lazy_stream(r["words"], r["offsets"], stream)
+    else:
+        np.testing.assert_array_equal(r["words"], stream)
     np.testing.assert_array_equal(bits(r["rgb"]), bits(rgb_o))
     np.testing.assert_array_equal(r["last"], l_o)
 
@@ -360,10 +410,13 @@ def test_single_gaussian_and_k1():
 
 def test_deterministic_repeat(tiny):
     sc, cam = tiny[0], tiny[1]
-    a = run_stage_pipeline("exact", sc, cam)
-    b = run_stage_pipeline("exact", sc, cam)
+    a = run_stage_pipeline("exact", sc, cam, repair_in_raster=0, tile_cull=0)
+    b = run_stage_pipeline("exact", sc, cam, repair_in_raster=0, tile_cull=0)
     np.testing.assert_array_equal(a["words"], b["words"])
     np.testing.assert_array_equal(bits(a["rgb"]), bits(b["rgb"]))
+    c = run_stage_pipeline("exact", sc, cam)  # in-raster repair: same image, same last ids
+    np.testing.assert_array_equal(bits(a["rgb"]), bits(c["rgb"]))
+    np.testing.assert_array_equal(a["last"], c["last"])
 
 
 def test_invalid_arguments_rejected():
@@ -398,10 +451,15 @@ def test_fullsize_mid_projection_and_lists_bitexact(mid):
     _, _, f = gpu_project(ctx, sc, cam)
     assert_projection_equal(P, f)
     for mode in ("global", "exact"):
-        r = run_stage_pipeline(mode, sc, cam)
+        r = run_stage_pipeline(mode, sc, cam, repair_in_raster=0, tile_cull=0)
         assert r["m"] == ent[0].shape[0]
         np.testing.assert_array_equal(r["words"], stream)
         np.testing.assert_array_equal(r["offsets"][:: (1 if mode == "global" else 64)], off)
+    r = run_stage_pipeline("exact", sc, cam, tile_cull=0)  # repair left to the raster
+    np.testing.assert_array_equal(r["offsets"][::64], off)
+    assert_lazy_stream(r["words"], r["offsets"], stream)
+    r = run_stage_pipeline("exact", sc, cam, repair_in_raster=0)  # tile cull while binning
+    assert_culled_stream(r["words"], r["offsets"], 64, off, stream, eager=True)
 
 
 def test_fullsize_mid_sampled_tiles_in_bench_configuration(mid):
@@ -434,3 +492,52 @@ def test_fullsize_mid_sampled_tiles_in_bench_configuration(mid):
             np.testing.assert_array_equal(bits(alpha[ys, xs]), bits(a_o[ys, xs]))
             np.testing.assert_array_equal(last[ys, xs], l_o[ys, xs])
     np.testing.assert_array_equal(bits(images["exact"]), bits(images["global"]))
+
+
+@pytest.mark.parametrize("mode", ["global", "exact", "paper"])
+def test_render_over_capacity_without_sync_reports_error(tiny, mode):
+    """With too little reserved capacity and no host read of M, the frame must
+    raise GS_ERR_CAPACITY through the error word and touch nothing out of
+    bounds (the image is then background only)."""
+    sc, cam = tiny[0], tiny[1]
+    ctx = G.Context(mode)
+    ctx.reserve(sc.n, 1000, cam.width, cam.height)
+    ds = G.DeviceScene.from_numpy(sc)
+    rgb, alpha, last = ctx.render(ds, cam, bg=(0.5, 0.5, 0.5), flags=G.RENDER_NO_SYNC)
+    torch.cuda.synchronize()
+    assert ctx.error() == 2
+    assert np.all(alpha.cpu().numpy() == 0) and np.all(last.cpu().numpy() == -1)
+    ctx.clear_error()
+    rgb, alpha, last = ctx.render(ds, cam)  # with the read of M it regrows and renders
+    torch.cuda.synchronize()
+    assert ctx.error() == 0 and alpha.cpu().numpy().max() > 0.5
+
+
+def test_render_graph_replay_matches_and_recaptures(tiny):
+    """GS_RENDER_GRAPH: the captured frame replays to the same image, and a
+    new camera forces a new capture (not a stale replay)."""
+    sc, cam = tiny[0], tiny[1]
+    rgb_o, a_o, l_o = tiny[6]
+    ctx = G.Context("exact")
+    ds = G.DeviceScene.from_numpy(sc)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        ctx.render(ds, cam)  # sizes the scratch
+        with pytest.raises(G.TileGSError):
+            with torch.cuda.stream(torch.cuda.default_stream()):
+                ctx.render(ds, cam, flags=G.RENDER_GRAPH)
+        out = (torch.empty((256, 256, 3), device="cuda"), torch.empty((256, 256), device="cuda"),
+               torch.empty((256, 256), dtype=torch.int32, device="cuda"))
+        for _ in range(3):
+            out[0].zero_()
+            ctx.render(ds, cam, out=out, flags=G.RENDER_GRAPH)
+            torch.cuda.current_stream().synchronize()
+            np.testing.assert_array_equal(bits(out[0].cpu().numpy()), bits(rgb_o))
+            np.testing.assert_array_equal(out[2].cpu().numpy(), l_o)
+        cam2 = scenes.Camera(scenes.look_at((0.3, 0.2, 2.8)), 256.0, 256.0, 128.0, 128.0, 256, 256)
+        _, _, _, (rgb2, _, _) = O.render(sc, cam2)
+        ctx.render(ds, cam2)  # may grow scratch outside the capture
+        ctx.render(ds, cam2, out=out, flags=G.RENDER_GRAPH)
+        torch.cuda.current_stream().synchronize()
+        np.testing.assert_array_equal(bits(out[0].cpu().numpy()), bits(rgb2))
+    assert ctx.error() == 0

@@ -285,7 +285,7 @@ def test_composite_two_layer_order():
         T = (1 - a[0]) * (1 - a[1])
         np.testing.assert_allclose(rgb[4, 4], C + T * np.array(bg), atol=2e-6)
         assert abs(alpha[4, 4] - (1 - T)) < 2e-6
-        assert last[4, 4] == 1
+        assert last[4, 4] == order[1]  # the id of the last applied Gaussian
 
 
 def _scene_all(sc, cam, tile=16):
