@@ -4,7 +4,7 @@
  * The method is "TileGS: Tile-Local Depth Binning for Gaussian Splatting
  * Rasterization".  A frame runs:
  *   gs_project        -> per-Gaussian 2D mean / conic / depth / tile rect / colour
- *                        (Sec. 3.1, "projected Gaussian inputs")
+ *                        (Sec. 3.1, the method's projected inputs)
  *   gs_tile_intersect -> one entry per (Gaussian, covered tile)       (Sec. 3.1)
  *   gs_sort_or_bin    -> either the baseline global (tile, depth) sort (Sec. 3.1)
  *                        or depth-range estimation + tile-local bin construction

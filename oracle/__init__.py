@@ -99,6 +99,16 @@ def lib():
         L.orc64_composite_pixel.restype = C.c_double
         L.orc64_composite_pixel.argtypes = [C.c_double, C.c_double, _f64p, _f64p, _f32p, _f64p,
                                             _u32p, C.c_int64, _f64p]
+        _i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+        L.orc_composite_grad.restype = None
+        L.orc_composite_grad.argtypes = [_f32p, _f32p, _f32p, _f32p, _i32p, C.c_int, _u64p, C.c_int, C.c_int,
+                                         C.c_int, _f32p, _f32p, C.c_void_p, _f64p, _f64p, _f64p, _f64p, C.c_void_p]
+        L.orc64_composite_frozen.restype = None
+        L.orc64_composite_frozen.argtypes = [_f64p, _f64p, _f64p, _f64p, _i64p, _i32p, C.c_int, C.c_int, _f64p,
+                                             _f64p, _f64p]
+        L.orc_applied_lists.restype = C.c_int64
+        L.orc_applied_lists.argtypes = [_f32p, _f32p, _f32p, _i32p, C.c_int, _u64p, C.c_int, C.c_int, C.c_int,
+                                        _i64p, _i32p, C.c_int64]
         _lib = L
     return _lib
 
@@ -281,3 +291,43 @@ def set_threads(n: int) -> None:
     """Threads used by the oracle's compositing loop (OpenMP over tiles)."""
     lib().orc_set_threads.argtypes = [C.c_int]
     lib().orc_set_threads(int(n))
+
+
+def composite_grad(proj, offsets, stream, width, height, dl_drgb, dl_dalpha=None, tile=16, bg=(0.0, 0.0, 0.0),
+                   K=1, with_abs=False):
+    """Gradient of the compositing (float32 decisions, double arithmetic):
+    dict of mean2d [n,2], conic [n,3], opacity [n], rgb [n,3] (float64), and
+    with_abs: "abs" [n,9], the sums of the absolute per-pixel terms."""
+    n = proj["mean2d"].shape[0]
+    g = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)))
+    if with_abs:
+        g["abs"] = np.zeros((n, 9))
+    da = None if dl_dalpha is None else _c(dl_dalpha, np.float32)
+    lib().orc_composite_grad(_c(proj["mean2d"], np.float32), _c(proj["conic"], np.float32),
+                             _c(proj["opacity"], np.float32), _c(proj["rgb"], np.float32), _c(offsets, np.int32), K,
+                             _c(stream, np.uint64), width, height, tile, np.asarray(bg, np.float32),
+                             _c(dl_drgb, np.float32), None if da is None else da.ctypes.data,
+                             g["mean2d"], g["conic"], g["opacity"], g["rgb"],
+                             g["abs"].ctypes.data if with_abs else None)
+    return g
+
+
+def applied_lists(proj, offsets, stream, width, height, tile=16, K=1):
+    P = width * height
+    off = np.zeros(P + 1, np.int64)
+    L = lib()
+    args = (_c(proj["mean2d"], np.float32), _c(proj["conic"], np.float32), _c(proj["opacity"], np.float32),
+            _c(offsets, np.int32), K, _c(stream, np.uint64), width, height, tile)
+    na = L.orc_applied_lists(*args, off, np.zeros(1, np.int32), 0)
+    ap = np.zeros(max(na, 1), np.int32)
+    L.orc_applied_lists(*args, off, ap, na)
+    return off, ap[:na]
+
+
+def composite_frozen64(mean2d, conic, opacity, rgb, applied_off, applied, width, height, bg=(0.0, 0.0, 0.0)):
+    out_rgb = np.zeros((height, width, 3))
+    out_a = np.zeros((height, width))
+    lib().orc64_composite_frozen(_c(mean2d, np.float64), _c(conic, np.float64), _c(opacity, np.float64),
+                                 _c(rgb, np.float64), _c(applied_off, np.int64), _c(applied, np.int32), width, height,
+                                 np.asarray(bg, np.float64), out_rgb, out_a)
+    return out_rgb, out_a

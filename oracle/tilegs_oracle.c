@@ -100,7 +100,7 @@ float orc_logf(float x)
 }
 
 /* ------------------------------------------------------------------------ */
-/* Projection (Sec. 3.1: "projected Gaussian inputs", unchanged from 3DGS).   */
+/* Projection (Sec. 3.1: the method starts from 3DGS's projected Gaussians). */
 /* ------------------------------------------------------------------------ */
 
 /* Real spherical-harmonic basis up to degree 3 (orthonormal on the unit
@@ -344,8 +344,8 @@ void orc_sort_tiles(int64_t m, const uint32_t* tile, const uint32_t* zbits, cons
 }
 
 /* ------------------------------------------------------------------------ */
-/* Front-to-back compositing (Sec. 3.1; supplement, binned raster traversal:  */
-/* "the same opacity/conic test as the baseline").                            */
+/* Front-to-back compositing (Sec. 3.1; supplement, binned raster traversal: */
+/* the binned raster keeps the baseline's per-pixel opacity/conic test).     */
 /* ------------------------------------------------------------------------ */
 
 /*
@@ -742,4 +742,186 @@ void orc_set_threads(int n)
 #else
     (void)n;
 #endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Backward of the compositing (gradient of the image w.r.t. the projected    */
+/* 2D parameters).  The paper leaves the backward to future work (Sec. 7):    */
+/* it has to follow the order the forward composites in.                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For every pixel of every tile: replay the forward over the tile's span of
+ * `stream` with its float32 decisions (which entries are skipped, where the
+ * pixel stops, whether alpha is clamped -- exactly orc_composite's), then
+ * accumulate in double the derivatives of
+ *   out_rgb = sum_i c_i a_i T_i + T_N bg,  out_alpha = 1 - T_N,
+ *   a_i = min(0.99, o_i exp(-q_i)),  q_i = 1/2 (a dx^2 + 2 b dx dy + c dy^2),
+ *   T_{i+1} = T_i (1 - a_i),  d = mean - pixel centre,
+ * w.r.t. mean2d, conic (a, b, c), opacity and rgb, weighted by dl_drgb [H,W,3]
+ * and dl_dalpha [H,W] (nullable).  A clamped alpha (o exp(-q) > 0.99 in
+ * float32) passes no gradient to o or q.  Gradients are added into
+ * g_mean2d [n,2], g_conic [n,3], g_opac [n], g_rgb [n,3] (double,
+ * caller-zeroed); g_abs [n,9] (nullable) receives the sums of the absolute
+ * per-pixel terms in the order (mx, my, a, b, c, o, r, g, b), the scale of
+ * the rounding error any float32 summation of the same terms can make.
+ */
+void orc_composite_grad(const float* mean2d, const float* conic, const float* opac, const float* rgb,
+                        const int32_t* offsets, int K, const uint64_t* stream, int width, int height,
+                        int tile, const float* bg, const float* dl_drgb, const float* dl_dalpha,
+                        double* g_mean2d, double* g_conic, double* g_opac, double* g_rgb, double* g_abs)
+{
+    const int tiles_x = (width + tile - 1) / tile;
+    const int tiles_y = (height + tile - 1) / tile;
+    int32_t* applied = NULL;
+    unsigned char* clamped = NULL;
+    int64_t cap = 0;
+    for (int32_t t = 0; t < tiles_x * tiles_y; ++t) {
+        const int tx = t % tiles_x, ty = t / tiles_x;
+        const int32_t s0 = offsets[(int64_t)t * K], s1 = offsets[(int64_t)(t + 1) * K];
+        if (s1 - s0 > cap) {
+            cap = s1 - s0;
+            applied = (int32_t*)realloc(applied, (size_t)cap * sizeof(int32_t));
+            clamped = (unsigned char*)realloc(clamped, (size_t)cap);
+        }
+        for (int j = ty * tile; j < ty * tile + tile && j < height; ++j)
+            for (int i = tx * tile; i < tx * tile + tile && i < width; ++i) {
+                const float pxc = (float)i + 0.5f, pyc = (float)j + 0.5f;
+                /* pass 1: the forward's float32 decisions */
+                float T = 1.0f;
+                int64_t na = 0;
+                for (int32_t s = s0; s < s1; ++s) {
+                    const uint32_t g = (uint32_t)(stream[s] & 0xffffffffu);
+                    const float dx = mean2d[2 * g] - pxc, dy = mean2d[2 * g + 1] - pyc;
+                    const float ha = 0.5f * conic[3 * g], hb = conic[3 * g + 1], hc = 0.5f * conic[3 * g + 2];
+                    const float q = fmaf(dx, fmaf(ha, dx, hb * dy), (hc * dy) * dy);
+                    if (!(q >= 0.0f)) continue;
+                    const float oe = opac[g] * orc_expf(-q);
+                    const float alpha = fminf(0.99f, oe);
+                    if (alpha < 1.0f / 255.0f) continue;
+                    const float Tn = T * (1.0f - alpha);
+                    if (Tn < 1e-4f) break;
+                    T = Tn;
+                    clamped[na] = oe > 0.99f;
+                    applied[na++] = (int32_t)g;
+                }
+                /* pass 2: double-precision values and derivatives over the applied list */
+                const int64_t p = (int64_t)j * width + i;
+                const double px = (double)i + 0.5, py = (double)j + 0.5;
+                double Tf = 1.0;
+                for (int64_t k = 0; k < na; ++k) {
+                    const int32_t g = applied[k];
+                    const double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
+                    const double q = 0.5 * (conic[3 * g] * dx * dx + conic[3 * g + 2] * dy * dy) + conic[3 * g + 1] * dx * dy;
+                    const double a = clamped[k] ? 0.99 : opac[g] * exp(-q);
+                    Tf *= 1.0 - a;
+                }
+                const double dA = dl_dalpha ? dl_dalpha[p] : 0.0;
+                /* back to front: S = colour composited behind the entry (incl. background) */
+                double S[3] = {Tf * bg[0], Tf * bg[1], Tf * bg[2]};
+                double Tb = Tf; /* transmittance after the entry */
+                for (int64_t k = na - 1; k >= 0; --k) {
+                    const int32_t g = applied[k];
+                    const double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
+                    const double ca = conic[3 * g], cb = conic[3 * g + 1], cc = conic[3 * g + 2];
+                    const double q = 0.5 * (ca * dx * dx + cc * dy * dy) + cb * dx * dy;
+                    const double G = exp(-q);
+                    const double a = clamped[k] ? 0.99 : opac[g] * G;
+                    const double Ti = Tb / (1.0 - a); /* transmittance before the entry */
+                    double dl_da = dA * Tf / (1.0 - a);
+                    double term[9];
+                    for (int ch = 0; ch < 3; ++ch) {
+                        const double dC = dl_drgb[3 * p + ch];
+                        term[6 + ch] = dC * a * Ti;
+                        dl_da += dC * (rgb[3 * g + ch] * Ti - S[ch] / (1.0 - a));
+                    }
+                    if (!clamped[k]) {
+                        const double dl_dq = -dl_da * opac[g] * G;
+                        term[0] = dl_dq * (ca * dx + cb * dy);
+                        term[1] = dl_dq * (cb * dx + cc * dy);
+                        term[2] = dl_dq * 0.5 * dx * dx;
+                        term[3] = dl_dq * dx * dy;
+                        term[4] = dl_dq * 0.5 * dy * dy;
+                        term[5] = dl_da * G;
+                    } else {
+                        for (int v = 0; v < 6; ++v) term[v] = 0.0;
+                    }
+                    g_mean2d[2 * (int64_t)g] += term[0];
+                    g_mean2d[2 * (int64_t)g + 1] += term[1];
+                    for (int v = 0; v < 3; ++v) g_conic[3 * (int64_t)g + v] += term[2 + v];
+                    g_opac[g] += term[5];
+                    for (int v = 0; v < 3; ++v) g_rgb[3 * (int64_t)g + v] += term[6 + v];
+                    if (g_abs)
+                        for (int v = 0; v < 9; ++v) g_abs[9 * (int64_t)g + v] += fabs(term[v]);
+                    for (int ch = 0; ch < 3; ++ch) S[ch] += rgb[3 * g + ch] * a * Ti;
+                    Tb = Ti;
+                }
+            }
+    }
+    free(applied);
+    free(clamped);
+}
+
+/*
+ * The double-precision forward over frozen per-pixel lists: applied_off
+ * [P+1] / applied [..] give, per pixel (row-major), the gids the forward
+ * applied, in order.  No threshold decision is taken, so the map from the 2D
+ * parameters to (out_rgb, out_alpha) is smooth and central finite differences
+ * of it check orc_composite_grad.
+ */
+void orc64_composite_frozen(const double* mean2d, const double* conic, const double* opac, const double* rgb,
+                            const int64_t* applied_off, const int32_t* applied, int width, int height,
+                            const double* bg, double* out_rgb, double* out_alpha)
+{
+    for (int j = 0; j < height; ++j)
+        for (int i = 0; i < width; ++i) {
+            const int64_t p = (int64_t)j * width + i;
+            const double px = (double)i + 0.5, py = (double)j + 0.5;
+            double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+            for (int64_t k = applied_off[p]; k < applied_off[p + 1]; ++k) {
+                const int32_t g = applied[k];
+                const double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
+                const double q = 0.5 * (conic[3 * g] * dx * dx + conic[3 * g + 2] * dy * dy) + conic[3 * g + 1] * dx * dy;
+                const double a = fmin(0.99, opac[g] * exp(-q));
+                for (int ch = 0; ch < 3; ++ch) C[ch] += rgb[3 * g + ch] * a * T;
+                T *= 1.0 - a;
+            }
+            for (int ch = 0; ch < 3; ++ch) out_rgb[3 * p + ch] = C[ch] + T * bg[ch];
+            out_alpha[p] = 1.0 - T;
+        }
+}
+
+/* The applied lists of the float32 forward (for the frozen forward above):
+ * returns the total count; writes applied_off [P+1] and applied (capacity cap). */
+int64_t orc_applied_lists(const float* mean2d, const float* conic, const float* opac, const int32_t* offsets,
+                          int K, const uint64_t* stream, int width, int height, int tile,
+                          int64_t* applied_off, int32_t* applied, int64_t cap)
+{
+    const int tiles_x = (width + tile - 1) / tile;
+    int64_t na = 0;
+    for (int j = 0; j < height; ++j)
+        for (int i = 0; i < width; ++i) {
+            const int64_t p = (int64_t)j * width + i;
+            applied_off[p] = na;
+            const int32_t t = (j / tile) * tiles_x + (i / tile);
+            const int32_t s0 = offsets[(int64_t)t * K], s1 = offsets[(int64_t)(t + 1) * K];
+            const float pxc = (float)i + 0.5f, pyc = (float)j + 0.5f;
+            float T = 1.0f;
+            for (int32_t s = s0; s < s1; ++s) {
+                const uint32_t g = (uint32_t)(stream[s] & 0xffffffffu);
+                const float dx = mean2d[2 * g] - pxc, dy = mean2d[2 * g + 1] - pyc;
+                const float ha = 0.5f * conic[3 * g], hb = conic[3 * g + 1], hc = 0.5f * conic[3 * g + 2];
+                const float q = fmaf(dx, fmaf(ha, dx, hb * dy), (hc * dy) * dy);
+                if (!(q >= 0.0f)) continue;
+                const float alpha = fminf(0.99f, opac[g] * orc_expf(-q));
+                if (alpha < 1.0f / 255.0f) continue;
+                const float Tn = T * (1.0f - alpha);
+                if (Tn < 1e-4f) break;
+                T = Tn;
+                if (na < cap) applied[na] = (int32_t)g;
+                ++na;
+            }
+        }
+    applied_off[(int64_t)width * height] = na;
+    return na;
 }

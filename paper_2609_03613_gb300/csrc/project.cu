@@ -1,7 +1,7 @@
 // project.cu -- K1+K2: SH colour and EWA projection of 3D Gaussians.
 //
-// The paper keeps the 3DGS projection unchanged ("projected Gaussian inputs",
-// Sec. 3.1) without printing it.  The reading implemented here, in this exact
+// The paper keeps the 3DGS projection unchanged (its input is the projected
+// Gaussians, Sec. 3.1) without printing it.  The reading implemented here, in this exact
 // float32 operation order (compiled with -fmad=false):
 //   p_c = R m + t; cull unless near < z < far and opacity >= 1/255;
 //   Sigma = (R_q S)(R_q S)^T; Sigma_c = R Sigma R^T;
