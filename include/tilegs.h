@@ -274,6 +274,37 @@ int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_cam
                      const float* bg, float* rgb, float* alpha, int32_t* last, int32_t* ntests,
                      void* stream);
 
+/*
+ * Backward of gs_rasterize_fwd: the gradient of a loss L(rgb, alpha) w.r.t.
+ * the projected 2D parameters.  The paper has no backward (Sec. 7 leaves it
+ * to future work and asks that it follow the forward's compositing order);
+ * this one walks every tile's span in exactly the forward's order, with the
+ * forward's float32 decisions, for the same stream, offsets and context
+ * configuration, and differentiates
+ *   rgb = sum_i c_i a_i T_i + T_N bg,  alpha = 1 - T_N,
+ *   a_i = min(0.99, o_i exp(-q_i)),  q_i = 1/2 d^T conic d,  d = mean - centre
+ * (a clamped a_i passes no gradient to o_i or q_i; skipped entries and
+ * entries after the stop get none).
+ *   rgb, alpha: the forward's outputs [H,W,3], [H,W] for these inputs and bg.
+ *   dl_drgb [H,W,3], dl_dalpha [H,W] (nullable: 0): dL/drgb, dL/dalpha.
+ *   grad: caller-owned, 256-byte aligned, gs_grad2d_bytes(n) bytes, zeroed
+ *   and then written; field f at gs_grad2d_offset(n, f):
+ *     0  float4[n] {dL/dmean_x, dL/dmean_y, dL/dconic_a, dL/dconic_b}
+ *     1  float4[n] {dL/dconic_c, dL/dopacity, 0, 0}
+ *     2  float4[n] {dL/dr, dL/dg, dL/db, 0}
+ *   (the same element layout as the projected fields GS_P_XY_AB, GS_P_C_O_Z
+ *   and GS_P_RGB; conic = (a, b, c) of q = 1/2 (a dx^2 + 2 b dx dy + c dy^2)).
+ * Sums over pixels use float atomics: results are reproducible to rounding,
+ * not bitwise.  Errors: GS_ERR_INVALID_ARG (null pointers, bad stride,
+ * misaligned grad), GS_ERR_CUDA.
+ */
+size_t gs_grad2d_bytes(int64_t n);
+size_t gs_grad2d_offset(int64_t n, int32_t field);
+int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
+                     const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
+                     const float* rgb, const float* alpha, const float* dl_drgb, const float* dl_dalpha,
+                     void* grad, void* stream);
+
 /* ---------------------------------------------------------------- whole frame */
 typedef struct gs_scene {
     const float* means;

@@ -759,7 +759,9 @@ void orc_set_threads(int n)
  *   a_i = min(0.99, o_i exp(-q_i)),  q_i = 1/2 (a dx^2 + 2 b dx dy + c dy^2),
  *   T_{i+1} = T_i (1 - a_i),  d = mean - pixel centre,
  * w.r.t. mean2d, conic (a, b, c), opacity and rgb, weighted by dl_drgb [H,W,3]
- * and dl_dalpha [H,W] (nullable).  A clamped alpha (o exp(-q) > 0.99 in
+ * and dl_dalpha [H,W] (nullable), over the pixels of the listed tiles
+ * (tiles_sel[n_sel], each listed once; all tiles when NULL -- the same as a
+ * zero incoming gradient elsewhere).  A clamped alpha (o exp(-q) > 0.99 in
  * float32) passes no gradient to o or q.  Gradients are added into
  * g_mean2d [n,2], g_conic [n,3], g_opac [n], g_rgb [n,3] (double,
  * caller-zeroed); g_abs [n,9] (nullable) receives the sums of the absolute
@@ -769,14 +771,17 @@ void orc_set_threads(int n)
 void orc_composite_grad(const float* mean2d, const float* conic, const float* opac, const float* rgb,
                         const int32_t* offsets, int K, const uint64_t* stream, int width, int height,
                         int tile, const float* bg, const float* dl_drgb, const float* dl_dalpha,
+                        const int32_t* tiles_sel, int64_t n_sel,
                         double* g_mean2d, double* g_conic, double* g_opac, double* g_rgb, double* g_abs)
 {
     const int tiles_x = (width + tile - 1) / tile;
     const int tiles_y = (height + tile - 1) / tile;
+    const int64_t nt = tiles_sel ? n_sel : (int64_t)tiles_x * tiles_y;
     int32_t* applied = NULL;
     unsigned char* clamped = NULL;
     int64_t cap = 0;
-    for (int32_t t = 0; t < tiles_x * tiles_y; ++t) {
+    for (int64_t it = 0; it < nt; ++it) {
+        const int32_t t = tiles_sel ? tiles_sel[it] : (int32_t)it;
         const int tx = t % tiles_x, ty = t / tiles_x;
         const int32_t s0 = offsets[(int64_t)t * K], s1 = offsets[(int64_t)(t + 1) * K];
         if (s1 - s0 > cap) {

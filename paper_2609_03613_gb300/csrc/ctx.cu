@@ -217,6 +217,13 @@ extern "C" size_t gs_projected_offset(int64_t n, int32_t field)
 
 extern "C" size_t gs_projected_bytes(int64_t n) { return gs_projected_offset(n, GS_P_NFIELDS); }
 
+extern "C" size_t gs_grad2d_offset(int64_t n, int32_t field)
+{
+    return (size_t)(field < 0 ? 0 : field > 3 ? 3 : field) * align256((size_t)n * 16);
+}
+
+extern "C" size_t gs_grad2d_bytes(int64_t n) { return gs_grad2d_offset(n, 3); }
+
 extern "C" size_t gs_isect_offset(int64_t m_cap, int32_t field)
 {
     return (size_t)field * align256((size_t)m_cap * 4);
@@ -396,6 +403,23 @@ extern "C" int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, c
                        offsets_stride, bg, rgb, alpha, last, ntests, baseline, st);
     stage_end(ctx, GS_STAGE_RASTER, st);
     return r;
+}
+
+extern "C" int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
+                                const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
+                                const float* out_rgb, const float* out_alpha, const float* dl_drgb,
+                                const float* dl_dalpha, void* grad, void* stream)
+{
+    if (!ctx || !cam_ok(cam) || n < 0 || !offsets || !out_rgb || !out_alpha || !dl_drgb || !grad)
+        return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!projected || !stream_words)) return GS_ERR_INVALID_ARG;
+    if (offsets_stride < 1 || offsets_stride > GS_MAX_K) return GS_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(grad) & 255u) != 0) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    GS_CUDA_TRY(cudaMemsetAsync(grad, 0, gs_grad2d_bytes(n), st));
+    if (n == 0) return GS_OK;
+    return raster_bwd(ctx, proj_view(const_cast<void*>(projected), n), cam, stream_words, offsets, offsets_stride,
+                      out_rgb, out_alpha, dl_drgb, dl_dalpha, grad_view(grad, n), st);
 }
 
 // ------------------------------------------------------------------ whole frame

@@ -63,6 +63,24 @@ inline IsectView isect_view(void* base, int64_t m_cap)
     return v;
 }
 
+// Gradient buffer of gs_rasterize_bwd: three float4 fields mirroring the
+// first three fields of the projected record.
+struct GradView {
+    float4* xy_ab;  // {dmean_x, dmean_y, dconic_a, dconic_b}
+    float4* c_o_z;  // {dconic_c, dopacity, 0, 0}
+    float4* rgb;    // {dr, dg, db, 0}
+};
+
+inline GradView grad_view(void* base, int64_t n)
+{
+    char* b = static_cast<char*>(base);
+    GradView v;
+    v.xy_ab = reinterpret_cast<float4*>(b + gs_grad2d_offset(n, 0));
+    v.c_o_z = reinterpret_cast<float4*>(b + gs_grad2d_offset(n, 1));
+    v.rgb = reinterpret_cast<float4*>(b + gs_grad2d_offset(n, 2));
+    return v;
+}
+
 // Live entry count: the device count when it fits the capacity, else 0 (the
 // emitter has raised GS_ERR_CAPACITY and written nothing).
 __device__ __forceinline__ int64_t live_count(const int64_t* m_dev, int64_t m_cap)
@@ -275,6 +293,11 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* stream_words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st);
+
+// raster_bwd.cu
+int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
+               int32_t stride, const float* out_rgb, const float* out_alpha, const float* dl_drgb,
+               const float* dl_dalpha, const GradView& gv, cudaStream_t st);
 
 // grow every stage's internal scratch for (n, m_cap, T) (synchronous)
 int reserve_internal(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t width, int32_t height);

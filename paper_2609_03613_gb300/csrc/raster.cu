@@ -22,14 +22,9 @@
 //               alpha >= 1/255 anywhere in the tile are dropped, order kept),
 //               colour staging, and a per-entry early-out q > tau with
 //               tau >= ln(255 o), past which alpha < 1/255 is certain.
-#include "device.cuh"
+#include "raster_common.cuh"
 
 namespace gs {
-
-struct RasterArgs {
-    int width, height, tiles_x, n_tiles, stride;
-    float bg0, bg1, bg2;
-};
 
 // Per-thread compositing state.
 struct PixelState {
@@ -39,45 +34,9 @@ struct PixelState {
     bool done;
 };
 
-template <int TILE, bool BASELINE>
-struct RasterShared {
-    static constexpr int BS = TILE * TILE;
-    static constexpr int BATCH = BS < 256 ? BS : 256;  // entries staged per batch
-    static constexpr int NW = BATCH / 32;              // warps that load a batch
-    float4 a[BATCH];                       // {mx, my, a/2, b}
-    float4 b[BATCH];                       // {c/2, o, tau, gid bits}
-    float4 c[BASELINE ? 1 : BATCH];        // colour (binned)
-    uint32_t g[BASELINE ? BATCH : 1];      // gid (baseline colour lookup)
-    int wc[NW];
-};
-
 // Composite n_entries stream words from src (global or shared memory) into
-// every pixel of the tile, in batches.
-// Returns true (uniformly) once every pixel of the tile has terminated.
-// Rows of the tile a warp owns: the strip mask bit w is set when the
-// entry's alpha >= 1/255 ellipse (the tile cull's bound tau / margin, widened
-// as there) can reach rows [y0 + w*RPW, y0 + (w+1)*RPW) of the tile.
-template <int TILE>
-__device__ __forceinline__ uint32_t strip_mask(float my, float ha, float hb, float hc, float tau, float margin,
-                                               float y0)
-{
-    constexpr int RPW = 32 / TILE > 0 ? 32 / TILE : 1;  // pixel rows per warp
-    constexpr int NWT = TILE * TILE / 32;               // warps per tile
-    const uint32_t all = NWT >= 32 ? 0xffffffffu : ((1u << NWT) - 1u);
-    if (!(margin > 0.0f)) return all;
-    const float D = 4.0f * ha * hc - hb * hb;
-    const float tp = tau / margin;
-    if (!(D > 0.0f) || !(tp > 0.0f)) return all;
-    const float dymax = sqrtf(4.0f * ha * tp / D) * (1.0f + 5e-3f) + 0.05f;
-    // pixel rows (centres y0 + row + 0.5) with |my - py| <= dymax
-    const float rlo = fmaxf(ceilf(my - dymax - y0 - 0.5f), 0.0f);
-    const float rhi = fminf(floorf(my + dymax - y0 - 0.5f), (float)(TILE - 1));
-    if (rlo > rhi) return 0u;
-    const int wlo = (int)rlo / RPW, whi = (int)rhi / RPW;
-    const uint32_t upto = whi >= 31 ? 0xffffffffu : ((2u << whi) - 1u);
-    return upto & ~((1u << wlo) - 1u) & all;
-}
-
+// every pixel of the tile, in batches.  Returns true (uniformly) once every
+// pixel of the tile has terminated.
 // cullmode bit 1: tile-alpha cull at staging; bit 2: per-warp strip mask.
 template <int TILE, bool BASELINE, bool COUNT>
 __device__ __forceinline__ bool raster_span(const uint64_t* src, int32_t n_entries,
@@ -86,57 +45,11 @@ __device__ __forceinline__ bool raster_span(const uint64_t* src, int32_t n_entri
                                             int cullmode, int tx, int ty, float pxc, float pyc, PixelState& st)
 {
     using SH = RasterShared<TILE, BASELINE>;
-    constexpr int BS = SH::BS, BATCH = SH::BATCH, NW = SH::NW;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int BS = SH::BS, BATCH = SH::BATCH;
+    const int warp = threadIdx.x >> 5;
     for (int32_t b0 = 0; b0 < n_entries; b0 += BATCH) {
         if (__syncthreads_count(st.done) == BS) return true;
-        const int32_t idx = b0 + threadIdx.x;
-        const bool valid = threadIdx.x < BATCH && idx < n_entries;
-        float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, Cc = A;
-        uint32_t g = 0;
-        bool keep = valid;
-        if (valid) {
-            g = (uint32_t)(src[idx] & 0xffffffffull);
-            const float4 p = __ldg(xy_ab + g);
-            const float4 q = __ldg(c_o_z + g);
-            A = make_float4(p.x, p.y, 0.5f * p.z, p.w);
-            B = make_float4(0.5f * q.x, q.y, q.w, __uint_as_float(g));
-            if (!BASELINE) {
-                Cc = __ldg(rgbv + g);
-                if (cullmode & 1)
-                    keep = !tile_culled(A.x, A.y, A.z, A.w, B.x, q.w, Cc.w, (float)(tx * TILE),
-                                        (float)(ty * TILE), (float)TILE);
-                const uint32_t m = (cullmode & 2) ? strip_mask<TILE>(A.y, A.z, A.w, B.x, q.w, Cc.w, (float)(ty * TILE))
-                                                  : 0xffffffffu;
-                keep = keep && m != 0u;
-                Cc.w = __uint_as_float(m);  // the colour record carries the mask
-            }
-        }
-        int cnt, pos;
-        if (BASELINE) {
-            pos = threadIdx.x;
-            cnt = min(BATCH, n_entries - b0);
-        } else {
-            // order-preserving compaction of the kept entries
-            const unsigned ball = __ballot_sync(0xffffffffu, keep);
-            if (lane == 0 && warp < NW) sh.wc[warp] = __popc(ball);
-            __syncthreads();
-            int wp = 0;
-            cnt = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                const int c = sh.wc[w];
-                wp += (w < warp) ? c : 0;
-                cnt += c;
-            }
-            pos = wp + __popc(ball & ((1u << lane) - 1u));
-        }
-        if (keep) {
-            sh.a[pos] = A;
-            sh.b[pos] = B;
-            if (BASELINE) sh.g[pos] = g;
-            else sh.c[pos] = Cc;
-        }
+        const int cnt = stage_batch<TILE, BASELINE>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
         __syncthreads();
         if (!st.done) {
             for (int k = 0; k < cnt; ++k) {
@@ -185,6 +98,22 @@ __device__ __forceinline__ bool raster_span(const uint64_t* src, int32_t n_entri
     return false;
 }
 
+template <int TILE, bool BASELINE, bool COUNT>
+struct FwdSpan {
+    RasterShared<TILE, BASELINE>& sh;
+    const float4* __restrict__ xy_ab;
+    const float4* __restrict__ c_o_z;
+    const float4* __restrict__ rgbv;
+    int cullmode, tx, ty;
+    float pxc, pyc;
+    PixelState& st;
+    __device__ __forceinline__ bool operator()(const uint64_t* src, int32_t n)
+    {
+        return raster_span<TILE, BASELINE, COUNT>(src, n, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st);
+    }
+    __device__ __forceinline__ bool done() const { return st.done; }
+};
+
 // LAZY (EXACT mode with the repair in the raster): the tile's segments are
 // walked front to back; each segment of 2..kRasterSortCap entries is loaded
 // into shared memory and sorted by (depth bits, gid) right before it is
@@ -197,10 +126,8 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
          float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
          int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total)
 {
-    constexpr int BS = TILE * TILE;
     __shared__ RasterShared<TILE, BASELINE> sh;
-    __shared__ uint64_t s_sort[LAZY ? kRasterSortCap : 1];
-    __shared__ int32_t s_off[LAZY ? GS_MAX_K + 1 : 1];
+    __shared__ WalkShared<LAZY> ws;
 
     const int t = blockIdx.x;
     const int tx = t % a.tiles_x, ty = t / a.tiles_x;
@@ -221,67 +148,8 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
     st.ops = 0;
     st.done = !inside;
 
-    if (!LAZY) {
-        const int32_t s0 = off[(int64_t)t * a.stride], s1 = off[(int64_t)(t + 1) * a.stride];
-        raster_span<TILE, BASELINE, COUNT>(words + s0, s1 - s0, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc,
-                                           st);
-    } else {
-        // chunks of consecutive segments (at most kRasterSortCap entries) are
-        // loaded into shared memory, every segment of the chunk is sorted
-        // (small ones by one warp each, long ones by the whole block), and the
-        // chunk is streamed in full batches across segment boundaries
-        constexpr int NWB = BS / 32;
-        __shared__ int s_big[GS_MAX_K];
-        __shared__ int s_nbig;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const int K = a.stride;
-        for (int b = threadIdx.x; b <= K; b += BS) s_off[b] = off[(int64_t)t * K + b];
-        __syncthreads();
-        int b = 0;
-        while (b < K) {
-            const int32_t c0 = s_off[b];
-            if (s_off[b + 1] - c0 > kRasterSortCap) {  // sorted before the raster
-                if (raster_span<TILE, BASELINE, COUNT>(words + c0, s_off[b + 1] - c0, sh, xy_ab, c_o_z, rgbv,
-                                                       cullmode, tx, ty, pxc, pyc, st))
-                    break;
-                ++b;
-                continue;
-            }
-            int e = b + 1;
-            while (e < K && s_off[e + 1] - c0 <= kRasterSortCap) ++e;
-            const int32_t len = s_off[e] - c0;
-            const int bfirst = b;
-            b = e;
-            if (len == 0) continue;
-            if (__syncthreads_count(st.done) == BS) break;
-            for (int i = threadIdx.x; i < len; i += BS) s_sort[i] = words[c0 + i];
-            if (threadIdx.x == 0) s_nbig = 0;
-            __syncthreads();
-            for (int j = bfirst + warp; j < e; j += NWB) {
-                const int l = s_off[j + 1] - s_off[j];
-                uint64_t* seg = s_sort + (s_off[j] - c0);
-                if (l < 2) continue;
-                if (l <= 32) {
-                    uint64_t v = lane < l ? seg[lane] : ~0ull;
-                    v = warp_bitonic32(v);
-                    if (lane < l) seg[lane] = v;
-                } else if (l <= 256) {
-                    bitonic_mem(seg, l, lane, 32, SyncWarp{});
-                } else if (lane == 0) {
-                    s_big[atomicAdd(&s_nbig, 1)] = j;
-                }
-            }
-            __syncthreads();
-            const int nbig = s_nbig;
-            for (int k = 0; k < nbig; ++k) {
-                const int j = s_big[k];
-                bitonic_mem(s_sort + (s_off[j] - c0), s_off[j + 1] - s_off[j], threadIdx.x, BS, SyncBlock{});
-            }
-            if (raster_span<TILE, BASELINE, COUNT>(s_sort, len, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc,
-                                                   st))
-                break;
-        }
-    }
+    FwdSpan<TILE, BASELINE, COUNT> span{sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st};
+    walk_tile<TILE, LAZY>(words, off, t, a.stride, ws, span);
     if (inside) {
         const int64_t p = (int64_t)py * a.width + px;
         out_rgb[3 * p] = fmaf(st.T, a.bg0, st.C0);

@@ -1,0 +1,257 @@
+// raster_bwd.cu -- K22: backward of the tile compositing.  The paper leaves
+// the backward pass to future work and requires it to follow the forward's
+// compositing order (Sec. 7); this kernel walks every tile's span exactly as
+// the forward does (raster_common.cuh: same staging, culls and, for EXACT
+// streams, the same in-raster segment sorts), one CTA per tile and one thread
+// per pixel.
+//
+// Each pixel recomputes the forward front to back with the forward's float32
+// operations, so its skip / stop / clamp decisions and its transmittance T_i
+// are bit-identical to the forward's; nothing is divided back out of the
+// final T.  With out = sum_i c_i a_i T_i + T_N bg (the forward's output),
+// S_i = out - sum_{j<=i} c_j a_j T_j (what lies behind entry i, background
+// included) and G = dL/dout, dA = dL/dalpha_out:
+//   dL/da_i = (G.c_i) T_i - (G.S_i - dA T_N) / (1 - a_i)
+//           = (G.c_i) T_i - (K - D_i) / (1 - a_i),
+//   K = G.out - dA T_N (per pixel),  D_i = sum_{j<=i} (G.c_j) a_j T_j,
+//   dL/dc_i = G a_i T_i;  and, unless the clamp a_i = 0.99 is active,
+//   with v_i = dL/da_i exp(-q_i):  dL/do_i = v_i,  dL/dq_i = -o_i v_i,
+//   q = 1/2 (a dx^2 + 2 b dx dy + c dy^2), d = mean - pixel centre.
+// Per entry the warp sums nine per-pixel terms (v, v dx, v dy, v dx^2,
+// v dx dy, v dy^2, G a T), the per-Gaussian factors (o, conic) are applied
+// once per tile, and the tile's sums go to global memory with one vector
+// atomic per gradient field per entry.
+#include "raster_common.cuh"
+
+namespace gs {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kTerms = 9;
+
+struct GradState {
+    float T;              // transmittance before the next entry (the forward's)
+    float D;              // sum over the applied entries so far of (G.c) a T
+    float K;              // G.out - dA T_N
+    float G0, G1, G2;     // dL/dout
+    bool done;
+};
+
+// Sums over the warp of eight per-lane values by a transposing butterfly
+// (12 shuffles instead of 40): returns in every lane the warp total of value
+// (lane >> 2) & 7.
+__device__ __forceinline__ float warp_sum8(const float (&v)[8], int lane)
+{
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float w[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        const float send = h16 ? v[s] : v[4 + s];
+        const float keep = h16 ? v[4 + s] : v[s];
+        w[s] = keep + __shfl_xor_sync(kFull, send, 16);
+    }
+    float x[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const float send = h8 ? w[s] : w[2 + s];
+        const float keep = h8 ? w[2 + s] : w[s];
+        x[s] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+    float y = (h4 ? x[1] : x[0]) + __shfl_xor_sync(kFull, h4 ? x[0] : x[1], 4);
+    y += __shfl_xor_sync(kFull, y, 2);
+    y += __shfl_xor_sync(kFull, y, 1);
+    return y;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+template <int TILE>
+struct BwdSpan {
+    using SH = RasterShared<TILE, false>;
+    static constexpr int BS = SH::BS, BATCH = SH::BATCH;
+    SH& sh;
+    float* acc;  // [BATCH][kTerms] shared
+    const float4* __restrict__ xy_ab;
+    const float4* __restrict__ c_o_z;
+    const float4* __restrict__ rgbv;
+    float4* __restrict__ g_xy_ab;
+    float4* __restrict__ g_c_o_z;
+    float4* __restrict__ g_rgb;
+    int cullmode, tx, ty;
+    float pxc, pyc;
+    GradState& st;
+
+    __device__ __forceinline__ bool done() const { return st.done; }
+
+    __device__ __forceinline__ bool operator()(const uint64_t* src, int32_t n_entries)
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        for (int32_t b0 = 0; b0 < n_entries; b0 += BATCH) {
+            if (__syncthreads_count(st.done) == BS) return true;
+            const int cnt = stage_batch<TILE, false>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
+            __syncthreads();
+            for (int k = 0; k < cnt; ++k) {
+                if (!((__float_as_uint(sh.c[k].w) >> warp) & 1u)) continue;  // warp-uniform
+                float v = 0.0f, wgt = 0.0f, dx = 0.0f, dy = 0.0f;
+                bool contrib = false;
+                if (!st.done) {
+                    const float4 ga = sh.a[k];
+                    const float4 gb = sh.b[k];
+                    dx = ga.x - pxc;
+                    dy = ga.y - pyc;
+                    const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
+                    if (__float_as_uint(q) <= __float_as_uint(gb.z)) {
+                        const float e = spec_exp_core(-q);
+                        const float oe = gb.y * e;
+                        const float alpha = fminf(0.99f, oe);
+                        if (alpha >= 1.0f / 255.0f) {
+                            const float om = 1.0f - alpha;
+                            const float Tn = st.T * om;
+                            if (Tn < 1e-4f) {
+                                st.done = true;
+                            } else {
+                                const float4 col = sh.c[k];
+                                wgt = alpha * st.T;
+                                const float gc = fmaf(st.G2, col.z, fmaf(st.G1, col.y, st.G0 * col.x));
+                                st.D = fmaf(gc, wgt, st.D);
+                                const float dl_da = fmaf(gc, st.T, -__fdividef(st.K - st.D, om));
+                                v = oe <= 0.99f ? dl_da * e : 0.0f;
+                                st.T = Tn;
+                                contrib = true;
+                            }
+                        }
+                    }
+                }
+                if (__ballot_sync(kFull, contrib) == 0u) {
+                    if (__all_sync(kFull, st.done)) break;
+                    continue;
+                }
+                const float vx = v * dx, vy = v * dy;
+                const float t8[8] = {v, vx, vy, vx * dx, vx * dy, vy * dy, wgt * st.G0, wgt * st.G1};
+                const float s8 = warp_sum8(t8, lane);
+                const float s9 = warp_sum(wgt * st.G2);
+                if ((lane & 3) == 0) atomicAdd(acc + k * kTerms + ((lane >> 2) & 7), s8);
+                else if (lane == 1) atomicAdd(acc + k * kTerms + 8, s9);
+            }
+            __syncthreads();
+            // the tile's sums of this batch -> per-Gaussian gradients
+            if ((int)threadIdx.x < cnt) {
+                float s[kTerms];
+                bool any = false;
+#pragma unroll
+                for (int j = 0; j < kTerms; ++j) {
+                    s[j] = acc[threadIdx.x * kTerms + j];
+                    acc[threadIdx.x * kTerms + j] = 0.0f;
+                    any = any || s[j] != 0.0f;
+                }
+                if (any) {
+                    const float4 A = sh.a[threadIdx.x], B = sh.b[threadIdx.x];
+                    const uint32_t g = __float_as_uint(B.w);
+                    const float o = B.y, ca = 2.0f * A.z, cb = A.w, cc = 2.0f * B.x;
+                    atomicAdd(g_xy_ab + g, make_float4(-o * fmaf(ca, s[1], cb * s[2]), -o * fmaf(cb, s[1], cc * s[2]),
+                                                       -0.5f * o * s[3], -o * s[4]));
+                    atomicAdd(reinterpret_cast<float2*>(g_c_o_z + g), make_float2(-0.5f * o * s[5], s[0]));
+                    atomicAdd(g_rgb + g, make_float4(s[6], s[7], s[8], 0.0f));
+                }
+            }
+        }
+        return false;
+    }
+};
+
+template <int TILE, bool LAZY>
+__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 4 : 1)
+k_raster_bwd(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
+             const uint64_t* __restrict__ words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
+             const float* __restrict__ out_rgb, const float* __restrict__ out_alpha,
+             const float* __restrict__ dl_drgb, const float* __restrict__ dl_dalpha, float4* __restrict__ g_xy_ab,
+             float4* __restrict__ g_c_o_z, float4* __restrict__ g_rgb)
+{
+    using SH = RasterShared<TILE, false>;
+    __shared__ SH sh;
+    __shared__ WalkShared<LAZY> ws;
+    __shared__ float acc[SH::BATCH * kTerms];
+
+    const int t = blockIdx.x;
+    const int tx = t % a.tiles_x, ty = t / a.tiles_x;
+    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int px = tx * TILE + lx, py = ty * TILE + ly;
+    const bool inside = px < a.width && py < a.height;
+
+    for (int i = threadIdx.x; i < SH::BATCH * kTerms; i += SH::BS) acc[i] = 0.0f;
+
+    GradState st;
+    st.T = 1.0f;
+    st.D = 0.0f;
+    st.K = 0.0f;
+    st.G0 = st.G1 = st.G2 = 0.0f;
+    st.done = !inside;
+    if (inside) {
+        const int64_t p = (int64_t)py * a.width + px;
+        st.G0 = dl_drgb[3 * p];
+        st.G1 = dl_drgb[3 * p + 1];
+        st.G2 = dl_drgb[3 * p + 2];
+        const float dA = dl_dalpha ? dl_dalpha[p] : 0.0f;
+        const float TN = 1.0f - out_alpha[p];
+        st.K = fmaf(st.G2, out_rgb[3 * p + 2], fmaf(st.G1, out_rgb[3 * p + 1], st.G0 * out_rgb[3 * p])) - dA * TN;
+    }
+    __syncthreads();
+
+    BwdSpan<TILE> span{sh,      acc,     xy_ab, c_o_z, rgbv, g_xy_ab, g_c_o_z, g_rgb, cullmode, tx,
+                       ty,      (float)px + 0.5f, (float)py + 0.5f, st};
+    walk_tile<TILE, LAZY>(words, off, t, a.stride, ws, span);
+}
+
+template <int TILE>
+void launch_bwd(bool lazy, unsigned grid, cudaStream_t st, const ProjView& pv, const uint64_t* words,
+                const int32_t* off, const RasterArgs& a, int cull, const float* out_rgb, const float* out_alpha,
+                const float* dl_drgb, const float* dl_dalpha, const GradView& gv)
+{
+    if (lazy)
+        k_raster_bwd<TILE, true><<<grid, TILE * TILE, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, cull,
+                                                               out_rgb, out_alpha, dl_drgb, dl_dalpha, gv.xy_ab,
+                                                               gv.c_o_z, gv.rgb);
+    else
+        k_raster_bwd<TILE, false><<<grid, TILE * TILE, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, cull,
+                                                                out_rgb, out_alpha, dl_drgb, dl_dalpha, gv.xy_ab,
+                                                                gv.c_o_z, gv.rgb);
+}
+
+}  // namespace
+
+int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
+               int32_t stride, const float* out_rgb, const float* out_alpha, const float* dl_drgb,
+               const float* dl_dalpha, const GradView& gv, cudaStream_t st)
+{
+    const int tile = ctx->cfg.tile_size;
+    RasterArgs a;
+    a.width = cam->width;
+    a.height = cam->height;
+    a.tiles_x = (cam->width + tile - 1) / tile;
+    a.n_tiles = gs_num_tiles(cam->width, cam->height, tile);
+    a.stride = stride;
+    a.bg0 = a.bg1 = a.bg2 = 0.0f;  // the background enters only through out_rgb
+    const bool lazy = ctx->cfg.mode == GS_MODE_BINNED_EXACT && ctx->cfg.repair_in_raster;
+    // the staging culls are conservative, so they change no decision: EXACT
+    // streams were culled when built (strip mask only), the others are culled
+    // here as in the binned forward
+    const int cull = !ctx->cfg.tile_cull ? 0 : (ctx->cfg.mode == GS_MODE_BINNED_EXACT ? 2 : 3);
+    const unsigned grid = (unsigned)a.n_tiles;
+    if (grid == 0) return GS_OK;
+    switch (tile) {
+        case 8: launch_bwd<8>(lazy, grid, st, pv, words, offsets, a, cull, out_rgb, out_alpha, dl_drgb, dl_dalpha, gv); break;
+        case 32: launch_bwd<32>(lazy, grid, st, pv, words, offsets, a, cull, out_rgb, out_alpha, dl_drgb, dl_dalpha, gv); break;
+        default: launch_bwd<16>(lazy, grid, st, pv, words, offsets, a, cull, out_rgb, out_alpha, dl_drgb, dl_dalpha, gv); break;
+    }
+    ctx->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+}  // namespace gs

@@ -1,0 +1,193 @@
+// raster_common.cuh -- what the forward raster (raster.cu) and its backward
+// (raster_bwd.cu) share: the batch staging of a tile's entries into shared
+// memory (with the conservative tile-alpha cull and the per-warp strip mask)
+// and the walk over a tile's span -- either the whole span at once, or, for
+// EXACT streams whose repair runs in the raster, chunk by chunk with each
+// segment of 2..kRasterSortCap entries sorted in shared memory by (depth bits,
+// gid) right before it is composited (Sec. 3.5 selective repair; supplement,
+// binned raster traversal after repair).  Both kernels therefore visit every
+// tile's entries in the same order.
+#pragma once
+#include "device.cuh"
+
+namespace gs {
+
+struct RasterArgs {
+    int width, height, tiles_x, n_tiles, stride;
+    float bg0, bg1, bg2;
+};
+
+template <int TILE, bool BASELINE>
+struct RasterShared {
+    static constexpr int BS = TILE * TILE;
+    static constexpr int BATCH = BS < 256 ? BS : 256;  // entries staged per batch
+    static constexpr int NW = BATCH / 32;              // warps that load a batch
+    float4 a[BATCH];                       // {mx, my, a/2, b}
+    float4 b[BATCH];                       // {c/2, o, tau, gid bits}
+    float4 c[BASELINE ? 1 : BATCH];        // colour (binned)
+    uint32_t g[BASELINE ? BATCH : 1];      // gid (baseline colour lookup)
+    int wc[NW];
+};
+
+// Rows of the tile a warp owns: the strip mask bit w is set when the
+// entry's alpha >= 1/255 ellipse (the tile cull's bound tau / margin, widened
+// as there) can reach rows [y0 + w*RPW, y0 + (w+1)*RPW) of the tile.
+template <int TILE>
+__device__ __forceinline__ uint32_t strip_mask(float my, float ha, float hb, float hc, float tau, float margin,
+                                               float y0)
+{
+    constexpr int RPW = 32 / TILE > 0 ? 32 / TILE : 1;  // pixel rows per warp
+    constexpr int NWT = TILE * TILE / 32;               // warps per tile
+    const uint32_t all = NWT >= 32 ? 0xffffffffu : ((1u << NWT) - 1u);
+    if (!(margin > 0.0f)) return all;
+    const float D = 4.0f * ha * hc - hb * hb;
+    const float tp = tau / margin;
+    if (!(D > 0.0f) || !(tp > 0.0f)) return all;
+    const float dymax = sqrtf(4.0f * ha * tp / D) * (1.0f + 5e-3f) + 0.05f;
+    // pixel rows (centres y0 + row + 0.5) with |my - py| <= dymax
+    const float rlo = fmaxf(ceilf(my - dymax - y0 - 0.5f), 0.0f);
+    const float rhi = fminf(floorf(my + dymax - y0 - 0.5f), (float)(TILE - 1));
+    if (rlo > rhi) return 0u;
+    const int wlo = (int)rlo / RPW, whi = (int)rhi / RPW;
+    const uint32_t upto = whi >= 31 ? 0xffffffffu : ((2u << whi) - 1u);
+    return upto & ~((1u << wlo) - 1u) & all;
+}
+
+// Stage the batch [b0, b0 + BATCH) of n_entries stream words from src (global
+// or shared memory): per entry {mx, my, a/2, b}, {c/2, o, tau, gid bits} and,
+// binned, the colour with the strip mask in .w.  Entries the tile cull or the
+// strip mask drop are compacted away in order.  Returns the number staged
+// (block-uniform); the caller synchronises the block before reading sh.
+template <int TILE, bool BASELINE>
+__device__ __forceinline__ int stage_batch(const uint64_t* src, int32_t b0, int32_t n_entries,
+                                           RasterShared<TILE, BASELINE>& sh, const float4* __restrict__ xy_ab,
+                                           const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
+                                           int cullmode, int tx, int ty)
+{
+    using SH = RasterShared<TILE, BASELINE>;
+    constexpr int BATCH = SH::BATCH, NW = SH::NW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t idx = b0 + threadIdx.x;
+    const bool valid = threadIdx.x < BATCH && idx < n_entries;
+    float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, Cc = A;
+    uint32_t g = 0;
+    bool keep = valid;
+    if (valid) {
+        g = (uint32_t)(src[idx] & 0xffffffffull);
+        const float4 p = __ldg(xy_ab + g);
+        const float4 q = __ldg(c_o_z + g);
+        A = make_float4(p.x, p.y, 0.5f * p.z, p.w);
+        B = make_float4(0.5f * q.x, q.y, q.w, __uint_as_float(g));
+        if (!BASELINE) {
+            Cc = __ldg(rgbv + g);
+            if (cullmode & 1)
+                keep = !tile_culled(A.x, A.y, A.z, A.w, B.x, q.w, Cc.w, (float)(tx * TILE), (float)(ty * TILE),
+                                    (float)TILE);
+            const uint32_t m = (cullmode & 2) ? strip_mask<TILE>(A.y, A.z, A.w, B.x, q.w, Cc.w, (float)(ty * TILE))
+                                              : 0xffffffffu;
+            keep = keep && m != 0u;
+            Cc.w = __uint_as_float(m);  // the colour record carries the mask
+        }
+    }
+    int cnt, pos;
+    if (BASELINE) {
+        pos = threadIdx.x;
+        cnt = min(BATCH, n_entries - b0);
+    } else {
+        // order-preserving compaction of the kept entries
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0 && warp < NW) sh.wc[warp] = __popc(ball);
+        __syncthreads();
+        int wp = 0;
+        cnt = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int c = sh.wc[w];
+            wp += (w < warp) ? c : 0;
+            cnt += c;
+        }
+        pos = wp + __popc(ball & ((1u << lane) - 1u));
+    }
+    if (keep) {
+        sh.a[pos] = A;
+        sh.b[pos] = B;
+        if (BASELINE) sh.g[pos] = g;
+        else sh.c[pos] = Cc;
+    }
+    return cnt;
+}
+
+// Shared memory of the tile walk.
+template <bool LAZY>
+struct WalkShared {
+    uint64_t sort[LAZY ? kRasterSortCap : 1];
+    int32_t off[LAZY ? GS_MAX_K + 1 : 1];
+    int big[LAZY ? GS_MAX_K : 1];
+    int nbig;
+};
+
+// Walk tile t's span of the stream front to back, handing runs of entries to
+// span(src, n) (returns true, block-uniformly, once every pixel of the tile
+// has terminated; span.done() is the calling thread's termination flag).
+// Not LAZY: one run, the span [off[t*K], off[(t+1)*K]).  LAZY: chunks of
+// consecutive segments of at most kRasterSortCap entries are loaded into
+// shared memory and every segment of the chunk is sorted (small ones by one
+// warp each, long ones by the whole block); a segment longer than the cap was
+// sorted before the raster and is handed over in place.
+template <int TILE, bool LAZY, class Span>
+__device__ __forceinline__ void walk_tile(const uint64_t* __restrict__ words, const int32_t* __restrict__ off,
+                                          int t, int K, WalkShared<LAZY>& ws, Span& span)
+{
+    constexpr int BS = TILE * TILE;
+    if (!LAZY) {
+        const int32_t s0 = off[(int64_t)t * K], s1 = off[(int64_t)(t + 1) * K];
+        span(words + s0, s1 - s0);
+        return;
+    }
+    constexpr int NWB = BS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int b = threadIdx.x; b <= K; b += BS) ws.off[b] = off[(int64_t)t * K + b];
+    __syncthreads();
+    int b = 0;
+    while (b < K) {
+        const int32_t c0 = ws.off[b];
+        if (ws.off[b + 1] - c0 > kRasterSortCap) {  // sorted before the raster
+            if (span(words + c0, ws.off[b + 1] - c0)) break;
+            ++b;
+            continue;
+        }
+        int e = b + 1;
+        while (e < K && ws.off[e + 1] - c0 <= kRasterSortCap) ++e;
+        const int32_t len = ws.off[e] - c0;
+        const int bfirst = b;
+        b = e;
+        if (len == 0) continue;
+        if (__syncthreads_count(span.done()) == BS) break;
+        for (int i = threadIdx.x; i < len; i += BS) ws.sort[i] = words[c0 + i];
+        if (threadIdx.x == 0) ws.nbig = 0;
+        __syncthreads();
+        for (int j = bfirst + warp; j < e; j += NWB) {
+            const int l = ws.off[j + 1] - ws.off[j];
+            uint64_t* seg = ws.sort + (ws.off[j] - c0);
+            if (l < 2) continue;
+            if (l <= 32) {
+                uint64_t v = lane < l ? seg[lane] : ~0ull;
+                v = warp_bitonic32(v);
+                if (lane < l) seg[lane] = v;
+            } else if (l <= 256) {
+                bitonic_mem(seg, l, lane, 32, SyncWarp{});
+            } else if (lane == 0) {
+                ws.big[atomicAdd(&ws.nbig, 1)] = j;
+            }
+        }
+        __syncthreads();
+        const int nbig = ws.nbig;
+        for (int k = 0; k < nbig; ++k) {
+            const int j = ws.big[k];
+            bitonic_mem(ws.sort + (ws.off[j] - c0), ws.off[j + 1] - ws.off[j], threadIdx.x, BS, SyncBlock{});
+        }
+        if (span(ws.sort, len)) break;
+    }
+}
+
+}  // namespace gs

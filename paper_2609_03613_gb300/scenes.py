@@ -210,6 +210,14 @@ def grad_check_scene(n: int = 64, seed: int = 6) -> tuple[Scene, Camera]:
     return scene, cam
 
 
+def incoming_grads(height: int, width: int, seed: int = 5):
+    """Seeded upstream gradients dL/drgb [H,W,3] and dL/dalpha [H,W] (N(0,1), float32)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dC = rng.normal(0.0, 1.0, (height, width, 3)).astype(np.float32)
+    dA = rng.normal(0.0, 1.0, (height, width)).astype(np.float32)
+    return dC, dA
+
+
 def workload(name: str):
     """Named workloads: returns (scene, camera or list of cameras)."""
     if name == "tiny":

@@ -35,6 +35,7 @@ EXPORTS = [
     "gs_isect_offset", "gs_num_tiles", "gs_project", "gs_tile_intersect", "gs_sort_or_bin",
     "gs_depth_range", "gs_bin_build", "gs_repair", "gs_rasterize_fwd", "gs_render",
     "gs_last_entry_count", "gs_launch_count", "gs_last_raster_ops", "gs_depth_range_noalloc",
+    "gs_grad2d_bytes", "gs_grad2d_offset", "gs_rasterize_bwd",
 ]
 
 
@@ -117,6 +118,9 @@ def lib():
         "gs_last_raster_ops": (i64, [vp, vp]),
         "gs_depth_range_noalloc": (C.c_int, [C.POINTER(GsConfig), vp, vp, i64, C.POINTER(GsCamera), vp, i64,
                                              vp, vp, vp]),
+        "gs_grad2d_bytes": (sz, [i64]),
+        "gs_grad2d_offset": (sz, [i64, i32]),
+        "gs_rasterize_bwd": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -344,6 +348,24 @@ class Context:
         return (rgb, alpha, last, nt) if count_tests else (rgb, alpha, last)
 
     # ------------------------------------------------------------- whole frame
+    def rasterize_bwd(self, projected, n, cam, words, offsets, rgb, alpha, dl_drgb, dl_dalpha=None,
+                      stride=None, grad=None):
+        """Backward of rasterize_fwd: returns the gradient buffer (uint8,
+        gs_grad2d_bytes(n)); grad_fields() gives its [n,4] float views."""
+        import torch
+        if grad is None:
+            grad = torch.empty(int(lib().gs_grad2d_bytes(n)), dtype=torch.uint8, device=projected.device)
+        for t, shape in ((rgb, (cam.height, cam.width, 3)), (alpha, (cam.height, cam.width)),
+                         (dl_drgb, (cam.height, cam.width, 3)),
+                         (dl_dalpha, (cam.height, cam.width))):
+            if t is not None and (t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shape):
+                raise TileGSError(f"gs_rasterize_bwd: expected a contiguous float32 tensor of shape {shape}")
+        c = gs_camera(cam)
+        check(lib().gs_rasterize_bwd(self.h, _ptr(projected), n, C.byref(c), _ptr(words), _ptr(offsets),
+                                     self.stride if stride is None else int(stride), _ptr(rgb), _ptr(alpha),
+                                     _ptr(dl_drgb), _ptr(dl_dalpha), _ptr(grad), _stream()), "gs_rasterize_bwd")
+        return grad
+
     def render(self, sc: DeviceScene, cam, bg=(0.0, 0.0, 0.0), out=None, flags=0):
         """One frame through gs_render (all intermediates in context scratch)."""
         import torch
@@ -383,6 +405,17 @@ def projected_fields(projected, n):
     rect = projected[o[3]:o[3] + 8 * n].view(torch.int32).view(n, 2)
     radius = projected[o[4]:o[4] + 4 * n].view(torch.int32)
     return dict(xy_ab=xy_ab, c_o_z=c_o_z, rgb=rgb, rect=rect, radius=radius)
+
+
+def grad_fields(grad, n):
+    """[n,4] float32 views of a gs_rasterize_bwd gradient buffer, keyed like
+    the projected fields they differentiate: xy_ab {dmx, dmy, da, db},
+    c_o_z {dc, dopacity, 0, 0}, rgb {dr, dg, db, 0}."""
+    import torch
+    L = lib()
+    o = [int(L.gs_grad2d_offset(n, f)) for f in range(3)]
+    return {k: grad[o[f]:o[f] + 16 * n].view(torch.float32).view(n, 4)
+            for f, k in enumerate(("xy_ab", "c_o_z", "rgb"))}
 
 
 def depth_range_noalloc(cfg: GsConfig, projected, scales, n, cam, isect, m_cap, m_dev, zrange):

@@ -170,3 +170,15 @@ def test_grad_abs_sums_bound_the_gradient():
     g = O.composite_grad(proj, off, words, cam.width, cam.height, dC, dA, bg=(0.2, 0.1, 0.3), with_abs=True)
     flat = np.concatenate([g["mean2d"], g["conic"], g["opacity"][:, None], g["rgb"]], axis=1)
     assert np.all(np.abs(flat) <= g["abs"] * (1 + 1e-12))
+
+
+def test_grad_tile_subsets_partition_the_frame():
+    # per-pixel terms only: the gradients of complementary tile subsets add up to the whole frame's
+    sc, cam, proj, off, words, rgb, alpha, dC, dA = _grad_case()
+    W, H = cam.width, cam.height
+    full = O.composite_grad(proj, off, words, W, H, dC, dA, bg=(0.2, 0.1, 0.3))
+    a = O.composite_grad(proj, off, words, W, H, dC, dA, bg=(0.2, 0.1, 0.3), tiles=[0, 3])
+    b = O.composite_grad(proj, off, words, W, H, dC, dA, bg=(0.2, 0.1, 0.3), tiles=[1, 2])
+    for k in full:
+        np.testing.assert_allclose(a[k] + b[k], full[k], rtol=1e-12, atol=1e-14)
+        assert np.any(a[k] != full[k])
