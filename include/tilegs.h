@@ -265,6 +265,11 @@ int gs_depth_range_noalloc(const gs_config* cfg, const void* projected, const fl
  *   bg: HOST float[3].  rgb [H,W,3], alpha [H,W] (= 1 - T), last [H,W] (id of
  *   the last applied Gaussian, -1 if none); ntests [H,W] optional: entries
  *   each pixel visited, the stopping one included.
+ *   final_T [H,W] and tile_end [T] (both optional, for gs_rasterize_bwd): the
+ *   final transmittance T of each pixel (exact; alpha = 1 - T is rounded),
+ *   and per tile the stream index at which its compositing ended (the span
+ *   end, or the position in compositing order where every pixel of the tile
+ *   had stopped).
  * The GLOBAL kernel is the plain baseline (gsplat-style batch staging); the
  * binned kernel adds the conservative tile-alpha cull and colour staging of
  * the paper's default configuration.  Both give identical images.
@@ -272,20 +277,22 @@ int gs_depth_range_noalloc(const gs_config* cfg, const void* projected, const fl
 int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
                      const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
                      const float* bg, float* rgb, float* alpha, int32_t* last, int32_t* ntests,
-                     void* stream);
+                     float* final_T, int32_t* tile_end, void* stream);
 
 /*
  * Backward of gs_rasterize_fwd: the gradient of a loss L(rgb, alpha) w.r.t.
  * the projected 2D parameters.  The paper has no backward (Sec. 7 leaves it
  * to future work and asks that it follow the forward's compositing order);
- * this one walks every tile's span in exactly the forward's order, with the
- * forward's float32 decisions, for the same stream, offsets and context
- * configuration, and differentiates
+ * this one walks each tile's span in the forward's order reversed, from the
+ * forward's tile_end back to the span start, for the same stream, offsets
+ * and context configuration, and differentiates
  *   rgb = sum_i c_i a_i T_i + T_N bg,  alpha = 1 - T_N,
  *   a_i = min(0.99, o_i exp(-q_i)),  q_i = 1/2 d^T conic d,  d = mean - centre
- * (a clamped a_i passes no gradient to o_i or q_i; skipped entries and
- * entries after the stop get none).
- *   rgb, alpha: the forward's outputs [H,W,3], [H,W] for these inputs and bg.
+ * over the entries the forward applied (its float32 skip tests are repeated
+ * bit for bit; T_i is recovered from the saved final T as T_{i+1}/(1 - a_i);
+ * a clamped a_i passes no gradient to o_i or q_i).
+ *   bg: HOST float[3], the forward's.  last, final_T, tile_end: the forward's
+ *   outputs for these inputs.
  *   dl_drgb [H,W,3], dl_dalpha [H,W] (nullable: 0): dL/drgb, dL/dalpha.
  *   grad: caller-owned, 256-byte aligned, gs_grad2d_bytes(n) bytes, zeroed
  *   and then written; field f at gs_grad2d_offset(n, f):
@@ -302,8 +309,8 @@ size_t gs_grad2d_bytes(int64_t n);
 size_t gs_grad2d_offset(int64_t n, int32_t field);
 int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
                      const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
-                     const float* rgb, const float* alpha, const float* dl_drgb, const float* dl_dalpha,
-                     void* grad, void* stream);
+                     const float* bg, const int32_t* last, const float* final_T, const int32_t* tile_end,
+                     const float* dl_drgb, const float* dl_dalpha, void* grad, void* stream);
 
 /* ---------------------------------------------------------------- whole frame */
 typedef struct gs_scene {

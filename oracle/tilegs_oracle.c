@@ -764,9 +764,12 @@ void orc_set_threads(int n)
  * zero incoming gradient elsewhere).  A clamped alpha (o exp(-q) > 0.99 in
  * float32) passes no gradient to o or q.  Gradients are added into
  * g_mean2d [n,2], g_conic [n,3], g_opac [n], g_rgb [n,3] (double,
- * caller-zeroed); g_abs [n,9] (nullable) receives the sums of the absolute
- * per-pixel terms in the order (mx, my, a, b, c, o, r, g, b), the scale of
- * the rounding error any float32 summation of the same terms can make.
+ * caller-zeroed); g_abs [n,9] (nullable) receives, in the order
+ * (mx, my, a, b, c, o, r, g, b), the error scale of a float32 evaluation:
+ * the sums over pixels of each term's magnitude with dL/da replaced by
+ * |G.c| T_i + (|G|.S_i + |dA| T_N) / (1 - a_i) -- the magnitudes of the two
+ * parts dL/da is the difference of (|G| and S taken per channel, S the
+ * colour behind the entry, background included).
  */
 void orc_composite_grad(const float* mean2d, const float* conic, const float* opac, const float* rgb,
                         const int32_t* offsets, int K, const uint64_t* stream, int width, int height,
@@ -825,6 +828,8 @@ void orc_composite_grad(const float* mean2d, const float* conic, const float* op
                 /* back to front: S = colour composited behind the entry (incl. background) */
                 double S[3] = {Tf * bg[0], Tf * bg[1], Tf * bg[2]};
                 double Tb = Tf; /* transmittance after the entry */
+                double Gabs[3], dCmag = 0.0;
+                for (int ch = 0; ch < 3; ++ch) Gabs[ch] = fabs((double)dl_drgb[3 * p + ch]);
                 for (int64_t k = na - 1; k >= 0; --k) {
                     const int32_t g = applied[k];
                     const double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
@@ -834,30 +839,33 @@ void orc_composite_grad(const float* mean2d, const float* conic, const float* op
                     const double a = clamped[k] ? 0.99 : opac[g] * G;
                     const double Ti = Tb / (1.0 - a); /* transmittance before the entry */
                     double dl_da = dA * Tf / (1.0 - a);
-                    double term[9];
+                    double term[9], absdl = fabs(dA) * Tf;
+                    dCmag = 0.0;
                     for (int ch = 0; ch < 3; ++ch) {
                         const double dC = dl_drgb[3 * p + ch];
                         term[6 + ch] = dC * a * Ti;
                         dl_da += dC * (rgb[3 * g + ch] * Ti - S[ch] / (1.0 - a));
+                        dCmag += Gabs[ch] * fabs((double)rgb[3 * g + ch]);
+                        absdl += Gabs[ch] * fabs(S[ch]);
                     }
-                    if (!clamped[k]) {
-                        const double dl_dq = -dl_da * opac[g] * G;
-                        term[0] = dl_dq * (ca * dx + cb * dy);
-                        term[1] = dl_dq * (cb * dx + cc * dy);
-                        term[2] = dl_dq * 0.5 * dx * dx;
-                        term[3] = dl_dq * dx * dy;
-                        term[4] = dl_dq * 0.5 * dy * dy;
-                        term[5] = dl_da * G;
-                    } else {
-                        for (int v = 0; v < 6; ++v) term[v] = 0.0;
+                    absdl = dCmag * Ti + absdl / (1.0 - a);
+                    /* dL/dq = -dL/da o G; q's partials w.r.t. (mx, my, a, b, c) */
+                    const double dq[5] = {ca * dx + cb * dy, cb * dx + cc * dy, 0.5 * dx * dx, dx * dy, 0.5 * dy * dy};
+                    double mag[9];
+                    for (int v = 0; v < 5; ++v) {
+                        term[v] = clamped[k] ? 0.0 : -dl_da * opac[g] * G * dq[v];
+                        mag[v] = clamped[k] ? 0.0 : absdl * opac[g] * G * fabs(dq[v]);
                     }
+                    term[5] = clamped[k] ? 0.0 : dl_da * G;
+                    mag[5] = clamped[k] ? 0.0 : absdl * G;
+                    for (int v = 6; v < 9; ++v) mag[v] = fabs(term[v]);
                     g_mean2d[2 * (int64_t)g] += term[0];
                     g_mean2d[2 * (int64_t)g + 1] += term[1];
                     for (int v = 0; v < 3; ++v) g_conic[3 * (int64_t)g + v] += term[2 + v];
                     g_opac[g] += term[5];
                     for (int v = 0; v < 3; ++v) g_rgb[3 * (int64_t)g + v] += term[6 + v];
                     if (g_abs)
-                        for (int v = 0; v < 9; ++v) g_abs[9 * (int64_t)g + v] += fabs(term[v]);
+                        for (int v = 0; v < 9; ++v) g_abs[9 * (int64_t)g + v] += mag[v];
                     for (int ch = 0; ch < 3; ++ch) S[ch] += rgb[3 * g + ch] * a * Ti;
                     Tb = Ti;
                 }

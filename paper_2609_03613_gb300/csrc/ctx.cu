@@ -390,7 +390,7 @@ extern "C" int gs_sort_or_bin(gs_ctx* ctx, const void* projected, const float* s
 extern "C" int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
                                 const uint64_t* stream_words, const int32_t* offsets,
                                 int32_t offsets_stride, const float* bg, float* rgb, float* alpha,
-                                int32_t* last, int32_t* ntests, void* stream)
+                                int32_t* last, int32_t* ntests, float* final_T, int32_t* tile_end, void* stream)
 {
     if (!ctx || !cam_ok(cam) || n < 0 || !offsets || !bg || !rgb || !alpha || !last)
         return GS_ERR_INVALID_ARG;
@@ -400,17 +400,18 @@ extern "C" int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, c
     const bool baseline = (ctx->cfg.mode == GS_MODE_GLOBAL_SORT);
     stage_begin(ctx, GS_STAGE_RASTER, st);
     int r = raster_fwd(ctx, proj_view(const_cast<void*>(projected), n), cam, stream_words, offsets,
-                       offsets_stride, bg, rgb, alpha, last, ntests, baseline, st);
+                       offsets_stride, bg, rgb, alpha, last, ntests, baseline, st, final_T, tile_end);
     stage_end(ctx, GS_STAGE_RASTER, st);
     return r;
 }
 
 extern "C" int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
                                 const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
-                                const float* out_rgb, const float* out_alpha, const float* dl_drgb,
-                                const float* dl_dalpha, void* grad, void* stream)
+                                const float* bg, const int32_t* last, const float* final_T,
+                                const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, void* grad,
+                                void* stream)
 {
-    if (!ctx || !cam_ok(cam) || n < 0 || !offsets || !out_rgb || !out_alpha || !dl_drgb || !grad)
+    if (!ctx || !cam_ok(cam) || n < 0 || !offsets || !bg || !last || !final_T || !tile_end || !dl_drgb || !grad)
         return GS_ERR_INVALID_ARG;
     if (n > 0 && (!projected || !stream_words)) return GS_ERR_INVALID_ARG;
     if (offsets_stride < 1 || offsets_stride > GS_MAX_K) return GS_ERR_INVALID_ARG;
@@ -419,7 +420,7 @@ extern "C" int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, c
     GS_CUDA_TRY(cudaMemsetAsync(grad, 0, gs_grad2d_bytes(n), st));
     if (n == 0) return GS_OK;
     return raster_bwd(ctx, proj_view(const_cast<void*>(projected), n), cam, stream_words, offsets, offsets_stride,
-                      out_rgb, out_alpha, dl_drgb, dl_dalpha, grad_view(grad, n), st);
+                      bg, last, final_T, tile_end, dl_drgb, dl_dalpha, grad_view(grad, n), st);
 }
 
 // ------------------------------------------------------------------ whole frame

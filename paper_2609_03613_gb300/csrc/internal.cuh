@@ -292,12 +292,14 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
 // raster.cu
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* stream_words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
-               int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st);
+               int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T = nullptr,
+               int32_t* tile_end = nullptr);
 
 // raster_bwd.cu
 int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
-               int32_t stride, const float* out_rgb, const float* out_alpha, const float* dl_drgb,
-               const float* dl_dalpha, const GradView& gv, cudaStream_t st);
+               int32_t stride, const float* bg, const int32_t* last, const float* final_T,
+               const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, const GradView& gv,
+               cudaStream_t st);
 
 // grow every stage's internal scratch for (n, m_cap, T) (synchronous)
 int reserve_internal(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t width, int32_t height);

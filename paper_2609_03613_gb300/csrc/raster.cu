@@ -35,11 +35,12 @@ struct PixelState {
 };
 
 // Composite n_entries stream words from src (global or shared memory) into
-// every pixel of the tile, in batches.  Returns true (uniformly) once every
+// every pixel of the tile, in batches.  Returns -1 after the last entry, or,
+// block-uniformly, the offset of the first batch left unprocessed once every
 // pixel of the tile has terminated.
 // cullmode bit 1: tile-alpha cull at staging; bit 2: per-warp strip mask.
 template <int TILE, bool BASELINE, bool COUNT>
-__device__ __forceinline__ bool raster_span(const uint64_t* src, int32_t n_entries,
+__device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_entries,
                                             RasterShared<TILE, BASELINE>& sh, const float4* __restrict__ xy_ab,
                                             const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
                                             int cullmode, int tx, int ty, float pxc, float pyc, PixelState& st)
@@ -48,7 +49,7 @@ __device__ __forceinline__ bool raster_span(const uint64_t* src, int32_t n_entri
     constexpr int BS = SH::BS, BATCH = SH::BATCH;
     const int warp = threadIdx.x >> 5;
     for (int32_t b0 = 0; b0 < n_entries; b0 += BATCH) {
-        if (__syncthreads_count(st.done) == BS) return true;
+        if (__syncthreads_count(st.done) == BS) return b0;
         const int cnt = stage_batch<TILE, BASELINE>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
         __syncthreads();
         if (!st.done) {
@@ -95,7 +96,7 @@ __device__ __forceinline__ bool raster_span(const uint64_t* src, int32_t n_entri
             }
         }
     }
-    return false;
+    return -1;
 }
 
 template <int TILE, bool BASELINE, bool COUNT>
@@ -107,7 +108,7 @@ struct FwdSpan {
     int cullmode, tx, ty;
     float pxc, pyc;
     PixelState& st;
-    __device__ __forceinline__ bool operator()(const uint64_t* src, int32_t n)
+    __device__ __forceinline__ int32_t operator()(const uint64_t* src, int32_t n)
     {
         return raster_span<TILE, BASELINE, COUNT>(src, n, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st);
     }
@@ -124,7 +125,8 @@ __global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 1)
 k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
          const uint64_t* __restrict__ words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
          float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
-         int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total)
+         int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total, float* __restrict__ out_T,
+         int32_t* __restrict__ out_end)
 {
     __shared__ RasterShared<TILE, BASELINE> sh;
     __shared__ WalkShared<LAZY> ws;
@@ -149,7 +151,8 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
     st.done = !inside;
 
     FwdSpan<TILE, BASELINE, COUNT> span{sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st};
-    walk_tile<TILE, LAZY>(words, off, t, a.stride, ws, span);
+    const int32_t end = walk_tile<TILE, LAZY>(words, off, t, a.stride, ws, span);
+    if (out_end && threadIdx.x == 0) out_end[t] = end;
     if (inside) {
         const int64_t p = (int64_t)py * a.width + px;
         out_rgb[3 * p] = fmaf(st.T, a.bg0, st.C0);
@@ -157,6 +160,7 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
         out_rgb[3 * p + 2] = fmaf(st.T, a.bg2, st.C2);
         out_alpha[p] = 1.0f - st.T;
         out_last[p] = st.last;
+        if (out_T) out_T[p] = st.T;
         if (COUNT) out_ntests[p] = st.ntests;
     }
     if (COUNT) {
@@ -173,12 +177,13 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
 template <int TILE>
 static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cudaStream_t st, const ProjView& pv,
                         const uint64_t* words, const int32_t* off, const RasterArgs& a, int cull, float* rgb,
-                        float* alpha, int32_t* last, int32_t* ntests, unsigned long long* ops)
+                        float* alpha, int32_t* last, int32_t* ntests, unsigned long long* ops, float* final_T,
+                        int32_t* tile_end)
 {
     constexpr int BS = TILE * TILE;
 #define GS_RASTER_LAUNCH(B, CNT, LZ)                                                                        \
     k_raster<TILE, B, CNT, LZ><<<grid, BS, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, (B) ? 0 : cull, \
-                                                   rgb, alpha, last, ntests, ops)
+                                                   rgb, alpha, last, ntests, ops, final_T, tile_end)
     if (baseline) {
         if (count) GS_RASTER_LAUNCH(true, true, false);
         else GS_RASTER_LAUNCH(true, false, false);
@@ -194,7 +199,7 @@ static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cud
 
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
-               int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st)
+               int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T, int32_t* tile_end)
 {
     const int tile = ctx->cfg.tile_size;
     RasterArgs a;
@@ -217,9 +222,9 @@ int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
     unsigned long long* ops = reinterpret_cast<unsigned long long*>(ctx->d_ops);
     if (count) GS_CUDA_TRY(cudaMemsetAsync(ops, 0, sizeof(unsigned long long), st));
     switch (tile) {
-        case 8: launch_tile<8>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops); break;
-        case 32: launch_tile<32>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops); break;
-        default: launch_tile<16>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops); break;
+        case 8: launch_tile<8>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end); break;
+        case 32: launch_tile<32>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end); break;
+        default: launch_tile<16>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());

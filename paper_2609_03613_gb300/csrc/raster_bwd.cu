@@ -1,25 +1,25 @@
 // raster_bwd.cu -- K22: backward of the tile compositing.  The paper leaves
 // the backward pass to future work and requires it to follow the forward's
-// compositing order (Sec. 7); this kernel walks every tile's span exactly as
-// the forward does (raster_common.cuh: same staging, culls and, for EXACT
-// streams, the same in-raster segment sorts), one CTA per tile and one thread
-// per pixel.
+// compositing order (Sec. 7); this kernel walks every tile's span as the
+// forward did (raster_common.cuh: same runs, staging, culls and, for EXACT
+// streams, the same in-raster segment sorts), but back to front, from the
+// position where the forward's tile ended.  One CTA per tile, one thread per
+// pixel.
 //
-// Each pixel recomputes the forward front to back with the forward's float32
-// operations, so its skip / stop / clamp decisions and its transmittance T_i
-// are bit-identical to the forward's; nothing is divided back out of the
-// final T.  With out = sum_i c_i a_i T_i + T_N bg (the forward's output),
-// S_i = out - sum_{j<=i} c_j a_j T_j (what lies behind entry i, background
-// included) and G = dL/dout, dA = dL/dalpha_out:
-//   dL/da_i = (G.c_i) T_i - (G.S_i - dA T_N) / (1 - a_i)
-//           = (G.c_i) T_i - (K - D_i) / (1 - a_i),
-//   K = G.out - dA T_N (per pixel),  D_i = sum_{j<=i} (G.c_j) a_j T_j,
+// Each pixel starts from the forward's saved final transmittance T_N and the
+// id of its last applied Gaussian, becomes active when the walk reaches that
+// entry, and then, entry by entry towards the front, repeats the forward's
+// float32 skip test (q, exp, alpha >= 1/255; the same bits as the forward)
+// and recovers T_i = T_{i+1} / (1 - a_i).  With G = dL/drgb, dA = dL/dalpha
+// and S_i the colour behind entry i (background included), accumulated from
+// the back so that it stays accurate deep in the list:
+//   dL/da_i = (G.c_i) T_i - (G.S_i - dA T_N) / (1 - a_i),
 //   dL/dc_i = G a_i T_i;  and, unless the clamp a_i = 0.99 is active,
 //   with v_i = dL/da_i exp(-q_i):  dL/do_i = v_i,  dL/dq_i = -o_i v_i,
 //   q = 1/2 (a dx^2 + 2 b dx dy + c dy^2), d = mean - pixel centre.
 // Per entry the warp sums nine per-pixel terms (v, v dx, v dy, v dx^2,
 // v dx dy, v dy^2, G a T), the per-Gaussian factors (o, conic) are applied
-// once per tile, and the tile's sums go to global memory with one vector
+// once per tile and batch, and the sums go to global memory with one vector
 // atomic per gradient field per entry.
 #include "raster_common.cuh"
 
@@ -31,11 +31,11 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kTerms = 9;
 
 struct GradState {
-    float T;              // transmittance before the next entry (the forward's)
-    float D;              // sum over the applied entries so far of (G.c) a T
-    float K;              // G.out - dA T_N
-    float G0, G1, G2;     // dL/dout
-    bool done;
+    float T;           // transmittance behind the current entry (starts at the forward's final T)
+    float GS;          // G.S - dA T_N, S = colour behind the current entry, background included
+    float G0, G1, G2;  // dL/drgb
+    uint32_t last;     // id of the last Gaussian the forward applied (0xffffffff: none)
+    bool active;       // the walk has reached that entry
 };
 
 // Sums over the warp of eight per-lane values by a transposing butterfly
@@ -87,22 +87,21 @@ struct BwdSpan {
     float pxc, pyc;
     GradState& st;
 
-    __device__ __forceinline__ bool done() const { return st.done; }
-
-    __device__ __forceinline__ bool operator()(const uint64_t* src, int32_t n_entries)
+    __device__ __forceinline__ void operator()(const uint64_t* src, int32_t n_entries)
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int32_t b0 = 0; b0 < n_entries; b0 += BATCH) {
-            if (__syncthreads_count(st.done) == BS) return true;
+        for (int32_t b0 = n_entries > 0 ? ((n_entries - 1) / BATCH) * BATCH : -1; b0 >= 0; b0 -= BATCH) {
+            __syncthreads();  // the previous batch's staging and sums are consumed
             const int cnt = stage_batch<TILE, false>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
             __syncthreads();
-            for (int k = 0; k < cnt; ++k) {
+            for (int k = cnt - 1; k >= 0; --k) {
                 if (!((__float_as_uint(sh.c[k].w) >> warp) & 1u)) continue;  // warp-uniform
+                const float4 gb = sh.b[k];
+                if (!st.active) st.active = __float_as_uint(gb.w) == st.last;
                 float v = 0.0f, wgt = 0.0f, dx = 0.0f, dy = 0.0f;
                 bool contrib = false;
-                if (!st.done) {
+                if (st.active) {
                     const float4 ga = sh.a[k];
-                    const float4 gb = sh.b[k];
                     dx = ga.x - pxc;
                     dy = ga.y - pyc;
                     const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
@@ -111,27 +110,20 @@ struct BwdSpan {
                         const float oe = gb.y * e;
                         const float alpha = fminf(0.99f, oe);
                         if (alpha >= 1.0f / 255.0f) {
-                            const float om = 1.0f - alpha;
-                            const float Tn = st.T * om;
-                            if (Tn < 1e-4f) {
-                                st.done = true;
-                            } else {
-                                const float4 col = sh.c[k];
-                                wgt = alpha * st.T;
-                                const float gc = fmaf(st.G2, col.z, fmaf(st.G1, col.y, st.G0 * col.x));
-                                st.D = fmaf(gc, wgt, st.D);
-                                const float dl_da = fmaf(gc, st.T, -__fdividef(st.K - st.D, om));
-                                v = oe <= 0.99f ? dl_da * e : 0.0f;
-                                st.T = Tn;
-                                contrib = true;
-                            }
+                            const float r = __fdividef(1.0f, 1.0f - alpha);
+                            const float Ti = st.T * r;
+                            const float4 col = sh.c[k];
+                            wgt = alpha * Ti;
+                            const float gc = fmaf(st.G2, col.z, fmaf(st.G1, col.y, st.G0 * col.x));
+                            const float dl_da = fmaf(gc, Ti, -st.GS * r);
+                            v = oe <= 0.99f ? dl_da * e : 0.0f;
+                            st.GS = fmaf(gc, wgt, st.GS);
+                            st.T = Ti;
+                            contrib = true;
                         }
                     }
                 }
-                if (__ballot_sync(kFull, contrib) == 0u) {
-                    if (__all_sync(kFull, st.done)) break;
-                    continue;
-                }
+                if (__ballot_sync(kFull, contrib) == 0u) continue;
                 const float vx = v * dx, vy = v * dy;
                 const float t8[8] = {v, vx, vy, vx * dx, vx * dy, vy * dy, wgt * st.G0, wgt * st.G1};
                 const float s8 = warp_sum8(t8, lane);
@@ -161,7 +153,6 @@ struct BwdSpan {
                 }
             }
         }
-        return false;
     }
 };
 
@@ -169,9 +160,10 @@ template <int TILE, bool LAZY>
 __global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 4 : 1)
 k_raster_bwd(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
              const uint64_t* __restrict__ words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
-             const float* __restrict__ out_rgb, const float* __restrict__ out_alpha,
-             const float* __restrict__ dl_drgb, const float* __restrict__ dl_dalpha, float4* __restrict__ g_xy_ab,
-             float4* __restrict__ g_c_o_z, float4* __restrict__ g_rgb)
+             const int32_t* __restrict__ last, const float* __restrict__ final_T,
+             const int32_t* __restrict__ tile_end, const float* __restrict__ dl_drgb,
+             const float* __restrict__ dl_dalpha, float4* __restrict__ g_xy_ab, float4* __restrict__ g_c_o_z,
+             float4* __restrict__ g_rgb)
 {
     using SH = RasterShared<TILE, false>;
     __shared__ SH sh;
@@ -188,46 +180,47 @@ k_raster_bwd(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z,
 
     GradState st;
     st.T = 1.0f;
-    st.D = 0.0f;
-    st.K = 0.0f;
+    st.GS = 0.0f;
     st.G0 = st.G1 = st.G2 = 0.0f;
-    st.done = !inside;
+    st.last = 0xffffffffu;
+    st.active = false;
     if (inside) {
         const int64_t p = (int64_t)py * a.width + px;
         st.G0 = dl_drgb[3 * p];
         st.G1 = dl_drgb[3 * p + 1];
         st.G2 = dl_drgb[3 * p + 2];
         const float dA = dl_dalpha ? dl_dalpha[p] : 0.0f;
-        const float TN = 1.0f - out_alpha[p];
-        st.K = fmaf(st.G2, out_rgb[3 * p + 2], fmaf(st.G1, out_rgb[3 * p + 1], st.G0 * out_rgb[3 * p])) - dA * TN;
+        st.T = final_T[p];
+        st.GS = st.T * (fmaf(st.G2, a.bg2, fmaf(st.G1, a.bg1, st.G0 * a.bg0)) - dA);
+        st.last = (uint32_t)last[p];
     }
-    __syncthreads();
 
-    BwdSpan<TILE> span{sh,      acc,     xy_ab, c_o_z, rgbv, g_xy_ab, g_c_o_z, g_rgb, cullmode, tx,
-                       ty,      (float)px + 0.5f, (float)py + 0.5f, st};
-    walk_tile<TILE, LAZY>(words, off, t, a.stride, ws, span);
+    BwdSpan<TILE> span{sh, acc, xy_ab, c_o_z, rgbv, g_xy_ab, g_c_o_z, g_rgb, cullmode, tx, ty,
+                       (float)px + 0.5f, (float)py + 0.5f, st};
+    walk_tile_rev<TILE, LAZY>(words, off, t, a.stride, tile_end[t], ws, span);
 }
 
 template <int TILE>
 void launch_bwd(bool lazy, unsigned grid, cudaStream_t st, const ProjView& pv, const uint64_t* words,
-                const int32_t* off, const RasterArgs& a, int cull, const float* out_rgb, const float* out_alpha,
-                const float* dl_drgb, const float* dl_dalpha, const GradView& gv)
+                const int32_t* off, const RasterArgs& a, int cull, const int32_t* last, const float* final_T,
+                const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, const GradView& gv)
 {
     if (lazy)
         k_raster_bwd<TILE, true><<<grid, TILE * TILE, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, cull,
-                                                               out_rgb, out_alpha, dl_drgb, dl_dalpha, gv.xy_ab,
+                                                               last, final_T, tile_end, dl_drgb, dl_dalpha, gv.xy_ab,
                                                                gv.c_o_z, gv.rgb);
     else
         k_raster_bwd<TILE, false><<<grid, TILE * TILE, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, cull,
-                                                                out_rgb, out_alpha, dl_drgb, dl_dalpha, gv.xy_ab,
+                                                                last, final_T, tile_end, dl_drgb, dl_dalpha, gv.xy_ab,
                                                                 gv.c_o_z, gv.rgb);
 }
 
 }  // namespace
 
 int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
-               int32_t stride, const float* out_rgb, const float* out_alpha, const float* dl_drgb,
-               const float* dl_dalpha, const GradView& gv, cudaStream_t st)
+               int32_t stride, const float* bg, const int32_t* last, const float* final_T,
+               const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, const GradView& gv,
+               cudaStream_t st)
 {
     const int tile = ctx->cfg.tile_size;
     RasterArgs a;
@@ -236,7 +229,9 @@ int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
     a.tiles_x = (cam->width + tile - 1) / tile;
     a.n_tiles = gs_num_tiles(cam->width, cam->height, tile);
     a.stride = stride;
-    a.bg0 = a.bg1 = a.bg2 = 0.0f;  // the background enters only through out_rgb
+    a.bg0 = bg[0];
+    a.bg1 = bg[1];
+    a.bg2 = bg[2];
     const bool lazy = ctx->cfg.mode == GS_MODE_BINNED_EXACT && ctx->cfg.repair_in_raster;
     // the staging culls are conservative, so they change no decision: EXACT
     // streams were culled when built (strip mask only), the others are culled
@@ -245,9 +240,9 @@ int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
     const unsigned grid = (unsigned)a.n_tiles;
     if (grid == 0) return GS_OK;
     switch (tile) {
-        case 8: launch_bwd<8>(lazy, grid, st, pv, words, offsets, a, cull, out_rgb, out_alpha, dl_drgb, dl_dalpha, gv); break;
-        case 32: launch_bwd<32>(lazy, grid, st, pv, words, offsets, a, cull, out_rgb, out_alpha, dl_drgb, dl_dalpha, gv); break;
-        default: launch_bwd<16>(lazy, grid, st, pv, words, offsets, a, cull, out_rgb, out_alpha, dl_drgb, dl_dalpha, gv); break;
+        case 8: launch_bwd<8>(lazy, grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
+        case 32: launch_bwd<32>(lazy, grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
+        default: launch_bwd<16>(lazy, grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());

@@ -122,37 +122,76 @@ template <bool LAZY>
 struct WalkShared {
     uint64_t sort[LAZY ? kRasterSortCap : 1];
     int32_t off[LAZY ? GS_MAX_K + 1 : 1];
-    int big[LAZY ? GS_MAX_K : 1];
+    int big[LAZY ? 2 * GS_MAX_K : 1];  // segments sorted by the whole block (the reverse walk keeps its run list first)
     int nbig;
+    int nsort;
 };
 
+// Load the chunk [c0, c0 + len) (bins bfirst..e-1) into ws.sort and sort each
+// of its segments by (depth bits, gid): segments of up to 32 entries in
+// registers by one warp, up to 256 in shared memory by one warp, longer ones by
+// the whole block.  ws.big[base..] collects the long ones.
+template <int TILE, bool LAZY>
+__device__ __forceinline__ void load_sort_chunk(const uint64_t* __restrict__ words, int32_t c0, int32_t len,
+                                                int bfirst, int e, WalkShared<LAZY>& ws, int base = 0)
+{
+    constexpr int BS = TILE * TILE;
+    constexpr int NWB = BS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < len; i += BS) ws.sort[i] = words[c0 + i];
+    if (threadIdx.x == 0) ws.nsort = base;
+    __syncthreads();
+    for (int j = bfirst + warp; j < e; j += NWB) {
+        const int l = ws.off[j + 1] - ws.off[j];
+        uint64_t* seg = ws.sort + (ws.off[j] - c0);
+        if (l < 2) continue;
+        if (l <= 32) {
+            uint64_t v = lane < l ? seg[lane] : ~0ull;
+            v = warp_bitonic32(v);
+            if (lane < l) seg[lane] = v;
+        } else if (l <= 256) {
+            bitonic_mem(seg, l, lane, 32, SyncWarp{});
+        } else if (lane == 0) {
+            ws.big[atomicAdd(&ws.nsort, 1)] = j;
+        }
+    }
+    __syncthreads();
+    const int nbig = ws.nsort;
+    for (int k = base; k < nbig; ++k) {
+        const int j = ws.big[k];
+        bitonic_mem(ws.sort + (ws.off[j] - c0), ws.off[j + 1] - ws.off[j], threadIdx.x, BS, SyncBlock{});
+    }
+}
+
 // Walk tile t's span of the stream front to back, handing runs of entries to
-// span(src, n) (returns true, block-uniformly, once every pixel of the tile
-// has terminated; span.done() is the calling thread's termination flag).
+// span(src, n) (returns -1 after consuming all n, or, block-uniformly, the
+// offset within the run at which every pixel of the tile had terminated;
+// span.done() is the calling thread's termination flag).
 // Not LAZY: one run, the span [off[t*K], off[(t+1)*K]).  LAZY: chunks of
 // consecutive segments of at most kRasterSortCap entries are loaded into
 // shared memory and every segment of the chunk is sorted (small ones by one
 // warp each, long ones by the whole block); a segment longer than the cap was
 // sorted before the raster and is handed over in place.
+// Returns the stream index at which the walk ended: the tile's span end, or
+// the position (in the composited order) where every pixel had terminated.
 template <int TILE, bool LAZY, class Span>
-__device__ __forceinline__ void walk_tile(const uint64_t* __restrict__ words, const int32_t* __restrict__ off,
-                                          int t, int K, WalkShared<LAZY>& ws, Span& span)
+__device__ __forceinline__ int32_t walk_tile(const uint64_t* __restrict__ words, const int32_t* __restrict__ off,
+                                             int t, int K, WalkShared<LAZY>& ws, Span& span)
 {
     constexpr int BS = TILE * TILE;
     if (!LAZY) {
         const int32_t s0 = off[(int64_t)t * K], s1 = off[(int64_t)(t + 1) * K];
-        span(words + s0, s1 - s0);
-        return;
+        const int32_t r = span(words + s0, s1 - s0);
+        return r < 0 ? s1 : s0 + r;
     }
-    constexpr int NWB = BS / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int b = threadIdx.x; b <= K; b += BS) ws.off[b] = off[(int64_t)t * K + b];
     __syncthreads();
     int b = 0;
     while (b < K) {
         const int32_t c0 = ws.off[b];
         if (ws.off[b + 1] - c0 > kRasterSortCap) {  // sorted before the raster
-            if (span(words + c0, ws.off[b + 1] - c0)) break;
+            const int32_t r = span(words + c0, ws.off[b + 1] - c0);
+            if (r >= 0) return c0 + r;
             ++b;
             continue;
         }
@@ -162,31 +201,67 @@ __device__ __forceinline__ void walk_tile(const uint64_t* __restrict__ words, co
         const int bfirst = b;
         b = e;
         if (len == 0) continue;
-        if (__syncthreads_count(span.done()) == BS) break;
-        for (int i = threadIdx.x; i < len; i += BS) ws.sort[i] = words[c0 + i];
-        if (threadIdx.x == 0) ws.nbig = 0;
-        __syncthreads();
-        for (int j = bfirst + warp; j < e; j += NWB) {
-            const int l = ws.off[j + 1] - ws.off[j];
-            uint64_t* seg = ws.sort + (ws.off[j] - c0);
-            if (l < 2) continue;
-            if (l <= 32) {
-                uint64_t v = lane < l ? seg[lane] : ~0ull;
-                v = warp_bitonic32(v);
-                if (lane < l) seg[lane] = v;
-            } else if (l <= 256) {
-                bitonic_mem(seg, l, lane, 32, SyncWarp{});
-            } else if (lane == 0) {
-                ws.big[atomicAdd(&ws.nbig, 1)] = j;
+        if (__syncthreads_count(span.done()) == BS) return c0;
+        load_sort_chunk<TILE>(words, c0, len, bfirst, e, ws);
+        const int32_t r = span(ws.sort, len);
+        if (r >= 0) return c0 + r;
+    }
+    return ws.off[K];
+}
+
+// The walk of walk_tile in reverse, over the entries before stream index
+// `end` (a walk_tile result): the same runs, chunks and in-chunk sorts,
+// handed to span(src, n) from the last run to the first.
+template <int TILE, bool LAZY, class Span>
+__device__ __forceinline__ void walk_tile_rev(const uint64_t* __restrict__ words, const int32_t* __restrict__ off,
+                                              int t, int K, int32_t end, WalkShared<LAZY>& ws, Span& span)
+{
+    constexpr int BS = TILE * TILE;
+    if (!LAZY) {
+        const int32_t s0 = off[(int64_t)t * K], s1 = off[(int64_t)(t + 1) * K];
+        const int32_t e = end < s1 ? end : s1;
+        if (e > s0) span(words + s0, e - s0);
+        return;
+    }
+    for (int b = threadIdx.x; b <= K; b += BS) ws.off[b] = off[(int64_t)t * K + b];
+    __syncthreads();
+    // the runs of the forward walk (first bin of each) up to `end`
+    if (threadIdx.x == 0) {
+        int nr = 0, b = 0;
+        while (b < K && ws.off[b] < end) {
+            const int32_t c0 = ws.off[b];
+            ws.big[nr++] = b;
+            if (ws.off[b + 1] - c0 > kRasterSortCap) {
+                ++b;
+                continue;
             }
+            int e = b + 1;
+            while (e < K && ws.off[e + 1] - c0 <= kRasterSortCap) ++e;
+            b = e;
         }
-        __syncthreads();
-        const int nbig = ws.nbig;
-        for (int k = 0; k < nbig; ++k) {
-            const int j = ws.big[k];
-            bitonic_mem(ws.sort + (ws.off[j] - c0), ws.off[j + 1] - ws.off[j], threadIdx.x, BS, SyncBlock{});
+        ws.nbig = nr;
+    }
+    __syncthreads();
+    const int nr = ws.nbig;
+    for (int r = nr - 1; r >= 0; --r) {
+        __syncthreads();  // ws.big / ws.sort of the previous run are no longer read
+        const int b = ws.big[r];
+        const int32_t c0 = ws.off[b];
+        if (ws.off[b + 1] - c0 > kRasterSortCap) {
+            const int32_t n = (end < ws.off[b + 1] ? end : ws.off[b + 1]) - c0;
+            span(words + c0, n);
+            continue;
         }
-        if (span(ws.sort, len)) break;
+        int e = b + 1;
+        while (e < K && ws.off[e + 1] - c0 <= kRasterSortCap) ++e;
+        const int32_t len = ws.off[e] - c0;
+        if (len == 0) continue;
+        const int32_t n = (end < ws.off[e] ? end : ws.off[e]) - c0;
+        // the whole chunk is sorted (its first n entries in sorted order are
+        // the ones the forward composited); big-segment ids go after the run
+        // list in ws.big
+        load_sort_chunk<TILE>(words, c0, len, b, e, ws, nr);
+        span(ws.sort, n);
     }
 }
 

@@ -110,7 +110,7 @@ def lib():
                                    vp]),
         "gs_repair": (C.c_int, [vp, C.POINTER(GsCamera), vp, vp, vp, vp, vp]),
         "gs_rasterize_fwd": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32,
-                                       C.POINTER(C.c_float), vp, vp, vp, vp, vp]),
+                                       C.POINTER(C.c_float), vp, vp, vp, vp, vp, vp, vp]),
         "gs_render": (C.c_int, [vp, C.POINTER(GsScene), C.POINTER(GsCamera),
                                 C.POINTER(C.c_float), vp, vp, vp, i32, vp]),
         "gs_last_entry_count": (i64, [vp]),
@@ -120,7 +120,8 @@ def lib():
                                              vp, vp, vp]),
         "gs_grad2d_bytes": (sz, [i64]),
         "gs_grad2d_offset": (sz, [i64, i32]),
-        "gs_rasterize_bwd": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32, vp, vp, vp, vp, vp, vp]),
+        "gs_rasterize_bwd": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32, C.POINTER(C.c_float), vp, vp,
+                                       vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -188,6 +189,15 @@ class DeviceScene:
 
 def n_tiles(width, height, tile=16) -> int:
     return int(lib().gs_num_tiles(width, height, tile))
+
+
+@dataclasses.dataclass
+class Saved:
+    """What rasterize_fwd(save=True) keeps for the backward."""
+    last: object
+    final_T: object
+    tile_end: object
+    bg: tuple
 
 
 class Context:
@@ -332,7 +342,9 @@ class Context:
         return sel
 
     def rasterize_fwd(self, projected, n, cam, words, offsets, stride=None, bg=(0.0, 0.0, 0.0),
-                      count_tests=False):
+                      count_tests=False, save=False):
+        """(rgb, alpha, last[, ntests]); with save=True also a Saved record
+        (final_T, tile_end, bg) for rasterize_bwd, appended last."""
         import torch
         dev = projected.device
         H, W = int(cam.height), int(cam.width)
@@ -340,30 +352,37 @@ class Context:
         alpha = torch.empty((H, W), dtype=torch.float32, device=dev)
         last = torch.empty((H, W), dtype=torch.int32, device=dev)
         nt = torch.empty((H, W), dtype=torch.int32, device=dev) if count_tests else None
+        fT = torch.empty((H, W), dtype=torch.float32, device=dev) if save else None
+        te = (torch.empty(n_tiles(W, H, self.cfg.tile_size), dtype=torch.int32, device=dev)
+              if save else None)
         bgv = (C.c_float * 3)(*[float(x) for x in bg])
         c = gs_camera(cam)
         check(lib().gs_rasterize_fwd(self.h, _ptr(projected), n, C.byref(c), _ptr(words), _ptr(offsets),
                                      self.stride if stride is None else int(stride), bgv, _ptr(rgb),
-                                     _ptr(alpha), _ptr(last), _ptr(nt), _stream()), "gs_rasterize_fwd")
-        return (rgb, alpha, last, nt) if count_tests else (rgb, alpha, last)
+                                     _ptr(alpha), _ptr(last), _ptr(nt), _ptr(fT), _ptr(te), _stream()),
+              "gs_rasterize_fwd")
+        out = (rgb, alpha, last) + ((nt,) if count_tests else ())
+        if save:
+            out = out + (Saved(last, fT, te, tuple(float(x) for x in bg)),)
+        return out
 
-    # ------------------------------------------------------------- whole frame
-    def rasterize_bwd(self, projected, n, cam, words, offsets, rgb, alpha, dl_drgb, dl_dalpha=None,
+    def rasterize_bwd(self, projected, n, cam, words, offsets, saved, dl_drgb, dl_dalpha=None,
                       stride=None, grad=None):
-        """Backward of rasterize_fwd: returns the gradient buffer (uint8,
-        gs_grad2d_bytes(n)); grad_fields() gives its [n,4] float views."""
+        """Backward of rasterize_fwd(..., save=True) (saved = its Saved
+        record): returns the gradient buffer (uint8, gs_grad2d_bytes(n));
+        grad_fields() gives its [n,4] float views."""
         import torch
         if grad is None:
             grad = torch.empty(int(lib().gs_grad2d_bytes(n)), dtype=torch.uint8, device=projected.device)
-        for t, shape in ((rgb, (cam.height, cam.width, 3)), (alpha, (cam.height, cam.width)),
-                         (dl_drgb, (cam.height, cam.width, 3)),
-                         (dl_dalpha, (cam.height, cam.width))):
+        for t, shape in ((dl_drgb, (cam.height, cam.width, 3)), (dl_dalpha, (cam.height, cam.width))):
             if t is not None and (t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shape):
                 raise TileGSError(f"gs_rasterize_bwd: expected a contiguous float32 tensor of shape {shape}")
+        bgv = (C.c_float * 3)(*saved.bg)
         c = gs_camera(cam)
         check(lib().gs_rasterize_bwd(self.h, _ptr(projected), n, C.byref(c), _ptr(words), _ptr(offsets),
-                                     self.stride if stride is None else int(stride), _ptr(rgb), _ptr(alpha),
-                                     _ptr(dl_drgb), _ptr(dl_dalpha), _ptr(grad), _stream()), "gs_rasterize_bwd")
+                                     self.stride if stride is None else int(stride), bgv, _ptr(saved.last),
+                                     _ptr(saved.final_T), _ptr(saved.tile_end), _ptr(dl_drgb), _ptr(dl_dalpha),
+                                     _ptr(grad), _stream()), "gs_rasterize_bwd")
         return grad
 
     def render(self, sc: DeviceScene, cam, bg=(0.0, 0.0, 0.0), out=None, flags=0):
