@@ -102,7 +102,7 @@ def lib():
         _i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
         L.orc_composite_grad.restype = None
         L.orc_composite_grad.argtypes = [_f32p, _f32p, _f32p, _f32p, _i32p, C.c_int, _u64p, C.c_int, C.c_int,
-                                         C.c_int, _f32p, _f32p, C.c_void_p, C.c_void_p, C.c_int64,
+                                         C.c_int, _f32p, _f32p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
                                          _f64p, _f64p, _f64p, _f64p, C.c_void_p]
         L.orc64_composite_frozen.restype = None
         L.orc64_composite_frozen.argtypes = [_f64p, _f64p, _f64p, _f64p, _i64p, _i32p, C.c_int, C.c_int, _f64p,
@@ -295,12 +295,14 @@ def set_threads(n: int) -> None:
 
 
 def composite_grad(proj, offsets, stream, width, height, dl_drgb, dl_dalpha=None, tile=16, bg=(0.0, 0.0, 0.0),
-                   K=1, with_abs=False, tiles=None):
+                   K=1, with_abs=False, tiles=None, at_f32=False):
     """Gradient of the compositing (float32 decisions, double arithmetic):
     dict of mean2d [n,2], conic [n,3], opacity [n], rgb [n,3] (float64), and
     with_abs: "abs" [n,9], the sums of the absolute per-pixel terms.
     tiles: optional list of tile ids whose pixels contribute (the others are
-    as if their incoming gradient were zero)."""
+    as if their incoming gradient were zero).
+    at_f32: evaluate at the float32 forward's own exp, alpha and
+    transmittances instead of recomputing them in double."""
     n = proj["mean2d"].shape[0]
     g = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)))
     if with_abs:
@@ -312,7 +314,7 @@ def composite_grad(proj, offsets, stream, width, height, dl_drgb, dl_dalpha=None
                              _c(stream, np.uint64), width, height, tile, np.asarray(bg, np.float32),
                              _c(dl_drgb, np.float32), None if da is None else da.ctypes.data,
                              None if sel is None else sel.ctypes.data, 0 if sel is None else sel.shape[0],
-                             g["mean2d"], g["conic"], g["opacity"], g["rgb"],
+                             1 if at_f32 else 0, g["mean2d"], g["conic"], g["opacity"], g["rgb"],
                              g["abs"].ctypes.data if with_abs else None)
     return g
 

@@ -770,11 +770,16 @@ void orc_set_threads(int n)
  * |G.c| T_i + (|G|.S_i + |dA| T_N) / (1 - a_i) -- the magnitudes of the two
  * parts dL/da is the difference of (|G| and S taken per channel, S the
  * colour behind the entry, background included).
+ * at_f32 = 0: every value in double from the float32 inputs (the derivative
+ * of the exact compositing, pinned by finite differences).  at_f32 = 1: the
+ * same formulas, in double, at the float32 forward's own exp(-q), alpha and
+ * transmittances (recorded by the replay): the gradient of the image the
+ * float32 forward produced, without the forward's own rounding drift.
  */
 void orc_composite_grad(const float* mean2d, const float* conic, const float* opac, const float* rgb,
                         const int32_t* offsets, int K, const uint64_t* stream, int width, int height,
                         int tile, const float* bg, const float* dl_drgb, const float* dl_dalpha,
-                        const int32_t* tiles_sel, int64_t n_sel,
+                        const int32_t* tiles_sel, int64_t n_sel, int at_f32,
                         double* g_mean2d, double* g_conic, double* g_opac, double* g_rgb, double* g_abs)
 {
     const int tiles_x = (width + tile - 1) / tile;
@@ -782,6 +787,7 @@ void orc_composite_grad(const float* mean2d, const float* conic, const float* op
     const int64_t nt = tiles_sel ? n_sel : (int64_t)tiles_x * tiles_y;
     int32_t* applied = NULL;
     unsigned char* clamped = NULL;
+    float *ap_e = NULL, *ap_a = NULL, *ap_T = NULL; /* the float32 forward's exp(-q), alpha, T before */
     int64_t cap = 0;
     for (int64_t it = 0; it < nt; ++it) {
         const int32_t t = tiles_sel ? tiles_sel[it] : (int32_t)it;
@@ -791,6 +797,9 @@ void orc_composite_grad(const float* mean2d, const float* conic, const float* op
             cap = s1 - s0;
             applied = (int32_t*)realloc(applied, (size_t)cap * sizeof(int32_t));
             clamped = (unsigned char*)realloc(clamped, (size_t)cap);
+            ap_e = (float*)realloc(ap_e, (size_t)cap * sizeof(float));
+            ap_a = (float*)realloc(ap_a, (size_t)cap * sizeof(float));
+            ap_T = (float*)realloc(ap_T, (size_t)cap * sizeof(float));
         }
         for (int j = ty * tile; j < ty * tile + tile && j < height; ++j)
             for (int i = tx * tile; i < tx * tile + tile && i < width; ++i) {
@@ -804,25 +813,33 @@ void orc_composite_grad(const float* mean2d, const float* conic, const float* op
                     const float ha = 0.5f * conic[3 * g], hb = conic[3 * g + 1], hc = 0.5f * conic[3 * g + 2];
                     const float q = fmaf(dx, fmaf(ha, dx, hb * dy), (hc * dy) * dy);
                     if (!(q >= 0.0f)) continue;
-                    const float oe = opac[g] * orc_expf(-q);
+                    const float e = orc_expf(-q);
+                    const float oe = opac[g] * e;
                     const float alpha = fminf(0.99f, oe);
                     if (alpha < 1.0f / 255.0f) continue;
                     const float Tn = T * (1.0f - alpha);
                     if (Tn < 1e-4f) break;
-                    T = Tn;
                     clamped[na] = oe > 0.99f;
+                    ap_e[na] = e;
+                    ap_a[na] = alpha;
+                    ap_T[na] = T;
+                    T = Tn;
                     applied[na++] = (int32_t)g;
                 }
                 /* pass 2: double-precision values and derivatives over the applied list */
                 const int64_t p = (int64_t)j * width + i;
                 const double px = (double)i + 0.5, py = (double)j + 0.5;
                 double Tf = 1.0;
-                for (int64_t k = 0; k < na; ++k) {
-                    const int32_t g = applied[k];
-                    const double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
-                    const double q = 0.5 * (conic[3 * g] * dx * dx + conic[3 * g + 2] * dy * dy) + conic[3 * g + 1] * dx * dy;
-                    const double a = clamped[k] ? 0.99 : opac[g] * exp(-q);
-                    Tf *= 1.0 - a;
+                if (at_f32) {
+                    Tf = T;
+                } else {
+                    for (int64_t k = 0; k < na; ++k) {
+                        const int32_t g = applied[k];
+                        const double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
+                        const double q = 0.5 * (conic[3 * g] * dx * dx + conic[3 * g + 2] * dy * dy) + conic[3 * g + 1] * dx * dy;
+                        const double a = clamped[k] ? 0.99 : opac[g] * exp(-q);
+                        Tf *= 1.0 - a;
+                    }
                 }
                 const double dA = dl_dalpha ? dl_dalpha[p] : 0.0;
                 /* back to front: S = colour composited behind the entry (incl. background) */
@@ -835,9 +852,10 @@ void orc_composite_grad(const float* mean2d, const float* conic, const float* op
                     const double dx = mean2d[2 * g] - px, dy = mean2d[2 * g + 1] - py;
                     const double ca = conic[3 * g], cb = conic[3 * g + 1], cc = conic[3 * g + 2];
                     const double q = 0.5 * (ca * dx * dx + cc * dy * dy) + cb * dx * dy;
-                    const double G = exp(-q);
-                    const double a = clamped[k] ? 0.99 : opac[g] * G;
-                    const double Ti = Tb / (1.0 - a); /* transmittance before the entry */
+                    const double G = at_f32 ? (double)ap_e[k] : exp(-q);
+                    const double a = at_f32 ? (double)ap_a[k] : clamped[k] ? 0.99 : opac[g] * G;
+                    /* transmittance before the entry */
+                    const double Ti = at_f32 ? (double)ap_T[k] : Tb / (1.0 - a);
                     double dl_da = dA * Tf / (1.0 - a);
                     double term[9], absdl = fabs(dA) * Tf;
                     dCmag = 0.0;
@@ -873,6 +891,9 @@ void orc_composite_grad(const float* mean2d, const float* conic, const float* op
     }
     free(applied);
     free(clamped);
+    free(ap_e);
+    free(ap_a);
+    free(ap_T);
 }
 
 /*

@@ -110,7 +110,9 @@ struct BwdSpan {
                         const float oe = gb.y * e;
                         const float alpha = fminf(0.99f, oe);
                         if (alpha >= 1.0f / 255.0f) {
-                            const float r = __fdividef(1.0f, 1.0f - alpha);
+                            // correctly rounded: an approximate reciprocal's bias
+                            // compounds along the chain of recovered T_i
+                            const float r = __frcp_rn(1.0f - alpha);
                             const float Ti = st.T * r;
                             const float4 col = sh.c[k];
                             wgt = alpha * Ti;

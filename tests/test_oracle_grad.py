@@ -182,3 +182,31 @@ def test_grad_tile_subsets_partition_the_frame():
     for k in full:
         np.testing.assert_allclose(a[k] + b[k], full[k], rtol=1e-12, atol=1e-14)
         assert np.any(a[k] != full[k])
+
+
+def test_grad_at_float32_state_matches_exact_on_shallow_lists():
+    # at the float32 forward's own alphas and transmittances the gradient moves
+    # only by the forward's rounding (shallow lists: a few ulp per layer)
+    sc, cam, proj, off, words, rgb, alpha, dC, dA = _grad_case()
+    W, H = cam.width, cam.height
+    ex = O.composite_grad(proj, off, words, W, H, dC, dA, bg=(0.2, 0.1, 0.3))
+    f32 = O.composite_grad(proj, off, words, W, H, dC, dA, bg=(0.2, 0.1, 0.3), at_f32=True)
+    for k in ex:
+        rel = np.linalg.norm(f32[k] - ex[k]) / np.linalg.norm(ex[k])
+        assert 0.0 < rel < 2e-6, (k, rel)
+
+
+def test_grad_at_float32_state_closed_form_single_gaussian():
+    # one Gaussian centred on the pixel: q = 0, exp(-q) = 1 and alpha = o
+    # exactly in float32, so dL/dc = G o and dL/do = G.(c - bg) + dA
+    P = _proj([0.5, 0.5], [0.8, 0.15, 0.5], [0.7], [0.9, 0.2, 0.6])
+    bg = np.float32([0.1, 0.3, 0.05]).astype(np.float64)
+    dC = np.float32([0.7, -1.3, 0.4]).astype(np.float64)
+    dA = float(np.float32(-0.6))
+    off, words = _one_tile_stream([0])
+    g = O.composite_grad(P, off, words, 1, 1, dC.reshape(1, 1, 3), np.float32([[dA]]), bg=tuple(bg), at_f32=True)
+    o = float(P["opacity"][0])
+    col = P["rgb"][0].astype(np.float64)
+    np.testing.assert_allclose(g["rgb"][0], dC * o, rtol=1e-15)
+    np.testing.assert_allclose(g["opacity"][0], float(dC @ (col - bg)) + dA, rtol=1e-14)
+    assert np.all(g["mean2d"] == 0.0) and np.all(g["conic"] == 0.0)
