@@ -49,9 +49,11 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-train", action="store_true", help="skip the forward+backward training-step leg")
     ap.add_argument("--profile-frame", action="store_true",
                     help="for ncu: two warm-up frames, then one frame of each path, no timing")
     ap.add_argument("--modes", default="exact,global", help="paths run by --profile-frame")
+    ap.add_argument("--backward", action="store_true", help="--profile-frame: also one saved frame + backward")
     return ap.parse_args()
 
 
@@ -397,6 +399,52 @@ def run_ours(args):
         e2e = {"value": round(ws * P / e2e_s / 1e6, 4), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3, 3)}
 
+    # training step on the same workload: the frame (graph replay, saving the
+    # backward's state), the L1 loss gradient against a fixed U[0,1] target,
+    # and the raster backward
+    train = None
+    if not args.no_train:
+        target = torch.from_numpy(scenes.random_target(H, W, 5)).to(dev)
+        grad = torch.empty(int(G.lib().gs_grad2d_bytes(ds.n)), dtype=torch.uint8, device=dev)
+        dl = torch.empty((H, W, 3), device=dev)
+        flags_t = G.RENDER_NO_SYNC | G.RENDER_GRAPH | G.RENDER_SAVE
+        ctx_b.enable_timing(False)
+
+        def train_step(ev=None):
+            ctx_b.render(ds, cam, bg, out_b, flags=flags_t)
+            torch.sub(out_b[0], target, out=dl)
+            dl.sign_().mul_(1.0 / dl.numel())
+            if ev is not None:
+                ev[0].record()
+            ctx_b.render_bwd(dl, None, grad=grad)
+            if ev is not None:
+                ev[1].record()
+
+        n_t = max(20, args.steps // 3)
+        with torch.cuda.stream(side):
+            for _ in range(args.warmup):
+                train_step()
+        torch.cuda.synchronize()
+        ev_s = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_t)]
+        ev_b = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_t)]
+        l0 = ctx_b.launch_count()
+        with ClockSampler(local) as clk_t:
+            with torch.cuda.stream(side):
+                for i in range(n_t):
+                    flush.zero_()
+                    ev_s[i][0].record()
+                    train_step(ev_b[i])
+                    ev_s[i][1].record()
+            torch.cuda.synchronize()
+        assert ctx_b.error() == 0
+        step_ms = max_over_ranks(mean([a.elapsed_time(b) for a, b in ev_s]), dist, dev)
+        bwd_ms = mean([a.elapsed_time(b) for a, b in ev_b])
+        train = {"ms_per_step": round(step_ms, 4), "mpix_s": round(ws * P / (step_ms * 1e-3) / 1e6, 3),
+                 "raster_bwd_ms": round(bwd_ms, 4), "steps": n_t,
+                 "launches_per_step": (ctx_b.launch_count() - l0) / n_t,
+                 "step": "frame (CUDA graph, RENDER_SAVE) + L1 loss gradient vs a U[0,1] target + gs_render_bwd",
+                 "clocks": clk_t.summary()}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_block(scene, cam)
@@ -428,7 +476,7 @@ def run_ours(args):
         "frame_ms_min": round(min(ms_b), 4), "frame_ms_median": round(statistics.median(ms_b), 4),
         "frame_ms_without_graph": {"binned": round(mean(ms_b_ng), 4), "global_sort": round(mean(ms_g_ng), 4)},
         "wall_s_timed": round(wall_b, 3),
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "train_step": train,
         "gpu_launches": int(launches),
     }
     print(json.dumps(res), flush=True)
@@ -448,6 +496,13 @@ def run_profile_frame(args):
         torch.cuda.synchronize()
         assert ctx.error() == 0
         print(mode, "entries", ctx.last_entry_count(), flush=True)
+        if args.backward:
+            rgb, _, _ = ctx.render(ds, cam, flags=G.RENDER_SAVE)
+            target = torch.from_numpy(scenes.random_target(cam.height, cam.width, 5)).cuda()
+            dl = (torch.sign(rgb - target) / rgb.numel()).contiguous()
+            ctx.render_bwd(dl)
+            torch.cuda.synchronize()
+            assert ctx.error() == 0
 
 
 def main():

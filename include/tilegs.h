@@ -327,6 +327,10 @@ enum {
     GS_RENDER_HOST_INPUTS = 1,  /* scene arrays are HOST memory (pinned for async copies) */
     GS_RENDER_HOST_OUTPUTS = 2, /* rgb/alpha/last are HOST memory */
     GS_RENDER_NO_SYNC = 4,      /* do not read M back: use reserved capacity only */
+    GS_RENDER_SAVE = 16,        /* also keep, in the context, what gs_render_bwd needs:
+                                   the final transmittance and per-tile end of this
+                                   frame (the projected record, stream and offsets
+                                   stay in the context until the next gs_render) */
     GS_RENDER_GRAPH = 8         /* device buffers only: capture the frame's launches
                                    into a CUDA graph on the first call and replay it
                                    on later calls with identical arguments (pointers,
@@ -345,6 +349,17 @@ enum {
  */
 int gs_render(gs_ctx* ctx, const gs_scene* scene, const gs_camera* cam, const float* bg,
               float* rgb, float* alpha, int32_t* last, int32_t flags, void* stream);
+
+/*
+ * Backward of the last gs_render on this context, which must have had
+ * GS_RENDER_SAVE: gs_rasterize_bwd over that frame's projected record,
+ * stream, offsets, last ids, final transmittance and tile ends, with its
+ * camera and background.  dl_drgb [H,W,3], dl_dalpha [H,W] (nullable) as for
+ * gs_rasterize_bwd; grad: gs_grad2d_bytes(n) bytes for that frame's n,
+ * 256-byte aligned, zeroed and written.  Errors: GS_ERR_INVALID_ARG (no saved
+ * frame, null or misaligned pointers), GS_ERR_CUDA.
+ */
+int gs_render_bwd(gs_ctx* ctx, const float* dl_drgb, const float* dl_dalpha, void* grad, void* stream);
 
 /* Entry count of the last gs_render (host; valid after the stream synchronises). */
 int64_t gs_last_entry_count(gs_ctx* ctx);

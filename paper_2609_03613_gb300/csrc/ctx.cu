@@ -139,7 +139,8 @@ extern "C" int gs_destroy(gs_ctx* c)
     void* ptrs[] = {c->d_err, c->d_scan, c->d_goff, c->d_keys[0], c->d_keys[1], c->d_vals[0],
                     c->d_vals[1], c->d_hist, c->d_count, c->d_bin, c->d_bp, c->d_sel, c->d_tail,
                     c->d_tiles_order, c->d_tile_counter, c->r_proj, c->r_isect, c->r_stream,
-                    c->r_off, c->r_m, c->r_scene, c->r_out, c->d_ops, c->d_tiles, c->d_samples};
+                    c->r_off, c->r_m, c->r_scene, c->r_out, c->d_ops, c->d_tiles, c->d_samples,
+                    c->r_T, c->r_tend};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_m) cudaFreeHost(c->h_m);
@@ -474,6 +475,19 @@ extern "C" int64_t gs_last_raster_ops(gs_ctx* c, void* stream)
     return h;
 }
 
+// buffers of the state GS_RENDER_SAVE keeps for gs_render_bwd
+static int render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T)
+{
+    int r;
+    void* p = c->r_T;
+    if ((r = ensure(&p, &c->r_T_cap, (size_t)W * H * 4)) != GS_OK) return r;
+    c->r_T = (float*)p;
+    p = c->r_tend;
+    if ((r = ensure(&p, &c->r_tend_cap, (size_t)T * 4 + 4)) != GS_OK) return r;
+    c->r_tend = (int32_t*)p;
+    return GS_OK;
+}
+
 static int render_impl(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, const float* bg, float* rgb,
                        float* alpha, int32_t* last, int32_t flags, void* stream)
 {
@@ -562,11 +576,21 @@ static int render_impl(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, cons
                            c->r_off, nullptr, st);
     }
     if (r != GS_OK) return r;
+    const bool save = (flags & GS_RENDER_SAVE) != 0;
+    if (save && (r = render_save_buffers(c, W, H, T)) != GS_OK) return r;
+    c->r_saved = 0;
     stage_begin(c, GS_STAGE_RASTER, st);
     r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,
-                   c->cfg.mode == GS_MODE_GLOBAL_SORT, st);
+                   c->cfg.mode == GS_MODE_GLOBAL_SORT, st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr);
     stage_end(c, GS_STAGE_RASTER, st);
     if (r != GS_OK) return r;
+    if (save) {
+        c->r_saved = 1;
+        c->r_last = d_last;
+        c->r_n = n;
+        c->r_cam = *cam;
+        for (int k = 0; k < 3; ++k) c->r_bg[k] = bg[k];
+    }
     if (flags & GS_RENDER_HOST_OUTPUTS) {
         const size_t px = (size_t)W * H;
         GS_CUDA_TRY(cudaMemcpyAsync(rgb, d_rgb, px * 12, cudaMemcpyDeviceToHost, st));
@@ -599,11 +623,17 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
         gs_scene sc;
         gs_camera cam;
         float bg[3];
-        void *rgb, *alpha, *last, *proj, *isect, *stream, *off, *scene_copy, *out;
+        void *rgb, *alpha, *last, *proj, *isect, *stream, *off, *scene_copy, *out, *saved_T, *saved_end;
         int64_t m_cap;
         gs_config cfg;
-        int timing, device;
+        int timing, device, flags;
     } key;
+    if (flags & GS_RENDER_SAVE) {
+        // allocate outside the capture
+        int rs = render_save_buffers(c, cam->width, cam->height, gs_num_tiles(cam->width, cam->height,
+                                                                              c->cfg.tile_size));
+        if (rs != GS_OK) return rs;
+    }
     memset(&key, 0, sizeof(key));
     key.sc = *sc;
     key.cam = *cam;
@@ -621,6 +651,9 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
     key.cfg = c->cfg;
     key.timing = c->timing;
     key.device = c->device;
+    key.flags = flags;
+    key.saved_T = c->r_T;
+    key.saved_end = c->r_tend;
     static_assert(sizeof(Key) <= sizeof(c->gkey), "graph key");
     if (!(c->gexec && c->gkey_len == sizeof(Key) && memcmp(c->gkey, &key, sizeof(Key)) == 0)) {
         if (c->gexec) {
@@ -647,10 +680,34 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
         }
         c->glaunches = c->launches - l0;
         c->launches = l0;
+        c->g_last = c->r_last;  // the last-id buffer the captured frame writes
         memcpy(c->gkey, &key, sizeof(Key));
         c->gkey_len = sizeof(Key);
     }
     GS_CUDA_TRY(cudaGraphLaunch(c->gexec, st));
     c->launches += c->glaunches;
+    c->r_saved = 0;
+    if (flags & GS_RENDER_SAVE) {
+        // the replayed frame is the captured one: its saved state is current
+        c->r_saved = 1;
+        c->r_last = c->g_last;
+        c->r_n = sc->n;
+        c->r_cam = *cam;
+        for (int k = 0; k < 3; ++k) c->r_bg[k] = bg[k];
+    }
     return GS_OK;
+}
+
+extern "C" int gs_render_bwd(gs_ctx* c, const float* dl_drgb, const float* dl_dalpha, void* grad, void* stream)
+{
+    if (!c || !dl_drgb || !grad) return GS_ERR_INVALID_ARG;
+    if (!c->r_saved || !c->r_last) return GS_ERR_INVALID_ARG;  // no saved gs_render on this context
+    if ((reinterpret_cast<uintptr_t>(grad) & 255u) != 0) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = c->r_n;
+    GS_CUDA_TRY(cudaMemsetAsync(grad, 0, gs_grad2d_bytes(n), st));
+    if (n == 0) return GS_OK;
+    const int32_t stride = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : c->cfg.K;
+    return raster_bwd(c, proj_view(c->r_proj, n), &c->r_cam, c->r_stream, c->r_off, stride, c->r_bg, c->r_last,
+                      c->r_T, c->r_tend, dl_drgb, dl_dalpha, grad_view(grad, n), st);
 }

@@ -217,6 +217,14 @@ struct gs_ctx {
     int64_t* h_m = nullptr;  // pinned
     float* r_scene = nullptr; size_t r_scene_cap = 0;  // device copies of host inputs
     float* r_out = nullptr; size_t r_out_cap = 0;      // device outputs for host outputs
+    // saved state of the last gs_render with GS_RENDER_SAVE (for gs_render_bwd)
+    float* r_T = nullptr; size_t r_T_cap = 0;        // final transmittance [H,W]
+    int32_t* r_tend = nullptr; size_t r_tend_cap = 0; // per-tile end of the compositing [T]
+    const int32_t* r_last = nullptr;                  // the last-id buffer that render wrote (device)
+    int64_t r_n = -1;                                 // Gaussian count of that render
+    gs_camera r_cam;
+    float r_bg[3] = {0.f, 0.f, 0.f};
+    int r_saved = 0;
     int64_t last_m = 0;
     int64_t launches = 0;  // kernels this context has launched
     int64_t* d_ops = nullptr;  // compositing ops counted by the instrumented raster
@@ -225,6 +233,7 @@ struct gs_ctx {
     unsigned char gkey[512];
     size_t gkey_len = 0;
     int64_t glaunches = 0;
+    const int32_t* g_last = nullptr;  // last-id buffer of the captured frame
     int capturing = 0;
     // timing
     int timing = 0;

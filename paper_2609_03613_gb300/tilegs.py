@@ -24,7 +24,7 @@ MODE_GLOBAL_SORT, MODE_BINNED_EXACT, MODE_BINNED_PAPER, MODE_BINNED_NOREPAIR = 0
 MODES = {"global": 0, "exact": 1, "paper": 2, "norepair": 3}
 STAGES = ["project", "intersect", "depth_range", "bin", "repair", "sort", "raster"]
 MAX_K = 128
-RENDER_HOST_INPUTS, RENDER_HOST_OUTPUTS, RENDER_NO_SYNC, RENDER_GRAPH = 1, 2, 4, 8
+RENDER_HOST_INPUTS, RENDER_HOST_OUTPUTS, RENDER_NO_SYNC, RENDER_GRAPH, RENDER_SAVE = 1, 2, 4, 8, 16
 P_XY_AB, P_C_O_Z, P_RGB, P_RECT, P_RADIUS = range(5)
 
 # Every symbol include/tilegs.h declares (checked by the CPU export test).
@@ -35,7 +35,7 @@ EXPORTS = [
     "gs_isect_offset", "gs_num_tiles", "gs_project", "gs_tile_intersect", "gs_sort_or_bin",
     "gs_depth_range", "gs_bin_build", "gs_repair", "gs_rasterize_fwd", "gs_render",
     "gs_last_entry_count", "gs_launch_count", "gs_last_raster_ops", "gs_depth_range_noalloc",
-    "gs_grad2d_bytes", "gs_grad2d_offset", "gs_rasterize_bwd",
+    "gs_grad2d_bytes", "gs_grad2d_offset", "gs_rasterize_bwd", "gs_render_bwd",
 ]
 
 
@@ -119,6 +119,7 @@ def lib():
         "gs_depth_range_noalloc": (C.c_int, [C.POINTER(GsConfig), vp, vp, i64, C.POINTER(GsCamera), vp, i64,
                                              vp, vp, vp]),
         "gs_grad2d_bytes": (sz, [i64]),
+        "gs_render_bwd": (C.c_int, [vp, vp, vp, vp, vp]),
         "gs_grad2d_offset": (sz, [i64, i32]),
         "gs_rasterize_bwd": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32, C.POINTER(C.c_float), vp, vp,
                                        vp, vp, vp, vp, vp]),
@@ -401,7 +402,20 @@ class Context:
         c = gs_camera(cam)
         check(lib().gs_render(self.h, C.byref(s), C.byref(c), bgv, _ptr(rgb), _ptr(alpha), _ptr(last),
                               int(flags), _stream()), "gs_render")
+        self._saved_n = int(sc.n) if flags & RENDER_SAVE else None
         return rgb, alpha, last
+
+    def render_bwd(self, dl_drgb, dl_dalpha=None, grad=None):
+        """Backward of the last render(..., flags=RENDER_SAVE): the gradient
+        buffer (grad_fields() gives its [n,4] views)."""
+        import torch
+        n = getattr(self, "_saved_n", None)
+        if n is None:
+            raise TileGSError("gs_render_bwd: invalid argument (no render with RENDER_SAVE on this context)")
+        if grad is None:
+            grad = torch.empty(int(lib().gs_grad2d_bytes(n)), dtype=torch.uint8, device=dl_drgb.device)
+        check(lib().gs_render_bwd(self.h, _ptr(dl_drgb), _ptr(dl_dalpha), _ptr(grad), _stream()), "gs_render_bwd")
+        return grad
 
     def last_entry_count(self) -> int:
         return int(lib().gs_last_entry_count(self.h))

@@ -195,3 +195,37 @@ def test_autograd_l1_step_matches_direct_backward():
     dln = dl.cpu().numpy()
     assert_both({k: v.grad.cpu().numpy() for k, v in (("xy_ab", xy), ("c_o_z", coz), ("rgb", col))},
                 *oracle_grads(sc, cam, dln, None))
+
+
+def test_render_save_then_render_bwd_whole_frame_and_graph_replay():
+    sc = scenes.mixture_scene(120_000, 32)
+    cam = scenes.hd_camera(width=500, height=284, f=300.0)
+    bg = (0.1, 0.2, 0.3)
+    dC, dA = scenes.incoming_grads(cam.height, cam.width, seed=14)
+    dCd, dAd = torch.from_numpy(dC).cuda(), torch.from_numpy(dA).cuda()
+    ctx = G.Context("exact")
+    ds = G.DeviceScene.from_numpy(sc)
+    ctx.render(ds, cam, bg, flags=G.RENDER_SAVE)
+    got = {k: v.cpu().numpy() for k, v in G.grad_fields(ctx.render_bwd(dCd, dAd), sc.n).items()}
+    torch.cuda.synchronize()
+    assert ctx.error() == 0
+    assert_both(got, *oracle_grads(sc, cam, dC, dA, bg=bg))
+    # the same frame replayed from a CUDA graph, backward after each replay
+    side = torch.cuda.Stream()
+    out = tuple(torch.empty(s, dtype=d, device="cuda") for s, d in (((cam.height, cam.width, 3), torch.float32),
+                                                                    ((cam.height, cam.width), torch.float32),
+                                                                    ((cam.height, cam.width), torch.int32)))
+    grad = torch.empty(int(G.lib().gs_grad2d_bytes(sc.n)), dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            ctx.render(ds, cam, bg, out, flags=G.RENDER_NO_SYNC | G.RENDER_GRAPH | G.RENDER_SAVE)
+            ctx.render_bwd(dCd, dAd, grad=grad)
+    torch.cuda.synchronize()
+    assert ctx.error() == 0
+    rep = {k: v.cpu().numpy() for k, v in G.grad_fields(grad, sc.n).items()}
+    for k in got:
+        np.testing.assert_allclose(rep[k], got[k], rtol=1e-5, atol=1e-6 * float(np.abs(got[k]).max()))
+    # a frame rendered without RENDER_SAVE leaves nothing to differentiate
+    ctx.render(ds, cam, bg)
+    with pytest.raises(G.TileGSError, match="invalid argument"):
+        ctx.render_bwd(dCd, dAd)
