@@ -50,6 +50,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the forward+backward training-step leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 16-view batched-render leg")
     ap.add_argument("--profile-frame", action="store_true",
                     help="for ncu: two warm-up frames, then one frame of each path, no timing")
     ap.add_argument("--modes", default="exact,global", help="paths run by --profile-frame")
@@ -445,6 +446,10 @@ def run_ours(args):
                  "step": "frame (CUDA graph, RENDER_SAVE) + L1 loss gradient vs a U[0,1] target + gs_render_bwd",
                  "clocks": clk_t.summary()}
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_leg(args, dev, side, flush, dist)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_block(scene, cam)
@@ -477,9 +482,78 @@ def run_ours(args):
         "frame_ms_without_graph": {"binned": round(mean(ms_b_ng), 4), "global_sort": round(mean(ms_g_ng), 4)},
         "wall_s_timed": round(wall_b, 3),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "train_step": train,
+        "batch16": batch,
         "gpu_launches": int(launches),
     }
     print(json.dumps(res), flush=True)
+
+
+def batch_leg(args, dev, side, flush, dist):
+    """16 views of a 2M-Gaussian scene (resolutions 512^2 .. 1080p): one
+    gs_render_batch graph (default per-view config, then autotuned) against
+    16 single-view graphs issued back to back."""
+    import torch
+
+    from paper_2609_03613_gb300 import scenes, tilegs as G
+    scene, cams = scenes.workload("batch16")
+    ds = G.DeviceScene.from_numpy(scene, dev)
+    P = sum(c.width * c.height for c in cams)
+    steps = max(10, args.steps // 15)
+
+    def timed(fn, n):
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        with torch.cuda.stream(side):
+            for i in range(n):
+                flush.zero_()
+                ev[i][0].record()
+                fn()
+                ev[i][1].record()
+        torch.cuda.synchronize()
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / n, dist, dev)
+
+    gflags = G.RENDER_NO_SYNC | G.RENDER_GRAPH
+    # 16 single-view contexts, each replaying its own frame graph
+    singles = []
+    for cam in cams:
+        c = G.Context("exact")
+        out = c.render(ds, cam)
+        torch.cuda.synchronize()
+        c.reserve(ds.n, int(c.last_entry_count() * 1.25) + 1024, cam.width, cam.height)
+        singles.append((c, cam, out))
+
+    def run_singles():
+        for c, cam, out in singles:
+            c.render(ds, cam, (0.0, 0.0, 0.0), out, flags=gflags)
+
+    ms_single = timed(run_singles, steps)
+    del singles
+    ctx = G.Context("exact")
+    outs = ctx.render_batch(ds, cams)
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    ms_batch = timed(lambda: ctx.render_batch(ds, cams, (0.0, 0.0, 0.0), outs, flags=gflags), steps)
+    launches = (ctx.launch_count() - l0) / (steps + 3)
+    t0 = time.perf_counter()
+    best = ctx.batch_autotune(ds, cams, tune_tile=True, iters=2)
+    tune_s = time.perf_counter() - t0
+    outs = ctx.render_batch(ds, cams)
+    torch.cuda.synchronize()
+    ms_tuned = timed(lambda: ctx.render_batch(ds, cams, (0.0, 0.0, 0.0), outs, flags=gflags), steps)
+    assert ctx.error() == 0
+    cfgs = [(ctx.batch_view_config(v).tile_size, ctx.batch_view_config(v).K) for v in range(len(cams))]
+    return {"views": len(cams), "gaussians": ds.n, "pixels": P, "steps": steps,
+            "resolutions": [f"{c.width}x{c.height}" for c in cams],
+            "single_view_graphs_ms": round(ms_single, 4), "batch_graph_ms": round(ms_batch, 4),
+            "batch_tuned_ms": round(ms_tuned, 4),
+            "mpix_s": {"single_view_graphs": round(P / (ms_single * 1e-3) / 1e6, 2),
+                       "batch": round(P / (ms_batch * 1e-3) / 1e6, 2),
+                       "batch_tuned": round(P / (ms_tuned * 1e-3) / 1e6, 2)},
+            "launches_per_batch": launches, "tuned_tile_K": cfgs, "tune_s": round(tune_s, 2),
+            "tuned_view_ms": [round(x, 4) for x in best]}
 
 
 def run_profile_frame(args):

@@ -82,6 +82,7 @@ typedef struct gs_camera {
 
 /* ---------------------------------------------------------------- config */
 #define GS_MAX_K 128
+#define GS_MAX_VIEWS 32 /* views of one gs_render_batch call */
 typedef struct gs_config {
     int32_t mode;          /* GS_MODE_* */
     int32_t tile_size;     /* 8, 16 or 32 pixels (16 = the paper's) */
@@ -361,10 +362,57 @@ int gs_render(gs_ctx* ctx, const gs_scene* scene, const gs_camera* cam, const fl
  */
 int gs_render_bwd(gs_ctx* ctx, const float* dl_drgb, const float* dl_dalpha, void* grad, void* stream);
 
+/*
+ * Several views of one scene in one call (the paper renders single views; this
+ * is the batched form a training or serving system needs).  Every view runs
+ * the whole-frame pipeline of gs_render in its own sub-context of ctx, with
+ * the configuration set for it by gs_batch_set_view_config / gs_batch_autotune
+ * (default: ctx's): one projection launch serves all views (each Gaussian is
+ * read once and projected n_cams times), then each view's intersect / bin /
+ * repair / raster runs on its own stream, forked from and joined back into
+ * `stream`.
+ *   cams: HOST array [n_cams], 1 <= n_cams <= GS_MAX_VIEWS.
+ *   rgb, alpha: HOST arrays [n_cams] of DEVICE pointers ([H_v,W_v,3], [H_v,W_v]);
+ *   last: HOST array of DEVICE pointers (nullable array; null entries: not
+ *   written).  bg: HOST float[3].  Device scene arrays only.
+ *   flags: GS_RENDER_NO_SYNC (no entry-count readback; capacity from earlier
+ *   calls), GS_RENDER_GRAPH (device buffers, non-default stream: the whole
+ *   batch is captured once and replayed while the arguments are unchanged;
+ *   every view must have been sized by an earlier call without NO_SYNC).
+ *   Host-buffer and SAVE flags are rejected.
+ * Each view's image is the one gs_render gives for that camera and the view's
+ * configuration.  Errors: as gs_render; GS_ERR_INVALID_ARG for bad counts.
+ */
+int gs_render_batch(gs_ctx* ctx, const gs_scene* scene, const gs_camera* cams, int32_t n_cams, const float* bg,
+                    float* const* rgb, float* const* alpha, int32_t* const* last, int32_t flags, void* stream);
+
+/* Configuration of batch view `view` (0 <= view < GS_MAX_VIEWS); cfg NULL
+ * resets it to the context's. */
+int gs_batch_set_view_config(gs_ctx* ctx, int32_t view, const gs_config* cfg);
+int gs_batch_get_view_config(gs_ctx* ctx, int32_t view, gs_config* cfg);
+
+/* Entry count of view `view` in the last gs_render_batch (host; valid after
+ * the stream synchronises; -1 if the view does not exist). */
+int64_t gs_batch_last_entry_count(gs_ctx* ctx, int32_t view);
+
+/*
+ * Choose each view's tile size (8, 16, 32; only when tune_tile != 0) and bin
+ * count K (32, 64, 128; binned modes) by timing `iters` whole frames of that
+ * view for every candidate (CUDA events on `stream`, synchronous), and set
+ * them with gs_batch_set_view_config.  best_ms: HOST [n_cams] (nullable), the
+ * chosen candidates' mean frame times.  K never changes an EXACT image; the
+ * tile size can, for Gaussians that reach alpha >= 1/255 outside their 3-sigma
+ * square (opacity above ~0.35), because their tile rectangles differ.
+ * Allocates (temporary contexts and output buffers).
+ */
+int gs_batch_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* cams, int32_t n_cams,
+                      int32_t tune_tile, int32_t iters, float* best_ms, void* stream);
+
 /* Entry count of the last gs_render (host; valid after the stream synchronises). */
 int64_t gs_last_entry_count(gs_ctx* ctx);
 
-/* Number of CUDA kernels this context has launched so far (host counter). */
+/* Number of CUDA kernels this context (and its batch sub-contexts) has
+ * launched so far (host counter). */
 int64_t gs_launch_count(const gs_ctx* ctx);
 
 /* Float32 operations of the compositing definition executed by the last

@@ -145,6 +145,7 @@ extern "C" int gs_destroy(gs_ctx* c)
         if (p) cudaFree(p);
     if (c->h_m) cudaFreeHost(c->h_m);
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    batch_destroy(c);
     if (c->ev_ok)
         for (int s = 0; s < GS_STAGE_COUNT; ++s) {
             cudaEventDestroy(c->ev_b[s]);
@@ -174,6 +175,7 @@ extern "C" int gs_get_error(gs_ctx* c, void* stream)
     int h = 0;
     GS_CUDA_TRY(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     GS_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (h == 0) h = batch_error(c, (cudaStream_t)stream);
     return h;
 }
 
@@ -181,7 +183,7 @@ extern "C" int gs_clear_error(gs_ctx* c, void* stream)
 {
     if (!c) return GS_ERR_INVALID_ARG;
     GS_CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), (cudaStream_t)stream));
-    return GS_OK;
+    return batch_clear_error(c, (cudaStream_t)stream);
 }
 
 extern "C" int gs_enable_timing(gs_ctx* c, int32_t on)
@@ -238,7 +240,7 @@ extern "C" int32_t gs_num_tiles(int32_t width, int32_t height, int32_t tile)
     return ((width + tile - 1) / tile) * ((height + tile - 1) / tile);
 }
 
-static bool cam_ok(const gs_camera* cam)
+bool gs::camera_ok(const gs_camera* cam)
 {
     if (!cam) return false;
     if (cam->width <= 0 || cam->height <= 0 || cam->width > 65535 * 8 || cam->height > 65535 * 8)
@@ -247,6 +249,8 @@ static bool cam_ok(const gs_camera* cam)
     if (!(cam->near_plane >= 0.0f) || !(cam->far_plane > cam->near_plane)) return false;
     return true;
 }
+
+static bool cam_ok(const gs_camera* cam) { return camera_ok(cam); }
 
 // ------------------------------------------------------------------ entry points
 namespace gs {
@@ -425,7 +429,7 @@ extern "C" int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, c
 }
 
 // ------------------------------------------------------------------ whole frame
-static int render_buffers(gs_ctx* c, int64_t n, int64_t m_cap, int32_t T)
+int gs::render_buffers(gs_ctx* c, int64_t n, int64_t m_cap, int32_t T)
 {
     int r;
     if ((r = ensure(&c->r_proj, &c->r_proj_cap, gs_projected_bytes(n))) != GS_OK) return r;
@@ -463,7 +467,7 @@ extern "C" int gs_reserve(gs_ctx* c, int64_t n, int64_t m_cap, int32_t width, in
 
 extern "C" int64_t gs_last_entry_count(gs_ctx* c) { return c ? c->last_m : -1; }
 
-extern "C" int64_t gs_launch_count(const gs_ctx* c) { return c ? c->launches : -1; }
+extern "C" int64_t gs_launch_count(const gs_ctx* c) { return c ? c->launches + batch_launch_count(c) : -1; }
 
 extern "C" int64_t gs_last_raster_ops(gs_ctx* c, void* stream)
 {
@@ -476,7 +480,7 @@ extern "C" int64_t gs_last_raster_ops(gs_ctx* c, void* stream)
 }
 
 // buffers of the state GS_RENDER_SAVE keeps for gs_render_bwd
-static int render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T)
+int gs::render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T)
 {
     int r;
     void* p = c->r_T;
@@ -485,6 +489,71 @@ static int render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T)
     p = c->r_tend;
     if ((r = ensure(&p, &c->r_tend_cap, (size_t)T * 4 + 4)) != GS_OK) return r;
     c->r_tend = (int32_t*)p;
+    return GS_OK;
+}
+
+// Everything of a frame after the projection (the record is in c->r_proj):
+// intersect, sort or bin, repair, raster (and the saved state).  Device
+// outputs.  Without GS_RENDER_NO_SYNC the entry count is read back once to
+// grow the entry buffers.
+int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, const float* bg,
+                             float* d_rgb, float* d_alpha, int32_t* d_last, int32_t flags, cudaStream_t st)
+{
+    const int32_t W = cam->width, H = cam->height;
+    const int32_t T = gs_num_tiles(W, H, c->cfg.tile_size);
+    ProjView pv = proj_view(c->r_proj, n);
+    int r;
+    stage_begin(c, GS_STAGE_INTERSECT, st);
+    r = count_scan(c, pv, n, c->r_m, st);
+    if (r != GS_OK) return r;
+    if (!(flags & GS_RENDER_NO_SYNC)) {
+        // size the entry buffers: read M once, grow if needed
+        GS_CUDA_TRY(cudaMemcpyAsync(c->h_m, c->r_m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        GS_CUDA_TRY(cudaStreamSynchronize(st));
+        if (c->h_m[0] > c->r_m_cap) {
+            if ((r = render_buffers(c, n, c->h_m[0], T)) != GS_OK) return r;
+        }
+    }
+    const int32_t stride = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : c->cfg.K;
+    if (c->cfg.mode == GS_MODE_BINNED_EXACT) {
+        // the emission is fused with the bucketing by tile: no emission-order
+        // entries are written; depth samples map to gids through the offsets
+        stage_end(c, GS_STAGE_INTERSECT, st);
+        stage_begin(c, GS_STAGE_DEPTH_RANGE, st);
+        r = depth_range_goff(c, pv, scales, n, c->r_m_cap, c->r_m, cam, st);
+        stage_end(c, GS_STAGE_DEPTH_RANGE, st);
+        if (r != GS_OK) return r;
+        stage_begin(c, GS_STAGE_BIN, st);
+        r = exact_bins(c, pv, n, cam, true, c->r_m_cap, c->r_m, c->r_stream, c->r_off, st);
+        stage_end(c, GS_STAGE_BIN, st);
+        if (r != GS_OK) return r;
+        stage_begin(c, GS_STAGE_REPAIR, st);
+        r = repair_min(c, T, c->r_m, c->r_stream, c->r_off, nullptr,
+                       c->cfg.repair_in_raster ? kRasterSortCap + 1 : 2, st);
+        stage_end(c, GS_STAGE_REPAIR, st);
+    } else {
+        r = emit_only(c, pv, n, cam, isect_view(c->r_isect, c->r_m_cap), c->r_m_cap, c->r_m, st);
+        stage_end(c, GS_STAGE_INTERSECT, st);
+        if (r != GS_OK) return r;
+        r = gs_sort_or_bin(c, c->r_proj, scales, n, cam, c->r_isect, c->r_m_cap, c->r_m, c->r_stream,
+                           c->r_off, nullptr, st);
+    }
+    if (r != GS_OK) return r;
+    const bool save = (flags & GS_RENDER_SAVE) != 0;
+    if (save && (r = render_save_buffers(c, W, H, T)) != GS_OK) return r;
+    c->r_saved = 0;
+    stage_begin(c, GS_STAGE_RASTER, st);
+    r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,
+                   c->cfg.mode == GS_MODE_GLOBAL_SORT, st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr);
+    stage_end(c, GS_STAGE_RASTER, st);
+    if (r != GS_OK) return r;
+    if (save) {
+        c->r_saved = 1;
+        c->r_last = d_last;
+        c->r_n = n;
+        c->r_cam = *cam;
+        for (int k = 0; k < 3; ++k) c->r_bg[k] = bg[k];
+    }
     return GS_OK;
 }
 
@@ -540,57 +609,8 @@ static int render_impl(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, cons
         stage_end(c, GS_STAGE_PROJECT, st);
         if (r != GS_OK) return r;
     }
-    stage_begin(c, GS_STAGE_INTERSECT, st);
-    r = count_scan(c, pv, n, c->r_m, st);
+    r = render_after_project(c, n, scales, cam, bg, d_rgb, d_alpha, d_last, flags, st);
     if (r != GS_OK) return r;
-    if (!(flags & GS_RENDER_NO_SYNC)) {
-        // size the entry buffers: read M once, grow if needed
-        GS_CUDA_TRY(cudaMemcpyAsync(c->h_m, c->r_m, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        GS_CUDA_TRY(cudaStreamSynchronize(st));
-        if (c->h_m[0] > c->r_m_cap) {
-            if ((r = render_buffers(c, n, c->h_m[0], T)) != GS_OK) return r;
-        }
-    }
-    const int32_t stride = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : c->cfg.K;
-    if (c->cfg.mode == GS_MODE_BINNED_EXACT) {
-        // the emission is fused with the bucketing by tile: no emission-order
-        // entries are written; depth samples map to gids through the offsets
-        stage_end(c, GS_STAGE_INTERSECT, st);
-        stage_begin(c, GS_STAGE_DEPTH_RANGE, st);
-        r = depth_range_goff(c, pv, scales, n, c->r_m_cap, c->r_m, cam, st);
-        stage_end(c, GS_STAGE_DEPTH_RANGE, st);
-        if (r != GS_OK) return r;
-        stage_begin(c, GS_STAGE_BIN, st);
-        r = exact_bins(c, pv, n, cam, true, c->r_m_cap, c->r_m, c->r_stream, c->r_off, st);
-        stage_end(c, GS_STAGE_BIN, st);
-        if (r != GS_OK) return r;
-        stage_begin(c, GS_STAGE_REPAIR, st);
-        r = repair_min(c, T, c->r_m, c->r_stream, c->r_off, nullptr,
-                       c->cfg.repair_in_raster ? kRasterSortCap + 1 : 2, st);
-        stage_end(c, GS_STAGE_REPAIR, st);
-    } else {
-        r = emit_only(c, pv, n, cam, isect_view(c->r_isect, c->r_m_cap), c->r_m_cap, c->r_m, st);
-        stage_end(c, GS_STAGE_INTERSECT, st);
-        if (r != GS_OK) return r;
-        r = gs_sort_or_bin(c, c->r_proj, scales, n, cam, c->r_isect, c->r_m_cap, c->r_m, c->r_stream,
-                           c->r_off, nullptr, st);
-    }
-    if (r != GS_OK) return r;
-    const bool save = (flags & GS_RENDER_SAVE) != 0;
-    if (save && (r = render_save_buffers(c, W, H, T)) != GS_OK) return r;
-    c->r_saved = 0;
-    stage_begin(c, GS_STAGE_RASTER, st);
-    r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,
-                   c->cfg.mode == GS_MODE_GLOBAL_SORT, st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr);
-    stage_end(c, GS_STAGE_RASTER, st);
-    if (r != GS_OK) return r;
-    if (save) {
-        c->r_saved = 1;
-        c->r_last = d_last;
-        c->r_n = n;
-        c->r_cam = *cam;
-        for (int k = 0; k < 3; ++k) c->r_bg[k] = bg[k];
-    }
     if (flags & GS_RENDER_HOST_OUTPUTS) {
         const size_t px = (size_t)W * H;
         GS_CUDA_TRY(cudaMemcpyAsync(rgb, d_rgb, px * 12, cudaMemcpyDeviceToHost, st));

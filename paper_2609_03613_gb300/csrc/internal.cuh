@@ -174,6 +174,10 @@ struct BinParams {
 }  // namespace gs
 
 // ------------------------------------------------------------------ context
+namespace gs {
+struct BatchState;
+}
+
 struct gs_ctx {
     gs_config cfg;
     int device = 0;
@@ -235,6 +239,8 @@ struct gs_ctx {
     int64_t glaunches = 0;
     const int32_t* g_last = nullptr;  // last-id buffer of the captured frame
     int capturing = 0;
+    // batched multi-view rendering (gs_render_batch)
+    gs::BatchState* batch = nullptr;
     // timing
     int timing = 0;
     cudaEvent_t ev_b[GS_STAGE_COUNT];
@@ -309,6 +315,26 @@ int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
                int32_t stride, const float* bg, const int32_t* last, const float* final_T,
                const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, const GradView& gv,
                cudaStream_t st);
+
+// ctx.cu: whole-frame pieces the batched render reuses
+bool camera_ok(const gs_camera* cam);
+int render_buffers(gs_ctx* c, int64_t n, int64_t m_cap, int32_t T);
+int render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T);
+int render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, const float* bg,
+                         float* d_rgb, float* d_alpha, int32_t* d_last, int32_t flags, cudaStream_t st);
+
+// project.cu
+constexpr int kMaxBatchViews = GS_MAX_VIEWS;
+int launch_project_batch(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
+                         const float* opac, const float* sh, int32_t sh_degree, int64_t n, int nviews,
+                         const gs_camera* cams, const int* tiles, const ProjView* pvs, cudaStream_t st);
+
+// batch.cu: per-context batch state (sub-contexts, streams, graph)
+struct BatchState;
+void batch_destroy(gs_ctx* c);
+int batch_error(gs_ctx* c, cudaStream_t st);
+int batch_clear_error(gs_ctx* c, cudaStream_t st);
+int64_t batch_launch_count(const gs_ctx* c);  // kernels launched by the batch's sub-contexts
 
 // grow every stage's internal scratch for (n, m_cap, T) (synchronous)
 int reserve_internal(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t width, int32_t height);

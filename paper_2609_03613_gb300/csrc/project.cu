@@ -11,7 +11,11 @@
 //   rect = tiles met by the (mean +- radius) square, clamped; cull if empty;
 //   rgb = max(sum_k Y_k(dir) sh_k + 0.5, 0), dir = normalize(m - campos).
 // One thread per Gaussian; the block's SH coefficients (contiguous in memory)
-// are staged through shared memory with coalesced float4 loads.
+// are staged through shared memory with coalesced float4 loads.  The batched
+// kernel projects each Gaussian for every view of a batch from one read of its
+// parameters.
+#include <string.h>
+
 #include "internal.cuh"
 
 namespace gs {
@@ -57,46 +61,44 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y)
 
 constexpr int kProjBlock = 128;
 
+// Stage the block's SH coefficients (contiguous in memory) through shared
+// memory with coalesced float4 loads where the array is 16-byte aligned.
+template <int PER>
+__device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_aligned, int64_t base, int64_t n,
+                                         float* s_sh)
+{
+    const int cnt = (int)((n - base) < kProjBlock ? (n - base) : kProjBlock);
+    const int total = cnt * PER;
+    const float* src = sh + base * PER;
+    int k0 = 0;
+    if (sh_aligned) {
+        const float4* src4 = reinterpret_cast<const float4*>(src);
+        float4* dst4 = reinterpret_cast<float4*>(s_sh);
+        for (int k = threadIdx.x; k < total / 4; k += kProjBlock) dst4[k] = __ldg(src4 + k);
+        k0 = (total / 4) * 4;
+    }
+    for (int k = k0 + threadIdx.x; k < total; k += kProjBlock) s_sh[k] = __ldg(src + k);
+    __syncthreads();
+}
+
+// One Gaussian seen by one camera: the record fields, all zero when culled.
+// (mx, my, mz), o, q4 and (s0, s1, s2) are the Gaussian's parameters, cs its
+// SH coefficients (NC x 3, coefficient-major).
 template <int DEG>
-__global__ void __launch_bounds__(kProjBlock)
-k_project(const float* __restrict__ means, const float* __restrict__ scales,
-          const float4* __restrict__ quats, const float* __restrict__ opac,
-          const float* __restrict__ sh, int sh_aligned, int64_t n, CamArgs cam, ProjView pv)
+__device__ __forceinline__ void project_one(float mx, float my, float mz, float o, float4 q4, float s0, float s1,
+                                            float s2, const float* cs, const CamArgs& cam, float4& o_xy_ab,
+                                            float4& o_c_o_z, float4& o_rgb, uint2& o_rect, int& o_radius)
 {
     constexpr int NC = (DEG + 1) * (DEG + 1);
-    constexpr int PER = NC * 3;  // floats of SH per Gaussian
-    __shared__ __align__(16) float s_sh[kProjBlock * PER];
-    const int64_t base = (int64_t)blockIdx.x * kProjBlock;
-    const int cnt = (int)((n - base) < kProjBlock ? (n - base) : kProjBlock);
-    {
-        const int total = cnt * PER;
-        const float* src = sh + base * PER;
-        int k0 = 0;
-        if (sh_aligned) {
-            const float4* src4 = reinterpret_cast<const float4*>(src);
-            float4* dst4 = reinterpret_cast<float4*>(s_sh);
-            for (int k = threadIdx.x; k < total / 4; k += kProjBlock) dst4[k] = __ldg(src4 + k);
-            k0 = (total / 4) * 4;
-        }
-        for (int k = k0 + threadIdx.x; k < total; k += kProjBlock) s_sh[k] = __ldg(src + k);
-    }
-    __syncthreads();
-    const int64_t i = base + threadIdx.x;
-    if (i >= n) return;
-
     const float* W = cam.W;
-    float4 o_xy_ab = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 o_c_o_z = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 o_rgb = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint2 o_rect = make_uint2(0u, 0u);
-    int o_radius = 0;
-
-    const float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
+    o_xy_ab = make_float4(0.f, 0.f, 0.f, 0.f);
+    o_c_o_z = make_float4(0.f, 0.f, 0.f, 0.f);
+    o_rgb = make_float4(0.f, 0.f, 0.f, 0.f);
+    o_rect = make_uint2(0u, 0u);
+    o_radius = 0;
     const float xc = W[0] * mx + W[1] * my + W[2] * mz + W[3];
     const float yc = W[4] * mx + W[5] * my + W[6] * mz + W[7];
     const float zc = W[8] * mx + W[9] * my + W[10] * mz + W[11];
-    const float o = __ldg(opac + i);
-    const float4 q4 = __ldg(quats + i);
     const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     bool vis = (zc > cam.near_plane && zc < cam.far_plane) && (o >= 1.0f / 255.0f) && (qn > 0.0f);
     if (vis) {
@@ -111,7 +113,6 @@ k_project(const float* __restrict__ means, const float* __restrict__ scales,
         Rq[2][0] = 2.0f * (x * z - w * y);
         Rq[2][1] = 2.0f * (y * z + w * x);
         Rq[2][2] = 1.0f - 2.0f * (x * x + y * y);
-        const float s0 = __ldg(scales + 3 * i), s1 = __ldg(scales + 3 * i + 1), s2 = __ldg(scales + 3 * i + 2);
         float M[3][3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -191,7 +192,6 @@ k_project(const float* __restrict__ means, const float* __restrict__ scales,
                 }
                 float Y[16];
                 sh_basis(dx, dy, dz, Y);
-                const float* cs = s_sh + threadIdx.x * PER;
                 float col[3];
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
@@ -218,19 +218,76 @@ k_project(const float* __restrict__ means, const float* __restrict__ scales,
             }
         }
     }
-    pv.xy_ab[i] = o_xy_ab;
-    pv.c_o_z[i] = o_c_o_z;
-    pv.rgb[i] = o_rgb;
-    pv.rect[i] = o_rect;
-    pv.radius[i] = o_radius;
 }
 
-int launch_project(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
-                   const float* opac, const float* sh, int32_t sh_degree, int64_t n,
-                   const gs_camera* cam, const ProjView& pv, cudaStream_t st)
+template <int DEG>
+__global__ void __launch_bounds__(kProjBlock)
+k_project(const float* __restrict__ means, const float* __restrict__ scales,
+          const float4* __restrict__ quats, const float* __restrict__ opac,
+          const float* __restrict__ sh, int sh_aligned, int64_t n, CamArgs cam, ProjView pv)
 {
-    if (n <= 0) return GS_OK;
-    if (reinterpret_cast<uintptr_t>(quats) & 15) return GS_ERR_INVALID_ARG;  // float4 loads
+    constexpr int NC = (DEG + 1) * (DEG + 1);
+    constexpr int PER = NC * 3;  // floats of SH per Gaussian
+    __shared__ __align__(16) float s_sh[kProjBlock * PER];
+    const int64_t base = (int64_t)blockIdx.x * kProjBlock;
+    stage_sh<PER>(sh, sh_aligned, base, n, s_sh);
+    const int64_t i = base + threadIdx.x;
+    if (i >= n) return;
+    float4 a, b, c;
+    uint2 rect;
+    int radius;
+    project_one<DEG>(__ldg(means + 3 * i), __ldg(means + 3 * i + 1), __ldg(means + 3 * i + 2), __ldg(opac + i),
+                     __ldg(quats + i), __ldg(scales + 3 * i), __ldg(scales + 3 * i + 1), __ldg(scales + 3 * i + 2),
+                     s_sh + threadIdx.x * PER, cam, a, b, c, rect, radius);
+    pv.xy_ab[i] = a;
+    pv.c_o_z[i] = b;
+    pv.rgb[i] = c;
+    pv.rect[i] = rect;
+    pv.radius[i] = radius;
+}
+
+// Views of one batched projection launch (kernel parameters).
+struct BatchCams {
+    CamArgs cam[kMaxBatchViews];
+    ProjView pv[kMaxBatchViews];
+    int nviews;
+};
+
+// The same Gaussian for every view of the batch: its parameters (and SH
+// coefficients) are read from HBM once and projected V times.
+template <int DEG>
+__global__ void __launch_bounds__(kProjBlock)
+k_project_batch(const float* __restrict__ means, const float* __restrict__ scales,
+                const float4* __restrict__ quats, const float* __restrict__ opac,
+                const float* __restrict__ sh, int sh_aligned, int64_t n, const __grid_constant__ BatchCams bc)
+{
+    constexpr int NC = (DEG + 1) * (DEG + 1);
+    constexpr int PER = NC * 3;
+    __shared__ __align__(16) float s_sh[kProjBlock * PER];
+    const int64_t base = (int64_t)blockIdx.x * kProjBlock;
+    stage_sh<PER>(sh, sh_aligned, base, n, s_sh);
+    const int64_t i = base + threadIdx.x;
+    if (i >= n) return;
+    const float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
+    const float o = __ldg(opac + i);
+    const float4 q4 = __ldg(quats + i);
+    const float s0 = __ldg(scales + 3 * i), s1 = __ldg(scales + 3 * i + 1), s2 = __ldg(scales + 3 * i + 2);
+    for (int v = 0; v < bc.nviews; ++v) {
+        float4 a, b, c;
+        uint2 rect;
+        int radius;
+        project_one<DEG>(mx, my, mz, o, q4, s0, s1, s2, s_sh + threadIdx.x * PER, bc.cam[v], a, b, c, rect, radius);
+        const ProjView& pv = bc.pv[v];
+        pv.xy_ab[i] = a;
+        pv.c_o_z[i] = b;
+        pv.rgb[i] = c;
+        pv.rect[i] = rect;
+        pv.radius[i] = radius;
+    }
+}
+
+static CamArgs cam_args(const gs_camera* cam, int tile)
+{
     CamArgs ca;
     for (int k = 0; k < 16; ++k) ca.W[k] = cam->viewmat[k];
     ca.fx = cam->fx;
@@ -241,9 +298,47 @@ int launch_project(gs_ctx* ctx, const float* means, const float* scales, const f
     ca.height = cam->height;
     ca.near_plane = cam->near_plane;
     ca.far_plane = cam->far_plane;
-    ca.tile = ctx->cfg.tile_size;
-    ca.tiles_x = (cam->width + ca.tile - 1) / ca.tile;
-    ca.tiles_y = (cam->height + ca.tile - 1) / ca.tile;
+    ca.tile = tile;
+    ca.tiles_x = (cam->width + tile - 1) / tile;
+    ca.tiles_y = (cam->height + tile - 1) / tile;
+    return ca;
+}
+
+int launch_project_batch(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
+                         const float* opac, const float* sh, int32_t sh_degree, int64_t n, int nviews,
+                         const gs_camera* cams, const int* tiles, const ProjView* pvs, cudaStream_t st)
+{
+    if (n <= 0 || nviews <= 0) return GS_OK;
+    if (nviews > kMaxBatchViews) return GS_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(quats) & 15) return GS_ERR_INVALID_ARG;  // float4 loads
+    BatchCams bc;
+    memset(&bc, 0, sizeof(bc));
+    bc.nviews = nviews;
+    for (int v = 0; v < nviews; ++v) {
+        bc.cam[v] = cam_args(cams + v, tiles[v]);
+        bc.pv[v] = pvs[v];
+    }
+    const int aligned = (reinterpret_cast<uintptr_t>(sh) & 15) == 0;
+    const unsigned grid = (unsigned)((n + kProjBlock - 1) / kProjBlock);
+    const float4* q4 = reinterpret_cast<const float4*>(quats);
+    switch (sh_degree) {
+        case 0: k_project_batch<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc); break;
+        case 1: k_project_batch<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc); break;
+        case 2: k_project_batch<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc); break;
+        default: k_project_batch<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc); break;
+    }
+    ctx->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int launch_project(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
+                   const float* opac, const float* sh, int32_t sh_degree, int64_t n,
+                   const gs_camera* cam, const ProjView& pv, cudaStream_t st)
+{
+    if (n <= 0) return GS_OK;
+    if (reinterpret_cast<uintptr_t>(quats) & 15) return GS_ERR_INVALID_ARG;  // float4 loads
+    const CamArgs ca = cam_args(cam, ctx->cfg.tile_size);
     const int aligned = (reinterpret_cast<uintptr_t>(sh) & 15) == 0;
     const unsigned grid = (unsigned)((n + kProjBlock - 1) / kProjBlock);
     const float4* q4 = reinterpret_cast<const float4*>(quats);

@@ -24,6 +24,7 @@ MODE_GLOBAL_SORT, MODE_BINNED_EXACT, MODE_BINNED_PAPER, MODE_BINNED_NOREPAIR = 0
 MODES = {"global": 0, "exact": 1, "paper": 2, "norepair": 3}
 STAGES = ["project", "intersect", "depth_range", "bin", "repair", "sort", "raster"]
 MAX_K = 128
+MAX_VIEWS = 32
 RENDER_HOST_INPUTS, RENDER_HOST_OUTPUTS, RENDER_NO_SYNC, RENDER_GRAPH, RENDER_SAVE = 1, 2, 4, 8, 16
 P_XY_AB, P_C_O_Z, P_RGB, P_RECT, P_RADIUS = range(5)
 
@@ -36,6 +37,8 @@ EXPORTS = [
     "gs_depth_range", "gs_bin_build", "gs_repair", "gs_rasterize_fwd", "gs_render",
     "gs_last_entry_count", "gs_launch_count", "gs_last_raster_ops", "gs_depth_range_noalloc",
     "gs_grad2d_bytes", "gs_grad2d_offset", "gs_rasterize_bwd", "gs_render_bwd",
+    "gs_render_batch", "gs_batch_set_view_config", "gs_batch_get_view_config", "gs_batch_last_entry_count",
+    "gs_batch_autotune",
 ]
 
 
@@ -120,6 +123,13 @@ def lib():
                                              vp, vp, vp]),
         "gs_grad2d_bytes": (sz, [i64]),
         "gs_render_bwd": (C.c_int, [vp, vp, vp, vp, vp]),
+        "gs_render_batch": (C.c_int, [vp, C.POINTER(GsScene), C.POINTER(GsCamera), i32, C.POINTER(C.c_float),
+                                      C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i32, vp]),
+        "gs_batch_set_view_config": (C.c_int, [vp, i32, C.POINTER(GsConfig)]),
+        "gs_batch_get_view_config": (C.c_int, [vp, i32, C.POINTER(GsConfig)]),
+        "gs_batch_last_entry_count": (i64, [vp, i32]),
+        "gs_batch_autotune": (C.c_int, [vp, C.POINTER(GsScene), C.POINTER(GsCamera), i32, i32, i32,
+                                        C.POINTER(C.c_float), vp]),
         "gs_grad2d_offset": (sz, [i64, i32]),
         "gs_rasterize_bwd": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32, C.POINTER(C.c_float), vp, vp,
                                        vp, vp, vp, vp, vp]),
@@ -416,6 +426,57 @@ class Context:
             grad = torch.empty(int(lib().gs_grad2d_bytes(n)), dtype=torch.uint8, device=dl_drgb.device)
         check(lib().gs_render_bwd(self.h, _ptr(dl_drgb), _ptr(dl_dalpha), _ptr(grad), _stream()), "gs_render_bwd")
         return grad
+
+    # ------------------------------------------------------------- batches
+    def render_batch(self, sc: DeviceScene, cams, bg=(0.0, 0.0, 0.0), outs=None, flags=0):
+        """All views of cams in one gs_render_batch call.  outs: list of
+        (rgb, alpha, last) per view (allocated when None).  Returns outs."""
+        import torch
+        dev = sc.means.device
+        if outs is None:
+            outs = [(torch.empty((c.height, c.width, 3), dtype=torch.float32, device=dev),
+                     torch.empty((c.height, c.width), dtype=torch.float32, device=dev),
+                     torch.empty((c.height, c.width), dtype=torch.int32, device=dev)) for c in cams]
+        nv = len(cams)
+        carr = (GsCamera * nv)(*[gs_camera(c) for c in cams])
+        P = C.c_void_p * nv
+        rgb = P(*[_ptr(o[0]) for o in outs])
+        alpha = P(*[_ptr(o[1]) for o in outs])
+        last = P(*[_ptr(o[2]) if len(o) > 2 else None for o in outs])
+        s = GsScene(_ptr(sc.means), _ptr(sc.scales), _ptr(sc.quats), _ptr(sc.opacities), _ptr(sc.sh),
+                    sc.sh_degree, sc.n)
+        bgv = (C.c_float * 3)(*[float(x) for x in bg])
+        check(lib().gs_render_batch(self.h, C.byref(s), carr, nv, bgv, rgb, alpha, last, int(flags), _stream()),
+              "gs_render_batch")
+        return outs
+
+    def batch_view_config(self, view) -> GsConfig:
+        cfg = GsConfig()
+        check(lib().gs_batch_get_view_config(self.h, int(view), C.byref(cfg)), "gs_batch_get_view_config")
+        return cfg
+
+    def set_batch_view_config(self, view, cfg=None, **kw):
+        if cfg is None and kw:
+            cfg = GsConfig.from_buffer_copy(self.cfg)
+            for k, v in kw.items():
+                setattr(cfg, k, MODES[v] if k == "mode" and isinstance(v, str) else v)
+        check(lib().gs_batch_set_view_config(self.h, int(view), None if cfg is None else C.byref(cfg)),
+              "gs_batch_set_view_config")
+
+    def batch_entry_count(self, view) -> int:
+        return int(lib().gs_batch_last_entry_count(self.h, int(view)))
+
+    def batch_autotune(self, sc: DeviceScene, cams, tune_tile=True, iters=3):
+        """Times the candidates per view and sets each view's config; returns the
+        chosen configs' frame times (ms)."""
+        nv = len(cams)
+        carr = (GsCamera * nv)(*[gs_camera(c) for c in cams])
+        s = GsScene(_ptr(sc.means), _ptr(sc.scales), _ptr(sc.quats), _ptr(sc.opacities), _ptr(sc.sh),
+                    sc.sh_degree, sc.n)
+        best = (C.c_float * nv)()
+        check(lib().gs_batch_autotune(self.h, C.byref(s), carr, nv, 1 if tune_tile else 0, int(iters), best,
+                                      _stream()), "gs_batch_autotune")
+        return list(best)
 
     def last_entry_count(self) -> int:
         return int(lib().gs_last_entry_count(self.h))
