@@ -83,6 +83,12 @@ typedef struct gs_camera {
 /* ---------------------------------------------------------------- config */
 #define GS_MAX_K 128
 #define GS_MAX_VIEWS 32 /* views of one gs_render_batch call */
+/* bin planner network: 8 features -> 64 -> 64 -> 6 classes (ReLU, float32) */
+#define GS_PLAN_FEATURES 8
+#define GS_PLAN_HIDDEN 64
+#define GS_PLAN_CLASSES 6
+#define GS_PLAN_PARAMS (GS_PLAN_HIDDEN * GS_PLAN_FEATURES + GS_PLAN_HIDDEN + GS_PLAN_HIDDEN * GS_PLAN_HIDDEN + \
+                        GS_PLAN_HIDDEN + GS_PLAN_CLASSES * GS_PLAN_HIDDEN + GS_PLAN_CLASSES)
 typedef struct gs_config {
     int32_t mode;          /* GS_MODE_* */
     int32_t tile_size;     /* 8, 16 or 32 pixels (16 = the paper's) */
@@ -104,6 +110,15 @@ typedef struct gs_config {
                               pixel's termination are never sorted.  The image is
                               identical either way; with 0 the stream is fully
                               sorted by gs_sort_or_bin. */
+    int32_t chunk_cap;     /* EXACT with repair_in_raster: the most entries of
+                              consecutive bins the raster loads and sorts at once
+                              (a tile's repair bins; a single longer segment of up
+                              to 2048 forms one on its own); 32..2048, 0 = 256 */
+    int32_t planner;       /* EXACT with repair_in_raster, 1: each tile's chunk
+                              size comes from the bin planner (an MLP over the
+                              tile's depth-bin statistics, weights set with
+                              gs_planner_set_weights); 0: chunk_cap everywhere.
+                              Changes speed only, never the image. */
 } gs_config;
 
 /* Fill *cfg with the paper's defaults (supplement, default No-GW configuration
@@ -312,6 +327,54 @@ int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_cam
                      const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
                      const float* bg, const int32_t* last, const float* final_T, const int32_t* tile_end,
                      const float* dl_drgb, const float* dl_dalpha, void* grad, void* stream);
+
+/*
+ * gs_rasterize_fwd with a per-tile chunk plan (EXACT with repair_in_raster):
+ * plan [T] (nullable) gives each tile's chunk size class c -- chunks of at
+ * most 64 << c entries (c = 0..5) -- in place of cfg.chunk_cap; tile_cycles
+ * [T] (nullable) receives each tile's clock64() cycles inside the raster
+ * (the planner's training labels).  Other arguments as gs_rasterize_fwd; the
+ * image does not depend on the plan.
+ */
+int gs_rasterize_fwd_plan(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
+                          const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
+                          const float* bg, float* rgb, float* alpha, int32_t* last, const uint8_t* plan,
+                          long long* tile_cycles, void* stream);
+
+/* ---------------------------------------------------------------- bin planner */
+/*
+ * The learned bin planner (the paper uses one bin count and spacing for every
+ * tile, Sec. 5.3, and leaves distribution-dependent settings to future work,
+ * Sec. 7).  Per tile, an MLP maps 8 statistics of the tile's culled span and
+ * fine-bin counts to a chunk size class: how many consecutive bins the EXACT
+ * raster loads, sorts and composites at a time, i.e. the tile's bin count
+ * and the split depths where its bins end.  The image never changes.
+ *
+ * gs_tile_features: features [T][GS_PLAN_FEATURES] (device) of a binned
+ *   stream's offsets (stride = K): log1p(n), log1p(max bin), nonempty/K,
+ *   first/K, last/K, log1p(first bin count), log1p(entries in the K/8 bins
+ *   from the first nonempty one), log1p(n/nonempty).
+ * gs_planner_set_weights: GS_PLAN_PARAMS floats (host or device; NULL turns
+ *   the planner off), packed W1[64][8] b1 W2[64][64] b2 W3[6][64] b3.
+ * gs_plan_tiles: plan [T] = argmax class of each tile (device).
+ * Training kernels (device buffers, batch B):
+ *   gs_mlp_forward: acts [B][128] = (h1, h2), logits [B][6];
+ *   gs_mlp_loss_grad: mean softmax cross entropy into loss[0] and its
+ *   gradient dlogits [B][6] for labels [B] in 0..5;
+ *   gs_mlp_backward: deltas [B][128] scratch, grads [GS_PLAN_PARAMS] (overwritten);
+ *   gs_adam_step: one Adam update (Kingma & Ba) with bias correction, step >= 1.
+ */
+int gs_tile_features(gs_ctx* ctx, const gs_camera* cam, const int32_t* offsets, int32_t stride, float* features,
+                     void* stream);
+int gs_planner_set_weights(gs_ctx* ctx, const float* params, void* stream);
+int gs_plan_tiles(gs_ctx* ctx, const float* features, int32_t n_tiles, uint8_t* plan, void* stream);
+int gs_mlp_forward(const float* params, const float* X, int32_t B, float* acts, float* logits, void* stream);
+int gs_mlp_loss_grad(const float* logits, const int32_t* labels, int32_t B, float* dlogits, float* loss,
+                     void* stream);
+int gs_mlp_backward(const float* params, const float* X, const float* acts, const float* dlogits, int32_t B,
+                    float* deltas, float* grads, void* stream);
+int gs_adam_step(float* params, const float* grads, float* m, float* v, int32_t n, float lr, float beta1,
+                 float beta2, float eps, int32_t step, void* stream);
 
 /* ---------------------------------------------------------------- whole frame */
 typedef struct gs_scene {

@@ -46,6 +46,8 @@ extern "C" void gs_config_default(gs_config* cfg, int32_t mode)
     cfg->tile_cull = 1;
     cfg->persistent = 1;
     cfg->repair_in_raster = (mode == GS_MODE_BINNED_EXACT) ? 1 : 0;
+    cfg->chunk_cap = 256;
+    cfg->planner = 0;
 }
 
 namespace gs {
@@ -62,6 +64,8 @@ int check_config(const gs_config* c)
     if (!(c->pad >= 0.0f) || !(c->eps > 0.0f) || !(c->repair_budget_frac >= 0.0f))
         return GS_ERR_INVALID_ARG;
     if (c->mode == GS_MODE_BINNED_EXACT && c->near_shift) return GS_ERR_INVALID_ARG;
+    if (c->chunk_cap != 0 && (c->chunk_cap < 32 || c->chunk_cap > 2048)) return GS_ERR_INVALID_ARG;
+    if (c->planner != 0 && c->planner != 1) return GS_ERR_INVALID_ARG;
     return GS_OK;
 }
 
@@ -140,7 +144,7 @@ extern "C" int gs_destroy(gs_ctx* c)
                     c->d_vals[1], c->d_hist, c->d_count, c->d_bin, c->d_bp, c->d_sel, c->d_tail,
                     c->d_tiles_order, c->d_tile_counter, c->r_proj, c->r_isect, c->r_stream,
                     c->r_off, c->r_m, c->r_scene, c->r_out, c->d_ops, c->d_tiles, c->d_samples,
-                    c->r_T, c->r_tend};
+                    c->r_T, c->r_tend, c->d_planner, c->d_feat, c->d_plan};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_m) cudaFreeHost(c->h_m);
@@ -410,6 +414,24 @@ extern "C" int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, c
     return r;
 }
 
+extern "C" int gs_rasterize_fwd_plan(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
+                                     const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
+                                     const float* bg, float* rgb, float* alpha, int32_t* last, const uint8_t* plan,
+                                     long long* tile_cycles, void* stream)
+{
+    if (!ctx || !cam_ok(cam) || n < 0 || !offsets || !bg || !rgb || !alpha || !last)
+        return GS_ERR_INVALID_ARG;
+    if (n > 0 && (!projected || !stream_words)) return GS_ERR_INVALID_ARG;
+    if (offsets_stride < 1 || offsets_stride > GS_MAX_K) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool baseline = (ctx->cfg.mode == GS_MODE_GLOBAL_SORT);
+    stage_begin(ctx, GS_STAGE_RASTER, st);
+    int r = raster_fwd(ctx, proj_view(const_cast<void*>(projected), n), cam, stream_words, offsets, offsets_stride,
+                       bg, rgb, alpha, last, nullptr, baseline, st, nullptr, nullptr, plan, tile_cycles);
+    stage_end(ctx, GS_STAGE_RASTER, st);
+    return r;
+}
+
 extern "C" int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
                                 const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
                                 const float* bg, const int32_t* last, const float* final_T,
@@ -479,6 +501,19 @@ extern "C" int64_t gs_last_raster_ops(gs_ctx* c, void* stream)
     return h;
 }
 
+// per-frame planner features and plan
+int gs::planner_buffers(gs_ctx* c, int32_t T)
+{
+    int r;
+    void* p = c->d_feat;
+    if ((r = ensure(&p, &c->feat_cap, (size_t)T * GS_PLAN_FEATURES * 4 + 16)) != GS_OK) return r;
+    c->d_feat = (float*)p;
+    p = c->d_plan;
+    if ((r = ensure(&p, &c->plan_cap_bytes, (size_t)T + 16)) != GS_OK) return r;
+    c->d_plan = (uint8_t*)p;
+    return GS_OK;
+}
+
 // buffers of the state GS_RENDER_SAVE keeps for gs_render_bwd
 int gs::render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T)
 {
@@ -543,8 +578,17 @@ int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs
     if (save && (r = render_save_buffers(c, W, H, T)) != GS_OK) return r;
     c->r_saved = 0;
     stage_begin(c, GS_STAGE_RASTER, st);
+    const uint8_t* plan = nullptr;
+    if (c->cfg.planner && c->cfg.mode == GS_MODE_BINNED_EXACT && c->cfg.repair_in_raster) {
+        if (!c->planner_ready) return GS_ERR_INVALID_ARG;  // gs_planner_set_weights first
+        if ((r = planner_buffers(c, T)) != GS_OK) return r;
+        if ((r = gs_tile_features(c, cam, c->r_off, stride, c->d_feat, st)) != GS_OK) return r;
+        if ((r = gs_plan_tiles(c, c->d_feat, T, c->d_plan, st)) != GS_OK) return r;
+        plan = c->d_plan;
+    }
     r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,
-                   c->cfg.mode == GS_MODE_GLOBAL_SORT, st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr);
+                   c->cfg.mode == GS_MODE_GLOBAL_SORT, st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr,
+                   plan, nullptr);
     stage_end(c, GS_STAGE_RASTER, st);
     if (r != GS_OK) return r;
     if (save) {

@@ -239,6 +239,11 @@ struct gs_ctx {
     int64_t glaunches = 0;
     const int32_t* g_last = nullptr;  // last-id buffer of the captured frame
     int capturing = 0;
+    // bin planner (planner.cu): MLP parameters, per-frame features and plan
+    float* d_planner = nullptr;
+    int planner_ready = 0;
+    float* d_feat = nullptr; size_t feat_cap = 0;
+    uint8_t* d_plan = nullptr; size_t plan_cap_bytes = 0;
     // batched multi-view rendering (gs_render_batch)
     gs::BatchState* batch = nullptr;
     // timing
@@ -300,6 +305,11 @@ int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* str
 // segments longer than this are sorted before the raster when the raster
 // sorts the segments it reaches
 constexpr int kRasterSortCap = 2048;
+// repair-bin (chunk) size classes of the per-tile plan: 64 << class entries
+constexpr int kPlanClasses = 6;
+__host__ __device__ inline int plan_cap(int cls) { return 64 << (cls < 0 ? 0 : cls > 5 ? 5 : cls); }
+// the configured chunk size of the lazy EXACT raster
+inline int chunk_cap(const gs_config& cfg) { return cfg.chunk_cap > 0 ? cfg.chunk_cap : 256; }
 // depth range with samples mapped to gids through the per-Gaussian offsets
 int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64_t n, int64_t m_cap,
                      const int64_t* m_dev, const gs_camera* cam, cudaStream_t st);
@@ -308,7 +318,7 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* stream_words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T = nullptr,
-               int32_t* tile_end = nullptr);
+               int32_t* tile_end = nullptr, const uint8_t* plan = nullptr, long long* tile_cycles = nullptr);
 
 // raster_bwd.cu
 int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
@@ -320,6 +330,7 @@ int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
 bool camera_ok(const gs_camera* cam);
 int render_buffers(gs_ctx* c, int64_t n, int64_t m_cap, int32_t T);
 int render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T);
+int planner_buffers(gs_ctx* c, int32_t T);
 int render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, const float* bg,
                          float* d_rgb, float* d_alpha, int32_t* d_last, int32_t flags, cudaStream_t st);
 

@@ -1,0 +1,346 @@
+// planner.cu -- K23: the learned bin planner.  The paper uses one bin count
+// and spacing for every tile (Sec. 5.3 ablates K for the whole frame; Sec. 7
+// leaves settings that follow the depth distribution or the resolution to
+// future work); here a small MLP picks,
+// per tile, how the tile's fine depth bins are grouped into repair bins (the
+// chunks the EXACT raster loads, sorts and composites one at a time): a chunk
+// size class c gives chunks of at most 64 << c entries, so it fixes the tile's
+// bin count and the split depths where its bins end.  The image never
+// changes (every chunk's segments are sorted exactly); only the speed does.
+//
+// Features per tile, from its culled span and the K fine-bin counts n_b:
+//   f0 log1p(n)        n = entries of the tile
+//   f1 log1p(max n_b)
+//   f2 nonempty / K
+//   f3 first nonempty bin / K      (1 when the tile is empty)
+//   f4 last nonempty bin / K       (0 when empty)
+//   f5 log1p(n_first)              count of the first nonempty bin
+//   f6 log1p(front)                entries in the K/8 bins from the first nonempty one
+//   f7 log1p(n / nonempty)         mean occupancy of a nonempty bin
+// Network: 8 -> 64 -> 64 -> 6, ReLU, float32; parameters packed as
+//   W1[64][8] b1[64] W2[64][64] b2[64] W3[6][64] b3[6]  (5126 floats).
+// Training runs on the GPU with the kernels below (forward, softmax cross
+// entropy, backward, Adam), on labels the raster itself measures (per-tile
+// cycles of every class, gs_rasterize_fwd_plan).
+#include "internal.cuh"
+
+namespace gs {
+
+constexpr int kF = GS_PLAN_FEATURES, kH = GS_PLAN_HIDDEN, kC = GS_PLAN_CLASSES;
+constexpr int oW1 = 0, oB1 = oW1 + kH * kF, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH, oB3 = oW3 + kC * kH;
+static_assert(oB3 + kC == GS_PLAN_PARAMS, "parameter layout");
+static_assert(kC == kPlanClasses, "plan classes");
+
+// one warp per tile; K <= GS_MAX_K (128) -> at most 4 bins per lane
+__global__ void k_tile_features(const int32_t* __restrict__ off, int K, int T, float* __restrict__ feat)
+{
+    const int lane = threadIdx.x & 31;
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (t >= T) return;
+    const int32_t* o = off + (int64_t)t * K;
+    int cnt[4];
+    int mx = 0, ne = 0, first = K, last = -1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int b = lane + 32 * j;
+        cnt[j] = b < K ? o[b + 1] - o[b] : 0;
+        mx = max(mx, cnt[j]);
+        if (cnt[j] > 0) {
+            ++ne;
+            first = min(first, b);
+            last = max(last, b);
+        }
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, s));
+        ne += __shfl_xor_sync(0xffffffffu, ne, s);
+        first = min(first, __shfl_xor_sync(0xffffffffu, first, s));
+        last = max(last, __shfl_xor_sync(0xffffffffu, last, s));
+    }
+    const int span = K / 8 > 0 ? K / 8 : 1;
+    int front = 0, nfirst = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int b = lane + 32 * j;
+        if (b >= first && b < first + span) front += cnt[j];
+        if (b == first) nfirst = cnt[j];
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+        front += __shfl_xor_sync(0xffffffffu, front, s);
+        nfirst += __shfl_xor_sync(0xffffffffu, nfirst, s);
+    }
+    if (lane == 0) {
+        const int n = o[K] - o[0];
+        float* f = feat + (int64_t)t * kF;
+        const float fk = (float)K;
+        f[0] = log1pf((float)n);
+        f[1] = log1pf((float)mx);
+        f[2] = (float)ne / fk;
+        f[3] = ne > 0 ? (float)first / fk : 1.0f;
+        f[4] = ne > 0 ? (float)last / fk : 0.0f;
+        f[5] = log1pf((float)nfirst);
+        f[6] = log1pf((float)front);
+        f[7] = ne > 0 ? log1pf((float)n / (float)ne) : 0.0f;
+    }
+}
+
+// hidden activations of one sample (ReLU outputs)
+__device__ __forceinline__ void mlp_hidden(const float* __restrict__ P, const float* x, float* h1, float* h2)
+{
+    for (int j = 0; j < kH; ++j) {
+        float a = P[oB1 + j];
+#pragma unroll
+        for (int i = 0; i < kF; ++i) a = fmaf(P[oW1 + j * kF + i], x[i], a);
+        h1[j] = fmaxf(a, 0.0f);
+    }
+    for (int j = 0; j < kH; ++j) {
+        float a = P[oB2 + j];
+        for (int i = 0; i < kH; ++i) a = fmaf(P[oW2 + j * kH + i], h1[i], a);
+        h2[j] = fmaxf(a, 0.0f);
+    }
+}
+
+__device__ __forceinline__ void mlp_logits(const float* __restrict__ P, const float* h2, float* z)
+{
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+        float a = P[oB3 + c];
+        for (int i = 0; i < kH; ++i) a = fmaf(P[oW3 + c * kH + i], h2[i], a);
+        z[c] = a;
+    }
+}
+
+// inference: one thread per tile, parameters staged in shared memory;
+// plan[t] = argmax of the logits (lowest class on ties)
+__global__ void __launch_bounds__(128) k_plan_tiles(const float* __restrict__ params, const float* __restrict__ feat,
+                                                    int T, uint8_t* __restrict__ plan)
+{
+    __shared__ float P[GS_PLAN_PARAMS];
+    for (int i = threadIdx.x; i < GS_PLAN_PARAMS; i += blockDim.x) P[i] = params[i];
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= T) return;
+    float x[kF], h1[kH], h2[kH], z[kC];
+#pragma unroll
+    for (int i = 0; i < kF; ++i) x[i] = feat[(int64_t)t * kF + i];
+    mlp_hidden(P, x, h1, h2);
+    mlp_logits(P, h2, z);
+    int best = 0;
+#pragma unroll
+    for (int c = 1; c < kC; ++c)
+        if (z[c] > z[best]) best = c;
+    plan[t] = (uint8_t)best;
+}
+
+// training forward: acts [B][2H] = (h1, h2), logits [B][C]
+__global__ void k_mlp_forward(const float* __restrict__ P, const float* __restrict__ X, int B,
+                              float* __restrict__ acts, float* __restrict__ logits)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B) return;
+    float x[kF], h1[kH], h2[kH], z[kC];
+#pragma unroll
+    for (int i = 0; i < kF; ++i) x[i] = X[(int64_t)s * kF + i];
+    mlp_hidden(P, x, h1, h2);
+    mlp_logits(P, h2, z);
+    float* a = acts + (int64_t)s * 2 * kH;
+    for (int j = 0; j < kH; ++j) {
+        a[j] = h1[j];
+        a[kH + j] = h2[j];
+    }
+#pragma unroll
+    for (int c = 0; c < kC; ++c) logits[(int64_t)s * kC + c] = z[c];
+}
+
+// mean softmax cross entropy over the batch: dlogits = (softmax - onehot) / B,
+// loss[0] += sum of per-sample losses / B
+__global__ void k_mlp_xent(const float* __restrict__ logits, const int32_t* __restrict__ labels, int B,
+                           float* __restrict__ dlogits, float* __restrict__ loss)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    float l = 0.0f;
+    if (s < B) {
+        const float* z = logits + (int64_t)s * kC;
+        float m = z[0];
+#pragma unroll
+        for (int c = 1; c < kC; ++c) m = fmaxf(m, z[c]);
+        float e[kC], sum = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kC; ++c) {
+            e[c] = expf(z[c] - m);
+            sum += e[c];
+        }
+        const int y = min(max(labels[s], 0), kC - 1);  // labels outside 0..5 count as the nearest class
+        const float inv = 1.0f / (sum * (float)B);
+#pragma unroll
+        for (int c = 0; c < kC; ++c) dlogits[(int64_t)s * kC + c] = e[c] * inv - (c == y ? 1.0f / (float)B : 0.0f);
+        l = (logf(sum) + m - z[y]) / (float)B;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0 && l != 0.0f) atomicAdd(loss, l);
+}
+
+// per-sample deltas of the two hidden layers: d2 = (W3^T dz) * [h2 > 0],
+// d1 = (W2^T d2) * [h1 > 0]; deltas [B][2H] = (d1, d2)
+__global__ void k_mlp_deltas(const float* __restrict__ P, const float* __restrict__ acts,
+                             const float* __restrict__ dlogits, int B, float* __restrict__ deltas)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= B) return;
+    const float* a = acts + (int64_t)s * 2 * kH;
+    const float* dz = dlogits + (int64_t)s * kC;
+    float d2[kH];
+    for (int i = 0; i < kH; ++i) {
+        float g = 0.0f;
+#pragma unroll
+        for (int c = 0; c < kC; ++c) g = fmaf(P[oW3 + c * kH + i], dz[c], g);
+        d2[i] = a[kH + i] > 0.0f ? g : 0.0f;
+    }
+    float* d = deltas + (int64_t)s * 2 * kH;
+    for (int i = 0; i < kH; ++i) {
+        float g = 0.0f;
+        for (int j = 0; j < kH; ++j) g = fmaf(P[oW2 + j * kH + i], d2[j], g);
+        d[i] = a[i] > 0.0f ? g : 0.0f;
+        d[kH + i] = d2[i];
+    }
+}
+
+// parameter gradients, one thread per parameter, summed over the batch:
+// dW1 = d1 x^T, db1 = sum d1, dW2 = d2 h1^T, db2 = sum d2, dW3 = dz h2^T, db3 = sum dz
+__global__ void k_mlp_wgrad(const float* __restrict__ X, const float* __restrict__ acts,
+                            const float* __restrict__ deltas, const float* __restrict__ dlogits, int B,
+                            float* __restrict__ grads)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= GS_PLAN_PARAMS) return;
+    float g = 0.0f;
+    if (p < oB1) {
+        const int j = (p - oW1) / kF, i = (p - oW1) % kF;
+        for (int s = 0; s < B; ++s) g = fmaf(deltas[(int64_t)s * 2 * kH + j], X[(int64_t)s * kF + i], g);
+    } else if (p < oW2) {
+        const int j = p - oB1;
+        for (int s = 0; s < B; ++s) g += deltas[(int64_t)s * 2 * kH + j];
+    } else if (p < oB2) {
+        const int j = (p - oW2) / kH, i = (p - oW2) % kH;
+        for (int s = 0; s < B; ++s) g = fmaf(deltas[(int64_t)s * 2 * kH + kH + j], acts[(int64_t)s * 2 * kH + i], g);
+    } else if (p < oW3) {
+        const int j = p - oB2;
+        for (int s = 0; s < B; ++s) g += deltas[(int64_t)s * 2 * kH + kH + j];
+    } else if (p < oB3) {
+        const int c = (p - oW3) / kH, i = (p - oW3) % kH;
+        for (int s = 0; s < B; ++s) g = fmaf(dlogits[(int64_t)s * kC + c], acts[(int64_t)s * 2 * kH + kH + i], g);
+    } else {
+        const int c = p - oB3;
+        for (int s = 0; s < B; ++s) g += dlogits[(int64_t)s * kC + c];
+    }
+    grads[p] = g;
+}
+
+// Adam (Kingma & Ba, 2015) with bias correction, step t >= 1
+__global__ void k_adam(float* __restrict__ params, const float* __restrict__ grads, float* __restrict__ m,
+                       float* __restrict__ v, int n, float lr, float b1, float b2, float eps, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = grads[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * g;
+    const float vi = b2 * v[i] + (1.0f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    params[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int gs_tile_features(gs_ctx* c, const gs_camera* cam, const int32_t* offsets, int32_t stride,
+                                float* features, void* stream)
+{
+    if (!c || !cam || !offsets || !features || stride < 1 || stride > GS_MAX_K) return GS_ERR_INVALID_ARG;
+    const int T = gs_num_tiles(cam->width, cam->height, c->cfg.tile_size);
+    if (T <= 0) return GS_ERR_INVALID_ARG;
+    const int threads = 256;
+    const unsigned grid = (unsigned)(((int64_t)T * 32 + threads - 1) / threads);
+    k_tile_features<<<grid, threads, 0, (cudaStream_t)stream>>>(offsets, stride, T, features);
+    c->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+extern "C" int gs_planner_set_weights(gs_ctx* c, const float* params, void* stream)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!params) {
+        c->planner_ready = 0;
+        return GS_OK;
+    }
+    if (!c->d_planner) {
+        void* p = nullptr;
+        size_t cap = 0;
+        const int r = ensure(&p, &cap, GS_PLAN_PARAMS * sizeof(float));
+        if (r != GS_OK) return r;
+        c->d_planner = (float*)p;
+    }
+    GS_CUDA_TRY(cudaMemcpyAsync(c->d_planner, params, GS_PLAN_PARAMS * sizeof(float), cudaMemcpyDefault,
+                                (cudaStream_t)stream));
+    c->planner_ready = 1;
+    return GS_OK;
+}
+
+extern "C" int gs_plan_tiles(gs_ctx* c, const float* features, int32_t n_tiles, uint8_t* plan, void* stream)
+{
+    if (!c || !features || !plan || n_tiles < 0) return GS_ERR_INVALID_ARG;
+    if (!c->planner_ready) return GS_ERR_INVALID_ARG;
+    if (n_tiles == 0) return GS_OK;
+    k_plan_tiles<<<(unsigned)((n_tiles + 127) / 128), 128, 0, (cudaStream_t)stream>>>(c->d_planner, features, n_tiles,
+                                                                                       plan);
+    c->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+extern "C" int gs_mlp_forward(const float* params, const float* X, int32_t B, float* acts, float* logits,
+                              void* stream)
+{
+    if (!params || !X || !acts || !logits || B < 1) return GS_ERR_INVALID_ARG;
+    k_mlp_forward<<<(unsigned)((B + 127) / 128), 128, 0, (cudaStream_t)stream>>>(params, X, B, acts, logits);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+extern "C" int gs_mlp_loss_grad(const float* logits, const int32_t* labels, int32_t B, float* dlogits, float* loss,
+                                void* stream)
+{
+    if (!logits || !labels || !dlogits || !loss || B < 1) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    GS_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+    k_mlp_xent<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(logits, labels, B, dlogits, loss);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+extern "C" int gs_mlp_backward(const float* params, const float* X, const float* acts, const float* dlogits,
+                               int32_t B, float* deltas, float* grads, void* stream)
+{
+    if (!params || !X || !acts || !dlogits || !deltas || !grads || B < 1) return GS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    k_mlp_deltas<<<(unsigned)((B + 127) / 128), 128, 0, st>>>(params, acts, dlogits, B, deltas);
+    k_mlp_wgrad<<<(unsigned)((GS_PLAN_PARAMS + 127) / 128), 128, 0, st>>>(X, acts, deltas, dlogits, B, grads);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+extern "C" int gs_adam_step(float* params, const float* grads, float* m, float* v, int32_t n, float lr, float beta1,
+                            float beta2, float eps, int32_t step, void* stream)
+{
+    if (!params || !grads || !m || !v || n < 1 || step < 1 || !(lr > 0.0f)) return GS_ERR_INVALID_ARG;
+    const float c1 = 1.0f - powf(beta1, (float)step), c2 = 1.0f - powf(beta2, (float)step);
+    k_adam<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(params, grads, m, v, n, lr, beta1, beta2,
+                                                                          eps, c1, c2);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}

@@ -126,7 +126,8 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
          const uint64_t* __restrict__ words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
          float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
          int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total, float* __restrict__ out_T,
-         int32_t* __restrict__ out_end)
+         int32_t* __restrict__ out_end, const uint8_t* __restrict__ plan, int default_cap,
+         long long* __restrict__ tile_cycles)
 {
     __shared__ RasterShared<TILE, BASELINE> sh;
     __shared__ WalkShared<LAZY> ws;
@@ -150,9 +151,16 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
     st.ops = 0;
     st.done = !inside;
 
+    long long c_start = 0;
+    if (tile_cycles && threadIdx.x == 0) c_start = clock64();
+    const int cap = plan ? plan_cap(plan[t]) : default_cap;
     FwdSpan<TILE, BASELINE, COUNT> span{sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st};
-    const int32_t end = walk_tile<TILE, LAZY>(words, off, t, a.stride, ws, span);
+    const int32_t end = walk_tile<TILE, LAZY>(words, off, t, a.stride, cap, ws, span);
     if (out_end && threadIdx.x == 0) out_end[t] = end;
+    if (tile_cycles) {
+        __syncthreads();
+        if (threadIdx.x == 0) tile_cycles[t] = clock64() - c_start;
+    }
     if (inside) {
         const int64_t p = (int64_t)py * a.width + px;
         out_rgb[3 * p] = fmaf(st.T, a.bg0, st.C0);
@@ -178,12 +186,13 @@ template <int TILE>
 static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cudaStream_t st, const ProjView& pv,
                         const uint64_t* words, const int32_t* off, const RasterArgs& a, int cull, float* rgb,
                         float* alpha, int32_t* last, int32_t* ntests, unsigned long long* ops, float* final_T,
-                        int32_t* tile_end)
+                        int32_t* tile_end, const uint8_t* plan, int cap, long long* cycles)
 {
     constexpr int BS = TILE * TILE;
 #define GS_RASTER_LAUNCH(B, CNT, LZ)                                                                        \
     k_raster<TILE, B, CNT, LZ><<<grid, BS, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, (B) ? 0 : cull, \
-                                                   rgb, alpha, last, ntests, ops, final_T, tile_end)
+                                                   rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap,     \
+                                                   cycles)
     if (baseline) {
         if (count) GS_RASTER_LAUNCH(true, true, false);
         else GS_RASTER_LAUNCH(true, false, false);
@@ -199,7 +208,8 @@ static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cud
 
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
-               int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T, int32_t* tile_end)
+               int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T, int32_t* tile_end,
+               const uint8_t* plan, long long* tile_cycles)
 {
     const int tile = ctx->cfg.tile_size;
     RasterArgs a;
@@ -217,14 +227,15 @@ int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
     // EXACT streams are culled when they are built: no second tile test at
     // staging, only the per-warp strip mask
     const int cull_here = !cull ? 0 : (ctx->cfg.mode == GS_MODE_BINNED_EXACT ? 2 : 3);
+    const int cap = chunk_cap(ctx->cfg);
     const unsigned grid = (unsigned)a.n_tiles;
     if (grid == 0) return GS_OK;
     unsigned long long* ops = reinterpret_cast<unsigned long long*>(ctx->d_ops);
     if (count) GS_CUDA_TRY(cudaMemsetAsync(ops, 0, sizeof(unsigned long long), st));
     switch (tile) {
-        case 8: launch_tile<8>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end); break;
-        case 32: launch_tile<32>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end); break;
-        default: launch_tile<16>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end); break;
+        case 8: launch_tile<8>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap, tile_cycles); break;
+        case 32: launch_tile<32>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap, tile_cycles); break;
+        default: launch_tile<16>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap, tile_cycles); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());

@@ -168,15 +168,18 @@ __device__ __forceinline__ void load_sort_chunk(const uint64_t* __restrict__ wor
 // offset within the run at which every pixel of the tile had terminated;
 // span.done() is the calling thread's termination flag).
 // Not LAZY: one run, the span [off[t*K], off[(t+1)*K]).  LAZY: chunks of
-// consecutive segments of at most kRasterSortCap entries are loaded into
-// shared memory and every segment of the chunk is sorted (small ones by one
-// warp each, long ones by the whole block); a segment longer than the cap was
-// sorted before the raster and is handed over in place.
+// consecutive segments of at most `cap` entries (a single segment of up to
+// kRasterSortCap entries forms a chunk of its own) are loaded into shared
+// memory and every segment of the chunk is sorted (small ones by one warp
+// each, long ones by the whole block); a segment longer than kRasterSortCap
+// was sorted before the raster and is handed over in place.  The chunks are
+// the tile's repair bins: `cap` sets their count and their split depths (the
+// bin boundaries where a chunk ends).
 // Returns the stream index at which the walk ended: the tile's span end, or
 // the position (in the composited order) where every pixel had terminated.
 template <int TILE, bool LAZY, class Span>
 __device__ __forceinline__ int32_t walk_tile(const uint64_t* __restrict__ words, const int32_t* __restrict__ off,
-                                             int t, int K, WalkShared<LAZY>& ws, Span& span)
+                                             int t, int K, int cap, WalkShared<LAZY>& ws, Span& span)
 {
     constexpr int BS = TILE * TILE;
     if (!LAZY) {
@@ -196,7 +199,7 @@ __device__ __forceinline__ int32_t walk_tile(const uint64_t* __restrict__ words,
             continue;
         }
         int e = b + 1;
-        while (e < K && ws.off[e + 1] - c0 <= kRasterSortCap) ++e;
+        while (e < K && ws.off[e + 1] - c0 <= cap) ++e;
         const int32_t len = ws.off[e] - c0;
         const int bfirst = b;
         b = e;

@@ -25,6 +25,9 @@ MODES = {"global": 0, "exact": 1, "paper": 2, "norepair": 3}
 STAGES = ["project", "intersect", "depth_range", "bin", "repair", "sort", "raster"]
 MAX_K = 128
 MAX_VIEWS = 32
+PLAN_FEATURES, PLAN_HIDDEN, PLAN_CLASSES = 8, 64, 6
+PLAN_PARAMS = PLAN_HIDDEN * PLAN_FEATURES + PLAN_HIDDEN + PLAN_HIDDEN * PLAN_HIDDEN + PLAN_HIDDEN + \
+    PLAN_CLASSES * PLAN_HIDDEN + PLAN_CLASSES
 RENDER_HOST_INPUTS, RENDER_HOST_OUTPUTS, RENDER_NO_SYNC, RENDER_GRAPH, RENDER_SAVE = 1, 2, 4, 8, 16
 P_XY_AB, P_C_O_Z, P_RGB, P_RECT, P_RADIUS = range(5)
 
@@ -38,7 +41,8 @@ EXPORTS = [
     "gs_last_entry_count", "gs_launch_count", "gs_last_raster_ops", "gs_depth_range_noalloc",
     "gs_grad2d_bytes", "gs_grad2d_offset", "gs_rasterize_bwd", "gs_render_bwd",
     "gs_render_batch", "gs_batch_set_view_config", "gs_batch_get_view_config", "gs_batch_last_entry_count",
-    "gs_batch_autotune",
+    "gs_batch_autotune", "gs_rasterize_fwd_plan", "gs_tile_features", "gs_planner_set_weights", "gs_plan_tiles",
+    "gs_mlp_forward", "gs_mlp_loss_grad", "gs_mlp_backward", "gs_adam_step",
 ]
 
 
@@ -57,7 +61,8 @@ class GsConfig(C.Structure):
                 ("sample_count", C.c_int32), ("p_lo", C.c_float), ("p_hi", C.c_float),
                 ("pad", C.c_float), ("near_alpha", C.c_float), ("near_gamma", C.c_float),
                 ("eps", C.c_float), ("repair_budget_frac", C.c_float), ("near_shift", C.c_int32),
-                ("tile_cull", C.c_int32), ("persistent", C.c_int32), ("repair_in_raster", C.c_int32)]
+                ("tile_cull", C.c_int32), ("persistent", C.c_int32), ("repair_in_raster", C.c_int32),
+                ("chunk_cap", C.c_int32), ("planner", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -128,6 +133,15 @@ def lib():
         "gs_batch_set_view_config": (C.c_int, [vp, i32, C.POINTER(GsConfig)]),
         "gs_batch_get_view_config": (C.c_int, [vp, i32, C.POINTER(GsConfig)]),
         "gs_batch_last_entry_count": (i64, [vp, i32]),
+        "gs_rasterize_fwd_plan": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32, C.POINTER(C.c_float),
+                                            vp, vp, vp, vp, vp, vp]),
+        "gs_tile_features": (C.c_int, [vp, C.POINTER(GsCamera), vp, i32, vp, vp]),
+        "gs_planner_set_weights": (C.c_int, [vp, vp, vp]),
+        "gs_plan_tiles": (C.c_int, [vp, vp, i32, vp, vp]),
+        "gs_mlp_forward": (C.c_int, [vp, vp, i32, vp, vp, vp]),
+        "gs_mlp_loss_grad": (C.c_int, [vp, vp, i32, vp, vp, vp]),
+        "gs_mlp_backward": (C.c_int, [vp, vp, vp, vp, i32, vp, vp, vp]),
+        "gs_adam_step": (C.c_int, [vp, vp, vp, vp, i32, C.c_float, C.c_float, C.c_float, C.c_float, i32, vp]),
         "gs_batch_autotune": (C.c_int, [vp, C.POINTER(GsScene), C.POINTER(GsCamera), i32, i32, i32,
                                         C.POINTER(C.c_float), vp]),
         "gs_grad2d_offset": (sz, [i64, i32]),
@@ -427,6 +441,54 @@ class Context:
         check(lib().gs_render_bwd(self.h, _ptr(dl_drgb), _ptr(dl_dalpha), _ptr(grad), _stream()), "gs_render_bwd")
         return grad
 
+    # ------------------------------------------------------------- bin planner
+    def rasterize_fwd_plan(self, projected, n, cam, words, offsets, plan=None, cycles=False, stride=None,
+                           bg=(0.0, 0.0, 0.0)):
+        """(rgb, alpha, last, tile_cycles or None) with an optional per-tile
+        chunk-class plan (uint8 [T])."""
+        import torch
+        dev = projected.device
+        H, W = int(cam.height), int(cam.width)
+        rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+        alpha = torch.empty((H, W), dtype=torch.float32, device=dev)
+        last = torch.empty((H, W), dtype=torch.int32, device=dev)
+        cyc = (torch.zeros(n_tiles(W, H, self.cfg.tile_size), dtype=torch.int64, device=dev) if cycles else None)
+        bgv = (C.c_float * 3)(*[float(x) for x in bg])
+        c = gs_camera(cam)
+        check(lib().gs_rasterize_fwd_plan(self.h, _ptr(projected), n, C.byref(c), _ptr(words), _ptr(offsets),
+                                          self.stride if stride is None else int(stride), bgv, _ptr(rgb),
+                                          _ptr(alpha), _ptr(last), _ptr(plan), _ptr(cyc), _stream()),
+              "gs_rasterize_fwd_plan")
+        return rgb, alpha, last, cyc
+
+    def tile_features(self, cam, offsets, stride=None):
+        import torch
+        T = n_tiles(cam.width, cam.height, self.cfg.tile_size)
+        f = torch.empty((T, PLAN_FEATURES), dtype=torch.float32, device=offsets.device)
+        c = gs_camera(cam)
+        check(lib().gs_tile_features(self.h, C.byref(c), _ptr(offsets), self.stride if stride is None else int(stride),
+                                     _ptr(f), _stream()), "gs_tile_features")
+        return f
+
+    def set_planner_weights(self, params):
+        """params: float32 tensor of PLAN_PARAMS values (device or CPU), or None."""
+        import torch
+        if params is None:
+            check(lib().gs_planner_set_weights(self.h, None, _stream()), "gs_planner_set_weights")
+            return
+        p = torch.as_tensor(params, dtype=torch.float32).contiguous()
+        if p.numel() != PLAN_PARAMS:
+            raise TileGSError(f"gs_planner_set_weights: invalid argument (expected {PLAN_PARAMS} floats)")
+        self._planner_params = p  # kept alive until the copy has run
+        check(lib().gs_planner_set_weights(self.h, _ptr(p), _stream()), "gs_planner_set_weights")
+
+    def plan_tiles(self, features):
+        import torch
+        plan = torch.empty(features.shape[0], dtype=torch.uint8, device=features.device)
+        check(lib().gs_plan_tiles(self.h, _ptr(features), int(features.shape[0]), _ptr(plan), _stream()),
+              "gs_plan_tiles")
+        return plan
+
     # ------------------------------------------------------------- batches
     def render_batch(self, sc: DeviceScene, cams, bg=(0.0, 0.0, 0.0), outs=None, flags=0):
         """All views of cams in one gs_render_batch call.  outs: list of
@@ -499,6 +561,43 @@ def projected_fields(projected, n):
     rect = projected[o[3]:o[3] + 8 * n].view(torch.int32).view(n, 2)
     radius = projected[o[4]:o[4] + 4 * n].view(torch.int32)
     return dict(xy_ab=xy_ab, c_o_z=c_o_z, rgb=rgb, rect=rect, radius=radius)
+
+
+def mlp_forward(params, X):
+    """Planner network on X [B][8] (device float32): (acts [B][128], logits [B][6])."""
+    import torch
+    B = int(X.shape[0])
+    acts = torch.empty((B, 2 * PLAN_HIDDEN), dtype=torch.float32, device=X.device)
+    logits = torch.empty((B, PLAN_CLASSES), dtype=torch.float32, device=X.device)
+    check(lib().gs_mlp_forward(_ptr(params), _ptr(X), B, _ptr(acts), _ptr(logits), _stream()), "gs_mlp_forward")
+    return acts, logits
+
+
+def mlp_loss_grad(logits, labels):
+    """(loss [1], dlogits [B][6]) of the mean softmax cross entropy."""
+    import torch
+    B = int(logits.shape[0])
+    d = torch.empty_like(logits)
+    loss = torch.empty(1, dtype=torch.float32, device=logits.device)
+    check(lib().gs_mlp_loss_grad(_ptr(logits), _ptr(labels), B, _ptr(d), _ptr(loss), _stream()), "gs_mlp_loss_grad")
+    return loss, d
+
+
+def mlp_backward(params, X, acts, dlogits, grads=None, deltas=None):
+    import torch
+    B = int(X.shape[0])
+    if deltas is None:
+        deltas = torch.empty((B, 2 * PLAN_HIDDEN), dtype=torch.float32, device=X.device)
+    if grads is None:
+        grads = torch.empty(PLAN_PARAMS, dtype=torch.float32, device=X.device)
+    check(lib().gs_mlp_backward(_ptr(params), _ptr(X), _ptr(acts), _ptr(dlogits), B, _ptr(deltas), _ptr(grads),
+                                _stream()), "gs_mlp_backward")
+    return grads
+
+
+def adam_step(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    check(lib().gs_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(params.numel()), float(lr),
+                             float(beta1), float(beta2), float(eps), int(step), _stream()), "gs_adam_step")
 
 
 def grad_fields(grad, n):
