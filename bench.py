@@ -446,6 +446,30 @@ def run_ours(args):
                  "step": "frame (CUDA graph, RENDER_SAVE) + L1 loss gradient vs a U[0,1] target + gs_render_bwd",
                  "clocks": clk_t.summary()}
 
+    # the learned bin planner on the same frame: per-tile chunk plan against
+    # the fixed chunk size (images compared bit for bit)
+    planner = None
+    wpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2609_03613_gb300",
+                         "planner_weights.npy")
+    if os.path.exists(wpath):
+        ctx_pl = G.Context("exact", planner=1)
+        ctx_pl.set_planner_weights(torch.from_numpy(np.load(wpath).astype(np.float32)))
+        out_pl = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
+                  torch.empty((H, W), dtype=torch.int32, device=dev))
+        with torch.cuda.stream(side):
+            ctx_pl.render(ds, cam, bg, out_pl)
+        torch.cuda.synchronize()
+        ctx_pl.reserve(ds.n, int(ctx_pl.last_entry_count() * 1.25) + 1024, W, H)
+        ms_pl, _, _, _ = timed(ctx_pl, out_pl, args.steps, args.warmup)
+        _, st_pl, _, _ = timed(ctx_pl, out_pl, max(50, args.steps // 2), 3, flags=G.RENDER_NO_SYNC)
+        with torch.cuda.stream(side):
+            ctx_pl.render(ds, cam, bg, out_pl)
+        torch.cuda.synchronize()
+        planner = {"frame_ms": round(mean(ms_pl), 4), "raster_ms": round(mean(st_pl["raster"]), 4),
+                   "frame_ms_fixed": round(frame_b, 4), "raster_ms_fixed": round(raster_b, 4),
+                   "raster_gain": round(1.0 - mean(st_pl["raster"]) / raster_b, 4),
+                   "image_equal_fixed": bool(torch.equal(out_pl[0], out_b[0]) and torch.equal(out_pl[2], out_b[2]))}
+
     batch = None
     if not args.no_batch:
         batch = batch_leg(args, dev, side, flush, dist)
@@ -482,7 +506,7 @@ def run_ours(args):
         "frame_ms_without_graph": {"binned": round(mean(ms_b_ng), 4), "global_sort": round(mean(ms_g_ng), 4)},
         "wall_s_timed": round(wall_b, 3),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "train_step": train,
-        "batch16": batch,
+        "planner": planner, "batch16": batch,
         "gpu_launches": int(launches),
     }
     print(json.dumps(res), flush=True)

@@ -6,7 +6,10 @@ Data (one "render" = one seeded scene and camera, EXACT mode, K = 64):
   * gs_tile_features gives each tile's 8 features;
   * the raster runs once per chunk class c = 0..5 with every tile forced to c
     (gs_rasterize_fwd_plan) and records each tile's clock64() cycles, `reps`
-    times; the label of a tile is the class of its smallest median cycles.
+    times; the label of a tile is the class of its smallest median cycles
+    (softmax cross entropy on these labels saved more cycles on a held-out
+    split than an expected-cost loss or labels that keep the default class
+    within a few percent).
 Training: mini-batch Adam on the GPU, entirely through the library's own
 kernels (gs_mlp_forward, gs_mlp_loss_grad, gs_mlp_backward, gs_adam_step).
 Feature standardisation is folded into the first layer afterwards, so the
@@ -101,7 +104,7 @@ def fold_standardisation(params, mu, sd):
     return p.astype(np.float32)
 
 
-def train(X, y, epochs=40, batch=4096, lr=3e-3, seed=0):
+def train(X, y, epochs=20, batch=4096, lr=3e-3, seed=0):
     """Adam on the GPU through the library kernels; returns (params, loss history)."""
     import torch
     dev = torch.device("cuda")
@@ -131,9 +134,9 @@ def train(X, y, epochs=40, batch=4096, lr=3e-3, seed=0):
     return fold_standardisation(P.cpu().numpy(), mu, sd), hist
 
 
-def labels_of(cycles, default_class=2, margin=0.03):
-    """argmin class per tile; tiles whose best class is within `margin` of the
-    default's cycles keep the default (the measurement cannot tell them apart)."""
+def labels_of(cycles, default_class=2, margin=0.0):
+    """argmin class per tile; with margin > 0, tiles whose best class is within
+    `margin` of the default's cycles keep the default."""
     best = np.argmin(cycles, axis=1)
     dflt = cycles[:, default_class]
     keep_default = cycles[np.arange(len(best)), best] >= (1.0 - margin) * dflt
@@ -181,7 +184,7 @@ def main():
     ap.add_argument("--scenes", type=int, default=20)
     ap.add_argument("--views", type=int, default=10)
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--epochs", type=int, default=20)
     ap.add_argument("--dump", default=None, help="npz of a 300k-tile sample of the logged data")
     args = ap.parse_args()
     t0 = time.time()
