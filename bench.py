@@ -222,7 +222,7 @@ def run_reference(args):
 # --------------------------------------------------------------------- ours
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("raster.cu", "internal.cuh", "device.cuh"):
+    for f in ("raster.cu", "raster_common.cuh", "internal.cuh", "device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2609_03613_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -285,13 +285,17 @@ int gs_depth_range_noalloc(const gs_config* cfg, const void* projected, const fl
  *   final transmittance T of each pixel (exact; alpha = 1 - T is rounded),
  *   and per tile the stream index at which its compositing ended (the span
  *   end, or the position in compositing order where every pixel of the tile
- *   had stopped).
+ *   had stopped).  With tile_end, an EXACT stream whose repair runs in the
+ *   raster is modified in place: the segments the raster sorted are stored
+ *   back sorted, so [span start, tile_end) of every tile is left in
+ *   (depth, gid) order (the stream stays valid for any later raster).
+ * stream_words is only read otherwise.
  * The GLOBAL kernel is the plain baseline (gsplat-style batch staging); the
  * binned kernel adds the conservative tile-alpha cull and colour staging of
  * the paper's default configuration.  Both give identical images.
  */
 int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
-                     const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
+                     uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
                      const float* bg, float* rgb, float* alpha, int32_t* last, int32_t* ntests,
                      float* final_T, int32_t* tile_end, void* stream);
 
@@ -300,7 +304,8 @@ int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_cam
  * the projected 2D parameters.  The paper has no backward (Sec. 7 leaves it
  * to future work and asks that it follow the forward's compositing order);
  * this one walks each tile's span in the forward's order reversed, from the
- * forward's tile_end back to the span start, for the same stream, offsets
+ * forward's tile_end back to the span start, for the same stream (as the
+ * forward that saved tile_end left it: composited prefixes sorted), offsets
  * and context configuration, and differentiates
  *   rgb = sum_i c_i a_i T_i + T_N bg,  alpha = 1 - T_N,
  *   a_i = min(0.99, o_i exp(-q_i)),  q_i = 1/2 d^T conic d,  d = mean - centre
@@ -337,7 +342,7 @@ int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_cam
  * image does not depend on the plan.
  */
 int gs_rasterize_fwd_plan(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
-                          const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
+                          uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
                           const float* bg, float* rgb, float* alpha, int32_t* last, const uint8_t* plan,
                           long long* tile_cycles, void* stream);
 

@@ -397,7 +397,7 @@ extern "C" int gs_sort_or_bin(gs_ctx* ctx, const void* projected, const float* s
 }
 
 extern "C" int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
-                                const uint64_t* stream_words, const int32_t* offsets,
+                                uint64_t* stream_words, const int32_t* offsets,
                                 int32_t offsets_stride, const float* bg, float* rgb, float* alpha,
                                 int32_t* last, int32_t* ntests, float* final_T, int32_t* tile_end, void* stream)
 {
@@ -415,7 +415,7 @@ extern "C" int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, c
 }
 
 extern "C" int gs_rasterize_fwd_plan(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
-                                     const uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
+                                     uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
                                      const float* bg, float* rgb, float* alpha, int32_t* last, const uint8_t* plan,
                                      long long* tile_cycles, void* stream)
 {
@@ -582,8 +582,7 @@ int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs
     if (c->cfg.planner && c->cfg.mode == GS_MODE_BINNED_EXACT && c->cfg.repair_in_raster) {
         if (!c->planner_ready) return GS_ERR_INVALID_ARG;  // gs_planner_set_weights first
         if ((r = planner_buffers(c, T)) != GS_OK) return r;
-        if ((r = gs_tile_features(c, cam, c->r_off, stride, c->d_feat, st)) != GS_OK) return r;
-        if ((r = gs_plan_tiles(c, c->d_feat, T, c->d_plan, st)) != GS_OK) return r;
+        if ((r = plan_frame(c, c->r_off, stride, T, c->d_plan, st)) != GS_OK) return r;
         plan = c->d_plan;
     }
     r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,

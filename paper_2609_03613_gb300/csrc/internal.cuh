@@ -315,7 +315,7 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
                      const int64_t* m_dev, const gs_camera* cam, cudaStream_t st);
 
 // raster.cu
-int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* stream_words,
+int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* stream_words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T = nullptr,
                int32_t* tile_end = nullptr, const uint8_t* plan = nullptr, long long* tile_cycles = nullptr);
@@ -331,6 +331,8 @@ bool camera_ok(const gs_camera* cam);
 int render_buffers(gs_ctx* c, int64_t n, int64_t m_cap, int32_t T);
 int render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T);
 int planner_buffers(gs_ctx* c, int32_t T);
+// planner.cu: features and plan of every tile of a binned stream, one launch
+int plan_frame(gs_ctx* c, const int32_t* offsets, int32_t K, int32_t T, uint8_t* plan, cudaStream_t st);
 int render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, const float* bg,
                          float* d_rgb, float* d_alpha, int32_t* d_last, int32_t flags, cudaStream_t st);
 

@@ -31,12 +31,11 @@ constexpr int oW1 = 0, oB1 = oW1 + kH * kF, oW2 = oB1 + kH, oB2 = oW2 + kH * kH,
 static_assert(oB3 + kC == GS_PLAN_PARAMS, "parameter layout");
 static_assert(kC == kPlanClasses, "plan classes");
 
-// one warp per tile; K <= GS_MAX_K (128) -> at most 4 bins per lane
-__global__ void k_tile_features(const int32_t* __restrict__ off, int K, int T, float* __restrict__ feat)
+// The features of tile t, in every lane of the calling warp (K <= GS_MAX_K,
+// so at most 4 bins per lane).
+__device__ __forceinline__ void warp_tile_features(const int32_t* __restrict__ off, int K, int t, float (&f)[kF])
 {
     const int lane = threadIdx.x & 31;
-    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (t >= T) return;
     const int32_t* o = off + (int64_t)t * K;
     int cnt[4];
     int mx = 0, ne = 0, first = K, last = -1;
@@ -71,19 +70,84 @@ __global__ void k_tile_features(const int32_t* __restrict__ off, int K, int T, f
         front += __shfl_xor_sync(0xffffffffu, front, s);
         nfirst += __shfl_xor_sync(0xffffffffu, nfirst, s);
     }
-    if (lane == 0) {
-        const int n = o[K] - o[0];
-        float* f = feat + (int64_t)t * kF;
-        const float fk = (float)K;
-        f[0] = log1pf((float)n);
-        f[1] = log1pf((float)mx);
-        f[2] = (float)ne / fk;
-        f[3] = ne > 0 ? (float)first / fk : 1.0f;
-        f[4] = ne > 0 ? (float)last / fk : 0.0f;
-        f[5] = log1pf((float)nfirst);
-        f[6] = log1pf((float)front);
-        f[7] = ne > 0 ? log1pf((float)n / (float)ne) : 0.0f;
+    const int n = o[K] - o[0];
+    const float fk = (float)K;
+    f[0] = log1pf((float)n);
+    f[1] = log1pf((float)mx);
+    f[2] = (float)ne / fk;
+    f[3] = ne > 0 ? (float)first / fk : 1.0f;
+    f[4] = ne > 0 ? (float)last / fk : 0.0f;
+    f[5] = log1pf((float)nfirst);
+    f[6] = log1pf((float)front);
+    f[7] = ne > 0 ? log1pf((float)n / (float)ne) : 0.0f;
+}
+
+// one warp per tile
+__global__ void k_tile_features(const int32_t* __restrict__ off, int K, int T, float* __restrict__ feat)
+{
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (t >= T) return;
+    float f[kF];
+    warp_tile_features(off, K, t, f);
+    if ((threadIdx.x & 31) < kF) {
+        float v = f[0];
+#pragma unroll
+        for (int i = 1; i < kF; ++i)
+            if ((threadIdx.x & 31) == i) v = f[i];
+        feat[(int64_t)t * kF + (threadIdx.x & 31)] = v;
     }
+}
+
+// The planner network for one tile by one warp (features in every lane):
+// lane l holds hidden units l and l + 32 of both layers; the logits are warp
+// sums.  Returns the argmax class (lowest on ties) in every lane.
+__device__ __forceinline__ int warp_plan(const float* __restrict__ P, const float (&f)[kF])
+{
+    const int lane = threadIdx.x & 31;
+    float h1[2], h2[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int j = lane + 32 * u;
+        float a = __ldg(P + oB1 + j);
+#pragma unroll
+        for (int i = 0; i < kF; ++i) a = fmaf(__ldg(P + oW1 + j * kF + i), f[i], a);
+        h1[u] = fmaxf(a, 0.0f);
+    }
+    float a0 = __ldg(P + oB2 + lane), a1 = __ldg(P + oB2 + lane + 32);
+#pragma unroll 8
+    for (int i = 0; i < kH; ++i) {
+        const float hi = __shfl_sync(0xffffffffu, h1[i >> 5], i & 31);
+        a0 = fmaf(__ldg(P + oW2 + lane * kH + i), hi, a0);
+        a1 = fmaf(__ldg(P + oW2 + (lane + 32) * kH + i), hi, a1);
+    }
+    h2[0] = fmaxf(a0, 0.0f);
+    h2[1] = fmaxf(a1, 0.0f);
+    int best = 0;
+    float zbest = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+        float z = fmaf(__ldg(P + oW3 + c * kH + lane), h2[0], __ldg(P + oW3 + c * kH + lane + 32) * h2[1]);
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) z += __shfl_xor_sync(0xffffffffu, z, s);
+        z += __ldg(P + oB3 + c);
+        if (c == 0 || z > zbest) {
+            zbest = z;
+            best = c;
+        }
+    }
+    return best;
+}
+
+// features and plan of every tile in one launch (the render path)
+__global__ void k_plan_fused(const int32_t* __restrict__ off, int K, int T, const float* __restrict__ params,
+                             uint8_t* __restrict__ plan)
+{
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (t >= T) return;
+    float f[kF];
+    warp_tile_features(off, K, t, f);
+    const int c = warp_plan(params, f);
+    if ((threadIdx.x & 31) == 0) plan[t] = (uint8_t)c;
 }
 
 // hidden activations of one sample (ReLU outputs)
@@ -112,26 +176,17 @@ __device__ __forceinline__ void mlp_logits(const float* __restrict__ P, const fl
     }
 }
 
-// inference: one thread per tile, parameters staged in shared memory;
-// plan[t] = argmax of the logits (lowest class on ties)
-__global__ void __launch_bounds__(128) k_plan_tiles(const float* __restrict__ params, const float* __restrict__ feat,
-                                                    int T, uint8_t* __restrict__ plan)
+// inference from given features: one warp per tile
+__global__ void k_plan_tiles(const float* __restrict__ params, const float* __restrict__ feat, int T,
+                             uint8_t* __restrict__ plan)
 {
-    __shared__ float P[GS_PLAN_PARAMS];
-    for (int i = threadIdx.x; i < GS_PLAN_PARAMS; i += blockDim.x) P[i] = params[i];
-    __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     if (t >= T) return;
-    float x[kF], h1[kH], h2[kH], z[kC];
+    float f[kF];
 #pragma unroll
-    for (int i = 0; i < kF; ++i) x[i] = feat[(int64_t)t * kF + i];
-    mlp_hidden(P, x, h1, h2);
-    mlp_logits(P, h2, z);
-    int best = 0;
-#pragma unroll
-    for (int c = 1; c < kC; ++c)
-        if (z[c] > z[best]) best = c;
-    plan[t] = (uint8_t)best;
+    for (int i = 0; i < kF; ++i) f[i] = feat[(int64_t)t * kF + i];
+    const int c = warp_plan(params, f);
+    if ((threadIdx.x & 31) == 0) plan[t] = (uint8_t)c;
 }
 
 // training forward: acts [B][2H] = (h1, h2), logits [B][C]
@@ -271,6 +326,18 @@ extern "C" int gs_tile_features(gs_ctx* c, const gs_camera* cam, const int32_t* 
     return GS_OK;
 }
 
+namespace gs {
+int plan_frame(gs_ctx* c, const int32_t* offsets, int32_t K, int32_t T, uint8_t* plan, cudaStream_t st)
+{
+    if (!c->planner_ready) return GS_ERR_INVALID_ARG;
+    if (T <= 0) return GS_OK;
+    k_plan_fused<<<(unsigned)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(offsets, K, T, c->d_planner, plan);
+    c->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+}  // namespace gs
+
 extern "C" int gs_planner_set_weights(gs_ctx* c, const float* params, void* stream)
 {
     if (!c) return GS_ERR_INVALID_ARG;
@@ -296,8 +363,8 @@ extern "C" int gs_plan_tiles(gs_ctx* c, const float* features, int32_t n_tiles, 
     if (!c || !features || !plan || n_tiles < 0) return GS_ERR_INVALID_ARG;
     if (!c->planner_ready) return GS_ERR_INVALID_ARG;
     if (n_tiles == 0) return GS_OK;
-    k_plan_tiles<<<(unsigned)((n_tiles + 127) / 128), 128, 0, (cudaStream_t)stream>>>(c->d_planner, features, n_tiles,
-                                                                                       plan);
+    k_plan_tiles<<<(unsigned)(((int64_t)n_tiles * 32 + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
+        c->d_planner, features, n_tiles, plan);
     c->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;

@@ -123,7 +123,7 @@ struct FwdSpan {
 template <int TILE, bool BASELINE, bool COUNT, bool LAZY>
 __global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 1)
 k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
-         const uint64_t* __restrict__ words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
+         uint64_t* words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
          float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
          int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total, float* __restrict__ out_T,
          int32_t* __restrict__ out_end, const uint8_t* __restrict__ plan, int default_cap,
@@ -155,7 +155,8 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
     if (tile_cycles && threadIdx.x == 0) c_start = clock64();
     const int cap = plan ? plan_cap(plan[t]) : default_cap;
     FwdSpan<TILE, BASELINE, COUNT> span{sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st};
-    const int32_t end = walk_tile<TILE, LAZY>(words, off, t, a.stride, cap, ws, span);
+    // saving for the backward: the sorted chunks go back into the stream
+    const int32_t end = walk_tile<TILE, LAZY>(words, off, t, a.stride, cap, ws, span, out_end ? words : nullptr);
     if (out_end && threadIdx.x == 0) out_end[t] = end;
     if (tile_cycles) {
         __syncthreads();
@@ -184,7 +185,7 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
 
 template <int TILE>
 static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cudaStream_t st, const ProjView& pv,
-                        const uint64_t* words, const int32_t* off, const RasterArgs& a, int cull, float* rgb,
+                        uint64_t* words, const int32_t* off, const RasterArgs& a, int cull, float* rgb,
                         float* alpha, int32_t* last, int32_t* ntests, unsigned long long* ops, float* final_T,
                         int32_t* tile_end, const uint8_t* plan, int cap, long long* cycles)
 {
@@ -206,7 +207,7 @@ static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cud
 #undef GS_RASTER_LAUNCH
 }
 
-int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words,
+int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T, int32_t* tile_end,
                const uint8_t* plan, long long* tile_cycles)

@@ -1,9 +1,10 @@
 // raster_bwd.cu -- K22: backward of the tile compositing.  The paper leaves
 // the backward pass to future work and requires it to follow the forward's
-// compositing order (Sec. 7); this kernel walks every tile's span as the
-// forward did (raster_common.cuh: same runs, staging, culls and, for EXACT
-// streams, the same in-raster segment sorts), but back to front, from the
-// position where the forward's tile ended.  One CTA per tile, one thread per
+// compositing order (Sec. 7); this kernel walks every tile's span in that
+// order, back to front, from the position where the forward's tile ended
+// (raster_common.cuh: same staging and culls; an EXACT forward that saved its
+// state wrote its in-raster sorts back, so the composited prefix is already
+// in order and nothing is sorted here).  One CTA per tile, one thread per
 // pixel.
 //
 // Each pixel starts from the forward's saved final transmittance T_N and the
@@ -158,8 +159,8 @@ struct BwdSpan {
     }
 };
 
-template <int TILE, bool LAZY>
-__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 4 : 1)
+template <int TILE>
+__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 1)
 k_raster_bwd(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
              const uint64_t* __restrict__ words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
              const int32_t* __restrict__ last, const float* __restrict__ final_T,
@@ -169,7 +170,6 @@ k_raster_bwd(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z,
 {
     using SH = RasterShared<TILE, false>;
     __shared__ SH sh;
-    __shared__ WalkShared<LAZY> ws;
     __shared__ float acc[SH::BATCH * kTerms];
 
     const int t = blockIdx.x;
@@ -199,22 +199,16 @@ k_raster_bwd(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z,
 
     BwdSpan<TILE> span{sh, acc, xy_ab, c_o_z, rgbv, g_xy_ab, g_c_o_z, g_rgb, cullmode, tx, ty,
                        (float)px + 0.5f, (float)py + 0.5f, st};
-    walk_tile_rev<TILE, LAZY>(words, off, t, a.stride, tile_end[t], ws, span);
+    walk_tile_rev(words, off, t, a.stride, tile_end[t], span);
 }
 
 template <int TILE>
-void launch_bwd(bool lazy, unsigned grid, cudaStream_t st, const ProjView& pv, const uint64_t* words,
-                const int32_t* off, const RasterArgs& a, int cull, const int32_t* last, const float* final_T,
-                const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, const GradView& gv)
+void launch_bwd(unsigned grid, cudaStream_t st, const ProjView& pv, const uint64_t* words, const int32_t* off,
+                const RasterArgs& a, int cull, const int32_t* last, const float* final_T, const int32_t* tile_end,
+                const float* dl_drgb, const float* dl_dalpha, const GradView& gv)
 {
-    if (lazy)
-        k_raster_bwd<TILE, true><<<grid, TILE * TILE, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, cull,
-                                                               last, final_T, tile_end, dl_drgb, dl_dalpha, gv.xy_ab,
-                                                               gv.c_o_z, gv.rgb);
-    else
-        k_raster_bwd<TILE, false><<<grid, TILE * TILE, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, cull,
-                                                                last, final_T, tile_end, dl_drgb, dl_dalpha, gv.xy_ab,
-                                                                gv.c_o_z, gv.rgb);
+    k_raster_bwd<TILE><<<grid, TILE * TILE, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, cull, last, final_T,
+                                                    tile_end, dl_drgb, dl_dalpha, gv.xy_ab, gv.c_o_z, gv.rgb);
 }
 
 }  // namespace
@@ -234,7 +228,6 @@ int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
     a.bg0 = bg[0];
     a.bg1 = bg[1];
     a.bg2 = bg[2];
-    const bool lazy = ctx->cfg.mode == GS_MODE_BINNED_EXACT && ctx->cfg.repair_in_raster;
     // the staging culls are conservative, so they change no decision: EXACT
     // streams were culled when built (strip mask only), the others are culled
     // here as in the binned forward
@@ -242,9 +235,9 @@ int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
     const unsigned grid = (unsigned)a.n_tiles;
     if (grid == 0) return GS_OK;
     switch (tile) {
-        case 8: launch_bwd<8>(lazy, grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
-        case 32: launch_bwd<32>(lazy, grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
-        default: launch_bwd<16>(lazy, grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
+        case 8: launch_bwd<8>(grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
+        case 32: launch_bwd<32>(grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
+        default: launch_bwd<16>(grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());

@@ -5,8 +5,9 @@
 // EXACT streams whose repair runs in the raster, chunk by chunk with each
 // segment of 2..kRasterSortCap entries sorted in shared memory by (depth bits,
 // gid) right before it is composited (Sec. 3.5 selective repair; supplement,
-// binned raster traversal after repair).  Both kernels therefore visit every
-// tile's entries in the same order.
+// binned raster traversal after repair).  A forward that saves its state for
+// the backward stores the sorted chunks back, so the backward walks the same
+// order in place.
 #pragma once
 #include "device.cuh"
 
@@ -122,8 +123,7 @@ template <bool LAZY>
 struct WalkShared {
     uint64_t sort[LAZY ? kRasterSortCap : 1];
     int32_t off[LAZY ? GS_MAX_K + 1 : 1];
-    int big[LAZY ? 2 * GS_MAX_K : 1];  // segments sorted by the whole block (the reverse walk keeps its run list first)
-    int nbig;
+    int big[LAZY ? GS_MAX_K : 1];  // segments sorted by the whole block
     int nsort;
 };
 
@@ -132,14 +132,14 @@ struct WalkShared {
 // registers by one warp, up to 256 in shared memory by one warp, longer ones by
 // the whole block.  ws.big[base..] collects the long ones.
 template <int TILE, bool LAZY>
-__device__ __forceinline__ void load_sort_chunk(const uint64_t* __restrict__ words, int32_t c0, int32_t len,
+__device__ __forceinline__ void load_sort_chunk(const uint64_t* words, int32_t c0, int32_t len,
                                                 int bfirst, int e, WalkShared<LAZY>& ws, int base = 0)
 {
     constexpr int BS = TILE * TILE;
     constexpr int NWB = BS / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < len; i += BS) ws.sort[i] = words[c0 + i];
-    if (threadIdx.x == 0) ws.nsort = base;
+    if (threadIdx.x == 0) ws.nsort = 0;
     __syncthreads();
     for (int j = bfirst + warp; j < e; j += NWB) {
         const int l = ws.off[j + 1] - ws.off[j];
@@ -157,7 +157,7 @@ __device__ __forceinline__ void load_sort_chunk(const uint64_t* __restrict__ wor
     }
     __syncthreads();
     const int nbig = ws.nsort;
-    for (int k = base; k < nbig; ++k) {
+    for (int k = 0; k < nbig; ++k) {
         const int j = ws.big[k];
         bitonic_mem(ws.sort + (ws.off[j] - c0), ws.off[j + 1] - ws.off[j], threadIdx.x, BS, SyncBlock{});
     }
@@ -177,9 +177,11 @@ __device__ __forceinline__ void load_sort_chunk(const uint64_t* __restrict__ wor
 // bin boundaries where a chunk ends).
 // Returns the stream index at which the walk ended: the tile's span end, or
 // the position (in the composited order) where every pixel had terminated.
+// With writeback (the stream itself), every sorted chunk is also stored back
+// in place, so the tile's composited prefix is left in (depth, gid) order.
 template <int TILE, bool LAZY, class Span>
-__device__ __forceinline__ int32_t walk_tile(const uint64_t* __restrict__ words, const int32_t* __restrict__ off,
-                                             int t, int K, int cap, WalkShared<LAZY>& ws, Span& span)
+__device__ __forceinline__ int32_t walk_tile(const uint64_t* words, const int32_t* __restrict__ off, int t, int K,
+                                             int cap, WalkShared<LAZY>& ws, Span& span, uint64_t* writeback = nullptr)
 {
     constexpr int BS = TILE * TILE;
     if (!LAZY) {
@@ -205,67 +207,26 @@ __device__ __forceinline__ int32_t walk_tile(const uint64_t* __restrict__ words,
         b = e;
         if (len == 0) continue;
         if (__syncthreads_count(span.done()) == BS) return c0;
-        load_sort_chunk<TILE>(words, c0, len, bfirst, e, ws);
+        load_sort_chunk<TILE>(words, c0, len, bfirst, e, ws);  // ends with a block barrier
+        if (writeback)
+            for (int i = threadIdx.x; i < len; i += BS) writeback[c0 + i] = ws.sort[i];
         const int32_t r = span(ws.sort, len);
         if (r >= 0) return c0 + r;
     }
     return ws.off[K];
 }
 
-// The walk of walk_tile in reverse, over the entries before stream index
-// `end` (a walk_tile result): the same runs, chunks and in-chunk sorts,
-// handed to span(src, n) from the last run to the first.
-template <int TILE, bool LAZY, class Span>
+// The walk of walk_tile in reverse over the entries before stream index
+// `end` (a walk_tile result), for a stream sorted throughout or one whose
+// composited prefixes the forward wrote back sorted: the span
+// [off[t*K], min(end, off[(t+1)*K])) handed to span(src, n) in place.
+template <class Span>
 __device__ __forceinline__ void walk_tile_rev(const uint64_t* __restrict__ words, const int32_t* __restrict__ off,
-                                              int t, int K, int32_t end, WalkShared<LAZY>& ws, Span& span)
+                                              int t, int K, int32_t end, Span& span)
 {
-    constexpr int BS = TILE * TILE;
-    if (!LAZY) {
-        const int32_t s0 = off[(int64_t)t * K], s1 = off[(int64_t)(t + 1) * K];
-        const int32_t e = end < s1 ? end : s1;
-        if (e > s0) span(words + s0, e - s0);
-        return;
-    }
-    for (int b = threadIdx.x; b <= K; b += BS) ws.off[b] = off[(int64_t)t * K + b];
-    __syncthreads();
-    // the runs of the forward walk (first bin of each) up to `end`
-    if (threadIdx.x == 0) {
-        int nr = 0, b = 0;
-        while (b < K && ws.off[b] < end) {
-            const int32_t c0 = ws.off[b];
-            ws.big[nr++] = b;
-            if (ws.off[b + 1] - c0 > kRasterSortCap) {
-                ++b;
-                continue;
-            }
-            int e = b + 1;
-            while (e < K && ws.off[e + 1] - c0 <= kRasterSortCap) ++e;
-            b = e;
-        }
-        ws.nbig = nr;
-    }
-    __syncthreads();
-    const int nr = ws.nbig;
-    for (int r = nr - 1; r >= 0; --r) {
-        __syncthreads();  // ws.big / ws.sort of the previous run are no longer read
-        const int b = ws.big[r];
-        const int32_t c0 = ws.off[b];
-        if (ws.off[b + 1] - c0 > kRasterSortCap) {
-            const int32_t n = (end < ws.off[b + 1] ? end : ws.off[b + 1]) - c0;
-            span(words + c0, n);
-            continue;
-        }
-        int e = b + 1;
-        while (e < K && ws.off[e + 1] - c0 <= kRasterSortCap) ++e;
-        const int32_t len = ws.off[e] - c0;
-        if (len == 0) continue;
-        const int32_t n = (end < ws.off[e] ? end : ws.off[e]) - c0;
-        // the whole chunk is sorted (its first n entries in sorted order are
-        // the ones the forward composited); big-segment ids go after the run
-        // list in ws.big
-        load_sort_chunk<TILE>(words, c0, len, b, e, ws, nr);
-        span(ws.sort, n);
-    }
+    const int32_t s0 = off[(int64_t)t * K], s1 = off[(int64_t)(t + 1) * K];
+    const int32_t e = end < s1 ? end : s1;
+    if (e > s0) span(words + s0, e - s0);
 }
 
 }  // namespace gs
