@@ -98,38 +98,70 @@ __global__ void k_tile_features(const int32_t* __restrict__ off, int K, int T, f
     }
 }
 
+// Inference parameters in shared memory, laid out so that lane l reads
+// consecutive words: W1t[i][j] = W1[j][i], W2t[i][j] = W2[j][i].
+struct PlanShared {
+    float W1t[kF * kH];
+    float b1[kH];
+    float W2t[kH * kH];
+    float b2[kH];
+    float W3[kC * kH];
+    float b3[kC];
+};
+
+__device__ __forceinline__ void stage_plan_params(const float* __restrict__ P, PlanShared& s)
+{
+    for (int k = threadIdx.x; k < kF * kH; k += blockDim.x) {
+        const int j = k / kF, i = k % kF;
+        s.W1t[i * kH + j] = P[oW1 + k];
+    }
+    for (int k = threadIdx.x; k < kH * kH; k += blockDim.x) {
+        const int j = k / kH, i = k % kH;
+        s.W2t[i * kH + j] = P[oW2 + k];
+    }
+    for (int k = threadIdx.x; k < kH; k += blockDim.x) {
+        s.b1[k] = P[oB1 + k];
+        s.b2[k] = P[oB2 + k];
+    }
+    for (int k = threadIdx.x; k < kC * kH; k += blockDim.x) s.W3[k] = P[oW3 + k];
+    for (int k = threadIdx.x; k < kC; k += blockDim.x) s.b3[k] = P[oB3 + k];
+    __syncthreads();
+}
+
 // The planner network for one tile by one warp (features in every lane):
 // lane l holds hidden units l and l + 32 of both layers; the logits are warp
 // sums.  Returns the argmax class (lowest on ties) in every lane.
-__device__ __forceinline__ int warp_plan(const float* __restrict__ P, const float (&f)[kF])
+__device__ __forceinline__ int warp_plan(const PlanShared& P, const float (&f)[kF])
 {
     const int lane = threadIdx.x & 31;
-    float h1[2], h2[2];
+    float h1[2];
 #pragma unroll
     for (int u = 0; u < 2; ++u) {
         const int j = lane + 32 * u;
-        float a = __ldg(P + oB1 + j);
+        float a = P.b1[j];
 #pragma unroll
-        for (int i = 0; i < kF; ++i) a = fmaf(__ldg(P + oW1 + j * kF + i), f[i], a);
+        for (int i = 0; i < kF; ++i) a = fmaf(P.W1t[i * kH + j], f[i], a);
         h1[u] = fmaxf(a, 0.0f);
     }
-    float a0 = __ldg(P + oB2 + lane), a1 = __ldg(P + oB2 + lane + 32);
+    float a0 = P.b2[lane], a1 = P.b2[lane + 32];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
 #pragma unroll 8
-    for (int i = 0; i < kH; ++i) {
-        const float hi = __shfl_sync(0xffffffffu, h1[i >> 5], i & 31);
-        a0 = fmaf(__ldg(P + oW2 + lane * kH + i), hi, a0);
-        a1 = fmaf(__ldg(P + oW2 + (lane + 32) * kH + i), hi, a1);
-    }
-    h2[0] = fmaxf(a0, 0.0f);
-    h2[1] = fmaxf(a1, 0.0f);
+        for (int i0 = 0; i0 < 32; ++i0) {
+            const int i = 32 * u + i0;
+            const float hi = __shfl_sync(0xffffffffu, h1[u], i0);
+            a0 = fmaf(P.W2t[i * kH + lane], hi, a0);
+            a1 = fmaf(P.W2t[i * kH + lane + 32], hi, a1);
+        }
+    const float h20 = fmaxf(a0, 0.0f), h21 = fmaxf(a1, 0.0f);
     int best = 0;
     float zbest = 0.0f;
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
-        float z = fmaf(__ldg(P + oW3 + c * kH + lane), h2[0], __ldg(P + oW3 + c * kH + lane + 32) * h2[1]);
+        float z = fmaf(P.W3[c * kH + lane], h20, P.W3[c * kH + lane + 32] * h21);
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) z += __shfl_xor_sync(0xffffffffu, z, s);
-        z += __ldg(P + oB3 + c);
+        z += P.b3[c];
         if (c == 0 || z > zbest) {
             zbest = z;
             best = c;
@@ -138,16 +170,20 @@ __device__ __forceinline__ int warp_plan(const float* __restrict__ P, const floa
     return best;
 }
 
-// features and plan of every tile in one launch (the render path)
-__global__ void k_plan_fused(const int32_t* __restrict__ off, int K, int T, const float* __restrict__ params,
-                             uint8_t* __restrict__ plan)
+// features and plan of every tile in one launch (the render path): blocks of
+// 8 warps stage the parameters once and loop over tiles, a warp per tile
+__global__ void __launch_bounds__(256) k_plan_fused(const int32_t* __restrict__ off, int K, int T,
+                                                    const float* __restrict__ params, uint8_t* __restrict__ plan)
 {
-    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (t >= T) return;
-    float f[kF];
-    warp_tile_features(off, K, t, f);
-    const int c = warp_plan(params, f);
-    if ((threadIdx.x & 31) == 0) plan[t] = (uint8_t)c;
+    __shared__ PlanShared P;
+    stage_plan_params(params, P);
+    const int warps = blockDim.x >> 5;
+    for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < T; t += gridDim.x * warps) {
+        float f[kF];
+        warp_tile_features(off, K, t, f);
+        const int c = warp_plan(P, f);
+        if ((threadIdx.x & 31) == 0) plan[t] = (uint8_t)c;
+    }
 }
 
 // hidden activations of one sample (ReLU outputs)
@@ -177,16 +213,19 @@ __device__ __forceinline__ void mlp_logits(const float* __restrict__ P, const fl
 }
 
 // inference from given features: one warp per tile
-__global__ void k_plan_tiles(const float* __restrict__ params, const float* __restrict__ feat, int T,
-                             uint8_t* __restrict__ plan)
+__global__ void __launch_bounds__(256) k_plan_tiles(const float* __restrict__ params, const float* __restrict__ feat,
+                                                    int T, uint8_t* __restrict__ plan)
 {
-    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (t >= T) return;
-    float f[kF];
+    __shared__ PlanShared P;
+    stage_plan_params(params, P);
+    const int warps = blockDim.x >> 5;
+    for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < T; t += gridDim.x * warps) {
+        float f[kF];
 #pragma unroll
-    for (int i = 0; i < kF; ++i) f[i] = feat[(int64_t)t * kF + i];
-    const int c = warp_plan(params, f);
-    if ((threadIdx.x & 31) == 0) plan[t] = (uint8_t)c;
+        for (int i = 0; i < kF; ++i) f[i] = feat[(int64_t)t * kF + i];
+        const int c = warp_plan(P, f);
+        if ((threadIdx.x & 31) == 0) plan[t] = (uint8_t)c;
+    }
 }
 
 // training forward: acts [B][2H] = (h1, h2), logits [B][C]
@@ -331,7 +370,8 @@ int plan_frame(gs_ctx* c, const int32_t* offsets, int32_t K, int32_t T, uint8_t*
 {
     if (!c->planner_ready) return GS_ERR_INVALID_ARG;
     if (T <= 0) return GS_OK;
-    k_plan_fused<<<(unsigned)(((int64_t)T * 32 + 255) / 256), 256, 0, st>>>(offsets, K, T, c->d_planner, plan);
+    const int grid = min((T + 7) / 8, c->num_sms * 4);
+    k_plan_fused<<<(unsigned)grid, 256, 0, st>>>(offsets, K, T, c->d_planner, plan);
     c->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -363,8 +403,8 @@ extern "C" int gs_plan_tiles(gs_ctx* c, const float* features, int32_t n_tiles, 
     if (!c || !features || !plan || n_tiles < 0) return GS_ERR_INVALID_ARG;
     if (!c->planner_ready) return GS_ERR_INVALID_ARG;
     if (n_tiles == 0) return GS_OK;
-    k_plan_tiles<<<(unsigned)(((int64_t)n_tiles * 32 + 255) / 256), 256, 0, (cudaStream_t)stream>>>(
-        c->d_planner, features, n_tiles, plan);
+    const int grid = min((n_tiles + 7) / 8, c->num_sms * 4);
+    k_plan_tiles<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(c->d_planner, features, n_tiles, plan);
     c->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
