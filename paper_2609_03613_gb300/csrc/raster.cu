@@ -52,9 +52,13 @@ __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_en
         if (__syncthreads_count(st.done) == BS) return b0;
         const int cnt = stage_batch<TILE, BASELINE>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
         __syncthreads();
+        // binned: the warp composites only the entries its strip mask admits
+        int nk = cnt;
+        if constexpr (!BASELINE) nk = __all_sync(0xffffffffu, st.done) ? 0 : warp_strip_list<TILE>(sh, cnt);
         if (!st.done) {
-            for (int k = 0; k < cnt; ++k) {
-                if (!BASELINE && !((__float_as_uint(sh.c[k].w) >> warp) & 1u)) continue;  // warp-uniform
+            for (int i = 0; i < nk; ++i) {
+                int k = i;
+                if constexpr (!BASELINE) k = sh.list[warp][i];
                 const float4 ga = sh.a[k];
                 const float4 gb = sh.b[k];
                 if (COUNT) {

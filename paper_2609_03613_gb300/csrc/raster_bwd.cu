@@ -95,8 +95,10 @@ struct BwdSpan {
             __syncthreads();  // the previous batch's staging and sums are consumed
             const int cnt = stage_batch<TILE, false>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
             __syncthreads();
-            for (int k = cnt - 1; k >= 0; --k) {
-                if (!((__float_as_uint(sh.c[k].w) >> warp) & 1u)) continue;  // warp-uniform
+            // the entries this warp's strip mask admits, walked back to front
+            const int nk = warp_strip_list<TILE>(sh, cnt);
+            for (int i = nk - 1; i >= 0; --i) {
+                const int k = sh.list[warp][i];
                 const float4 gb = sh.b[k];
                 if (!st.active) st.active = __float_as_uint(gb.w) == st.last;
                 float v = 0.0f, wgt = 0.0f, dx = 0.0f, dy = 0.0f;

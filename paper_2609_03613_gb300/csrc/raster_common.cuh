@@ -23,12 +23,32 @@ struct RasterShared {
     static constexpr int BS = TILE * TILE;
     static constexpr int BATCH = BS < 256 ? BS : 256;  // entries staged per batch
     static constexpr int NW = BATCH / 32;              // warps that load a batch
+    static constexpr int NWT = BS / 32;                // warps of the tile
     float4 a[BATCH];                       // {mx, my, a/2, b}
     float4 b[BATCH];                       // {c/2, o, tau, gid bits}
     float4 c[BASELINE ? 1 : BATCH];        // colour (binned)
     uint32_t g[BASELINE ? BATCH : 1];      // gid (baseline colour lookup)
+    uint8_t list[BASELINE ? 1 : NWT][BASELINE ? 1 : BATCH];  // per warp: staged entries its strip mask admits
     int wc[NW];
 };
+
+// The staged entries (of cnt) whose strip mask admits the calling warp, in
+// stage order, into sh.list[warp]; returns their count.  Whole warp.
+template <int TILE>
+__device__ __forceinline__ int warp_strip_list(RasterShared<TILE, false>& sh, int cnt)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int nw = 0;
+    for (int j0 = 0; j0 < cnt; j0 += 32) {
+        const int j = j0 + lane;
+        const bool mine = j < cnt && ((__float_as_uint(sh.c[j].w) >> warp) & 1u);
+        const unsigned bal = __ballot_sync(0xffffffffu, mine);
+        if (mine) sh.list[warp][nw + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)j;
+        nw += __popc(bal);
+    }
+    __syncwarp();
+    return nw;
+}
 
 // Rows of the tile a warp owns: the strip mask bit w is set when the
 // entry's alpha >= 1/255 ellipse (the tile cull's bound tau / margin, widened
