@@ -146,6 +146,13 @@ struct LoadRectRows {
     }
 };
 
+// Row record word: tile row (12 bits) | first tile of the span (12 bits) |
+// bin (8 bits); exact_bins checks tiles_x, tiles_y <= 4096 (K <= 128 < 256).
+__device__ __forceinline__ uint32_t row_record(int ty, int a, uint32_t bin)
+{
+    return (uint32_t)ty | ((uint32_t)a << 12) | (bin << 24);
+}
+
 // Warp-cooperative over (Gaussian, row) pairs: a warp owns 32 consecutive
 // Gaussians, whose rows are consecutive records [roff[g0], roff[g0 + 32)).
 // Each lane holds its Gaussian (record, bin); every row record is computed by
@@ -156,7 +163,7 @@ __global__ void __launch_bounds__(256)
 k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict__ roff, CullArgs ca, int tiles_x,
             const BinParams* __restrict__ bp, int K, const int64_t* __restrict__ m_dev, int64_t m_cap,
             int32_t* __restrict__ Drow, int64_t layer, uint8_t* __restrict__ gbin, uint32_t* __restrict__ rs_g,
-            uint32_t* __restrict__ rs_ya, uint32_t* __restrict__ rs_w)
+            uint32_t* __restrict__ rs_ya, uint32_t* __restrict__ rs_w, uint32_t* __restrict__ rs_z)
 {
     __shared__ float s_split[GS_MAX_K];
     for (int k = threadIdx.x; k < K - 1; k += blockDim.x) s_split[k] = bp->splits[k];
@@ -197,6 +204,7 @@ k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict
         const float mx = __shfl_sync(0xffffffffu, p.x, k), my = __shfl_sync(0xffffffffu, p.y, k);
         const float ca_ = __shfl_sync(0xffffffffu, p.z, k), cb = __shfl_sync(0xffffffffu, p.w, k);
         const float cc = __shfl_sync(0xffffffffu, q.x, k), tau = __shfl_sync(0xffffffffu, q.w, k);
+        const uint32_t zb = __shfl_sync(0xffffffffu, __float_as_uint(q.z), k);
         const float mg = __shfl_sync(0xffffffffu, margin, k);
         const uint32_t b = __shfl_sync(0xffffffffu, bin, k);
         const int32_t o = __shfl_sync(0xffffffffu, my_off, k);
@@ -206,8 +214,9 @@ k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict
             int a, x1;
             row_span(mx, my, 0.5f * ca_, cb, 0.5f * cc, tau, mg, ty, ca.tile, tx0, tx1, &a, &x1);
             rs_g[e] = (uint32_t)(g0 + k);
-            rs_ya[e] = (uint32_t)ty | ((uint32_t)a << 16);
+            rs_ya[e] = row_record(ty, a, b);
             rs_w[e] = (uint32_t)(x1 - a);
+            rs_z[e] = zb;
             if (x1 > a) {
                 int32_t* L = Drow + b * layer;
                 atomicAdd(&L[ty * W1 + a], 1);
@@ -243,12 +252,13 @@ k_layer_rows_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y, int64_t l
 // Warp-cooperative over the entries of 32 consecutive row records: a warp
 // scans the records' widths, then each lane takes every 32nd entry, finds its
 // record by a binary search over the prefix and takes a slot in the entry's
-// (tile, bin) segment; two entries per lane are in flight.
+// (tile, bin) segment -- the cursors start at the segment offsets, so the
+// atomic returns the slot itself; four entries per lane are in flight.  The
+// records carry the Gaussian's bin and depth bits, so nothing is gathered.
 __global__ void __launch_bounds__(256)
 k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ rs_w,
-                   const int32_t* __restrict__ roff, int64_t n, const float4* __restrict__ c_o_z,
-                   const uint8_t* __restrict__ gbin, int tiles_x, int K, const int64_t* __restrict__ m_dev,
-                   int64_t m_cap, const int32_t* __restrict__ off, int32_t* __restrict__ cur,
+                   const uint32_t* __restrict__ rs_z, const int32_t* __restrict__ roff, int64_t n, int tiles_x, int K,
+                   const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ cur,
                    uint64_t* __restrict__ words)
 {
     if (*m_dev > m_cap) return;
@@ -258,15 +268,12 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
     const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += wstride) {
         const int64_t k = c * 32 + lane;
-        uint32_t w = 0, g = 0, ya = 0, b = 0, z = 0;
+        uint32_t w = 0, g = 0, ya = 0, z = 0;
         if (k < R) {
             w = rs_w[k];
-            if (w) {
-                g = rs_g[k];
-                ya = rs_ya[k];
-                b = gbin[g];
-                z = __float_as_uint(c_o_z[g].z);
-            }
+            g = rs_g[k];
+            ya = rs_ya[k];
+            z = rs_z[k];
         }
         // inclusive prefix of the widths across the warp
         uint32_t incl = w;
@@ -277,12 +284,12 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
         }
         const uint32_t excl = incl - w;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        for (uint32_t e0 = 0; e0 < total; e0 += 64) {
-            int32_t p[2];
-            uint64_t word[2];
-            bool live[2];
+        for (uint32_t e0 = 0; e0 < total; e0 += 128) {
+            int32_t p[4];
+            uint64_t word[4];
+            bool live[4];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
+            for (int u = 0; u < 4; ++u) {
                 const uint32_t e = e0 + 32 * u + lane;
                 // owner: the last lane whose exclusive prefix is <= e
                 int o = 0;
@@ -293,17 +300,17 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
                 }
                 const uint32_t oex = __shfl_sync(0xffffffffu, excl, o);
                 const uint32_t og = __shfl_sync(0xffffffffu, g, o), oya = __shfl_sync(0xffffffffu, ya, o);
-                const uint32_t ob = __shfl_sync(0xffffffffu, b, o), oz = __shfl_sync(0xffffffffu, z, o);
+                const uint32_t oz = __shfl_sync(0xffffffffu, z, o);
                 live[u] = e < total;
                 if (live[u]) {
-                    const int ty = (int)(oya & 0xffffu), tx = (int)(oya >> 16) + (int)(e - oex);
-                    const int64_t qi = ((int64_t)ty * tiles_x + tx) * K + ob;
-                    p[u] = off[qi] + atomicAdd(&cur[qi], 1);
+                    const int ty = (int)(oya & 0xfffu), tx = (int)((oya >> 12) & 0xfffu) + (int)(e - oex);
+                    const int64_t qi = ((int64_t)ty * tiles_x + tx) * K + (oya >> 24);
+                    p[u] = atomicAdd(&cur[qi], 1);
                     word[u] = ((uint64_t)oz << 32) | og;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 2; ++u)
+            for (int u = 0; u < 4; ++u)
                 if (live[u]) words[p[u]] = word[u];
         }
     }
@@ -339,7 +346,7 @@ k_bin_scatter_rects(const uint2* __restrict__ rect, const float4* __restrict__ c
         for (int u = 0; u < 4; ++u)
             if (live[u]) {
                 const int64_t q = (int64_t)t[u] * K + b[u];
-                p[u] = off[q] + atomicAdd(&cur[q], 1);
+                p[u] = atomicAdd(&cur[q], 1);
             }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -378,7 +385,7 @@ struct ExactScratch {
     int32_t* cur;    // T*K scatter cursors
     uint8_t* gbin;   // n per-Gaussian bins
     int32_t* roff;   // n + 1 row-record offsets
-    uint32_t *rs_g, *rs_ya, *rs_w;  // row records (<= m_cap)
+    uint32_t *rs_g, *rs_ya, *rs_w, *rs_z;  // row records (<= m_cap)
     int64_t* total;  // scratch count
 };
 
@@ -388,14 +395,14 @@ static size_t exact_scratch(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t tiles
     const size_t layer = (size_t)(tiles_x + 1) * (tiles_y + 1);
     const size_t T = (size_t)tiles_x * tiles_y;
     const size_t mc = (size_t)(m_cap > 0 ? m_cap : 1), nn = (size_t)(n > 0 ? n : 1);
-    const size_t sizes[] = {layer * K * 4, T * K * 4, nn, (nn + 1) * 4, mc * 4, mc * 4, mc * 4, 8};
+    const size_t sizes[] = {layer * K * 4, T * K * 4, nn, (nn + 1) * 4, mc * 4, mc * 4, mc * 4, mc * 4, 8};
     size_t total = 0;
     for (size_t s : sizes) total += align256(s);
     if (v) {
         char* b = (char*)ctx->d_tiles;
         void** dst[] = {(void**)&v->D, (void**)&v->cur, (void**)&v->gbin, (void**)&v->roff, (void**)&v->rs_g,
-                        (void**)&v->rs_ya, (void**)&v->rs_w, (void**)&v->total};
-        for (int k = 0; k < 8; ++k) {
+                        (void**)&v->rs_ya, (void**)&v->rs_w, (void**)&v->rs_z, (void**)&v->total};
+        for (int k = 0; k < 9; ++k) {
             *dst[k] = b;
             b += align256(sizes[k]);
         }
@@ -422,7 +429,7 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
     ExactScratch v;
     exact_scratch(ctx, n, m_cap, tiles_x, tiles_y, K, &v);
     const size_t layer = (size_t)(tiles_x + 1) * (tiles_y + 1);
-    GS_CUDA_TRY(cudaMemsetAsync(v.cur, 0, (size_t)nseg * 4, st));
+    if (tiles_x > 4096 || tiles_y > 4096) return GS_ERR_INVALID_ARG;  // row-record packing
     GS_CUDA_TRY(cudaMemsetAsync(v.D, 0, layer * K * 4, st));
     const unsigned g_sm = (unsigned)ctx->num_sms * 8;
     k_capacity_check<<<1, 1, 0, st>>>(m_dev, m_cap, ctx->d_err);
@@ -436,15 +443,16 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
         if (warps > 0)
             k_row_spans<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(pv.rect, n, v.roff, ca, tiles_x, ctx->d_bp, K,
                                                                      m_dev, m_cap, v.D, rlayer, v.gbin, v.rs_g,
-                                                                     v.rs_ya, v.rs_w);
+                                                                     v.rs_ya, v.rs_w, v.rs_z);
         k_layer_rows_prefix<<<(unsigned)K, 1024, 0, st>>>(v.D, tiles_x, tiles_y, rlayer);
         ctx->launches += 2;
         if ((r = scan_impl(ctx, LoadLayerCount{v.D, K, tiles_x, tiles_x + 1, rlayer}, nseg, offsets, nullptr, st)) != GS_OK)
             return r;
         k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1);
+        GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)nseg * 4, cudaMemcpyDeviceToDevice, st));
         if (n > 0)
-            k_bin_scatter_rows<<<g_sm * 2, 256, 0, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.roff, n, pv.c_o_z, v.gbin, tiles_x,
-                                                         K, m_dev, m_cap, offsets, v.cur, words);
+            k_bin_scatter_rows<<<g_sm * 2, 256, 0, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, tiles_x, K, m_dev,
+                                                         m_cap, v.cur, words);
         ctx->launches += 2;
     } else {
         // whole rects per bin layer: four atomics per Gaussian, 2D prefix sums
@@ -456,6 +464,7 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
                            st)) != GS_OK)
             return r;
         k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1);
+        GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)nseg * 4, cudaMemcpyDeviceToDevice, st));
         const int64_t warps = (n + 31) / 32;
         if (warps > 0)
             k_bin_scatter_rects<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(pv.rect, pv.c_o_z, ctx->d_goff, v.gbin, n,
