@@ -157,12 +157,12 @@ __device__ __forceinline__ uint32_t row_record(int ty, int a, uint32_t bin)
 // Gaussians, whose rows are consecutive records [roff[g0], roff[g0 + 32)).
 // Each lane holds its Gaussian (record, bin); every row record is computed by
 // one lane from the owner's values (shuffled): the row's culled span, the
-// record (gid, row | start | bin, width, depth bits), and +1 / -1 at the span
-// ends in bin b of the row's difference array ([row][x][bin], bin innermost).
+// record (gid, row | start, width), and +1 / -1 at the span ends of layer b's
+// row (a per-row difference array).
 __global__ void __launch_bounds__(256)
 k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict__ roff, CullArgs ca, int tiles_x,
             const BinParams* __restrict__ bp, int K, const int64_t* __restrict__ m_dev, int64_t m_cap,
-            int32_t* __restrict__ Drow, uint8_t* __restrict__ gbin, uint32_t* __restrict__ rs_g,
+            int32_t* __restrict__ Drow, int64_t layer, uint8_t* __restrict__ gbin, uint32_t* __restrict__ rs_g,
             uint32_t* __restrict__ rs_ya, uint32_t* __restrict__ rs_w, uint32_t* __restrict__ rs_z)
 {
     __shared__ float s_split[GS_MAX_K];
@@ -218,31 +218,36 @@ k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict
             rs_w[e] = (uint32_t)(x1 - a);
             rs_z[e] = zb;
             if (x1 > a) {
-                // cell-major, bin innermost: [row][x][bin]
-                atomicAdd(&Drow[((int64_t)ty * W1 + a) * K + b], 1);
-                atomicAdd(&Drow[((int64_t)ty * W1 + x1) * K + b], -1);
+                int32_t* L = Drow + b * layer;
+                atomicAdd(&L[ty * W1 + a], 1);
+                atomicAdd(&L[ty * W1 + x1], -1);
             }
         }
     }
 }
 
-// Inclusive prefix along x of the [row][x][bin] difference counts: one
-// thread per (row, bin), consecutive bins in consecutive lanes (coalesced).
-__global__ void __launch_bounds__(256)
-k_cell_rows_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y, int K)
+// One block per layer: inclusive prefix along each row.
+__global__ void __launch_bounds__(1024)
+k_layer_rows_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y, int64_t layer)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= tiles_y * K) return;
-    const int y = i / K, b = i - y * K;
-    int32_t* row = D + (int64_t)y * (tiles_x + 1) * K + b;
-    int32_t carry = 0;
-#pragma unroll 4
-    for (int x = 0; x < tiles_x; ++x) {
-        carry += row[(int64_t)x * K];
-        row[(int64_t)x * K] = carry;
+    const int W1 = tiles_x + 1;
+    int32_t* L = D + (int64_t)blockIdx.x * layer;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int y = warp; y < tiles_y; y += blockDim.x / 32) {
+        int32_t carry = 0;
+        for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+            const int x = x0 + lane;
+            int32_t v = x < tiles_x ? L[y * W1 + x] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t u = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d) v += u;
+            }
+            if (x < tiles_x) L[y * W1 + x] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
     }
 }
-
 
 // Warp-cooperative over the entries of 32 consecutive row records: a warp
 // scans the records' widths, then each lane takes every 32nd entry, finds its
@@ -355,19 +360,6 @@ __global__ void k_capacity_check(const int64_t* __restrict__ m_dev, int64_t m_ca
 }
 
 // Count of segment q = t*K + b from the prefixed layers (tile-major order).
-// count[t, b] of the [row][x][bin] prefix (tile t = y * tiles_x + x)
-struct LoadCellCount {
-    const int32_t* D;
-    int K, tiles_x, W1;
-    __device__ int64_t operator()(int64_t q) const
-    {
-        const int64_t t = q / K;
-        const int b = (int)(q - t * K);
-        const int y = (int)(t / tiles_x), x = (int)(t - (int64_t)y * tiles_x);
-        return D[((int64_t)y * W1 + x) * K + b];
-    }
-};
-
 struct LoadLayerCount {
     const int32_t* D;
     int K, tiles_x, W1;
@@ -444,17 +436,17 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
     ctx->launches += 1;
     if (ctx->cfg.tile_cull) {
         // rows of every rect, each row's culled span, per-row difference counts
-
+        const int64_t rlayer = (int64_t)tiles_y * (tiles_x + 1);
         if ((r = scan_impl(ctx, LoadRectRows{pv.rect}, n, v.roff, v.total, st)) != GS_OK) return r;
         CullArgs ca{pv.xy_ab, pv.c_o_z, pv.rgb, tile};
         const int64_t warps = (n + 31) / 32;
         if (warps > 0)
             k_row_spans<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(pv.rect, n, v.roff, ca, tiles_x, ctx->d_bp, K,
-                                                                     m_dev, m_cap, v.D, v.gbin, v.rs_g, v.rs_ya,
-                                                                     v.rs_w, v.rs_z);
-        k_cell_rows_prefix<<<(unsigned)((tiles_y * K + 255) / 256), 256, 0, st>>>(v.D, tiles_x, tiles_y, K);
+                                                                     m_dev, m_cap, v.D, rlayer, v.gbin, v.rs_g,
+                                                                     v.rs_ya, v.rs_w, v.rs_z);
+        k_layer_rows_prefix<<<(unsigned)K, 1024, 0, st>>>(v.D, tiles_x, tiles_y, rlayer);
         ctx->launches += 2;
-        if ((r = scan_impl(ctx, LoadCellCount{v.D, K, tiles_x, tiles_x + 1}, nseg, offsets, nullptr, st)) != GS_OK)
+        if ((r = scan_impl(ctx, LoadLayerCount{v.D, K, tiles_x, tiles_x + 1, rlayer}, nseg, offsets, nullptr, st)) != GS_OK)
             return r;
         k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1);
         GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)nseg * 4, cudaMemcpyDeviceToDevice, st));
