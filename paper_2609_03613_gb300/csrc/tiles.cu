@@ -360,6 +360,34 @@ __global__ void k_capacity_check(const int64_t* __restrict__ m_dev, int64_t m_ca
 }
 
 // Count of segment q = t*K + b from the prefixed layers (tile-major order).
+// count[t, b] from the layer-major row prefix D [b][y][x] into C [t][b]
+// (t = y * tiles_x + x): 32 x 32 (x, b) blocks through shared memory, so both
+// the reads (along x) and the writes (along b) are coalesced.
+__global__ void __launch_bounds__(256)
+k_transpose_counts(const int32_t* __restrict__ D, int tiles_x, int tiles_y, int K, int64_t layer,
+                   int32_t* __restrict__ C)
+{
+    __shared__ int32_t s[32][33];
+    const int y = blockIdx.z;
+    const int x0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    const int W1 = tiles_x + 1;
+    const int lx = threadIdx.x & 31;
+    for (int r = threadIdx.x >> 5; r < 32; r += blockDim.x >> 5) {
+        const int b = b0 + r, x = x0 + lx;
+        s[r][lx] = (b < K && x < tiles_x) ? D[b * layer + (int64_t)y * W1 + x] : 0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.x >> 5; r < 32; r += blockDim.x >> 5) {
+        const int x = x0 + r, b = b0 + lx;
+        if (x < tiles_x && b < K) C[((int64_t)y * tiles_x + x) * K + b] = s[lx][r];
+    }
+}
+
+struct LoadPlainCount {
+    const int32_t* C;
+    __device__ int64_t operator()(int64_t q) const { return C[q]; }
+};
+
 struct LoadLayerCount {
     const int32_t* D;
     int K, tiles_x, W1;
@@ -445,9 +473,12 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
                                                                      m_dev, m_cap, v.D, rlayer, v.gbin, v.rs_g,
                                                                      v.rs_ya, v.rs_w, v.rs_z);
         k_layer_rows_prefix<<<(unsigned)K, 1024, 0, st>>>(v.D, tiles_x, tiles_y, rlayer);
-        ctx->launches += 2;
-        if ((r = scan_impl(ctx, LoadLayerCount{v.D, K, tiles_x, tiles_x + 1, rlayer}, nseg, offsets, nullptr, st)) != GS_OK)
-            return r;
+        // the counts tile-major (the cursor array serves as the staging copy;
+        // it is rewritten with the offsets below), then a coalesced scan
+        k_transpose_counts<<<dim3((unsigned)((tiles_x + 31) / 32), (unsigned)((K + 31) / 32), (unsigned)tiles_y), 256, 0,
+                             st>>>(v.D, tiles_x, tiles_y, K, rlayer, v.cur);
+        ctx->launches += 3;
+        if ((r = scan_impl(ctx, LoadPlainCount{v.cur}, nseg, offsets, nullptr, st)) != GS_OK) return r;
         k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1);
         GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)nseg * 4, cudaMemcpyDeviceToDevice, st));
         if (n > 0)
