@@ -84,25 +84,62 @@ struct GidFromSamples {
     __device__ uint32_t operator()(int64_t i, int64_t) const { return gid[i]; }
 };
 
-// Sample i of S' = min(S, M): entry j = floor(i M / S') of the emission order;
-// its Gaussian is the last one whose first entry is <= j (empty Gaussians
-// share their successor's offset and are skipped).  One thread per sample.
+// Sample i of S' = min(S, M) is entry j = floor(i M / S') of the emission
+// order.  Gaussian g owns entries [goff[g], goff[g+1]), so its samples are the
+// i with goff[g] <= floor(i M / S') < goff[g+1], i.e.
+// i in [ceil(goff[g] S' / M), ceil(goff[g+1] S' / M)) -- exact in integers.
+// One thread per Gaussian (coalesced reads of goff; empty Gaussians own none).
 __global__ void __launch_bounds__(256)
 k_sample_gids(const int32_t* __restrict__ goff, int64_t n, const int64_t* __restrict__ m_dev, int64_t m_cap, int S,
               uint32_t* __restrict__ out)
 {
     const int64_t M = live_count(m_dev, m_cap);
+    if (M <= 0) return;
     const int64_t ns = M < (int64_t)S ? M : (int64_t)S;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ns) return;
-    const int64_t j = (i * M) / ns;
-    int64_t lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if ((int64_t)goff[mid] <= j) lo = mid;
-        else hi = mid - 1;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = goff[g], b = goff[g + 1];
+        if (b <= a) continue;
+        const int64_t i0 = (a * ns + M - 1) / M, i1 = (b * ns + M - 1) / M;
+        for (int64_t i = i0; i < i1 && i < ns; ++i) out[i] = (uint32_t)g;
     }
-    out[i] = (uint32_t)lo;
+}
+
+// Rank search of one radix pass, by one warp: the digit d whose cumulative
+// count first reaches k (k >= 1), and k minus the counts below d, written by
+// the one lane that returns true.  Lane l holds digits 8l .. 8l+7.
+__device__ __forceinline__ bool warp_digit_select(const uint32_t* __restrict__ h, int64_t k, uint32_t* dsel,
+                                                  int64_t* krem)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t c[8], sum = 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        c[j] = h[8 * lane + j];
+        sum += c[j];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += u;
+    }
+    const unsigned hit = __ballot_sync(0xffffffffu, (int64_t)incl >= k);
+    const int L = hit ? __ffs(hit) - 1 : 31;
+    const uint32_t before = __shfl_sync(0xffffffffu, incl - sum, L);
+    if (lane == L) {
+        int64_t kk = k - (int64_t)before;
+        uint32_t d = 8u * L + 7u;
+        for (int j = 0; j < 8; ++j) {
+            if ((int64_t)c[j] >= kk) {
+                d = 8u * L + j;
+                break;
+            }
+            kk -= c[j];
+        }
+        *dsel = d;
+        *krem = kk;
+    }
+    return lane == L;
 }
 
 template <class GidOf>
@@ -144,28 +181,33 @@ k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales
         __syncthreads();
         // radix select (positive floats: bit order = value order), 8 bits at a time
         uint32_t mask = 0u;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
         for (int shift = 24; shift >= 0; shift -= 8) {
             for (int d = threadIdx.x; d < 512; d += blockDim.x) s_h[d >> 8][d & 255] = 0u;
             __syncthreads();
             const uint32_t p0 = s_pref[0], p1 = s_pref[1];
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const uint32_t v = s_v[i];
+            // histograms of the digit among the values matching each prefix;
+            // equal digits of a warp add once (most samples share the top byte)
+            for (int b0 = 0; b0 < n; b0 += blockDim.x) {
+                const int i = b0 + threadIdx.x;
+                const bool valid = i < n;
+                const uint32_t v = valid ? s_v[i] : 0u;
                 const uint32_t dg = (v >> shift) & 255u;
-                if ((v & mask) == p0) atomicAdd(&s_h[0][dg], 1u);
-                if ((v & mask) == p1) atomicAdd(&s_h[1][dg], 1u);
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    const bool sel = valid && (v & mask) == (t ? p1 : p0);
+                    const unsigned peers = __match_any_sync(0xffffffffu, sel ? dg : (0x100u | (uint32_t)lane));
+                    if (sel && lane == __ffs(peers) - 1) atomicAdd(&s_h[t][dg], (uint32_t)__popc(peers));
+                }
             }
             __syncthreads();
-            if (threadIdx.x < 2) {
-                const int t = threadIdx.x;
-                int64_t k = s_k[t];
+            if (warp < 2) {
                 uint32_t dsel = 255u;
-                for (uint32_t d = 0; d < 256; ++d) {
-                    const uint32_t c = s_h[t][d];
-                    if ((int64_t)c >= k) { dsel = d; break; }
-                    k -= c;
+                int64_t krem = 0;
+                if (warp_digit_select(s_h[warp], s_k[warp], &dsel, &krem)) {
+                    s_k[warp] = krem;
+                    s_pref[warp] |= dsel << shift;
                 }
-                s_k[t] = k;
-                s_pref[t] |= dsel << shift;
             }
             mask |= 255u << shift;
             __syncthreads();
@@ -255,7 +297,8 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
     a.K = c.K;
     int r = samples_reserve(ctx);
     if (r != GS_OK) return r;
-    k_sample_gids<<<(unsigned)((a.S + 255) / 256), 256, 0, st>>>(ctx->d_goff, n, m_dev, m_cap, a.S, ctx->d_samples);
+    if (n > 0)
+        k_sample_gids<<<(unsigned)ctx->num_sms * 4, 256, 0, st>>>(ctx->d_goff, n, m_dev, m_cap, a.S, ctx->d_samples);
     k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, GidFromSamples{ctx->d_samples}, m_dev, m_cap, a,
                                              ctx->d_bp);
     ctx->launches += 2;
