@@ -152,6 +152,7 @@ k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales
     __shared__ uint32_t s_h[2][256];
     __shared__ uint32_t s_pref[2];
     __shared__ int64_t s_k[2];
+    __shared__ int s_low;
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
     const int64_t M = live_count(m_dev, m_cap);
@@ -173,43 +174,60 @@ k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales
         zmin = lo_clamp;
         zmax = a.far_plane;
     } else {
-        if (threadIdx.x == 0) {
-            s_k[0] = rank_of(a.p_lo, n);
-            s_k[1] = rank_of(a.p_hi, n);
-            s_pref[0] = s_pref[1] = 0u;
+        // the bits every sample shares (those of the block's min and max)
+        // need no pass: start below the highest bit where samples differ
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        uint32_t lo_v = 0xffffffffu, hi_v = 0u;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            lo_v = min(lo_v, s_v[i]);
+            hi_v = max(hi_v, s_v[i]);
+        }
+        lo_v = __reduce_min_sync(0xffffffffu, lo_v);
+        hi_v = __reduce_max_sync(0xffffffffu, hi_v);
+        if (lane == 0) {
+            s_h[0][warp] = lo_v;
+            s_h[1][warp] = hi_v;
         }
         __syncthreads();
-        // radix select (positive floats: bit order = value order), 8 bits at a time
-        uint32_t mask = 0u;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        for (int shift = 24; shift >= 0; shift -= 8) {
+        if (warp == 0) {
+            const int nw = blockDim.x >> 5;
+            lo_v = __reduce_min_sync(0xffffffffu, lane < nw ? s_h[0][lane] : 0xffffffffu);
+            hi_v = __reduce_max_sync(0xffffffffu, lane < nw ? s_h[1][lane] : 0u);
+            if (lane == 0) {
+                const int cp = lo_v == hi_v ? 32 : __clz(lo_v ^ hi_v);
+                const uint32_t top = cp == 32 ? 0xffffffffu : (cp == 0 ? 0u : ~(0xffffffffu >> cp));
+                s_pref[0] = s_pref[1] = lo_v & top;
+                s_k[0] = rank_of(a.p_lo, n);
+                s_k[1] = rank_of(a.p_hi, n);
+                s_low = 32 - cp;  // bits still to select
+            }
+        }
+        __syncthreads();
+        const int low = s_low;
+        uint32_t mask = low >= 32 ? 0u : ~((1u << low) - 1u);
+        // radix select (positive floats: bit order = value order), <= 8 bits a pass
+        for (int hi_bit = low; hi_bit > 0; hi_bit -= 8) {
+            const int shift = hi_bit > 8 ? hi_bit - 8 : 0;
+            const uint32_t dmask = (1u << (hi_bit - shift)) - 1u;
             for (int d = threadIdx.x; d < 512; d += blockDim.x) s_h[d >> 8][d & 255] = 0u;
             __syncthreads();
             const uint32_t p0 = s_pref[0], p1 = s_pref[1];
-            // histograms of the digit among the values matching each prefix;
-            // equal digits of a warp add once (most samples share the top byte)
-            for (int b0 = 0; b0 < n; b0 += blockDim.x) {
-                const int i = b0 + threadIdx.x;
-                const bool valid = i < n;
-                const uint32_t v = valid ? s_v[i] : 0u;
-                const uint32_t dg = (v >> shift) & 255u;
-#pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const bool sel = valid && (v & mask) == (t ? p1 : p0);
-                    const unsigned peers = __match_any_sync(0xffffffffu, sel ? dg : (0x100u | (uint32_t)lane));
-                    if (sel && lane == __ffs(peers) - 1) atomicAdd(&s_h[t][dg], (uint32_t)__popc(peers));
-                }
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const uint32_t v = s_v[i];
+                const uint32_t dg = (v >> shift) & dmask;
+                if ((v & mask) == p0) atomicAdd(&s_h[0][dg], 1u);
+                if ((v & mask) == p1) atomicAdd(&s_h[1][dg], 1u);
             }
             __syncthreads();
             if (warp < 2) {
-                uint32_t dsel = 255u;
+                uint32_t dsel = 0u;
                 int64_t krem = 0;
                 if (warp_digit_select(s_h[warp], s_k[warp], &dsel, &krem)) {
                     s_k[warp] = krem;
                     s_pref[warp] |= dsel << shift;
                 }
             }
-            mask |= 255u << shift;
+            mask |= dmask << shift;
             __syncthreads();
         }
         const float zlo = __uint_as_float(s_pref[0]);
