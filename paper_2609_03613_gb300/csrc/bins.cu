@@ -158,14 +158,23 @@ k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales
     const int64_t M = live_count(m_dev, m_cap);
     const int64_t ns = M < (int64_t)a.S ? M : (int64_t)a.S;
     const float lo_clamp = fmaxf(a.near_plane, a.eps);
-    for (int64_t i = threadIdx.x; i < ns; i += blockDim.x) {
-        const int64_t j = (i * M) / ns;
-        const uint32_t g = gid_of(i, j);
-        float z = c_o_z[g].z;
-        if (a.near_shift) z = zkey_of(z, scales, g, a.near_alpha, a.near_gamma);
-        if (!(z > 0.0f)) continue;
-        z = fminf(fmaxf(z, lo_clamp), a.far_plane);
-        s_v[atomicAdd(&s_n, 1)] = __float_as_uint(z);
+    // the positive keys, compacted with one shared atomic per warp and round
+    for (int64_t b0 = 0; b0 < ns; b0 += blockDim.x) {
+        const int64_t i = b0 + threadIdx.x;
+        float z = 0.0f;
+        if (i < ns) {
+            const int64_t j = (i * M) / ns;
+            const uint32_t g = gid_of(i, j);
+            z = c_o_z[g].z;
+            if (a.near_shift) z = zkey_of(z, scales, g, a.near_alpha, a.near_gamma);
+        }
+        const bool keep = i < ns && z > 0.0f;
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const int lane = threadIdx.x & 31;
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&s_n, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) s_v[base + __popc(bal & ((1u << lane) - 1u))] = __float_as_uint(fminf(fmaxf(z, lo_clamp), a.far_plane));
     }
     __syncthreads();
     const int n = s_n;
