@@ -26,9 +26,6 @@
 
 namespace gs {
 
-// 16x16 binned tiles use the two-pixels-per-thread kernel unless this is set.
-constexpr bool kRaster1pxOnly = false;
-
 // Per-thread compositing state.
 struct PixelState {
     float T, C0, C1, C2;
@@ -190,151 +187,6 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
     }
 }
 
-// ---------------------------------------------------------------- 2 px / thread
-// The binned kernel with two vertically adjacent pixels per thread (16x16
-// tiles: 128 threads, warp w owns rows 4w..4w+3): each staged entry's loads,
-// dx and loop overhead serve two pixels.  Every pixel runs the same float32
-// operations in the same order as above, so the image is the same bit for bit.
-template <int TILE, bool COUNT>
-__device__ __forceinline__ int32_t raster_span2(const uint64_t* src, int32_t n_entries,
-                                                RasterShared<TILE, false, 2>& sh, const float4* __restrict__ xy_ab,
-                                                const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
-                                                int cullmode, int tx, int ty, float pxc, const float (&pyc)[2],
-                                                PixelState (&st)[2])
-{
-    using SH = RasterShared<TILE, false, 2>;
-    constexpr int BS = SH::BS, BATCH = SH::BATCH;
-    const int warp = threadIdx.x >> 5;
-    for (int32_t b0 = 0; b0 < n_entries; b0 += BATCH) {
-        const bool both = st[0].done && st[1].done;
-        if (__syncthreads_count(both) == BS) return b0;
-        const int cnt = stage_batch<TILE, false, 2>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
-        __syncthreads();
-        const int nk = __all_sync(0xffffffffu, both) ? 0 : warp_strip_list<TILE, 2>(sh, cnt);
-        if (!both) {
-            for (int i = 0; i < nk; ++i) {
-                const int k = sh.list[warp][i];
-                const float4 ga = sh.a[k];
-                const float4 gb = sh.b[k];
-                const float dx = ga.x - pxc;
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    PixelState& s = st[u];
-                    if (s.done) continue;
-                    if (COUNT) {
-                        ++s.ntests;
-                        s.ops += 8;
-                    }
-                    const float dy = ga.y - pyc[u];
-                    const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
-                    if (__float_as_uint(q) > __float_as_uint(gb.z)) continue;
-                    const float e = spec_exp_core(-q);
-                    const float alpha = fminf(0.99f, gb.y * e);
-                    if (COUNT) s.ops += 17;
-                    if (alpha < 1.0f / 255.0f) continue;
-                    const float Tn = s.T * (1.0f - alpha);
-                    if (COUNT) s.ops += 3;
-                    if (Tn < 1e-4f) {
-                        s.done = true;
-                        continue;
-                    }
-                    if (COUNT) s.ops += 4;
-                    const float w = alpha * s.T;
-                    const float4 col = sh.c[k];
-                    s.C0 = fmaf(col.x, w, s.C0);
-                    s.C1 = fmaf(col.y, w, s.C1);
-                    s.C2 = fmaf(col.z, w, s.C2);
-                    s.T = Tn;
-                    s.last = __float_as_int(gb.w);
-                }
-                if (st[0].done && st[1].done) break;
-            }
-        }
-    }
-    return -1;
-}
-
-template <int TILE, bool COUNT>
-struct FwdSpan2 {
-    RasterShared<TILE, false, 2>& sh;
-    const float4* __restrict__ xy_ab;
-    const float4* __restrict__ c_o_z;
-    const float4* __restrict__ rgbv;
-    int cullmode, tx, ty;
-    float pxc;
-    const float (&pyc)[2];
-    PixelState (&st)[2];
-    __device__ __forceinline__ int32_t operator()(const uint64_t* src, int32_t n)
-    {
-        return raster_span2<TILE, COUNT>(src, n, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st);
-    }
-    __device__ __forceinline__ bool done() const { return st[0].done && st[1].done; }
-};
-
-template <int TILE, bool COUNT, bool LAZY>
-__global__ void __launch_bounds__(TILE * TILE / 2, 8)
-k_raster2(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
-          uint64_t* words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
-          float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
-          int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total, float* __restrict__ out_T,
-          int32_t* __restrict__ out_end, const uint8_t* __restrict__ plan, int default_cap,
-          long long* __restrict__ tile_cycles)
-{
-    constexpr int NT = TILE * TILE / 2;
-    __shared__ RasterShared<TILE, false, 2> sh;
-    __shared__ WalkShared<LAZY> ws;
-
-    const int t = blockIdx.x;
-    const int tx = t % a.tiles_x, ty = t / a.tiles_x;
-    const int lx = threadIdx.x % TILE, ly = 2 * (threadIdx.x / TILE);
-    const int px = tx * TILE + lx, py = ty * TILE + ly;
-    const float pxc = (float)px + 0.5f;
-    const float pyc[2] = {(float)py + 0.5f, (float)(py + 1) + 0.5f};
-    PixelState st[2];
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        st[u].T = 1.0f;
-        st[u].C0 = st[u].C1 = st[u].C2 = 0.0f;
-        st[u].last = -1;
-        st[u].ntests = 0;
-        st[u].ops = 0;
-        st[u].done = !(px < a.width && py + u < a.height);
-    }
-    long long c_start = 0;
-    if (tile_cycles && threadIdx.x == 0) c_start = clock64();
-    const int cap = plan ? plan_cap(plan[t]) : default_cap;
-    FwdSpan2<TILE, COUNT> span{sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st};
-    const int32_t end = walk_tile<TILE, LAZY, NT>(words, off, t, a.stride, cap, ws, span, out_end ? words : nullptr);
-    if (out_end && threadIdx.x == 0) out_end[t] = end;
-    if (tile_cycles) {
-        __syncthreads();
-        if (threadIdx.x == 0) tile_cycles[t] = clock64() - c_start;
-    }
-    unsigned long long ops = 0;
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-        if (px < a.width && py + u < a.height) {
-            const int64_t p = (int64_t)(py + u) * a.width + px;
-            out_rgb[3 * p] = fmaf(st[u].T, a.bg0, st[u].C0);
-            out_rgb[3 * p + 1] = fmaf(st[u].T, a.bg1, st[u].C1);
-            out_rgb[3 * p + 2] = fmaf(st[u].T, a.bg2, st[u].C2);
-            out_alpha[p] = 1.0f - st[u].T;
-            out_last[p] = st[u].last;
-            if (out_T) out_T[p] = st[u].T;
-            if (COUNT) out_ntests[p] = st[u].ntests;
-        }
-        ops += st[u].ops;
-    }
-    if (COUNT) {
-        __shared__ unsigned long long s_ops;
-        if (threadIdx.x == 0) s_ops = 0;
-        __syncthreads();
-        atomicAdd(&s_ops, ops);
-        __syncthreads();
-        if (threadIdx.x == 0) atomicAdd(ops_total, s_ops);
-    }
-}
-
 template <int TILE>
 static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cudaStream_t st, const ProjView& pv,
                         uint64_t* words, const int32_t* off, const RasterArgs& a, int cull, float* rgb,
@@ -346,22 +198,6 @@ static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cud
     k_raster<TILE, B, CNT, LZ><<<grid, BS, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, (B) ? 0 : cull, \
                                                    rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap,     \
                                                    cycles)
-    if constexpr (TILE == 16 && !kRaster1pxOnly) {
-        if (!baseline) {
-#define GS_RASTER2_LAUNCH(CNT, LZ)                                                                          \
-    k_raster2<TILE, CNT, LZ><<<grid, BS / 2, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, cull, rgb, alpha, \
-                                                     last, ntests, ops, final_T, tile_end, plan, cap, cycles)
-        if (lazy) {
-            if (count) GS_RASTER2_LAUNCH(true, true);
-            else GS_RASTER2_LAUNCH(false, true);
-        } else {
-            if (count) GS_RASTER2_LAUNCH(true, false);
-            else GS_RASTER2_LAUNCH(false, false);
-        }
-#undef GS_RASTER2_LAUNCH
-            return;
-        }
-    }
     if (baseline) {
         if (count) GS_RASTER_LAUNCH(true, true, false);
         else GS_RASTER_LAUNCH(true, false, false);

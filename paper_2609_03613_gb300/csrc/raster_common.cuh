@@ -18,10 +18,9 @@ struct RasterArgs {
     float bg0, bg1, bg2;
 };
 
-// PPT: pixels per thread (1, or 2 vertically adjacent ones); BS threads.
-template <int TILE, bool BASELINE, int PPT = 1>
+template <int TILE, bool BASELINE>
 struct RasterShared {
-    static constexpr int BS = TILE * TILE / PPT;
+    static constexpr int BS = TILE * TILE;
     static constexpr int BATCH = BS < 256 ? BS : 256;  // entries staged per batch
     static constexpr int NW = BATCH / 32;              // warps that load a batch
     static constexpr int NWT = BS / 32;                // warps of the tile
@@ -35,8 +34,8 @@ struct RasterShared {
 
 // The staged entries (of cnt) whose strip mask admits the calling warp, in
 // stage order, into sh.list[warp]; returns their count.  Whole warp.
-template <int TILE, int PPT = 1>
-__device__ __forceinline__ int warp_strip_list(RasterShared<TILE, false, PPT>& sh, int cnt)
+template <int TILE>
+__device__ __forceinline__ int warp_strip_list(RasterShared<TILE, false>& sh, int cnt)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int nw = 0;
@@ -54,12 +53,12 @@ __device__ __forceinline__ int warp_strip_list(RasterShared<TILE, false, PPT>& s
 // Rows of the tile a warp owns: the strip mask bit w is set when the
 // entry's alpha >= 1/255 ellipse (the tile cull's bound tau / margin, widened
 // as there) can reach rows [y0 + w*RPW, y0 + (w+1)*RPW) of the tile.
-template <int TILE, int PPT = 1>
+template <int TILE>
 __device__ __forceinline__ uint32_t strip_mask(float my, float ha, float hb, float hc, float tau, float margin,
                                                float y0)
 {
-    constexpr int RPW = 32 * PPT / TILE > 0 ? 32 * PPT / TILE : 1;  // pixel rows per warp
-    constexpr int NWT = TILE * TILE / (32 * PPT);                   // warps per tile
+    constexpr int RPW = 32 / TILE > 0 ? 32 / TILE : 1;  // pixel rows per warp
+    constexpr int NWT = TILE * TILE / 32;               // warps per tile
     const uint32_t all = NWT >= 32 ? 0xffffffffu : ((1u << NWT) - 1u);
     if (!(margin > 0.0f)) return all;
     const float D = 4.0f * ha * hc - hb * hb;
@@ -80,13 +79,13 @@ __device__ __forceinline__ uint32_t strip_mask(float my, float ha, float hb, flo
 // binned, the colour with the strip mask in .w.  Entries the tile cull or the
 // strip mask drop are compacted away in order.  Returns the number staged
 // (block-uniform); the caller synchronises the block before reading sh.
-template <int TILE, bool BASELINE, int PPT = 1>
+template <int TILE, bool BASELINE>
 __device__ __forceinline__ int stage_batch(const uint64_t* src, int32_t b0, int32_t n_entries,
-                                           RasterShared<TILE, BASELINE, PPT>& sh, const float4* __restrict__ xy_ab,
+                                           RasterShared<TILE, BASELINE>& sh, const float4* __restrict__ xy_ab,
                                            const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
                                            int cullmode, int tx, int ty)
 {
-    using SH = RasterShared<TILE, BASELINE, PPT>;
+    using SH = RasterShared<TILE, BASELINE>;
     constexpr int BATCH = SH::BATCH, NW = SH::NW;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t idx = b0 + threadIdx.x;
@@ -105,9 +104,8 @@ __device__ __forceinline__ int stage_batch(const uint64_t* src, int32_t b0, int3
             if (cullmode & 1)
                 keep = !tile_culled(A.x, A.y, A.z, A.w, B.x, q.w, Cc.w, (float)(tx * TILE), (float)(ty * TILE),
                                     (float)TILE);
-            const uint32_t m = (cullmode & 2)
-                                   ? strip_mask<TILE, PPT>(A.y, A.z, A.w, B.x, q.w, Cc.w, (float)(ty * TILE))
-                                   : 0xffffffffu;
+            const uint32_t m = (cullmode & 2) ? strip_mask<TILE>(A.y, A.z, A.w, B.x, q.w, Cc.w, (float)(ty * TILE))
+                                              : 0xffffffffu;
             keep = keep && m != 0u;
             Cc.w = __uint_as_float(m);  // the colour record carries the mask
         }
@@ -152,12 +150,12 @@ struct WalkShared {
 // Load the chunk [c0, c0 + len) (bins bfirst..e-1) into ws.sort and sort each
 // of its segments by (depth bits, gid): segments of up to 32 entries in
 // registers by one warp, up to 256 in shared memory by one warp, longer ones by
-// the whole block (NT threads).  ws.big collects the long ones.
-template <int TILE, int NT = TILE * TILE, bool LAZY>
+// the whole block.  ws.big[base..] collects the long ones.
+template <int TILE, bool LAZY>
 __device__ __forceinline__ void load_sort_chunk(const uint64_t* words, int32_t c0, int32_t len,
-                                                int bfirst, int e, WalkShared<LAZY>& ws)
+                                                int bfirst, int e, WalkShared<LAZY>& ws, int base = 0)
 {
-    constexpr int BS = NT;
+    constexpr int BS = TILE * TILE;
     constexpr int NWB = BS / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < len; i += BS) ws.sort[i] = words[c0 + i];
@@ -201,11 +199,11 @@ __device__ __forceinline__ void load_sort_chunk(const uint64_t* words, int32_t c
 // the position (in the composited order) where every pixel had terminated.
 // With writeback (the stream itself), every sorted chunk is also stored back
 // in place, so the tile's composited prefix is left in (depth, gid) order.
-template <int TILE, bool LAZY, int NT = TILE * TILE, class Span>
+template <int TILE, bool LAZY, class Span>
 __device__ __forceinline__ int32_t walk_tile(const uint64_t* words, const int32_t* __restrict__ off, int t, int K,
                                              int cap, WalkShared<LAZY>& ws, Span& span, uint64_t* writeback = nullptr)
 {
-    constexpr int BS = NT;  // threads of the block
+    constexpr int BS = TILE * TILE;
     if (!LAZY) {
         const int32_t s0 = off[(int64_t)t * K], s1 = off[(int64_t)(t + 1) * K];
         const int32_t r = span(words + s0, s1 - s0);
@@ -229,7 +227,7 @@ __device__ __forceinline__ int32_t walk_tile(const uint64_t* words, const int32_
         b = e;
         if (len == 0) continue;
         if (__syncthreads_count(span.done()) == BS) return c0;
-        load_sort_chunk<TILE, NT>(words, c0, len, bfirst, e, ws);  // ends with a block barrier
+        load_sort_chunk<TILE>(words, c0, len, bfirst, e, ws);  // ends with a block barrier
         if (writeback)
             for (int i = threadIdx.x; i < len; i += BS) writeback[c0 + i] = ws.sort[i];
         const int32_t r = span(ws.sort, len);
