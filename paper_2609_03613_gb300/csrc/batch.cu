@@ -3,9 +3,12 @@
 //   * one projection launch for all views: each Gaussian's parameters and SH
 //     coefficients are read from HBM once and projected for every view
 //     (k_project_batch);
-//   * each view's intersect / bin / repair / raster runs on its own stream,
-//     forked from and joined back into the caller's stream, so small views
-//     and the tails of large ones overlap on the 152 SMs;
+//   * each view's intersect / bin / repair runs on its own stream, forked
+//     from and joined back into the caller's stream, so small views and the
+//     tails of large ones overlap on the 152 SMs;
+//   * one persistent raster launch composites every view's tiles (blocks take
+//     (view, tile) items from a counter) when all views are EXACT with 16x16
+//     tiles; otherwise each view's raster runs on its stream;
 //   * with GS_RENDER_GRAPH the whole batch (fork, V pipelines, join) is one
 //     CUDA graph, replayed while the arguments stay the same;
 //   * per-view tile size and bin count come from gs_batch_autotune, which
@@ -30,6 +33,7 @@ struct BatchState {
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
     int64_t glaunches = 0;
+    int32_t* d_counter = nullptr;  // work counter of the persistent multi-view raster
 };
 
 void batch_destroy(gs_ctx* c)
@@ -43,6 +47,7 @@ void batch_destroy(gs_ctx* c)
         if (b->join[v]) cudaEventDestroy(b->join[v]);
     }
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->d_counter) cudaFree(b->d_counter);
     delete b;
     c->batch = nullptr;
 }
@@ -73,7 +78,9 @@ static BatchState* batch_state(gs_ctx* c)
 {
     if (!c->batch) {
         BatchState* b = new BatchState();
-        if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+        if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMalloc(&b->d_counter, sizeof(int32_t)) != cudaSuccess) {
+            if (b->fork) cudaEventDestroy(b->fork);
             delete b;
             return nullptr;
         }
@@ -158,20 +165,46 @@ static int batch_impl(gs_ctx* c, const gs_scene* sc, const gs_camera* cams, int 
                                  cams, tiles, pvs, st);
         if (r != GS_OK) return r;
     }
+    // views that are EXACT with the repair in the raster, 16x16 tiles and no
+    // plan: their binning runs on their streams and all their tiles are
+    // composited by one persistent raster launch after the join (other views
+    // run their own raster on their stream)
     GS_CUDA_TRY(cudaEventRecord(b->fork, st));
+    RasterView rv[kMaxBatchViews];
+    int nfused = 0;
     for (int v = 0; v < nv; ++v) {
         gs_ctx* vc = b->views[v];
         cudaStream_t vs = b->streams[v];
         GS_CUDA_TRY(cudaStreamWaitEvent(vs, b->fork, 0));
         vc->capturing = c->capturing;
         int32_t* d_last = (last && last[v]) ? last[v] : reinterpret_cast<int32_t*>(vc->r_out);
-        r = render_after_project(vc, n, sc->scales, cams + v, bg, rgb[v], alpha[v], d_last, flags, vs);
+        const gs_config& vcfg = vc->cfg;
+        const bool fused = vcfg.mode == GS_MODE_BINNED_EXACT && vcfg.repair_in_raster && vcfg.tile_size == 16 &&
+                           !vcfg.planner;
+        if (fused) {
+            r = render_binning(vc, n, sc->scales, cams + v, flags, vs);
+            RasterView& x = rv[nfused++];
+            x.pv = proj_view(vc->r_proj, n);
+            x.cam = cams[v];
+            x.words = vc->r_stream;
+            x.offsets = vc->r_off;
+            x.stride = vc->cfg.K;
+            for (int k = 0; k < 3; ++k) x.bg[k] = bg[k];
+            x.cull = vc->cfg.tile_cull;
+            x.cap = chunk_cap(vc->cfg);
+            x.rgb = rgb[v];
+            x.alpha = alpha[v];
+            x.last = d_last;
+        } else {
+            r = render_after_project(vc, n, sc->scales, cams + v, bg, rgb[v], alpha[v], d_last, flags, vs);
+        }
         vc->capturing = 0;
         if (r != GS_OK) return r;
         GS_CUDA_TRY(cudaMemcpyAsync(vc->h_m + 1, vc->r_m, sizeof(int64_t), cudaMemcpyDeviceToHost, vs));
         GS_CUDA_TRY(cudaEventRecord(b->join[v], vs));
         GS_CUDA_TRY(cudaStreamWaitEvent(st, b->join[v], 0));
     }
+    if (nfused > 0) return raster_views(c, rv, nfused, b->d_counter, st);
     return GS_OK;
 }
 

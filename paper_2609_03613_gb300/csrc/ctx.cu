@@ -531,8 +531,8 @@ int gs::render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T)
 // intersect, sort or bin, repair, raster (and the saved state).  Device
 // outputs.  Without GS_RENDER_NO_SYNC the entry count is read back once to
 // grow the entry buffers.
-int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, const float* bg,
-                             float* d_rgb, float* d_alpha, int32_t* d_last, int32_t flags, cudaStream_t st)
+int gs::render_binning(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, int32_t flags,
+                       cudaStream_t st)
 {
     const int32_t W = cam->width, H = cam->height;
     const int32_t T = gs_num_tiles(W, H, c->cfg.tile_size);
@@ -573,6 +573,17 @@ int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs
         r = gs_sort_or_bin(c, c->r_proj, scales, n, cam, c->r_isect, c->r_m_cap, c->r_m, c->r_stream,
                            c->r_off, nullptr, st);
     }
+    return r;
+}
+
+int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, const float* bg,
+                             float* d_rgb, float* d_alpha, int32_t* d_last, int32_t flags, cudaStream_t st)
+{
+    const int32_t W = cam->width, H = cam->height;
+    const int32_t T = gs_num_tiles(W, H, c->cfg.tile_size);
+    const int32_t stride = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : c->cfg.K;
+    ProjView pv = proj_view(c->r_proj, n);
+    int r = render_binning(c, n, scales, cam, flags, st);
     if (r != GS_OK) return r;
     const bool save = (flags & GS_RENDER_SAVE) != 0;
     if (save && (r = render_save_buffers(c, W, H, T)) != GS_OK) return r;

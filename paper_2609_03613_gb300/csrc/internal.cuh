@@ -320,6 +320,22 @@ int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* 
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T = nullptr,
                int32_t* tile_end = nullptr, const uint8_t* plan = nullptr, long long* tile_cycles = nullptr);
 
+// one EXACT (repair in the raster, 16x16 tiles) view of a batched raster
+struct RasterView {
+    ProjView pv;
+    gs_camera cam;
+    uint64_t* words;
+    const int32_t* offsets;
+    int32_t stride;
+    float bg[3];
+    int cull, cap;
+    float* rgb;
+    float* alpha;
+    int32_t* last;
+};
+// all views' tiles in one persistent launch (counter: one device int32)
+int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* counter, cudaStream_t st);
+
 // raster_bwd.cu
 int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
                int32_t stride, const float* bg, const int32_t* last, const float* final_T,
@@ -335,6 +351,10 @@ int planner_buffers(gs_ctx* c, int32_t T);
 int plan_frame(gs_ctx* c, const int32_t* offsets, int32_t K, int32_t T, uint8_t* plan, cudaStream_t st);
 int render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, const float* bg,
                          float* d_rgb, float* d_alpha, int32_t* d_last, int32_t flags, cudaStream_t st);
+// the frame up to the raster: intersect, sort or bin, repair (stream and
+// offsets in c->r_stream, c->r_off)
+int render_binning(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, int32_t flags,
+                   cudaStream_t st);
 
 // project.cu
 constexpr int kMaxBatchViews = GS_MAX_VIEWS;

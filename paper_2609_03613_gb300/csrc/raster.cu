@@ -22,6 +22,8 @@
 //               alpha >= 1/255 anywhere in the tile are dropped, order kept),
 //               colour staging, and a per-entry early-out q > tau with
 //               tau >= ln(255 o), past which alpha < 1/255 is certain.
+#include <string.h>
+
 #include "raster_common.cuh"
 
 namespace gs {
@@ -124,19 +126,16 @@ struct FwdSpan {
 // into shared memory and sorted by (depth bits, gid) right before it is
 // composited (longer ones were sorted eagerly), so segments after every
 // pixel's termination are never sorted.
+// One tile t by the whole block (the body of both raster kernels below).
 template <int TILE, bool BASELINE, bool COUNT, bool LAZY>
-__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 1)
-k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
-         uint64_t* words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
-         float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
-         int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total, float* __restrict__ out_T,
-         int32_t* __restrict__ out_end, const uint8_t* __restrict__ plan, int default_cap,
-         long long* __restrict__ tile_cycles)
+__device__ __forceinline__ void raster_tile(
+    int t, RasterShared<TILE, BASELINE>& sh, WalkShared<LAZY>& ws, const float4* __restrict__ xy_ab,
+    const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv, uint64_t* words,
+    const int32_t* __restrict__ off, const RasterArgs& a, int cullmode, float* __restrict__ out_rgb,
+    float* __restrict__ out_alpha, int32_t* __restrict__ out_last, int32_t* __restrict__ out_ntests,
+    unsigned long long* __restrict__ ops_total, float* __restrict__ out_T, int32_t* __restrict__ out_end,
+    const uint8_t* __restrict__ plan, int default_cap, long long* __restrict__ tile_cycles)
 {
-    __shared__ RasterShared<TILE, BASELINE> sh;
-    __shared__ WalkShared<LAZY> ws;
-
-    const int t = blockIdx.x;
     const int tx = t % a.tiles_x, ty = t / a.tiles_x;
     const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
     const int px = tx * TILE + lx, py = ty * TILE + ly;
@@ -184,6 +183,65 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
         atomicAdd(&s_ops, st.ops);
         __syncthreads();
         if (threadIdx.x == 0) atomicAdd(ops_total, s_ops);
+    }
+}
+
+
+template <int TILE, bool BASELINE, bool COUNT, bool LAZY>
+__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 1)
+k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
+         uint64_t* words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
+         float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
+         int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total, float* __restrict__ out_T,
+         int32_t* __restrict__ out_end, const uint8_t* __restrict__ plan, int default_cap,
+         long long* __restrict__ tile_cycles)
+{
+    __shared__ RasterShared<TILE, BASELINE> sh;
+    __shared__ WalkShared<LAZY> ws;
+    raster_tile<TILE, BASELINE, COUNT, LAZY>(blockIdx.x, sh, ws, xy_ab, c_o_z, rgbv, words, off, a, cullmode, out_rgb,
+                                             out_alpha, out_last, out_ntests, ops_total, out_T, out_end, plan,
+                                             default_cap, tile_cycles);
+}
+
+// Several views in one persistent launch: blocks take (view, tile) work items
+// from a counter, in view order, until all views' tiles are composited.
+struct ViewRasterSet {
+    struct View {
+        const float4* xy_ab;
+        const float4* c_o_z;
+        const float4* rgbv;
+        uint64_t* words;
+        const int32_t* off;
+        RasterArgs a;
+        int cullmode, cap;
+        float* rgb;
+        float* alpha;
+        int32_t* last;
+        int32_t item0;  // first work item of the view
+    } v[kMaxBatchViews];
+    int nviews;
+    int32_t total;
+};
+
+template <int TILE, bool LAZY>
+__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 1)
+k_raster_views(const __grid_constant__ ViewRasterSet vs, int32_t* __restrict__ counter)
+{
+    __shared__ RasterShared<TILE, false> sh;
+    __shared__ WalkShared<LAZY> ws;
+    __shared__ int32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();  // also: every thread is done with the previous tile's shared memory
+        const int32_t item = s_item;
+        __syncthreads();
+        if (item >= vs.total) break;
+        int v = 0;
+        while (v + 1 < vs.nviews && vs.v[v + 1].item0 <= item) ++v;
+        const ViewRasterSet::View& V = vs.v[v];
+        raster_tile<TILE, false, false, LAZY>(item - V.item0, sh, ws, V.xy_ab, V.c_o_z, V.rgbv, V.words, V.off, V.a,
+                                              V.cullmode, V.rgb, V.alpha, V.last, nullptr, nullptr, nullptr, nullptr,
+                                              nullptr, V.cap, nullptr);
     }
 }
 
@@ -242,6 +300,48 @@ int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* 
         case 32: launch_tile<32>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap, tile_cycles); break;
         default: launch_tile<16>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap, tile_cycles); break;
     }
+    ctx->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* counter, cudaStream_t st)
+{
+    if (nv < 1 || nv > kMaxBatchViews) return GS_ERR_INVALID_ARG;
+    ViewRasterSet vs;
+    memset(&vs, 0, sizeof(vs));
+    int32_t total = 0;
+    for (int i = 0; i < nv; ++i) {
+        const RasterView& r = views[i];
+        ViewRasterSet::View& V = vs.v[i];
+        const int tile = 16;
+        V.xy_ab = r.pv.xy_ab;
+        V.c_o_z = r.pv.c_o_z;
+        V.rgbv = r.pv.rgb;
+        V.words = r.words;
+        V.off = r.offsets;
+        V.a.width = r.cam.width;
+        V.a.height = r.cam.height;
+        V.a.tiles_x = (r.cam.width + tile - 1) / tile;
+        V.a.n_tiles = gs_num_tiles(r.cam.width, r.cam.height, tile);
+        V.a.stride = r.stride;
+        V.a.bg0 = r.bg[0];
+        V.a.bg1 = r.bg[1];
+        V.a.bg2 = r.bg[2];
+        V.cullmode = r.cull ? 2 : 0;
+        V.cap = r.cap;
+        V.rgb = r.rgb;
+        V.alpha = r.alpha;
+        V.last = r.last;
+        V.item0 = total;
+        total += V.a.n_tiles;
+    }
+    vs.nviews = nv;
+    vs.total = total;
+    if (total == 0) return GS_OK;
+    GS_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
+    const unsigned grid = (unsigned)(ctx->num_sms * 5 < total ? ctx->num_sms * 5 : total);
+    k_raster_views<16, true><<<grid, 256, 0, st>>>(vs, counter);
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
