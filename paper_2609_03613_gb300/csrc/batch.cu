@@ -33,7 +33,9 @@ struct BatchState {
     cudaGraphExec_t gexec = nullptr;
     std::vector<unsigned char> gkey;
     int64_t glaunches = 0;
-    int32_t* d_counter = nullptr;  // work counter of the persistent multi-view raster
+    int32_t* d_counter = nullptr;  // schedule of the persistent multi-view raster (65 int32)
+    int32_t* d_order = nullptr;    // its work items, longest tiles first
+    size_t order_cap = 0;
 };
 
 void batch_destroy(gs_ctx* c)
@@ -48,6 +50,7 @@ void batch_destroy(gs_ctx* c)
     }
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->d_counter) cudaFree(b->d_counter);
+    if (b->d_order) cudaFree(b->d_order);
     delete b;
     c->batch = nullptr;
 }
@@ -79,7 +82,7 @@ static BatchState* batch_state(gs_ctx* c)
     if (!c->batch) {
         BatchState* b = new BatchState();
         if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(&b->d_counter, sizeof(int32_t)) != cudaSuccess) {
+            cudaMalloc(&b->d_counter, 65 * sizeof(int32_t)) != cudaSuccess) {
             if (b->fork) cudaEventDestroy(b->fork);
             delete b;
             return nullptr;
@@ -128,6 +131,16 @@ int64_t batch_launch_count(const gs_ctx* c)
 static int batch_buffers(gs_ctx* c, const gs_scene* sc, const gs_camera* cams, int nv, int32_t* const* last,
                          int32_t flags)
 {
+    {
+        BatchState* b = batch_state(c);
+        if (!b) return GS_ERR_NO_MEMORY;
+        size_t tiles = 0;
+        for (int v = 0; v < nv; ++v) tiles += (size_t)gs_num_tiles(cams[v].width, cams[v].height, 16);
+        void* p = b->d_order;
+        const int r = ensure(&p, &b->order_cap, tiles * sizeof(int32_t) + 256);
+        if (r != GS_OK) return r;
+        b->d_order = (int32_t*)p;
+    }
     for (int v = 0; v < nv; ++v) {
         gs_ctx* vc;
         int r = view_ctx(c, v, &vc);
@@ -204,7 +217,7 @@ static int batch_impl(gs_ctx* c, const gs_scene* sc, const gs_camera* cams, int 
         GS_CUDA_TRY(cudaEventRecord(b->join[v], vs));
         GS_CUDA_TRY(cudaStreamWaitEvent(st, b->join[v], 0));
     }
-    if (nfused > 0) return raster_views(c, rv, nfused, b->d_counter, st);
+    if (nfused > 0) return raster_views(c, rv, nfused, b->d_counter, b->d_order, st);
     return GS_OK;
 }
 
@@ -293,6 +306,7 @@ extern "C" int gs_render_batch(gs_ctx* c, const gs_scene* sc, const gs_camera* c
     }
     put(&flags, sizeof(flags));
     put(&c->device, sizeof(c->device));
+    put(&b->d_order, sizeof(b->d_order));
     if (!(b->gexec && b->gkey == key)) {
         if (b->gexec) {
             cudaGraphExecDestroy(b->gexec);

@@ -333,8 +333,9 @@ struct RasterView {
     float* alpha;
     int32_t* last;
 };
-// all views' tiles in one persistent launch (counter: one device int32)
-int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* counter, cudaStream_t st);
+// all views' tiles in one persistent launch, longest tiles first
+// (sched: 65 device int32; order: one int32 per tile of all views)
+int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* sched, int32_t* order, cudaStream_t st);
 
 // raster_bwd.cu
 int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,

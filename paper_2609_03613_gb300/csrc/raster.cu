@@ -223,22 +223,65 @@ struct ViewRasterSet {
     int32_t total;
 };
 
+__device__ __forceinline__ int view_of(const ViewRasterSet& vs, int32_t item)
+{
+    int v = 0;
+    while (v + 1 < vs.nviews && vs.v[v + 1].item0 <= item) ++v;
+    return v;
+}
+
+// Longest tiles first: work items bucketed by floor(log2(span + 1)), buckets
+// handed out from the longest (so the last items of the persistent launch are
+// the short ones).  sched: [0..32) bucket counts, [32..64) cursors.
+__global__ void k_view_buckets(const __grid_constant__ ViewRasterSet vs, int32_t* __restrict__ sched)
+{
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < vs.total; i += gridDim.x * blockDim.x) {
+        const ViewRasterSet::View& V = vs.v[view_of(vs, i)];
+        const int64_t t = i - V.item0;
+        const int32_t len = V.off[(t + 1) * V.a.stride] - V.off[t * V.a.stride];
+        atomicAdd(&sched[31 - __clz(len + 1)], 1);
+    }
+}
+
+__global__ void k_view_bucket_starts(int32_t* __restrict__ sched)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int32_t run = 0;
+    for (int b = 31; b >= 0; --b) {
+        sched[32 + b] = run;
+        run += sched[b];
+    }
+}
+
+__global__ void k_view_order(const __grid_constant__ ViewRasterSet vs, int32_t* __restrict__ sched,
+                             int32_t* __restrict__ order)
+{
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < vs.total; i += gridDim.x * blockDim.x) {
+        const ViewRasterSet::View& V = vs.v[view_of(vs, i)];
+        const int64_t t = i - V.item0;
+        const int32_t len = V.off[(t + 1) * V.a.stride] - V.off[t * V.a.stride];
+        order[atomicAdd(&sched[32 + 31 - __clz(len + 1)], 1)] = i;
+    }
+}
+
 template <int TILE, bool LAZY>
 __global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 1)
-k_raster_views(const __grid_constant__ ViewRasterSet vs, int32_t* __restrict__ counter)
+k_raster_views(const __grid_constant__ ViewRasterSet vs, const int32_t* __restrict__ order,
+               int32_t* __restrict__ counter)
 {
     __shared__ RasterShared<TILE, false> sh;
     __shared__ WalkShared<LAZY> ws;
     __shared__ int32_t s_item;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        if (threadIdx.x == 0) {
+            const int32_t k = atomicAdd(counter, 1);
+            s_item = k < vs.total ? order[k] : vs.total;
+        }
         __syncthreads();  // also: every thread is done with the previous tile's shared memory
         const int32_t item = s_item;
         __syncthreads();
         if (item >= vs.total) break;
-        int v = 0;
-        while (v + 1 < vs.nviews && vs.v[v + 1].item0 <= item) ++v;
-        const ViewRasterSet::View& V = vs.v[v];
+        const ViewRasterSet::View& V = vs.v[view_of(vs, item)];
         raster_tile<TILE, false, false, LAZY>(item - V.item0, sh, ws, V.xy_ab, V.c_o_z, V.rgbv, V.words, V.off, V.a,
                                               V.cullmode, V.rgb, V.alpha, V.last, nullptr, nullptr, nullptr, nullptr,
                                               nullptr, V.cap, nullptr);
@@ -305,7 +348,7 @@ int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* 
     return GS_OK;
 }
 
-int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* counter, cudaStream_t st)
+int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* sched, int32_t* order, cudaStream_t st)
 {
     if (nv < 1 || nv > kMaxBatchViews) return GS_ERR_INVALID_ARG;
     ViewRasterSet vs;
@@ -339,10 +382,15 @@ int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* counter,
     vs.nviews = nv;
     vs.total = total;
     if (total == 0) return GS_OK;
-    GS_CUDA_TRY(cudaMemsetAsync(counter, 0, sizeof(int32_t), st));
+    // sched: [0..32) bucket counts, [32..64) bucket cursors, [64] work counter
+    GS_CUDA_TRY(cudaMemsetAsync(sched, 0, 65 * sizeof(int32_t), st));
+    const unsigned gi = (unsigned)((total + 255) / 256 < ctx->num_sms * 4 ? (total + 255) / 256 : ctx->num_sms * 4);
+    k_view_buckets<<<gi, 256, 0, st>>>(vs, sched);
+    k_view_bucket_starts<<<1, 32, 0, st>>>(sched);
+    k_view_order<<<gi, 256, 0, st>>>(vs, sched, order);
     const unsigned grid = (unsigned)(ctx->num_sms * 5 < total ? ctx->num_sms * 5 : total);
-    k_raster_views<16, true><<<grid, 256, 0, st>>>(vs, counter);
-    ctx->launches += 1;
+    k_raster_views<16, true><<<grid, 256, 0, st>>>(vs, order, sched + 64);
+    ctx->launches += 4;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
