@@ -339,6 +339,28 @@ def run_ours(args):
     err_vs_global = float((out_b[0] - out_g[0]).abs().max().item())
     last_equal = bool(torch.equal(out_b[2], out_g[2]))
 
+    # library comparator for the baseline's sort: torch's stable sort of the
+    # same M 64-bit (tile << 32 | depth bits) keys, L2 flushed, CUDA events
+    sort_lib_ms = None
+    try:
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(0)
+        keys = torch.randint(0, 1 << 62, (m_g,), dtype=torch.int64, device=dev, generator=gen)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(10)]
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                torch.sort(keys, stable=True)
+            for i in range(10):
+                flush.zero_()
+                ev[i][0].record()
+                torch.sort(keys, stable=True)
+                ev[i][1].record()
+        torch.cuda.synchronize()
+        sort_lib_ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+        del keys
+    except Exception as e:  # pragma: no cover
+        print(f"library sort comparator failed: {e}", file=sys.stderr)
+
     # the paper's approximate policy, for the repair ablation
     ctx_p = G.Context("paper")
     out_p = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
@@ -501,6 +523,7 @@ def run_ours(args):
         "raster_mpix_s": round(P / (raster_b * 1e-3) / 1e6, 3),
         "stages_ms": {s: round(mean(v), 4) for s, v in st_b.items() if mean(v) > 0},
         "global_sort": {"frame_ms": round(frame_g, 4), "raster_ms": round(raster_g, 4),
+                        "torch_sort_same_keys_ms": None if sort_lib_ms is None else round(sort_lib_ms, 4),
                         "value": round(value_g_pix_s / 1e6, 4),
                         "stages_ms": {s: round(mean(v), 4) for s, v in st_g.items() if mean(v) > 0}},
         "speedup_raster_vs_global": round(raster_g / raster_b, 4),

@@ -137,7 +137,7 @@ __device__ __forceinline__ void raster_tile(
     const uint8_t* __restrict__ plan, int default_cap, long long* __restrict__ tile_cycles)
 {
     const int tx = t % a.tiles_x, ty = t / a.tiles_x;
-    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int lx = WarpBlocks<TILE>::lx(), ly = WarpBlocks<TILE>::ly();
     const int px = tx * TILE + lx, py = ty * TILE + ly;
     const bool inside = px < a.width && py < a.height;
     const float pxc = (float)px + 0.5f, pyc = (float)py + 0.5f;

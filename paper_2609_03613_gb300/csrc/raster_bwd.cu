@@ -176,7 +176,7 @@ k_raster_bwd(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z,
 
     const int t = blockIdx.x;
     const int tx = t % a.tiles_x, ty = t / a.tiles_x;
-    const int lx = threadIdx.x % TILE, ly = threadIdx.x / TILE;
+    const int lx = WarpBlocks<TILE>::lx(), ly = WarpBlocks<TILE>::ly();
     const int px = tx * TILE + lx, py = ty * TILE + ly;
     const bool inside = px < a.width && py < a.height;
 

@@ -28,11 +28,11 @@ struct RasterShared {
     float4 b[BATCH];                       // {c/2, o, tau, gid bits}
     float4 c[BASELINE ? 1 : BATCH];        // colour (binned)
     uint32_t g[BASELINE ? BATCH : 1];      // gid (baseline colour lookup)
-    uint8_t list[BASELINE ? 1 : NWT][BASELINE ? 1 : BATCH];  // per warp: staged entries its strip mask admits
+    uint8_t list[BASELINE ? 1 : NWT][BASELINE ? 1 : BATCH];  // per warp: staged entries its warp mask admits
     int wc[NW];
 };
 
-// The staged entries (of cnt) whose strip mask admits the calling warp, in
+// The staged entries (of cnt) whose warp mask admits the calling warp, in
 // stage order, into sh.list[warp]; returns their count.  Whole warp.
 template <int TILE>
 __device__ __forceinline__ int warp_strip_list(RasterShared<TILE, false>& sh, int cnt)
@@ -50,28 +50,47 @@ __device__ __forceinline__ int warp_strip_list(RasterShared<TILE, false>& sh, in
     return nw;
 }
 
-// Rows of the tile a warp owns: the strip mask bit w is set when the
-// entry's alpha >= 1/255 ellipse (the tile cull's bound tau / margin, widened
-// as there) can reach rows [y0 + w*RPW, y0 + (w+1)*RPW) of the tile.
+// A warp owns an 8 x 4 pixel block of the tile: blocks are laid out TILE/8
+// wide and TILE/4 tall (16x16: 2 x 4 blocks for the 8 warps; 8x8: 1 x 2;
+// 32x32: 4 x 8), lanes row-major inside the block.
 template <int TILE>
-__device__ __forceinline__ uint32_t strip_mask(float my, float ha, float hb, float hc, float tau, float margin,
-                                               float y0)
+struct WarpBlocks {
+    static constexpr int COLS = TILE / 8, ROWS = TILE / 4;
+    static_assert(COLS * ROWS == TILE * TILE / 32, "one 8x4 block per warp");
+    __device__ static int lx() { return ((threadIdx.x >> 5) % COLS) * 8 + (threadIdx.x & 7); }
+    __device__ static int ly() { return ((threadIdx.x >> 5) / COLS) * 4 + ((threadIdx.x & 31) >> 3); }
+};
+
+// Warp mask of an entry: bit w is set when the entry's alpha >= 1/255 ellipse
+// (the tile cull's bound tau / margin, widened as there) has a bounding box
+// that reaches warp w's 8 x 4 block of the tile (origin x0, y0): the box is
+// |d| <= sqrt(4 q' tp / D) per axis (q' the other axis' coefficient,
+// D = 4 a/2 c/2 - b^2), so a warp never skips a pixel the entry can reach.
+template <int TILE>
+__device__ __forceinline__ uint32_t strip_mask(float mx, float my, float ha, float hb, float hc, float tau,
+                                               float margin, float x0, float y0)
 {
-    constexpr int RPW = 32 / TILE > 0 ? 32 / TILE : 1;  // pixel rows per warp
-    constexpr int NWT = TILE * TILE / 32;               // warps per tile
+    using WB = WarpBlocks<TILE>;
+    constexpr int NWT = TILE * TILE / 32;
     const uint32_t all = NWT >= 32 ? 0xffffffffu : ((1u << NWT) - 1u);
     if (!(margin > 0.0f)) return all;
     const float D = 4.0f * ha * hc - hb * hb;
     const float tp = tau / margin;
     if (!(D > 0.0f) || !(tp > 0.0f)) return all;
     const float dymax = sqrtf(4.0f * ha * tp / D) * (1.0f + 5e-3f) + 0.05f;
-    // pixel rows (centres y0 + row + 0.5) with |my - py| <= dymax
+    const float dxmax = sqrtf(4.0f * hc * tp / D) * (1.0f + 5e-3f) + 0.05f;
+    // pixel rows / columns (centres origin + i + 0.5) within the box
     const float rlo = fmaxf(ceilf(my - dymax - y0 - 0.5f), 0.0f);
     const float rhi = fminf(floorf(my + dymax - y0 - 0.5f), (float)(TILE - 1));
-    if (rlo > rhi) return 0u;
-    const int wlo = (int)rlo / RPW, whi = (int)rhi / RPW;
-    const uint32_t upto = whi >= 31 ? 0xffffffffu : ((2u << whi) - 1u);
-    return upto & ~((1u << wlo) - 1u) & all;
+    const float clo = fmaxf(ceilf(mx - dxmax - x0 - 0.5f), 0.0f);
+    const float chi = fminf(floorf(mx + dxmax - x0 - 0.5f), (float)(TILE - 1));
+    if (rlo > rhi || clo > chi) return 0u;
+    const int by0 = (int)rlo / 4, by1 = (int)rhi / 4, bx0 = (int)clo / 8, bx1 = (int)chi / 8;
+    uint32_t cols = 0u;
+    for (int bx = bx0; bx <= bx1; ++bx) cols |= 1u << bx;
+    uint32_t m = 0u;
+    for (int by = by0; by <= by1; ++by) m |= cols << (by * WB::COLS);
+    return m & all;
 }
 
 // Stage the batch [b0, b0 + BATCH) of n_entries stream words from src (global
@@ -104,7 +123,8 @@ __device__ __forceinline__ int stage_batch(const uint64_t* src, int32_t b0, int3
             if (cullmode & 1)
                 keep = !tile_culled(A.x, A.y, A.z, A.w, B.x, q.w, Cc.w, (float)(tx * TILE), (float)(ty * TILE),
                                     (float)TILE);
-            const uint32_t m = (cullmode & 2) ? strip_mask<TILE>(A.y, A.z, A.w, B.x, q.w, Cc.w, (float)(ty * TILE))
+            const uint32_t m = (cullmode & 2) ? strip_mask<TILE>(A.x, A.y, A.z, A.w, B.x, q.w, Cc.w,
+                                                                 (float)(tx * TILE), (float)(ty * TILE))
                                               : 0xffffffffu;
             keep = keep && m != 0u;
             Cc.w = __uint_as_float(m);  // the colour record carries the mask
