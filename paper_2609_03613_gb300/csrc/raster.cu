@@ -36,6 +36,49 @@ struct PixelState {
     bool done;
 };
 
+// One entry at one pixel, q given: the compositing definition's steps.
+// Returns true when the pixel stops (the entry is not applied).
+template <bool BASELINE, bool COUNT, class SH>
+__device__ __forceinline__ bool composite_entry(float q, const float4& ga, const float4& gb, const SH& sh, int k,
+                                                const float4* __restrict__ rgbv, PixelState& st)
+{
+    if (COUNT) {
+        ++st.ntests;
+        st.ops += 8;
+    }
+    if (BASELINE) {
+        if (!(q >= 0.0f)) return false;
+    } else {
+        // 0 <= q <= tau as one unsigned compare of the float bits
+        // (negative q and NaN compare above any positive tau)
+        if (__float_as_uint(q) > __float_as_uint(gb.z)) return false;
+    }
+    // the binned path reaches exp only for q <= tau (< 6), inside the core's
+    // range; the baseline evaluates every q >= 0 and needs the clamped form
+    // (exp(-q) for q > 87 would leave the 2^n range)
+    const float e = BASELINE ? spec_exp(-q) : spec_exp_core(-q);
+    const float alpha = fminf(0.99f, gb.y * e);
+    if (COUNT) st.ops += 17;
+    if (alpha < 1.0f / 255.0f) return false;
+    const float Tn = st.T * (1.0f - alpha);
+    if (COUNT) st.ops += 3;
+    if (Tn < 1e-4f) {
+        st.done = true;
+        return true;
+    }
+    if (COUNT) st.ops += 4;
+    const float w = alpha * st.T;
+    float4 col;
+    if constexpr (BASELINE) col = __ldg(rgbv + sh.g[k]);
+    else col = sh.c[k];
+    st.C0 = fmaf(col.x, w, st.C0);
+    st.C1 = fmaf(col.y, w, st.C1);
+    st.C2 = fmaf(col.z, w, st.C2);
+    st.T = Tn;
+    st.last = __float_as_int(gb.w);
+    return false;
+}
+
 // Composite n_entries stream words from src (global or shared memory) into
 // every pixel of the tile, in batches.  Returns -1 after the last entry, or,
 // block-uniformly, the offset of the first batch left unprocessed once every
@@ -58,47 +101,36 @@ __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_en
         int nk = cnt;
         if constexpr (!BASELINE) nk = __all_sync(0xffffffffu, st.done) ? 0 : warp_strip_list<TILE>(sh, cnt);
         if (!st.done) {
-            for (int i = 0; i < nk; ++i) {
-                int k = i;
-                if constexpr (!BASELINE) k = sh.list[warp][i];
-                const float4 ga = sh.a[k];
-                const float4 gb = sh.b[k];
-                if (COUNT) {
-                    ++st.ntests;
-                    st.ops += 8;
+            if constexpr (BASELINE) {
+                for (int k = 0; k < nk; ++k) {
+                    const float4 ga = sh.a[k];
+                    const float4 gb = sh.b[k];
+                    const float dx = ga.x - pxc, dy = ga.y - pyc;
+                    const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
+                    if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st)) break;
                 }
-                const float dx = ga.x - pxc, dy = ga.y - pyc;
-                const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
-                if (BASELINE) {
-                    if (!(q >= 0.0f)) continue;
-                } else {
-                    // 0 <= q <= tau as one unsigned compare of the float bits
-                    // (negative q and NaN compare above any positive tau)
-                    if (__float_as_uint(q) > __float_as_uint(gb.z)) continue;
+            } else {
+                // two entries a round: both q first (independent), then the
+                // two compositing steps in stream order
+                int i = 0;
+                for (; i + 1 < nk; i += 2) {
+                    const int k0 = sh.list[warp][i], k1 = sh.list[warp][i + 1];
+                    const float4 ga0 = sh.a[k0], gb0 = sh.b[k0];
+                    const float4 ga1 = sh.a[k1], gb1 = sh.b[k1];
+                    const float dx0 = ga0.x - pxc, dy0 = ga0.y - pyc;
+                    const float dx1 = ga1.x - pxc, dy1 = ga1.y - pyc;
+                    const float q0 = fmaf(dx0, fmaf(ga0.z, dx0, ga0.w * dy0), (gb0.x * dy0) * dy0);
+                    const float q1 = fmaf(dx1, fmaf(ga1.z, dx1, ga1.w * dy1), (gb1.x * dy1) * dy1);
+                    if (composite_entry<BASELINE, COUNT>(q0, ga0, gb0, sh, k0, rgbv, st)) break;
+                    if (composite_entry<BASELINE, COUNT>(q1, ga1, gb1, sh, k1, rgbv, st)) break;
                 }
-                // the binned path reaches exp only for q <= tau (< 6), inside the
-                // core's range; the baseline evaluates every q >= 0 and needs the
-                // clamped form (exp(-q) for q > 87 would leave the 2^n range)
-                const float e = BASELINE ? spec_exp(-q) : spec_exp_core(-q);
-                const float alpha = fminf(0.99f, gb.y * e);
-                if (COUNT) st.ops += 17;
-                if (alpha < 1.0f / 255.0f) continue;
-                const float Tn = st.T * (1.0f - alpha);
-                if (COUNT) st.ops += 3;
-                if (Tn < 1e-4f) {
-                    st.done = true;
-                    break;
+                if (!st.done && i < nk) {
+                    const int k = sh.list[warp][i];
+                    const float4 ga = sh.a[k], gb = sh.b[k];
+                    const float dx = ga.x - pxc, dy = ga.y - pyc;
+                    const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
+                    composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st);
                 }
-                if (COUNT) st.ops += 4;
-                const float w = alpha * st.T;
-                float4 col;
-                if (BASELINE) col = __ldg(rgbv + sh.g[k]);
-                else col = sh.c[k];
-                st.C0 = fmaf(col.x, w, st.C0);
-                st.C1 = fmaf(col.y, w, st.C1);
-                st.C2 = fmaf(col.z, w, st.C2);
-                st.T = Tn;
-                st.last = __float_as_int(gb.w);
             }
         }
     }
