@@ -253,8 +253,11 @@ k_layer_rows_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y, int64_t l
 // scans the records' widths, then each lane takes every 32nd entry, finds its
 // record by a binary search over the prefix and takes a slot in the entry's
 // (tile, bin) segment -- the cursors start at the segment offsets, so the
-// atomic returns the slot itself; four entries per lane are in flight.  The
+// atomic returns the slot itself; kScatterInFlight entries per lane are in
+// flight.  The
 // records carry the Gaussian's bin and depth bits, so nothing is gathered.
+constexpr int kScatterInFlight = 8;
+
 __global__ void __launch_bounds__(256)
 k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ rs_w,
                    const uint32_t* __restrict__ rs_z, const int32_t* __restrict__ roff, int64_t n, int tiles_x, int K,
@@ -284,12 +287,12 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
         }
         const uint32_t excl = incl - w;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        for (uint32_t e0 = 0; e0 < total; e0 += 128) {
-            int32_t p[4];
-            uint64_t word[4];
-            bool live[4];
+        for (uint32_t e0 = 0; e0 < total; e0 += 32 * kScatterInFlight) {
+            int32_t p[kScatterInFlight];
+            uint64_t word[kScatterInFlight];
+            bool live[kScatterInFlight];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kScatterInFlight; ++u) {
                 const uint32_t e = e0 + 32 * u + lane;
                 // owner: the last lane whose exclusive prefix is <= e
                 int o = 0;
@@ -310,7 +313,7 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < kScatterInFlight; ++u)
                 if (live[u]) words[p[u]] = word[u];
         }
     }
