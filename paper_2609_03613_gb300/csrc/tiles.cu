@@ -256,7 +256,7 @@ k_layer_rows_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y, int64_t l
 // atomic returns the slot itself; kScatterInFlight entries per lane are in
 // flight.  The
 // records carry the Gaussian's bin and depth bits, so nothing is gathered.
-constexpr int kScatterInFlight = 8;
+constexpr int kScatterInFlight = 4;
 
 __global__ void __launch_bounds__(256)
 k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ rs_w,
