@@ -61,23 +61,52 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y)
 
 constexpr int kProjBlock = 128;
 
-// Stage the block's SH coefficients (contiguous in memory) through shared
-// memory with coalesced float4 loads where the array is 16-byte aligned.
+// Stage the block's SH coefficients (contiguous in memory) into shared
+// memory.  With a 16-byte aligned array the TMA engine copies the block in one
+// bulk transfer (cp.async.bulk completing on an mbarrier; the multiple-of-16
+// prefix, any 4-byte tail by plain loads); the wait is bounded and reports
+// GS_ERR_TIMEOUT through err.  Otherwise coalesced plain loads.
 template <int PER>
 __device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_aligned, int64_t base, int64_t n,
-                                         float* s_sh)
+                                         float* s_sh, int* err)
 {
+    __shared__ __align__(8) uint64_t bar;
     const int cnt = (int)((n - base) < kProjBlock ? (n - base) : kProjBlock);
     const int total = cnt * PER;
     const float* src = sh + base * PER;
-    int k0 = 0;
     if (sh_aligned) {
-        const float4* src4 = reinterpret_cast<const float4*>(src);
-        float4* dst4 = reinterpret_cast<float4*>(s_sh);
-        for (int k = threadIdx.x; k < total / 4; k += kProjBlock) dst4[k] = __ldg(src4 + k);
-        k0 = (total / 4) * 4;
+        const uint32_t bytes = (uint32_t)(total * 4) & ~15u;
+        const uint32_t sbar = (uint32_t)__cvta_generic_to_shared(&bar);
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sbar), "r"(bytes)
+                         : "memory");
+            if (bytes > 0)
+                asm volatile(
+                    "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        (uint32_t)__cvta_generic_to_shared(s_sh)),
+                    "l"(src), "r"(bytes), "r"(sbar)
+                    : "memory");
+        }
+        for (int k = (int)(bytes / 4) + threadIdx.x; k < total; k += kProjBlock) s_sh[k] = __ldg(src + k);
+        // bounded wait for phase 0 of the barrier
+        uint32_t done = 0;
+        for (int it = 0; it < (1 << 22) && !done; ++it)
+            asm volatile(
+                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                : "=r"(done)
+                : "r"(sbar)
+                : "memory");
+        if (!done) raise_error(err, GS_ERR_TIMEOUT);
+        __syncthreads();
+        if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(sbar) : "memory");
+        return;
     }
-    for (int k = k0 + threadIdx.x; k < total; k += kProjBlock) s_sh[k] = __ldg(src + k);
+    for (int k = threadIdx.x; k < total; k += kProjBlock) s_sh[k] = __ldg(src + k);
     __syncthreads();
 }
 
@@ -224,13 +253,13 @@ template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
 k_project(const float* __restrict__ means, const float* __restrict__ scales,
           const float4* __restrict__ quats, const float* __restrict__ opac,
-          const float* __restrict__ sh, int sh_aligned, int64_t n, CamArgs cam, ProjView pv)
+          const float* __restrict__ sh, int sh_aligned, int64_t n, CamArgs cam, ProjView pv, int* err)
 {
     constexpr int NC = (DEG + 1) * (DEG + 1);
     constexpr int PER = NC * 3;  // floats of SH per Gaussian
     __shared__ __align__(16) float s_sh[kProjBlock * PER];
     const int64_t base = (int64_t)blockIdx.x * kProjBlock;
-    stage_sh<PER>(sh, sh_aligned, base, n, s_sh);
+    stage_sh<PER>(sh, sh_aligned, base, n, s_sh, err);
     const int64_t i = base + threadIdx.x;
     if (i >= n) return;
     float4 a, b, c;
@@ -259,13 +288,14 @@ template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
 k_project_batch(const float* __restrict__ means, const float* __restrict__ scales,
                 const float4* __restrict__ quats, const float* __restrict__ opac,
-                const float* __restrict__ sh, int sh_aligned, int64_t n, const __grid_constant__ BatchCams bc)
+                const float* __restrict__ sh, int sh_aligned, int64_t n, const __grid_constant__ BatchCams bc,
+                int* err)
 {
     constexpr int NC = (DEG + 1) * (DEG + 1);
     constexpr int PER = NC * 3;
     __shared__ __align__(16) float s_sh[kProjBlock * PER];
     const int64_t base = (int64_t)blockIdx.x * kProjBlock;
-    stage_sh<PER>(sh, sh_aligned, base, n, s_sh);
+    stage_sh<PER>(sh, sh_aligned, base, n, s_sh, err);
     const int64_t i = base + threadIdx.x;
     if (i >= n) return;
     const float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
@@ -322,10 +352,10 @@ int launch_project_batch(gs_ctx* ctx, const float* means, const float* scales, c
     const unsigned grid = (unsigned)((n + kProjBlock - 1) / kProjBlock);
     const float4* q4 = reinterpret_cast<const float4*>(quats);
     switch (sh_degree) {
-        case 0: k_project_batch<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc); break;
-        case 1: k_project_batch<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc); break;
-        case 2: k_project_batch<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc); break;
-        default: k_project_batch<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc); break;
+        case 0: k_project_batch<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, ctx->d_err); break;
+        case 1: k_project_batch<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, ctx->d_err); break;
+        case 2: k_project_batch<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, ctx->d_err); break;
+        default: k_project_batch<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, ctx->d_err); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
@@ -343,10 +373,10 @@ int launch_project(gs_ctx* ctx, const float* means, const float* scales, const f
     const unsigned grid = (unsigned)((n + kProjBlock - 1) / kProjBlock);
     const float4* q4 = reinterpret_cast<const float4*>(quats);
     switch (sh_degree) {
-        case 0: k_project<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv); break;
-        case 1: k_project<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv); break;
-        case 2: k_project<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv); break;
-        default: k_project<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv); break;
+        case 0: k_project<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, ctx->d_err); break;
+        case 1: k_project<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, ctx->d_err); break;
+        case 2: k_project<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, ctx->d_err); break;
+        default: k_project<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, ctx->d_err); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
