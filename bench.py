@@ -51,10 +51,13 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-train", action="store_true", help="skip the forward+backward training-step leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-view batched-render leg")
+    ap.add_argument("--no-spatial", action="store_true", help="skip the raster-order-aware storage leg")
     ap.add_argument("--profile-frame", action="store_true",
                     help="for ncu: two warm-up frames, then one frame of each path, no timing")
     ap.add_argument("--modes", default="exact,global", help="paths run by --profile-frame")
     ap.add_argument("--backward", action="store_true", help="--profile-frame: also one saved frame + backward")
+    ap.add_argument("--spatial", action="store_true",
+                    help="--profile-frame: render the scene in raster-order-aware (Morton) storage")
     return ap.parse_args()
 
 
@@ -267,25 +270,25 @@ def run_ours(args):
 
     side = torch.cuda.Stream(device=dev)  # graphs cannot be captured on the legacy stream
 
-    def make(mode):
+    def make(mode, sc_dev=ds):
         ctx = G.Context(mode)
         out = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
                torch.empty((H, W), dtype=torch.int32, device=dev))
         with torch.cuda.stream(side):
-            ctx.render(ds, cam, bg, out)  # sizes the scratch (one read of M)
+            ctx.render(sc_dev, cam, bg, out)  # sizes the scratch (one read of M)
         torch.cuda.synchronize()
         m = ctx.last_entry_count()
-        ctx.reserve(ds.n, int(m * 1.25) + 1024, W, H)
+        ctx.reserve(sc_dev.n, int(m * 1.25) + 1024, W, H)
         return ctx, out, m
 
-    def timed(ctx, out, steps, warmup, flags=G.RENDER_NO_SYNC | G.RENDER_GRAPH):
+    def timed(ctx, out, steps, warmup, flags=G.RENDER_NO_SYNC | G.RENDER_GRAPH, sc_dev=ds):
         # stage events only outside graphs (their records inside a captured
         # graph do not time the stages)
         staged = not (flags & G.RENDER_GRAPH)
         ctx.enable_timing(staged)
         with torch.cuda.stream(side):
             for _ in range(warmup):
-                ctx.render(ds, cam, bg, out, flags=flags)
+                ctx.render(sc_dev, cam, bg, out, flags=flags)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
         stage = {s: [] for s in G.STAGES}
@@ -298,7 +301,7 @@ def run_ours(args):
             for i in range(steps):
                 flush.zero_()
                 ev[i][0].record()
-                ctx.render(ds, cam, bg, out, flags=flags)
+                ctx.render(sc_dev, cam, bg, out, flags=flags)
                 ev[i][1].record()
                 if staged:
                     st = ctx.stage_times()  # events on the library's stream; synchronises
@@ -498,6 +501,37 @@ def run_ours(args):
                    "raster_gain": round(1.0 - mean(st_pl["raster"]) / raster_b, 4),
                    "image_equal_fixed": bool(torch.equal(out_pl[0], out_b[0]) and torch.equal(out_pl[2], out_b[2]))}
 
+    # raster-order-aware storage: the same scene with its Gaussians in the
+    # Morton order of their means (a per-scene step, timed once, outside the
+    # frames); the frame on it against the frame on the scene as generated
+    spatial = None
+    if not args.no_spatial:
+        ctx_o = G.Context("exact")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(side):
+            ctx_o.reorder_scene(ds)  # sizes the scratch
+            e0.record()
+            rs, _ = ctx_o.reorder_scene(ds)
+            e1.record()
+        torch.cuda.synchronize()
+        reorder_ms = e0.elapsed_time(e1)
+        ctx_s, out_s, m_s = make("exact", rs)
+        ms_s, _, _, _ = timed(ctx_s, out_s, args.steps, args.warmup, sc_dev=rs)
+        _, st_s, _, _ = timed(ctx_s, out_s, max(50, args.steps // 2), 3, flags=G.RENDER_NO_SYNC, sc_dev=rs)
+        with torch.cuda.stream(side):
+            ctx_s.render(rs, cam, bg, out_s)
+            ctx_b.render(ds, cam, bg, out_b)
+        torch.cuda.synchronize()
+        diff = (out_s[0] - out_b[0]).abs()
+        spatial = {"frame_ms": round(mean(ms_s), 4), "raster_ms": round(mean(st_s["raster"]), 4),
+                   "stages_ms": {s: round(mean(v), 4) for s, v in st_s.items() if mean(v) > 0},
+                   "frame_ms_as_generated": round(frame_b, 4), "raster_ms_as_generated": round(raster_b, 4),
+                   "frame_gain": round(1.0 - mean(ms_s) / frame_b, 4),
+                   "reorder_ms_once_per_scene": round(reorder_ms, 4), "entries_per_frame": m_s,
+                   "max_abs_err_vs_as_generated": float(diff.max().item()),
+                   "pixels_differing": int((diff.amax(dim=2) > 0).sum().item())}
+        del ctx_s, out_s, rs, ctx_o
+
     batch = None
     if not args.no_batch:
         batch = batch_leg(args, dev, side, flush, dist)
@@ -535,7 +569,7 @@ def run_ours(args):
         "frame_ms_without_graph": {"binned": round(mean(ms_b_ng), 4), "global_sort": round(mean(ms_g_ng), 4)},
         "wall_s_timed": round(wall_b, 3),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "train_step": train,
-        "planner": planner, "batch16": batch,
+        "planner": planner, "spatial_order": spatial, "batch16": batch,
         "gpu_launches": int(launches),
     }
     print(json.dumps(res), flush=True)
@@ -616,6 +650,9 @@ def run_profile_frame(args):
     from paper_2609_03613_gb300 import scenes, tilegs as G
     scene, cam = scenes.workload(WORKLOAD)
     ds = G.DeviceScene.from_numpy(scene, "cuda")
+    if args.spatial:
+        ds, _ = G.Context("exact").reorder_scene(ds)
+        torch.cuda.synchronize()
     for mode in args.modes.split(","):
         ctx = G.Context(mode)
         for _ in range(3):

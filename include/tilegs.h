@@ -381,6 +381,32 @@ int gs_mlp_backward(const float* params, const float* X, const float* acts, cons
 int gs_adam_step(float* params, const float* grads, float* m, float* v, int32_t n, float lr, float beta1,
                  float beta2, float eps, int32_t step, void* stream);
 
+/* ---------------------------------------------------------------- scene order */
+/*
+ * Raster-order-aware storage (the geometry-layout direction of Sec. 6.2,
+ * where per-Gaussian attribute gathers dominate the raster's memory traffic):
+ * a once-per-scene permutation putting the Gaussians in the Z-order (Morton
+ * order) of their means, so the Gaussians a tile composites lie close together
+ * in every per-Gaussian array.  The order, in float32 with one correctly
+ * rounded operation per step:
+ *   lo_a = min_i x_ia, hi_a = max_i x_ia (a = x, y, z over all n means),
+ *   s_a = 1024 / (hi_a - lo_a), or 0 when hi_a == lo_a,
+ *   c_a = min(1023, trunc((x_ia - lo_a) * s_a)),
+ *   code = OR over k < 10 of bit_k(c_x) << 3k | bit_k(c_y) << 3k+1 | bit_k(c_z) << 3k+2,
+ *   perm = the gids 0..n-1 stably sorted by code (ties keep gid order).
+ * gs_spatial_order: means [n][3] (device, finite) -> perm [n] int32 (device,
+ *   caller-owned): position i of the reordered scene holds Gaussian perm[i].
+ *   Context scratch grows to ~20 n bytes (allocates outside capture).
+ * gs_gather_rows: dst[i][0..width) = src[perm[i]][0..width) for float rows
+ *   (device; dst must not alias src).  A perm value outside [0, n) skips
+ *   its row and sets GS_ERR_INVALID_ARG in the device error word.
+ * Rendering the permuted scene gives the original image wherever no two
+ * Gaussians of a tile have bit-identical depths (ties follow the new gids).
+ */
+int gs_spatial_order(gs_ctx* ctx, const float* means, int64_t n, int32_t* perm, void* stream);
+int gs_gather_rows(gs_ctx* ctx, const int32_t* perm, int64_t n, const float* src, int32_t width, float* dst,
+                   void* stream);
+
 /* ---------------------------------------------------------------- whole frame */
 typedef struct gs_scene {
     const float* means;

@@ -144,7 +144,7 @@ extern "C" int gs_destroy(gs_ctx* c)
                     c->d_vals[1], c->d_hist, c->d_count, c->d_bin, c->d_bp, c->d_sel, c->d_tail,
                     c->d_tiles_order, c->d_tile_counter, c->r_proj, c->r_isect, c->r_stream,
                     c->r_off, c->r_m, c->r_scene, c->r_out, c->d_ops, c->d_tiles, c->d_samples,
-                    c->r_T, c->r_tend, c->d_planner, c->d_feat, c->d_plan};
+                    c->r_T, c->r_tend, c->d_planner, c->d_feat, c->d_plan, c->d_order_ws};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_m) cudaFreeHost(c->h_m);

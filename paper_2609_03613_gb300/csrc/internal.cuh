@@ -246,6 +246,9 @@ struct gs_ctx {
     uint8_t* d_plan = nullptr; size_t plan_cap_bytes = 0;
     // batched multi-view rendering (gs_render_batch)
     gs::BatchState* batch = nullptr;
+    // spatial order of a scene (order.cu)
+    void* d_order_ws = nullptr;
+    size_t order_ws_cap = 0;
     // timing
     int timing = 0;
     cudaEvent_t ev_b[GS_STAGE_COUNT];

@@ -42,7 +42,8 @@ EXPORTS = [
     "gs_grad2d_bytes", "gs_grad2d_offset", "gs_rasterize_bwd", "gs_render_bwd",
     "gs_render_batch", "gs_batch_set_view_config", "gs_batch_get_view_config", "gs_batch_last_entry_count",
     "gs_batch_autotune", "gs_rasterize_fwd_plan", "gs_tile_features", "gs_planner_set_weights", "gs_plan_tiles",
-    "gs_mlp_forward", "gs_mlp_loss_grad", "gs_mlp_backward", "gs_adam_step",
+    "gs_mlp_forward", "gs_mlp_loss_grad", "gs_mlp_backward", "gs_adam_step", "gs_spatial_order",
+    "gs_gather_rows",
 ]
 
 
@@ -145,6 +146,8 @@ def lib():
         "gs_batch_autotune": (C.c_int, [vp, C.POINTER(GsScene), C.POINTER(GsCamera), i32, i32, i32,
                                         C.POINTER(C.c_float), vp]),
         "gs_grad2d_offset": (sz, [i64, i32]),
+        "gs_spatial_order": (C.c_int, [vp, vp, i64, vp, vp]),
+        "gs_gather_rows": (C.c_int, [vp, vp, i64, vp, i32, vp, vp]),
         "gs_rasterize_bwd": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32, C.POINTER(C.c_float), vp, vp,
                                        vp, vp, vp, vp, vp]),
     }
@@ -488,6 +491,36 @@ class Context:
         check(lib().gs_plan_tiles(self.h, _ptr(features), int(features.shape[0]), _ptr(plan), _stream()),
               "gs_plan_tiles")
         return plan
+
+    # ------------------------------------------------------------- scene order
+    def spatial_order(self, means):
+        """perm [n] int32 (device): the Morton order of the means (gs_spatial_order)."""
+        import torch
+        n = int(means.shape[0])
+        perm = torch.empty(n, dtype=torch.int32, device=means.device)
+        check(lib().gs_spatial_order(self.h, _ptr(means.contiguous()), n, _ptr(perm), _stream()),
+              "gs_spatial_order")
+        return perm
+
+    def gather_rows(self, perm, src):
+        """dst[i] = src[perm[i]] for a float32 tensor of n rows (gs_gather_rows)."""
+        import torch
+        src = src.contiguous()
+        n = int(src.shape[0])
+        if int(perm.shape[0]) != n:
+            raise TileGSError("gs_gather_rows: invalid argument (perm and src lengths differ)")
+        width = int(src.numel() // n) if n else 1
+        dst = torch.empty_like(src)
+        check(lib().gs_gather_rows(self.h, _ptr(perm), n, _ptr(src), width, _ptr(dst), _stream()),
+              "gs_gather_rows")
+        return dst
+
+    def reorder_scene(self, sc: DeviceScene):
+        """(the scene in raster-order-aware storage, perm): every per-Gaussian
+        array gathered in the Morton order of the means."""
+        perm = self.spatial_order(sc.means)
+        g = lambda a: self.gather_rows(perm, a)
+        return DeviceScene(g(sc.means), g(sc.scales), g(sc.quats), g(sc.opacities), g(sc.sh), sc.sh_degree), perm
 
     # ------------------------------------------------------------- batches
     def render_batch(self, sc: DeviceScene, cams, bg=(0.0, 0.0, 0.0), outs=None, flags=0):
