@@ -95,12 +95,23 @@ k_sample_gids(const int32_t* __restrict__ goff, int64_t n, const int64_t* __rest
 {
     const int64_t M = live_count(m_dev, m_cap);
     if (M <= 0) return;
-    const int64_t ns = M < (int64_t)S ? M : (int64_t)S;
+    const uint64_t ns = (uint64_t)(M < (int64_t)S ? M : (int64_t)S);
+    const uint64_t uM = (uint64_t)M;
+    // ceil(x / M) by a multiply with inv = floor((2^64 - 1) / M): for
+    // x < 2^63 the product's high word is floor(x / M) or one less, and one
+    // comparison corrects it (x = goff * ns + M - 1 < 2^31 * 2^13 + 2^31)
+    const uint64_t inv = ~0ull / uM;
+    auto ceil_div = [&](uint64_t a) {
+        const uint64_t x = a * ns + uM - 1;
+        uint64_t q = __umul64hi(x, inv);
+        if ((q + 1) * uM <= x) ++q;
+        return q;
+    };
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = goff[g], b = goff[g + 1];
         if (b <= a) continue;
-        const int64_t i0 = (a * ns + M - 1) / M, i1 = (b * ns + M - 1) / M;
-        for (int64_t i = i0; i < i1 && i < ns; ++i) out[i] = (uint32_t)g;
+        const uint64_t i0 = ceil_div((uint64_t)a), i1 = ceil_div((uint64_t)b);
+        for (uint64_t i = i0; i < i1 && i < ns; ++i) out[i] = (uint32_t)g;
     }
 }
 
@@ -158,16 +169,31 @@ k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales
     const int64_t M = live_count(m_dev, m_cap);
     const int64_t ns = M < (int64_t)a.S ? M : (int64_t)a.S;
     const float lo_clamp = fmaxf(a.near_plane, a.eps);
-    // the positive keys, compacted with one shared atomic per warp and round
-    for (int64_t b0 = 0; b0 < ns; b0 += blockDim.x) {
-        const int64_t i = b0 + threadIdx.x;
+    // every sample's gid, then every depth (and scale) gathered at once, so
+    // the dependent loads cost two round trips rather than two per round
+    constexpr int kPer = kDrMaxS / kDrThreads;
+    uint32_t gk[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
+        gk[r] = i < ns ? gid_of(i, (i * M) / ns) : 0u;
+    }
+    float zk[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
         float z = 0.0f;
         if (i < ns) {
-            const int64_t j = (i * M) / ns;
-            const uint32_t g = gid_of(i, j);
-            z = c_o_z[g].z;
-            if (a.near_shift) z = zkey_of(z, scales, g, a.near_alpha, a.near_gamma);
+            z = c_o_z[gk[r]].z;
+            if (a.near_shift) z = zkey_of(z, scales, gk[r], a.near_alpha, a.near_gamma);
         }
+        zk[r] = z;
+    }
+    // the positive keys, compacted with one shared atomic per warp and round
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
+        const float z = zk[r];
         const bool keep = i < ns && z > 0.0f;
         const unsigned bal = __ballot_sync(0xffffffffu, keep);
         const int lane = threadIdx.x & 31;

@@ -539,7 +539,9 @@ int gs::render_binning(gs_ctx* c, int64_t n, const float* scales, const gs_camer
     ProjView pv = proj_view(c->r_proj, n);
     int r;
     stage_begin(c, GS_STAGE_INTERSECT, st);
-    r = count_scan(c, pv, n, c->r_m, st);
+    // EXACT with the tile cull: the row-record offsets in the same pass
+    const bool rows = c->cfg.mode == GS_MODE_BINNED_EXACT && c->cfg.tile_cull;
+    r = rows ? count_rows_scan(c, pv, n, c->r_m, st) : count_scan(c, pv, n, c->r_m, st);
     if (r != GS_OK) return r;
     if (!(flags & GS_RENDER_NO_SYNC)) {
         // size the entry buffers: read M once, grow if needed
@@ -559,7 +561,7 @@ int gs::render_binning(gs_ctx* c, int64_t n, const float* scales, const gs_camer
         stage_end(c, GS_STAGE_DEPTH_RANGE, st);
         if (r != GS_OK) return r;
         stage_begin(c, GS_STAGE_BIN, st);
-        r = exact_bins(c, pv, n, cam, true, c->r_m_cap, c->r_m, c->r_stream, c->r_off, st);
+        r = exact_bins(c, pv, n, cam, true, c->r_m_cap, c->r_m, c->r_stream, c->r_off, st, rows);
         stage_end(c, GS_STAGE_BIN, st);
         if (r != GS_OK) return r;
         stage_begin(c, GS_STAGE_REPAIR, st);

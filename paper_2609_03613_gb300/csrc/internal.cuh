@@ -275,6 +275,10 @@ int scan_tile_counts(gs_ctx* ctx, const uint2* rect, int64_t n, int32_t* out, in
 
 // tile counts -> per-Gaussian offsets (ctx->d_goff) and M; then the emission
 int count_scan(gs_ctx* ctx, const ProjView& pv, int64_t n, int64_t* m_dev, cudaStream_t st);
+// count_scan plus the EXACT row-record offsets in one pass
+int count_rows_scan(gs_ctx* ctx, const ProjView& pv, int64_t n, int64_t* m_dev, cudaStream_t st);
+int32_t* rows_offsets(gs_ctx* ctx, int64_t n);
+int64_t* rows_total(gs_ctx* ctx, int64_t n);
 int emit_only(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, const IsectView& is,
               int64_t m_cap, const int64_t* m_dev, cudaStream_t st);
 
@@ -299,8 +303,9 @@ int launch_depth_range_into(const gs_config& c, const ProjView& pv, const float*
 // (with the tile cull: per-row culled spans; without: layered difference
 // counts and the expansion, which needs ctx->d_goff -- computed here unless
 // goff_ready).  Segments are left unsorted.
+// rows_ready: count_rows_scan has also written the row-record offsets.
 int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, bool goff_ready, int64_t m_cap,
-               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st);
+               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st, bool rows_ready = false);
 // bins.cu: sort segments of length >= min_len (EXACT) or the rule/budget
 // selection (PAPER)
 int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* stream_words, const int32_t* offsets,

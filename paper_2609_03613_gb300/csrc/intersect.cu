@@ -11,15 +11,22 @@ namespace gs {
 
 int scan_reserve(gs_ctx* ctx, int64_t n)
 {
+    // two scans' block sums (scan2_impl)
     const int64_t nb = n > 0 ? (n + kScanTile - 1) / kScanTile : 1;
-    return ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)(nb + 1) * sizeof(int64_t));
+    return ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)2 * (nb + 1) * sizeof(int64_t));
 }
+
+// ctx->d_goff holds the per-Gaussian entry offsets [n+1], then the
+// per-Gaussian row-record offsets [n+1] and the row-record total (int64)
+static size_t goff_bytes(int64_t n) { return align256((size_t)(n + 1) * sizeof(int32_t)); }
+int32_t* rows_offsets(gs_ctx* ctx, int64_t n) { return (int32_t*)((char*)ctx->d_goff + goff_bytes(n)); }
+int64_t* rows_total(gs_ctx* ctx, int64_t n) { return (int64_t*)((char*)ctx->d_goff + 2 * goff_bytes(n)); }
 
 int goff_reserve(gs_ctx* ctx, int64_t n)
 {
     size_t cap = ctx->goff_cap;
     void* p = ctx->d_goff;
-    int r = ensure(&p, &cap, (size_t)(n + 1) * sizeof(int32_t));
+    int r = ensure(&p, &cap, 2 * goff_bytes(n) + sizeof(int64_t));
     ctx->d_goff = static_cast<int32_t*>(p);
     ctx->goff_cap = cap;
     return r;
@@ -75,6 +82,22 @@ int count_scan(gs_ctx* ctx, const ProjView& pv, int64_t n, int64_t* m_dev, cudaS
         return GS_OK;
     }
     return scan_tile_counts(ctx, pv.rect, n, ctx->d_goff, m_dev, st);
+}
+
+// count_scan and, in the same pass, the row-record offsets of the EXACT
+// bin construction (rows_offsets / rows_total)
+int count_rows_scan(gs_ctx* ctx, const ProjView& pv, int64_t n, int64_t* m_dev, cudaStream_t st)
+{
+    int r = goff_reserve(ctx, n);
+    if (r != GS_OK) return r;
+    if (n == 0) {
+        GS_CUDA_TRY(cudaMemsetAsync(m_dev, 0, sizeof(int64_t), st));
+        GS_CUDA_TRY(cudaMemsetAsync(rows_offsets(ctx, 0), 0, sizeof(int32_t), st));
+        GS_CUDA_TRY(cudaMemsetAsync(rows_total(ctx, 0), 0, sizeof(int64_t), st));
+        return GS_OK;
+    }
+    return scan2_impl(ctx, LoadRectCountRows{pv.rect}, n, ctx->d_goff, m_dev, rows_offsets(ctx, n),
+                      rows_total(ctx, n), st);
 }
 
 int emit_only(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, const IsectView& is,

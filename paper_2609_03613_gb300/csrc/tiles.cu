@@ -97,38 +97,59 @@ struct CullArgs {
 // whose x-projection is one interval, found from the band ends and the
 // ellipse's leftmost/rightmost points.  Every box is widened (5e-3 relative +
 // 0.05 px) to cover float32 rounding; margin 0 (ill-conditioned conic) keeps
-// the whole row.
-__device__ __forceinline__ void row_span(float mx, float my, float ha, float hb, float hc, float tau, float margin,
-                                         int ty, int tile, int tx0, int tx1, int* a, int* b)
+// the whole row.  The per-Gaussian part (RowGeom) is computed once by the
+// lane that owns the Gaussian; the widening also covers the reciprocals it
+// multiplies by in place of divisions.
+struct RowGeom {
+    float my, hb, inv2ha, a4tp, D, dymax, ext, dyl;  // dymax < 0: keep the whole row
+};
+
+__device__ __forceinline__ RowGeom row_geom(float ha, float hb, float hc, float tau, float margin, float my)
+{
+    RowGeom g;
+    g.my = my;
+    g.hb = hb;
+    g.inv2ha = 0.0f;
+    g.a4tp = g.D = g.ext = g.dyl = 0.0f;
+    g.dymax = -1.0f;
+    if (!(margin > 0.0f)) return g;
+    const float tp = tau / margin;
+    const float D = 4.0f * ha * hc - hb * hb;
+    if (!(D > 0.0f) || !(tp > 0.0f)) return g;
+    g.D = D;
+    g.a4tp = 4.0f * ha * tp;
+    g.dymax = sqrtf(g.a4tp / D) * (1.0f + 5e-3f) + 0.05f;
+    g.ext = sqrtf(4.0f * hc * tp / D);
+    g.dyl = hb * g.ext / (2.0f * hc);  // dy of the leftmost point (dx = -ext)
+    g.inv2ha = 1.0f / (2.0f * ha);
+    return g;
+}
+
+__device__ __forceinline__ void row_span(float mx, const RowGeom& g, int ty, int tile, float inv_tile, int tx0,
+                                         int tx1, int* a, int* b)
 {
     *a = tx0;
     *b = tx1;
-    if (!(margin > 0.0f)) return;
-    const float tp = tau / margin;
-    const float D = 4.0f * ha * hc - hb * hb;
-    if (!(D > 0.0f) || !(tp > 0.0f)) return;
+    if (g.dymax < 0.0f) return;
     const float y0 = (float)(ty * tile);
-    float yl = my - (y0 + (float)tile - 0.5f), yh = my - (y0 + 0.5f);
+    float yl = g.my - (y0 + (float)tile - 0.5f), yh = g.my - (y0 + 0.5f);
     yl = yl - (0.05f + 5e-3f * fabsf(yl));
     yh = yh + (0.05f + 5e-3f * fabsf(yh));
-    const float dymax = sqrtf(4.0f * ha * tp / D) * (1.0f + 5e-3f) + 0.05f;
-    const float ya = fmaxf(yl, -dymax), yb = fminf(yh, dymax);
+    const float ya = fmaxf(yl, -g.dymax), yb = fminf(yh, g.dymax);
     if (ya > yb) {
         *b = *a;  // the band misses the ellipse
         return;
     }
-    const float ext = sqrtf(4.0f * hc * tp / D);
-    const float dy_left = hb * ext / (2.0f * hc);  // dy of the leftmost point (dx = -ext)
-    const float s_a = sqrtf(fmaxf(0.0f, 4.0f * ha * tp - D * ya * ya));
-    const float s_b = sqrtf(fmaxf(0.0f, 4.0f * ha * tp - D * yb * yb));
-    const float La = (-hb * ya - s_a) / (2.0f * ha), Lb = (-hb * yb - s_b) / (2.0f * ha);
-    const float Ra = (-hb * ya + s_a) / (2.0f * ha), Rb = (-hb * yb + s_b) / (2.0f * ha);
-    float dxmin = (dy_left >= ya && dy_left <= yb) ? -ext : fminf(La, Lb);
-    float dxmax = (-dy_left >= ya && -dy_left <= yb) ? ext : fmaxf(Ra, Rb);
+    const float s_a = sqrtf(fmaxf(0.0f, g.a4tp - g.D * ya * ya));
+    const float s_b = sqrtf(fmaxf(0.0f, g.a4tp - g.D * yb * yb));
+    const float La = (-g.hb * ya - s_a) * g.inv2ha, Lb = (-g.hb * yb - s_b) * g.inv2ha;
+    const float Ra = (-g.hb * ya + s_a) * g.inv2ha, Rb = (-g.hb * yb + s_b) * g.inv2ha;
+    float dxmin = (g.dyl >= ya && g.dyl <= yb) ? -g.ext : fminf(La, Lb);
+    float dxmax = (-g.dyl >= ya && -g.dyl <= yb) ? g.ext : fmaxf(Ra, Rb);
     dxmin = dxmin - (0.05f + 5e-3f * fabsf(dxmin));
     dxmax = dxmax + (0.05f + 5e-3f * fabsf(dxmax));
     const float ft = (float)tile;
-    float fa = ceilf((mx - dxmax - (ft - 0.5f)) / ft), fb = floorf((mx - dxmin - 0.5f) / ft) + 1.0f;
+    float fa = ceilf((mx - dxmax - (ft - 0.5f)) * inv_tile), fb = floorf((mx - dxmin - 0.5f) * inv_tile) + 1.0f;
     fa = fminf(fmaxf(fa, (float)tx0), (float)tx1);
     fb = fminf(fmaxf(fb, (float)tx0), (float)tx1);
     *a = (int)fa;
@@ -191,6 +212,8 @@ k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict
             gbin[gl] = (uint8_t)bin;
         }
     }
+    const RowGeom mine = row_geom(0.5f * p.z, p.w, 0.5f * q.x, q.w, margin, p.y);
+    const float inv_tile = 1.0f / (float)ca.tile;  // exact: tiles are 8, 16 or 32
     const int W1 = tiles_x + 1;
     for (int32_t e0 = base; e0 < end; e0 += 32) {
         const int32_t e = e0 + lane;
@@ -201,18 +224,24 @@ k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict
             if (k + s < 32 && v <= e) k += s;
         }
         const uint32_t ra = __shfl_sync(0xffffffffu, r.x, k), rb = __shfl_sync(0xffffffffu, r.y, k);
-        const float mx = __shfl_sync(0xffffffffu, p.x, k), my = __shfl_sync(0xffffffffu, p.y, k);
-        const float ca_ = __shfl_sync(0xffffffffu, p.z, k), cb = __shfl_sync(0xffffffffu, p.w, k);
-        const float cc = __shfl_sync(0xffffffffu, q.x, k), tau = __shfl_sync(0xffffffffu, q.w, k);
+        const float mx = __shfl_sync(0xffffffffu, p.x, k);
+        RowGeom g;
+        g.my = __shfl_sync(0xffffffffu, mine.my, k);
+        g.hb = __shfl_sync(0xffffffffu, mine.hb, k);
+        g.inv2ha = __shfl_sync(0xffffffffu, mine.inv2ha, k);
+        g.a4tp = __shfl_sync(0xffffffffu, mine.a4tp, k);
+        g.D = __shfl_sync(0xffffffffu, mine.D, k);
+        g.dymax = __shfl_sync(0xffffffffu, mine.dymax, k);
+        g.ext = __shfl_sync(0xffffffffu, mine.ext, k);
+        g.dyl = __shfl_sync(0xffffffffu, mine.dyl, k);
         const uint32_t zb = __shfl_sync(0xffffffffu, __float_as_uint(q.z), k);
-        const float mg = __shfl_sync(0xffffffffu, margin, k);
         const uint32_t b = __shfl_sync(0xffffffffu, bin, k);
         const int32_t o = __shfl_sync(0xffffffffu, my_off, k);
         if (e < end) {
             const int tx0 = ra & 0xffff, ty0 = ra >> 16, tx1 = rb & 0xffff;
             const int ty = ty0 + (e - o);
             int a, x1;
-            row_span(mx, my, 0.5f * ca_, cb, 0.5f * cc, tau, mg, ty, ca.tile, tx0, tx1, &a, &x1);
+            row_span(mx, g, ty, ca.tile, inv_tile, tx0, tx1, &a, &x1);
             rs_g[e] = (uint32_t)(g0 + k);
             rs_ya[e] = row_record(ty, a, b);
             rs_w[e] = (uint32_t)(x1 - a);
@@ -450,7 +479,7 @@ int exact_bins_reserve(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t tiles_x, i
 }
 
 int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, bool goff_ready, int64_t m_cap,
-               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st)
+               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st, bool rows_ready)
 {
     const int tile = ctx->cfg.tile_size, K = ctx->cfg.K;
     const int32_t tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
@@ -468,7 +497,12 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
     if (ctx->cfg.tile_cull) {
         // rows of every rect, each row's culled span, per-row difference counts
         const int64_t rlayer = (int64_t)tiles_y * (tiles_x + 1);
-        if ((r = scan_impl(ctx, LoadRectRows{pv.rect}, n, v.roff, v.total, st)) != GS_OK) return r;
+        if (rows_ready && goff_ready) {
+            v.roff = rows_offsets(ctx, n);
+            v.total = rows_total(ctx, n);
+        } else if ((r = scan_impl(ctx, LoadRectRows{pv.rect}, n, v.roff, v.total, st)) != GS_OK) {
+            return r;
+        }
         CullArgs ca{pv.xy_ab, pv.c_o_z, pv.rgb, tile};
         const int64_t warps = (n + 31) / 32;
         if (warps > 0)
