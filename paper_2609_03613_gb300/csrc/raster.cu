@@ -88,13 +88,16 @@ template <int TILE, bool BASELINE, bool COUNT>
 __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_entries,
                                             RasterShared<TILE, BASELINE>& sh, const float4* __restrict__ xy_ab,
                                             const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
-                                            int cullmode, int tx, int ty, float pxc, float pyc, PixelState& st)
+                                            int cullmode, int tx, int ty, float pxc, float pyc, PixelState& st,
+                                            bool checked = false)
 {
     using SH = RasterShared<TILE, BASELINE>;
     constexpr int BS = SH::BS, BATCH = SH::BATCH;
     const int warp = threadIdx.x >> 5;
     for (int32_t b0 = 0; b0 < n_entries; b0 += BATCH) {
-        if (__syncthreads_count(st.done) == BS) return b0;
+        // checked: the caller has just counted the terminated pixels (block
+        // barrier included) with nothing composited since
+        if (!(checked && b0 == 0) && __syncthreads_count(st.done) == BS) return b0;
         const int cnt = stage_batch<TILE, BASELINE>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
         __syncthreads();
         // binned: the warp composites only the entries its strip mask admits
@@ -146,9 +149,10 @@ struct FwdSpan {
     int cullmode, tx, ty;
     float pxc, pyc;
     PixelState& st;
-    __device__ __forceinline__ int32_t operator()(const uint64_t* src, int32_t n)
+    __device__ __forceinline__ int32_t operator()(const uint64_t* src, int32_t n, bool checked = false)
     {
-        return raster_span<TILE, BASELINE, COUNT>(src, n, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st);
+        return raster_span<TILE, BASELINE, COUNT>(src, n, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st,
+                                                  checked);
     }
     __device__ __forceinline__ bool done() const { return st.done; }
 };

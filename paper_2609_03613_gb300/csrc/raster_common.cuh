@@ -29,7 +29,6 @@ struct RasterShared {
     float4 c[BASELINE ? 1 : BATCH];        // colour (binned)
     uint32_t g[BASELINE ? BATCH : 1];      // gid (baseline colour lookup)
     uint8_t list[BASELINE ? 1 : NWT][BASELINE ? 1 : BATCH];  // per warp: staged entries its warp mask admits
-    int wc[NW];
 };
 
 // The staged entries (of cnt) whose warp mask admits the calling warp, in
@@ -95,9 +94,9 @@ __device__ __forceinline__ uint32_t strip_mask(float mx, float my, float ha, flo
 
 // Stage the batch [b0, b0 + BATCH) of n_entries stream words from src (global
 // or shared memory): per entry {mx, my, a/2, b}, {c/2, o, tau, gid bits} and,
-// binned, the colour with the strip mask in .w.  Entries the tile cull or the
-// strip mask drop are compacted away in order.  Returns the number staged
-// (block-uniform); the caller synchronises the block before reading sh.
+// binned, the colour with the strip mask in .w (zero for an entry the tile
+// cull drops).  Returns the number staged (block-uniform); the caller
+// synchronises the block before reading sh.
 template <int TILE, bool BASELINE>
 __device__ __forceinline__ int stage_batch(const uint64_t* src, int32_t b0, int32_t n_entries,
                                            RasterShared<TILE, BASELINE>& sh, const float4* __restrict__ xy_ab,
@@ -105,8 +104,7 @@ __device__ __forceinline__ int stage_batch(const uint64_t* src, int32_t b0, int3
                                            int cullmode, int tx, int ty)
 {
     using SH = RasterShared<TILE, BASELINE>;
-    constexpr int BATCH = SH::BATCH, NW = SH::NW;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int BATCH = SH::BATCH;
     const int32_t idx = b0 + threadIdx.x;
     const bool valid = threadIdx.x < BATCH && idx < n_entries;
     float4 A = make_float4(0.f, 0.f, 0.f, 0.f), B = A, Cc = A;
@@ -126,30 +124,15 @@ __device__ __forceinline__ int stage_batch(const uint64_t* src, int32_t b0, int3
             const uint32_t m = (cullmode & 2) ? strip_mask<TILE>(A.x, A.y, A.z, A.w, B.x, q.w, Cc.w,
                                                                  (float)(tx * TILE), (float)(ty * TILE))
                                               : 0xffffffffu;
-            keep = keep && m != 0u;
-            Cc.w = __uint_as_float(m);  // the colour record carries the mask
+            Cc.w = __uint_as_float(keep ? m : 0u);  // the colour record carries the mask
         }
     }
-    int cnt, pos;
-    if (BASELINE) {
-        pos = threadIdx.x;
-        cnt = min(BATCH, n_entries - b0);
-    } else {
-        // order-preserving compaction of the kept entries
-        const unsigned ball = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0 && warp < NW) sh.wc[warp] = __popc(ball);
-        __syncthreads();
-        int wp = 0;
-        cnt = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const int c = sh.wc[w];
-            wp += (w < warp) ? c : 0;
-            cnt += c;
-        }
-        pos = wp + __popc(ball & ((1u << lane) - 1u));
-    }
-    if (keep) {
+    // entry i of the batch goes to slot i: the tile cull and the strip mask
+    // leave a zero mask, which no warp's list admits (stream order is kept
+    // without a compaction pass)
+    const int cnt = min(BATCH, n_entries - b0);
+    const int pos = threadIdx.x;
+    if (valid) {
         sh.a[pos] = A;
         sh.b[pos] = B;
         if (BASELINE) sh.g[pos] = g;
@@ -240,8 +223,19 @@ __device__ __forceinline__ int32_t walk_tile(const uint64_t* words, const int32_
             ++b;
             continue;
         }
+        // the chunk ends before the first bin j > b whose end passes c0 + cap
+        // (bin ends are nondecreasing, so the bins that fit are a prefix):
+        // counted 32 bins a ballot by every warp, in place of a serial walk
         int e = b + 1;
-        while (e < K && ws.off[e + 1] - c0 <= cap) ++e;
+        {
+            const int lane = threadIdx.x & 31;
+            for (int j0 = b + 1; j0 < K; j0 += 32) {
+                const int j = j0 + lane;
+                const int fit = __popc(__ballot_sync(0xffffffffu, j < K && ws.off[j + 1] - c0 <= cap));
+                e += fit;
+                if (fit < 32) break;
+            }
+        }
         const int32_t len = ws.off[e] - c0;
         const int bfirst = b;
         b = e;
@@ -250,7 +244,7 @@ __device__ __forceinline__ int32_t walk_tile(const uint64_t* words, const int32_
         load_sort_chunk<TILE>(words, c0, len, bfirst, e, ws);  // ends with a block barrier
         if (writeback)
             for (int i = threadIdx.x; i < len; i += BS) writeback[c0 + i] = ws.sort[i];
-        const int32_t r = span(ws.sort, len);
+        const int32_t r = span(ws.sort, len, true);  // termination just counted above
         if (r >= 0) return c0 + r;
     }
     return ws.off[K];
