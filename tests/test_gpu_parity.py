@@ -349,6 +349,31 @@ def test_render_host_buffers(tiny):
     np.testing.assert_array_equal(bits(out[0].numpy()), bits(rgb_o))
 
 
+def test_render_host_buffers_pageable_and_offset(tiny):
+    """Host buffers that are pageable, or page-locked but starting 4 bytes
+    past a 16-byte boundary, give the same image."""
+    sc, cam = tiny[0], tiny[1]
+    rgb_o, last_o = tiny[6][0], tiny[6][2]
+
+    def pinned_at_offset(a):
+        a = np.ascontiguousarray(a, np.float32)
+        buf = torch.empty(a.size + 1).pin_memory()
+        v = buf[1:].view(a.shape)
+        v.copy_(torch.from_numpy(a))
+        return v
+
+    page = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32))
+    for make in (pinned_at_offset, page):
+        ctx = G.Context("exact")
+        hs = G.DeviceScene(make(sc.means), make(sc.scales), make(sc.quats), make(sc.opacities), make(sc.sh),
+                           sc.sh_degree)
+        out = (torch.empty((256, 256, 3)), torch.empty((256, 256)), torch.empty((256, 256), dtype=torch.int32))
+        ctx.render(hs, cam, out=out, flags=G.RENDER_HOST_INPUTS | G.RENDER_HOST_OUTPUTS)
+        np.testing.assert_array_equal(bits(out[0].numpy()), bits(rgb_o))
+        np.testing.assert_array_equal(out[2].numpy(), last_o)
+        assert ctx.error() == 0
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_empty_scene():
