@@ -403,6 +403,16 @@ def run_ours(args):
                 "peak_source": (f"{n_sm} SMs x 128 fp32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled "
                                 "during the timed region)"),
                 "ops_per_launch": ops, "tests_per_launch": tests}
+    # the same kernel against its instruction-issue ceiling: warp instructions
+    # per launch from the ncu capture (only while the source is unchanged)
+    # over the live raster time, against 4 schedulers x 1 issue a clock per SM
+    winst = prof.get("warp_inst_per_launch") if (prof and traffic is not None) else None
+    if winst:
+        issue_peak = n_sm * 4 * sm_mhz * 1e6
+        issue = winst / (raster_b * 1e-3)
+        roofline["issue"] = {"achieved": round(issue / 1e9, 2), "peak": round(issue_peak / 1e9, 2),
+                             "unit": "G warp-inst/s", "frac": round(issue / issue_peak, 4),
+                             "warp_inst_per_launch": winst}
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
     e2e = None
