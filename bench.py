@@ -232,9 +232,15 @@ def run_reference(args):
 
 # --------------------------------------------------------------------- ours
 def kernel_hash() -> str:
+    """Hash of the source the binned raster kernel compiles from: its files and
+    the device part of internal.cuh (the host-side context struct after the
+    context marker does not change the kernel)."""
     h = hashlib.sha256()
     for f in ("raster.cu", "raster_common.cuh", "internal.cuh", "device.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2609_03613_gb300", "csrc", f), "rb").read())
+        b = open(os.path.join(ROOT, "paper_2609_03613_gb300", "csrc", f), "rb").read()
+        if f == "internal.cuh":
+            b = b.split(b"// ------------------------------------------------------------------ context")[0]
+        h.update(b)
     return h.hexdigest()[:16]
 
 

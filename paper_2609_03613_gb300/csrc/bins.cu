@@ -664,6 +664,43 @@ k_repair_tail(const int32_t* __restrict__ off, const int32_t* __restrict__ tail,
     }
 }
 
+// EXACT with the repair in the raster: only segments of at least min_len
+// entries are sorted here.  A flat pass over the offsets lists them (one
+// thread per segment; most frames have none), then one block per listed
+// segment sorts it -- in shared memory when it fits, else in place.
+__global__ void k_list_long(const int32_t* __restrict__ off, int64_t nseg, int min_len, int32_t* __restrict__ list,
+                            int32_t cap, int* err)
+{
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseg; q += (int64_t)gridDim.x * blockDim.x) {
+        if (off[q + 1] - off[q] < min_len) continue;
+        const int slot = atomicAdd(&list[0], 1);
+        if (slot < cap) list[1 + slot] = (int32_t)q;
+        else raise_error(err, GS_ERR_CAPACITY);
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+k_sort_listed(const int32_t* __restrict__ off, const int32_t* __restrict__ list, int32_t cap,
+              uint64_t* __restrict__ words)
+{
+    __shared__ uint64_t s_buf[kRpCtaCap];
+    const int nl = min(list[0], cap);
+    for (int k = blockIdx.x; k < nl; k += gridDim.x) {
+        const int32_t q = list[1 + k];
+        const int l = off[q + 1] - off[q];
+        uint64_t* seg = words + off[q];
+        if (l <= kRpCtaCap) {
+            for (int i = threadIdx.x; i < l; i += blockDim.x) s_buf[i] = seg[i];
+            __syncthreads();
+            bitonic_mem(s_buf, l, threadIdx.x, blockDim.x, SyncBlock{});
+            for (int i = threadIdx.x; i < l; i += blockDim.x) seg[i] = s_buf[i];
+        } else {
+            bitonic_mem(seg, l, threadIdx.x, blockDim.x, SyncBlock{});
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void k_fill_selected(const int32_t* __restrict__ off, int64_t nseg, const uint8_t* __restrict__ sel,
                                 int mode, int min_len, uint8_t* __restrict__ out)
 {
@@ -712,11 +749,21 @@ int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* wor
     const int32_t tail_cap = kTailCap;
     if ((r = bins_reserve(ctx, 1, nseg)) != GS_OK) return r;
     GS_CUDA_TRY(cudaMemsetAsync(ctx->d_tail, 0, 4, st));
-    if (n_tiles > 0)
+    if (c.mode == GS_MODE_BINNED_EXACT && min_len > kRpWarpCap) {
+        if (nseg > 0) {
+            const int64_t want = (nseg + 255) / 256;
+            const unsigned g = (unsigned)(want < (int64_t)grid ? want : (int64_t)grid);
+            k_list_long<<<g, 256, 0, st>>>(offsets, nseg, min_len, ctx->d_tail, tail_cap, ctx->d_err);
+            k_sort_listed<<<(unsigned)ctx->num_sms, 1024, 0, st>>>(offsets, ctx->d_tail, tail_cap, words);
+            ctx->launches += 2;
+        }
+    } else if (n_tiles > 0)
         k_repair_tiles<<<(unsigned)n_tiles, kRpThreads, 0, st>>>(offsets, c.K, sel, words, ctx->d_tail, tail_cap,
                                                                  ctx->d_err, min_len);
-    k_repair_tail<<<(unsigned)ctx->num_sms, 1024, 0, st>>>(offsets, ctx->d_tail, tail_cap, words);
-    ctx->launches += (n_tiles > 0 ? 2 : 1);
+    if (!(c.mode == GS_MODE_BINNED_EXACT && min_len > kRpWarpCap)) {
+        k_repair_tail<<<(unsigned)ctx->num_sms, 1024, 0, st>>>(offsets, ctx->d_tail, tail_cap, words);
+        ctx->launches += (n_tiles > 0 ? 2 : 1);
+    }
     GS_CUDA_TRY(cudaGetLastError());
     if (selected_out) {
         k_fill_selected<<<grid, 256, 0, st>>>(offsets, nseg, sel, c.mode, min_len < 2 ? 2 : min_len, selected_out);

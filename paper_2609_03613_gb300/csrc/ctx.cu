@@ -125,6 +125,8 @@ extern "C" int gs_create(gs_ctx** out, const gs_config* cfg)
     if (cudaMalloc(&c->d_tile_counter, 64 * sizeof(int32_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
     if (cudaMalloc(&c->r_m, 2 * sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
     if (cudaMalloc(&c->d_ops, sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
+    if (cudaMalloc(&c->d_scan_done, sizeof(unsigned int)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
+    cudaMemset(c->d_scan_done, 0, sizeof(unsigned int));
     if (cudaMallocHost(&c->h_m, 2 * sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
     c->ev_ok = 1;
     for (int s = 0; s < GS_STAGE_COUNT; ++s) {
@@ -144,7 +146,7 @@ extern "C" int gs_destroy(gs_ctx* c)
                     c->d_vals[1], c->d_hist, c->d_count, c->d_bin, c->d_bp, c->d_sel, c->d_tail,
                     c->d_tiles_order, c->d_tile_counter, c->r_proj, c->r_isect, c->r_stream,
                     c->r_off, c->r_m, c->r_scene, c->r_out, c->d_ops, c->d_tiles, c->d_samples,
-                    c->r_T, c->r_tend, c->d_planner, c->d_feat, c->d_plan, c->d_order_ws};
+                    c->r_T, c->r_tend, c->d_planner, c->d_feat, c->d_plan, c->d_order_ws, c->d_scan_done};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_m) cudaFreeHost(c->h_m);

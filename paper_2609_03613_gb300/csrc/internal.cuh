@@ -183,9 +183,10 @@ struct gs_ctx {
     int device = 0;
     int num_sms = 152;
     int* d_err = nullptr;
-    // scan scratch (block sums)
+    // scan scratch (block sums) and the scans' last-block counter (zeroed once)
     void* d_scan = nullptr;
     size_t scan_bytes = 0;
+    unsigned int* d_scan_done = nullptr;
     // per-Gaussian emission offsets [n+1]
     int32_t* d_goff = nullptr;
     size_t goff_cap = 0;

@@ -1,9 +1,10 @@
 // intersect.cu -- K3 tile intersection (Sec. 3.1: one record per covered
 // tile) and the device-wide exclusive scans it and the binning use.
 //
-// Scan: three kernels without inter-block waits (reduce per block ->
-// one-block scan of the block sums -> per-block rescan with the prefix), all
-// in int64 so an overflowing total is detected instead of wrapping.
+// Scan (scan.cuh): two kernels without inter-block waits (reduce per block,
+// the last block scanning the block sums -> per-block rescan with the
+// prefix), all in int64 so an overflowing total is detected instead of
+// wrapping.
 #include "device.cuh"
 #include "scan.cuh"
 

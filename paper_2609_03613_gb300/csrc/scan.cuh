@@ -1,7 +1,8 @@
 // scan.cuh -- device-wide exclusive scan of int64-valued items given by a
-// load functor: three kernels without inter-block waits (reduce per block ->
-// one-block scan of the block sums -> per-block rescan with the prefix), all
-// in int64 so an overflowing total is detected instead of wrapping.
+// load functor: two kernels without inter-block waits (reduce per block, the
+// last block to finish scanning the block sums -> per-block rescan with the
+// prefix), all in int64 so an overflowing total is detected instead of
+// wrapping.
 #pragma once
 
 #include "internal.cuh"
@@ -41,6 +42,40 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* s_wa
     return warp_prefix + incl - v;
 }
 
+// Exclusive scan of sums[0..nb) in place by one block; sums[nb] = grand total.
+__device__ __forceinline__ void scan_sums_body(int64_t* sums, int64_t nb)
+{
+    __shared__ int64_t s_warp[kScanThreads / 32];
+    int64_t carry = 0;
+    for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+        const int64_t i = b0 + threadIdx.x;
+        const int64_t v = i < nb ? __ldcg(sums + i) : 0;  // written by other blocks: read at L2
+        int64_t total;
+        const int64_t ex = block_exclusive_scan(v, s_warp, &total);
+        if (i < nb) sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+// Called by every block after it stored its block sum(s): the last block to
+// arrive (a counter, reset by that block) scans the sums; no block waits for
+// another.  Returns true in the block that did the scan.
+__device__ __forceinline__ bool last_block_scans(unsigned int* done, int64_t* sa, int64_t* sb)
+{
+    __shared__ bool s_last;
+    __threadfence();  // this thread's sum store is visible device-wide ...
+    __syncthreads();  // ... before the block counts itself done
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    scan_sums_body(sa, gridDim.x);
+    if (sb) scan_sums_body(sb, gridDim.x);
+    if (threadIdx.x == 0) *done = 0u;  // ready for the next scan on the stream
+    return true;
+}
+
 struct LoadI32 {
     const int32_t* p;
     __device__ int64_t operator()(int64_t i) const { return p[i]; }
@@ -74,7 +109,7 @@ struct LoadRectCountRows {
 // Block sums: every item of the block's tile loaded at once (coalesced,
 // all in flight), summed, then reduced across the block.
 template <class Load>
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Load ld, int64_t n, int64_t* sums)
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Load ld, int64_t n, int64_t* sums, unsigned int* done)
 {
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int64_t v[kScanItems];
@@ -98,28 +133,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Load ld, int64_t n
         for (int w = 0; w < kScanThreads / 32; ++w) t += s_warp[w];
         sums[blockIdx.x] = t;
     }
+    last_block_scans(done, sums, nullptr);
 }
 
-// Exclusive scan of sums[0..nb) in place by one block; sums[nb] = grand total.
-__device__ __forceinline__ void scan_sums_body(int64_t* sums, int64_t nb)
-{
-    __shared__ int64_t s_warp[kScanThreads / 32];
-    int64_t carry = 0;
-    for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
-        const int64_t i = b0 + threadIdx.x;
-        const int64_t v = i < nb ? sums[i] : 0;
-        int64_t total;
-        const int64_t ex = block_exclusive_scan(v, s_warp, &total);
-        if (i < nb) sums[i] = carry + ex;
-        carry += total;
-    }
-    if (threadIdx.x == 0) sums[nb] = carry;
-}
-
-static __global__ void __launch_bounds__(kScanThreads) k_scan_sums(int64_t* sums, int64_t nb)
-{
-    scan_sums_body(sums, nb);
-}
 
 // The block tile's items move between the striped order of coalesced global
 // accesses (item k*256 + t in thread t's slot k) and the blocked order of the
@@ -207,10 +223,11 @@ k_scan_down(Load ld, int64_t n, const int64_t* sums, int64_t nb, int32_t* out, i
 
 // ------------------------------------------------------------------ two scans in one pass
 // Two exclusive scans of per-item values produced by one load (for example a
-// rect's tile count and its row count): ld(i, a, b).  The same three kernels,
-// each carrying both values; sums hold [nb + 1] entries per scan.
+// rect's tile count and its row count): ld(i, a, b).  The same kernels, each
+// carrying both values; sums hold [nb + 1] entries per scan.
 template <class Load2>
-__global__ void __launch_bounds__(kScanThreads) k_scan2_reduce(Load2 ld, int64_t n, int64_t* sa, int64_t* sb)
+__global__ void __launch_bounds__(kScanThreads) k_scan2_reduce(Load2 ld, int64_t n, int64_t* sa, int64_t* sb,
+                                                               unsigned int* done)
 {
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     int64_t acc_a = 0, acc_b = 0;
@@ -240,12 +257,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan2_reduce(Load2 ld, int64_t
         for (int w = 0; w < kScanThreads / 32; ++w) t += s_warp[threadIdx.x][w];
         (threadIdx.x ? sb : sa)[blockIdx.x] = t;
     }
-}
-
-// block 0 scans sa, block 1 scans sb
-static __global__ void __launch_bounds__(kScanThreads) k_scan2_sums(int64_t* sa, int64_t* sb, int64_t nb)
-{
-    scan_sums_body(blockIdx.x ? sb : sa, nb);
+    last_block_scans(done, sa, sb);
 }
 
 template <class Load2>
@@ -299,10 +311,9 @@ static inline int scan2_impl(gs_ctx* ctx, Load2 ld, int64_t n, int32_t* oa, int6
     if (r != GS_OK) return r;
     int64_t* sa = static_cast<int64_t*>(ctx->d_scan);
     int64_t* sb = sa + nb + 1;
-    k_scan2_reduce<Load2><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sa, sb);
-    k_scan2_sums<<<2, kScanThreads, 0, st>>>(sa, sb, nb);
+    k_scan2_reduce<Load2><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sa, sb, ctx->d_scan_done);
     k_scan2_down<Load2><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sa, sb, nb, oa, ta, ob, tb, ctx->d_err);
-    ctx->launches += 3;
+    ctx->launches += 2;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
@@ -314,10 +325,9 @@ static inline int scan_impl(gs_ctx* ctx, Load ld, int64_t n, int32_t* out, int64
     int r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)(nb + 1) * sizeof(int64_t));
     if (r != GS_OK) return r;
     int64_t* sums = static_cast<int64_t*>(ctx->d_scan);
-    k_scan_reduce<Load><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sums);
-    k_scan_sums<<<1, kScanThreads, 0, st>>>(sums, nb);
+    k_scan_reduce<Load><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sums, ctx->d_scan_done);
     k_scan_down<Load><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sums, nb, out, total64, ctx->d_err);
-    ctx->launches += 3;
+    ctx->launches += 2;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }

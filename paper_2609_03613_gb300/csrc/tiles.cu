@@ -386,11 +386,6 @@ k_bin_scatter_rects(const uint2* __restrict__ rect, const float4* __restrict__ c
     }
 }
 
-__global__ void k_capacity_check(const int64_t* __restrict__ m_dev, int64_t m_cap, int* err)
-{
-    if (*m_dev > m_cap) raise_error(err, GS_ERR_CAPACITY);
-}
-
 // Count of segment q = t*K + b from the prefixed layers (tile-major order).
 // count[t, b] from the layer-major row prefix D [b][y][x] into C [t][b]
 // (t = y * tiles_x + x): 32 x 32 (x, b) blocks through shared memory, so both
@@ -433,9 +428,11 @@ struct LoadLayerCount {
     }
 };
 
-__global__ void k_zero_if_over(const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ off, int64_t nq)
+__global__ void k_zero_if_over(const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ off, int64_t nq,
+                               int* err)
 {
     if (*m_dev <= m_cap) return;  // over capacity: empty stream, nothing out of bounds downstream
+    if (blockIdx.x == 0 && threadIdx.x == 0) raise_error(err, GS_ERR_CAPACITY);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x)
         off[q] = 0;
 }
@@ -492,8 +489,6 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
     if (tiles_x > 4096 || tiles_y > 4096) return GS_ERR_INVALID_ARG;  // row-record packing
     GS_CUDA_TRY(cudaMemsetAsync(v.D, 0, layer * K * 4, st));
     const unsigned g_sm = (unsigned)ctx->num_sms * 8;
-    k_capacity_check<<<1, 1, 0, st>>>(m_dev, m_cap, ctx->d_err);
-    ctx->launches += 1;
     if (ctx->cfg.tile_cull) {
         // rows of every rect, each row's culled span, per-row difference counts
         const int64_t rlayer = (int64_t)tiles_y * (tiles_x + 1);
@@ -516,7 +511,7 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
                              st>>>(v.D, tiles_x, tiles_y, K, rlayer, v.cur);
         ctx->launches += 3;
         if ((r = scan_impl(ctx, LoadPlainCount{v.cur}, nseg, offsets, nullptr, st)) != GS_OK) return r;
-        k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1);
+        k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1, ctx->d_err);
         GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)nseg * 4, cudaMemcpyDeviceToDevice, st));
         if (n > 0)
             k_bin_scatter_rows<<<g_sm * 2, 256, 0, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, tiles_x, K, m_dev,
@@ -531,7 +526,7 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
         if ((r = scan_impl(ctx, LoadLayerCount{v.D, K, tiles_x, tiles_x + 1, (int64_t)layer}, nseg, offsets, nullptr,
                            st)) != GS_OK)
             return r;
-        k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1);
+        k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1, ctx->d_err);
         GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)nseg * 4, cudaMemcpyDeviceToDevice, st));
         const int64_t warps = (n + 31) / 32;
         if (warps > 0)
