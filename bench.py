@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--no-train", action="store_true", help="skip the forward+backward training-step leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the 16-view batched-render leg")
     ap.add_argument("--no-spatial", action="store_true", help="skip the raster-order-aware storage leg")
+    ap.add_argument("--no-heavy", action="store_true", help="skip the 3M / 6M-Gaussian depth-complexity leg")
     ap.add_argument("--profile-frame", action="store_true",
                     help="for ncu: two warm-up frames, then one frame of each path, no timing")
     ap.add_argument("--modes", default="exact,global", help="paths run by --profile-frame")
@@ -552,6 +553,10 @@ def run_ours(args):
     if not args.no_batch:
         batch = batch_leg(args, dev, side, flush, dist)
 
+    heavy = None
+    if not args.no_heavy:
+        heavy = heavy_leg(dev, side, flush)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_block(scene, cam)
@@ -585,10 +590,78 @@ def run_ours(args):
         "frame_ms_without_graph": {"binned": round(mean(ms_b_ng), 4), "global_sort": round(mean(ms_g_ng), 4)},
         "wall_s_timed": round(wall_b, 3),
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "train_step": train,
-        "planner": planner, "spatial_order": spatial, "batch16": batch,
+        "planner": planner, "spatial_order": spatial, "batch16": batch, "heavy": heavy,
         "gpu_launches": int(launches),
     }
     print(json.dumps(res), flush=True)
+
+
+def heavy_leg(dev, side, flush, frames=10):
+    """The depth-complexity sweep: 3M Gaussians at 1920x1080 and 6M at
+    3840x2160 with the camera inside a dense cluster (per-tile ranges of
+    ~18k-70k).  Graph-replayed frames of the binned EXACT path, the same path
+    with the trained bin planner and the global-sort baseline; raster ms from
+    the library's stage events in one un-captured frame; images compared."""
+    import numpy as np
+    import torch
+
+    from paper_2609_03613_gb300 import planner_train as PT, scenes, tilegs as G
+
+    weights = np.load(PT.WEIGHTS).astype(np.float32) if os.path.exists(PT.WEIGHTS) else None
+    res = {}
+    for name in ("heavy3m", "heavy6m_4k"):
+        sc, cam = scenes.workload(name)
+        ds = G.DeviceScene.from_numpy(sc, dev)
+        H, W = cam.height, cam.width
+        r = {"gaussians": sc.n, "resolution": f"{W}x{H}"}
+        ref = None
+        for label, mode, kw in (("exact", "exact", {}), ("planner", "exact", {"planner": 1}),
+                                ("global_sort", "global", {})):
+            if label == "planner" and weights is None:
+                continue
+            ctx = G.Context(mode, **kw)
+            if label == "planner":
+                ctx.set_planner_weights(torch.from_numpy(weights))
+            out = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
+                   torch.empty((H, W), dtype=torch.int32, device=dev))
+            with torch.cuda.stream(side):
+                ctx.render(ds, cam, (0, 0, 0), out)
+            torch.cuda.synchronize()
+            m = ctx.last_entry_count()
+            ctx.reserve(ds.n, int(m * 1.05) + 1024, W, H)
+            fl = G.RENDER_NO_SYNC | G.RENDER_GRAPH
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
+            with torch.cuda.stream(side):
+                for _ in range(3):
+                    ctx.render(ds, cam, (0, 0, 0), out, flags=fl)
+                for i in range(frames):
+                    flush.zero_()
+                    ev[i][0].record()
+                    ctx.render(ds, cam, (0, 0, 0), out, flags=fl)
+                    ev[i][1].record()
+                ctx.enable_timing(True)
+                ctx.render(ds, cam, (0, 0, 0), out, flags=G.RENDER_NO_SYNC)
+            torch.cuda.synchronize()
+            st = ctx.stage_times()
+            assert ctx.error() == 0
+            frame = sum(a.elapsed_time(b) for a, b in ev) / frames
+            r[label] = {"frame_ms": round(frame, 4), "raster_ms": round(st["raster"], 4),
+                        "stages_ms": {k: round(v, 4) for k, v in st.items() if v > 0}}
+            r["entries_per_frame"] = m
+            if ref is None:
+                ref = (out[0].clone(), out[2].clone())
+            else:
+                r[label]["image_equal_exact"] = bool(torch.equal(out[0], ref[0]) and torch.equal(out[2], ref[1]))
+            ctx.close()
+            del out
+            torch.cuda.empty_cache()
+        g, e = r["global_sort"], r["exact"]
+        r["speedup_frame_vs_global"] = round(g["frame_ms"] / e["frame_ms"], 3)
+        r["speedup_raster_vs_global"] = round(g["raster_ms"] / e["raster_ms"], 3)
+        res[name] = r
+        del ds, ref
+        torch.cuda.empty_cache()
+    return res
 
 
 def batch_leg(args, dev, side, flush, dist):

@@ -428,6 +428,8 @@ k_bin_scatter(IsectView is, const int64_t* __restrict__ m_dev, int64_t m_cap, in
 }
 
 constexpr int32_t kTailCap = 1 << 16;
+// long-segment list capacity: every segment may be long on deep frames
+static int32_t tail_capacity(int64_t nseg) { return nseg > kTailCap ? (int32_t)nseg : kTailCap; }
 
 int bins_reserve(gs_ctx* ctx, int64_t m_cap, int64_t nseg)
 {
@@ -442,7 +444,7 @@ int bins_reserve(gs_ctx* ctx, int64_t m_cap, int64_t nseg)
     if ((r = ensure(&p, &ctx->sel_cap, align256((size_t)nseg) + (size_t)(nseg + 1) * 8 + 256)) != GS_OK) return r;
     ctx->d_sel = (uint8_t*)p;
     p = ctx->d_tail;
-    if ((r = ensure(&p, &ctx->tail_cap, (size_t)(kTailCap + 1) * 4)) != GS_OK) return r;
+    if ((r = ensure(&p, &ctx->tail_cap, (size_t)(tail_capacity(nseg) + 1) * 4)) != GS_OK) return r;
     ctx->d_tail = (int32_t*)p;
     return GS_OK;
 }
@@ -746,7 +748,7 @@ int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* wor
         GS_CUDA_TRY(cudaGetLastError());
         sel = s;
     }
-    const int32_t tail_cap = kTailCap;
+    const int32_t tail_cap = tail_capacity(nseg);
     if ((r = bins_reserve(ctx, 1, nseg)) != GS_OK) return r;
     GS_CUDA_TRY(cudaMemsetAsync(ctx->d_tail, 0, 4, st));
     if (c.mode == GS_MODE_BINNED_EXACT && min_len > kRpWarpCap) {
