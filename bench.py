@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--backward", action="store_true", help="--profile-frame: also one saved frame + backward")
     ap.add_argument("--spatial", action="store_true",
                     help="--profile-frame: render the scene in raster-order-aware (Morton) storage")
+    ap.add_argument("--workload", default="mid", choices=["mid", "heavy3m", "heavy6m_4k"],
+                    help="--profile-frame: the workload rendered")
     return ap.parse_args()
 
 
@@ -737,7 +739,7 @@ def run_profile_frame(args):
     import torch
 
     from paper_2609_03613_gb300 import scenes, tilegs as G
-    scene, cam = scenes.workload(WORKLOAD)
+    scene, cam = scenes.workload(args.workload)
     ds = G.DeviceScene.from_numpy(scene, "cuda")
     if args.spatial:
         ds, _ = G.Context("exact").reorder_scene(ds)
