@@ -307,6 +307,8 @@ int launch_depth_range_into(const gs_config& c, const ProjView& pv, const float*
 // rows_ready: count_rows_scan has also written the row-record offsets.
 int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, bool goff_ready, int64_t m_cap,
                const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st, bool rows_ready = false);
+// tiles.cu: items of the grouped scatter's count scan (for reserving)
+int64_t group_scan_items(gs_ctx* ctx, int32_t tiles_y, int K);
 // bins.cu: sort segments of length >= min_len (EXACT) or the rule/budget
 // selection (PAPER)
 int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* stream_words, const int32_t* offsets,

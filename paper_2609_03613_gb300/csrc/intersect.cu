@@ -140,7 +140,10 @@ int reserve_internal(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t width, int32
     const int tile = ctx->cfg.tile_size;
     const int32_t tiles_x = (width + tile - 1) / tile, tiles_y = (height + tile - 1) / tile;
     const int64_t nseg = (int64_t)tiles_x * tiles_y * GS_MAX_K;
-    if ((r = scan_reserve(ctx, n > nseg ? n : nseg)) != GS_OK) return r;
+    int64_t nscan = n > nseg ? n : nseg;
+    const int64_t ngroup = group_scan_items(ctx, tiles_y, GS_MAX_K);
+    if (ngroup > nscan) nscan = ngroup;
+    if ((r = scan_reserve(ctx, nscan)) != GS_OK) return r;
     if ((r = goff_reserve(ctx, n)) != GS_OK) return r;
     if ((r = samples_reserve(ctx)) != GS_OK) return r;
     if (ctx->cfg.mode == GS_MODE_GLOBAL_SORT) return sort_reserve(ctx, m_cap);

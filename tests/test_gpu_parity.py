@@ -454,6 +454,26 @@ def test_invalid_arguments_rejected():
         ctx.set_config(tile_size=12)
 
 
+def test_grouped_scatter_for_deep_capacity(tiny):
+    """With a reserved capacity of >= 32768 entries per tile the binned EXACT
+    frame takes its deep-frame bin scatter (row records grouped by (tile row,
+    bin), cursors in shared memory): the same image as the oracle."""
+    sc, cam = tiny[0], tiny[1]
+    rgb_o, a_o, l_o = tiny[6]
+    T = G.n_tiles(cam.width, cam.height)
+    for cull in (1, 0):
+        ctx = G.Context("exact", tile_cull=cull)
+        ctx.reserve(sc.n, 40_000 * T, cam.width, cam.height)
+        ds = G.DeviceScene.from_numpy(sc)
+        out = (torch.empty((cam.height, cam.width, 3), device="cuda"), torch.empty((cam.height, cam.width), device="cuda"),
+               torch.empty((cam.height, cam.width), dtype=torch.int32, device="cuda"))
+        ctx.render(ds, cam, out=out, flags=G.RENDER_NO_SYNC)
+        torch.cuda.synchronize()
+        assert ctx.error() == 0
+        np.testing.assert_array_equal(bits(out[0].cpu().numpy()), bits(rgb_o))
+        np.testing.assert_array_equal(out[2].cpu().numpy(), l_o)
+
+
 # ------------------------------------------------------------------ full size
 
 @pytest.fixture(scope="module")
