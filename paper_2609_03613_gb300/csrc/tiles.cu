@@ -393,11 +393,14 @@ k_group_count(const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ r
     for (int i = threadIdx.x; i < nkeys; i += blockDim.x) H[(int64_t)i * C + c] = s_h[i];
 }
 
-// pass 2: list[Hs[key * C + c] + rank] = record index (any order within a key)
+// pass 2: list[Hs[key * C + c] + rank] = the record {gid, row word, width,
+// depth bits} (any order within a key), so the scatter reads its group
+// contiguously
 __global__ void __launch_bounds__(kGroupThreads)
-k_group_write(const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ rs_w, const int32_t* __restrict__ roff,
+k_group_write(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya,
+              const uint32_t* __restrict__ rs_w, const uint32_t* __restrict__ rs_z, const int32_t* __restrict__ roff,
               int64_t n, int K, int nkeys, const int64_t* __restrict__ m_dev, int64_t m_cap,
-              const int32_t* __restrict__ Hs, int32_t* __restrict__ list)
+              const int32_t* __restrict__ Hs, uint4* __restrict__ list)
 {
     extern __shared__ int32_t s_h[];  // [nkeys] next slot, from the slice's base
     const int C = gridDim.x, c = blockIdx.x;
@@ -406,16 +409,23 @@ k_group_write(const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ r
     __syncthreads();
     int64_t r0, r1;
     record_slice(roff[n], C, c, &r0, &r1);
-    for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x)
-        if (rs_w[k] != 0u) list[atomicAdd(&s_h[group_key(rs_ya[k], K)], 1)] = (int32_t)k;
+    for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
+        const uint32_t w = rs_w[k];
+        if (w == 0u) continue;
+        const uint32_t ya = rs_ya[k];
+        list[atomicAdd(&s_h[group_key(ya, K)], 1)] = make_uint4(rs_g[k], ya, w, rs_z[k]);
+    }
 }
 
 // one block per (tile row, bin): that bin's cursor of every tile of the row
-__global__ void __launch_bounds__(256)
-k_scatter_groups(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya,
-                 const uint32_t* __restrict__ rs_w, const uint32_t* __restrict__ rs_z, const int32_t* __restrict__ list,
-                 const int32_t* __restrict__ Hs, int C, const int32_t* __restrict__ offsets, int tiles_x, int K,
-                 const int64_t* __restrict__ m_dev, int64_t m_cap, uint64_t* __restrict__ words)
+// (1024 threads: the groups' sizes vary widely, and the largest bound the
+// kernel's tail)
+constexpr int kScatterGroupThreads = 1024;
+
+__global__ void __launch_bounds__(kScatterGroupThreads)
+k_scatter_groups(const uint4* __restrict__ list, const int32_t* __restrict__ Hs, int C,
+                 const int32_t* __restrict__ offsets, int tiles_x, int K, const int64_t* __restrict__ m_dev,
+                 int64_t m_cap, uint64_t* __restrict__ words)
 {
     extern __shared__ int32_t s_cur[];  // [tiles_x]
     const int key = blockIdx.x;
@@ -430,12 +440,11 @@ k_scatter_groups(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__
         const int32_t i = i0 + lane;
         uint32_t a = 0, w = 0, g = 0, z = 0;
         if (i < L1) {
-            const int32_t k = list[i];
-            const uint32_t ya = rs_ya[k];
-            a = (ya >> 12) & 0xfffu;
-            w = rs_w[k];
-            g = rs_g[k];
-            z = rs_z[k];
+            const uint4 rec = list[i];
+            g = rec.x;
+            a = (rec.y >> 12) & 0xfffu;
+            w = rec.z;
+            z = rec.w;
         }
         uint32_t incl = w;
 #pragma unroll
@@ -552,6 +561,14 @@ __global__ void k_zero_if_over(const int64_t* __restrict__ m_dev, int64_t m_cap,
         off[q] = 0;
 }
 
+// The grouped scatter pays off once the frame is deep: decided on the host
+// from the reserved entry capacity per tile (the entry count itself lives on
+// the device).
+static bool grouped_scatter(int64_t m_cap, int64_t T)
+{
+    return T > 0 && m_cap / T >= kGroupedMinPerTile;
+}
+
 struct ExactScratch {
     int32_t* D;      // K layers of (tiles_y + 1) x (tiles_x + 1) difference counts
     int32_t* cur;    // T*K scatter cursors
@@ -560,7 +577,7 @@ struct ExactScratch {
     uint32_t *rs_g, *rs_ya, *rs_w, *rs_z;  // row records (<= m_cap)
     int64_t* total;  // scratch count
     int32_t *H, *Hs; // per ((tile row, bin) key, slice) record counts and their exclusive scan
-    int32_t* list;   // record indices grouped by key (<= m_cap)
+    uint4* list;     // the records grouped by key (<= m_cap)
 };
 
 static size_t exact_scratch(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t tiles_x, int32_t tiles_y, int K,
@@ -571,7 +588,7 @@ static size_t exact_scratch(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t tiles
     const size_t mc = (size_t)(m_cap > 0 ? m_cap : 1), nn = (size_t)(n > 0 ? n : 1);
     const size_t nh = (size_t)tiles_y * K * group_slices(ctx->num_sms);
     const size_t sizes[] = {layer * K * 4, T * K * 4, nn, (nn + 1) * 4, mc * 4, mc * 4, mc * 4, mc * 4, 8,
-                            nh * 4, (nh + 1) * 4, mc * 4};
+                            nh * 4, (nh + 1) * 4, grouped_scatter(m_cap, (int64_t)T) ? mc * 16 : 16};
     size_t total = 0;
     for (size_t s : sizes) total += align256(s);
     if (v) {
@@ -599,14 +616,6 @@ int exact_bins_reserve(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t tiles_x, i
     int r = ensure(&p, &ctx->tiles_cap, exact_scratch(ctx, n, m_cap, tiles_x, tiles_y, K, nullptr));
     ctx->d_tiles = (int32_t*)p;
     return r;
-}
-
-// The grouped scatter pays off once the frame is deep: decided on the host
-// from the reserved entry capacity per tile (the entry count itself lives on
-// the device).
-static bool grouped_scatter(int64_t m_cap, int64_t T)
-{
-    return T > 0 && m_cap / T >= kGroupedMinPerTile;
 }
 
 int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, bool goff_ready, int64_t m_cap,
@@ -656,10 +665,10 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
                                                                     v.H);
             ctx->launches += 1;
             if ((r = scan_impl(ctx, LoadI32{v.H}, (int64_t)nkeys * C, v.Hs, nullptr, st)) != GS_OK) return r;
-            k_group_write<<<(unsigned)C, kGroupThreads, hsm, st>>>(v.rs_ya, v.rs_w, v.roff, n, K, nkeys, m_dev, m_cap,
-                                                                    v.Hs, v.list);
-            k_scatter_groups<<<(unsigned)nkeys, 256, (size_t)tiles_x * 4, st>>>(
-                v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.list, v.Hs, C, offsets, tiles_x, K, m_dev, m_cap, words);
+            k_group_write<<<(unsigned)C, kGroupThreads, hsm, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, K,
+                                                                    nkeys, m_dev, m_cap, v.Hs, v.list);
+            k_scatter_groups<<<(unsigned)nkeys, kScatterGroupThreads, (size_t)tiles_x * 4, st>>>(
+                v.list, v.Hs, C, offsets, tiles_x, K, m_dev, m_cap, words);
             ctx->launches += 2;
         } else if (n > 0) {
             GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)nseg * 4, cudaMemcpyDeviceToDevice, st));
