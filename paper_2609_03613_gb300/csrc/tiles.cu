@@ -358,9 +358,9 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
 constexpr int kGroupThreads = 1024;
 constexpr int kMaxGroupKeys = 12288;  // (tile row, bin) keys in 48 KB of shared memory
 // reserved entries per tile from which the grouped scatter is used: measured
-// slower at ~3k (1M Gaussians, 1080p: 0.234 vs 0.210 ms bin stage) and ~19k
-// (3M, 1080p: 0.94 vs 0.83 ms), faster at ~43k (6M, 4K: 5.4 vs 7.6 ms)
-constexpr int64_t kGroupedMinPerTile = 32768;
+// slower at ~3k (1M Gaussians, 1080p: bin stage 0.228 vs 0.210 ms), faster at
+// ~19k (3M, 1080p: 0.60 vs 0.83 ms) and ~43k (6M, 4K: 3.74 vs 7.6 ms)
+constexpr int64_t kGroupedMinPerTile = 8192;
 
 __host__ __device__ inline int group_slices(int num_sms) { return 2 * num_sms; }
 

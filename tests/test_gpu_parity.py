@@ -455,7 +455,7 @@ def test_invalid_arguments_rejected():
 
 
 def test_grouped_scatter_for_deep_capacity(tiny):
-    """With a reserved capacity of >= 32768 entries per tile the binned EXACT
+    """With a reserved capacity of >= 8192 entries per tile the binned EXACT
     frame takes its deep-frame bin scatter (row records grouped by (tile row,
     bin), cursors in shared memory): the same image as the oracle."""
     sc, cam = tiny[0], tiny[1]
@@ -463,7 +463,7 @@ def test_grouped_scatter_for_deep_capacity(tiny):
     T = G.n_tiles(cam.width, cam.height)
     for cull in (1, 0):
         ctx = G.Context("exact", tile_cull=cull)
-        ctx.reserve(sc.n, 40_000 * T, cam.width, cam.height)
+        ctx.reserve(sc.n, 10_000 * T, cam.width, cam.height)
         ds = G.DeviceScene.from_numpy(sc)
         out = (torch.empty((cam.height, cam.width, 3), device="cuda"), torch.empty((cam.height, cam.width), device="cuda"),
                torch.empty((cam.height, cam.width), dtype=torch.int32, device="cuda"))
