@@ -419,7 +419,7 @@ k_group_write(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs
 
 // one block per (tile row, bin): that bin's cursor of every tile of the row
 // (1024 threads: the groups' sizes vary widely, and the largest bound the
-// kernel's tail)
+// kernel's tail); a thread takes a record and walks its span of tiles
 constexpr int kScatterGroupThreads = 1024;
 
 __global__ void __launch_bounds__(kScatterGroupThreads)
@@ -435,39 +435,13 @@ k_scatter_groups(const uint4* __restrict__ list, const int32_t* __restrict__ Hs,
     if (L1 <= L0) return;
     for (int x = threadIdx.x; x < tiles_x; x += blockDim.x) s_cur[x] = offsets[((int64_t)ty * tiles_x + x) * K + b];
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int32_t i0 = L0 + warp * 32; i0 < L1; i0 += nwarps * 32) {
-        const int32_t i = i0 + lane;
-        uint32_t a = 0, w = 0, g = 0, z = 0;
-        if (i < L1) {
-            const uint4 rec = list[i];
-            g = rec.x;
-            a = (rec.y >> 12) & 0xfffu;
-            w = rec.z;
-            z = rec.w;
-        }
-        uint32_t incl = w;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += u;
-        }
-        const uint32_t excl = incl - w;
-        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        for (uint32_t e0 = 0; e0 < total; e0 += 32) {
-            const uint32_t e = e0 + lane;
-            int o = 0;
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) {
-                const uint32_t v = __shfl_sync(0xffffffffu, excl, (o + s) & 31);
-                if (o + s < 32 && v <= e) o += s;
-            }
-            const uint32_t oex = __shfl_sync(0xffffffffu, excl, o), oa = __shfl_sync(0xffffffffu, a, o);
-            const uint32_t og = __shfl_sync(0xffffffffu, g, o), oz = __shfl_sync(0xffffffffu, z, o);
-            if (e < total) {
-                const int32_t slot = atomicAdd(&s_cur[(int)(oa + (e - oex))], 1);
-                words[slot] = ((uint64_t)oz << 32) | og;
-            }
+    for (int32_t i = L0 + (int32_t)threadIdx.x; i < L1; i += (int32_t)blockDim.x) {
+        const uint4 rec = list[i];
+        const uint64_t word = ((uint64_t)rec.w << 32) | rec.x;
+        const int a = (int)((rec.y >> 12) & 0xfffu);
+        for (int j = 0; j < (int)rec.z; ++j) {
+            const int32_t slot = atomicAdd(&s_cur[a + j], 1);
+            words[slot] = word;
         }
     }
 }
