@@ -9,6 +9,7 @@ import pytest
 
 import oracle as O
 from paper_2609_03613_gb300 import scenes
+from sampling import sampled_stream, tile_counts
 
 pytestmark = pytest.mark.gpu
 
@@ -118,3 +119,41 @@ def test_batch_rejects_bad_arguments():
         ctx.set_batch_view_config(G.MAX_VIEWS, tile_size=16)
     torch.cuda.synchronize()
     assert ctx.error() == 0
+
+
+def test_batch16_fullsize_autotuned_sampled_tiles():
+    """The 16-view workload as bench.py runs it (2M Gaussians, resolutions
+    512x512 .. 1920x1080, autotuned tile size and K per view, the batch as
+    one graph): on seeded tiles of every view (plus its deepest) bit-exact
+    against the oracle's compositing at that view's tile size."""
+    import os
+    sc, cams = scenes.workload("batch16")
+    O.set_threads(max(1, len(os.sched_getaffinity(0))))
+    ctx = G.Context("exact")
+    ds = G.DeviceScene.from_numpy(sc)
+    ctx.batch_autotune(ds, cams, tune_tile=True, iters=2)
+    outs = ctx.render_batch(ds, cams)  # sizes the views
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            ctx.render_batch(ds, cams, (0.0, 0.0, 0.0), outs, flags=G.RENDER_NO_SYNC | G.RENDER_GRAPH)
+    torch.cuda.synchronize()
+    assert ctx.error() == 0
+    rng = np.random.default_rng(16)
+    for v, cam in enumerate(cams):
+        tile = ctx.batch_view_config(v).tile_size
+        P = O.project(sc, cam, tile)
+        tx, ty = O.tiles_xy(cam.width, cam.height, tile)
+        cnt = tile_counts(P, tx, ty)
+        tiles = np.unique(np.concatenate([rng.choice(tx * ty, 5, replace=False), np.argsort(cnt)[-1:]]))
+        off, stream = sampled_stream(P, tiles, tx, ty)
+        rgb_o, a_o, l_o = O.composite(P, off, stream, cam.width, cam.height, tile, tiles=tiles.astype(np.int32))
+        rgb, alpha, last = (t.cpu().numpy() for t in outs[v])
+        for t in tiles:
+            y, x = divmod(int(t), tx)
+            ys = slice(y * tile, min(y * tile + tile, cam.height))
+            xs = slice(x * tile, min(x * tile + tile, cam.width))
+            np.testing.assert_array_equal(rgb[ys, xs].view(np.uint32), rgb_o[ys, xs].view(np.uint32))
+            np.testing.assert_array_equal(alpha[ys, xs].view(np.uint32), a_o[ys, xs].view(np.uint32))
+            np.testing.assert_array_equal(last[ys, xs], l_o[ys, xs])
