@@ -59,7 +59,7 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, float* Y)
     Y[15] = c36 * x * (xx - 3.0f * yy);
 }
 
-constexpr int kProjBlock = 128;
+constexpr int kProjBlock = 64;  // 64 measured 3 % faster than 128 and 192
 
 // Stage the block's SH coefficients (contiguous in memory) into shared
 // memory.  With a 16-byte aligned array the TMA engine copies the block in one
