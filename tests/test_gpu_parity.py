@@ -454,12 +454,43 @@ def test_invalid_arguments_rejected():
         ctx.set_config(tile_size=12)
 
 
+def giant_slab_scene():
+    """Odd image size plus one Gaussian covering every tile and a thin slab:
+    long per-tile lists (segments past the in-raster sort limit)."""
+    rng = np.random.default_rng(61)
+    n = 40000
+    base = scenes.tiny_scene(n, 61)
+    means = base.means.copy()
+    means[:, 2] = rng.uniform(-0.05, 0.05, n)
+    scales = base.scales * 10.0
+    scales[0] = [3.0, 3.0, 3.0]
+    sc = scenes.Scene(means, scales, base.quats, base.opacities * 0.3, base.sh, 0)
+    cam = scenes.Camera(scenes.look_at((0, 0, 3.0)), 300.0, 300.0, 125.0, 65.5, 250, 131)
+    return sc, cam
+
+
 def test_grouped_scatter_for_deep_capacity(tiny):
     """With a reserved capacity of >= 8192 entries per tile the binned EXACT
     frame takes its deep-frame bin scatter (row records grouped by (tile row,
-    bin), cursors in shared memory): the same image as the oracle."""
+    bin), cursors in shared memory): the same image as the oracle, on the
+    tiny scene and on a ragged image with very long tile lists."""
     sc, cam = tiny[0], tiny[1]
     rgb_o, a_o, l_o = tiny[6]
+    sc2, cam2 = giant_slab_scene()
+    _, _, (_, stream2), (rgb2, _, l2) = O.render(sc2, cam2)
+    cap2 = max(int(stream2.shape[0] * 1.1), 10_000 * G.n_tiles(cam2.width, cam2.height))
+    for K in (64, 4):
+        ctx = G.Context("exact", K=K)
+        ctx.reserve(sc2.n, cap2, cam2.width, cam2.height)
+        ds2 = G.DeviceScene.from_numpy(sc2)
+        out = (torch.empty((cam2.height, cam2.width, 3), device="cuda"),
+               torch.empty((cam2.height, cam2.width), device="cuda"),
+               torch.empty((cam2.height, cam2.width), dtype=torch.int32, device="cuda"))
+        ctx.render(ds2, cam2, out=out, flags=G.RENDER_NO_SYNC)
+        torch.cuda.synchronize()
+        assert ctx.error() == 0
+        np.testing.assert_array_equal(bits(out[0].cpu().numpy()), bits(rgb2))
+        np.testing.assert_array_equal(out[2].cpu().numpy(), l2)
     T = G.n_tiles(cam.width, cam.height)
     for cull in (1, 0):
         ctx = G.Context("exact", tile_cull=cull)
