@@ -617,17 +617,24 @@ def heavy_leg(dev, side, flush, frames=10):
         H, W = cam.height, cam.width
         r = {"gaussians": sc.n, "resolution": f"{W}x{H}"}
         ref = None
-        for label, mode, kw in (("exact", "exact", {}), ("planner", "exact", {"planner": 1}),
-                                ("global_sort", "global", {})):
+        rs = None
+        for label, mode, kw in (("exact", "exact", {}), ("exact_morton_storage", "exact", {}),
+                                ("planner", "exact", {"planner": 1}), ("global_sort", "global", {})):
             if label == "planner" and weights is None:
                 continue
+            scene_dev = ds
+            if label == "exact_morton_storage":
+                # raster-order-aware storage (the scene permuted once; ties in
+                # depth may order differently, so its image is not compared)
+                rs, _ = G.Context("exact").reorder_scene(ds)
+                scene_dev = rs
             ctx = G.Context(mode, **kw)
             if label == "planner":
                 ctx.set_planner_weights(torch.from_numpy(weights))
             out = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
                    torch.empty((H, W), dtype=torch.int32, device=dev))
             with torch.cuda.stream(side):
-                ctx.render(ds, cam, (0, 0, 0), out)
+                ctx.render(scene_dev, cam, (0, 0, 0), out)
             torch.cuda.synchronize()
             m = ctx.last_entry_count()
             ctx.reserve(ds.n, int(m * 1.05) + 1024, W, H)
@@ -635,23 +642,28 @@ def heavy_leg(dev, side, flush, frames=10):
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(frames)]
             with torch.cuda.stream(side):
                 for _ in range(3):
-                    ctx.render(ds, cam, (0, 0, 0), out, flags=fl)
+                    ctx.render(scene_dev, cam, (0, 0, 0), out, flags=fl)
                 for i in range(frames):
                     flush.zero_()
                     ev[i][0].record()
-                    ctx.render(ds, cam, (0, 0, 0), out, flags=fl)
+                    ctx.render(scene_dev, cam, (0, 0, 0), out, flags=fl)
                     ev[i][1].record()
                 ctx.enable_timing(True)
-                ctx.render(ds, cam, (0, 0, 0), out, flags=G.RENDER_NO_SYNC)
+                ctx.render(scene_dev, cam, (0, 0, 0), out, flags=G.RENDER_NO_SYNC)
             torch.cuda.synchronize()
             st = ctx.stage_times()
             assert ctx.error() == 0
             frame = sum(a.elapsed_time(b) for a, b in ev) / frames
             r[label] = {"frame_ms": round(frame, 4), "raster_ms": round(st["raster"], 4),
                         "stages_ms": {k: round(v, 4) for k, v in st.items() if v > 0}}
-            r["entries_per_frame"] = m
+            if label != "exact_morton_storage":
+                r["entries_per_frame"] = m
             if ref is None:
                 ref = (out[0].clone(), out[2].clone())
+            elif label == "exact_morton_storage":
+                r[label]["max_abs_err_vs_exact"] = float((out[0] - ref[0]).abs().max().item())
+                del rs
+                rs = None
             else:
                 r[label]["image_equal_exact"] = bool(torch.equal(out[0], ref[0]) and torch.equal(out[2], ref[1]))
             ctx.close()
