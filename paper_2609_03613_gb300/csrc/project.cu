@@ -85,12 +85,17 @@ __device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_al
         if (threadIdx.x == 0) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sbar), "r"(bytes)
                          : "memory");
-            if (bytes > 0)
+            if (bytes > 0) {
+                // the scene is read once a frame: evict it first, so the
+                // projected records and the later stages keep L2
+                uint64_t pol;
+                asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
                 asm volatile(
-                    "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
                         (uint32_t)__cvta_generic_to_shared(s_sh)),
-                    "l"(src), "r"(bytes), "r"(sbar)
+                    "l"(src), "r"(bytes), "r"(sbar), "l"(pol)
                     : "memory");
+            }
         }
         for (int k = (int)(bytes / 4) + threadIdx.x; k < total; k += kProjBlock) s_sh[k] = __ldg(src + k);
         // bounded wait for phase 0 of the barrier
@@ -265,8 +270,8 @@ k_project(const float* __restrict__ means, const float* __restrict__ scales,
     float4 a, b, c;
     uint2 rect;
     int radius;
-    project_one<DEG>(__ldg(means + 3 * i), __ldg(means + 3 * i + 1), __ldg(means + 3 * i + 2), __ldg(opac + i),
-                     __ldg(quats + i), __ldg(scales + 3 * i), __ldg(scales + 3 * i + 1), __ldg(scales + 3 * i + 2),
+    project_one<DEG>(__ldcs(means + 3 * i), __ldcs(means + 3 * i + 1), __ldcs(means + 3 * i + 2), __ldcs(opac + i),
+                     __ldcs(quats + i), __ldcs(scales + 3 * i), __ldcs(scales + 3 * i + 1), __ldcs(scales + 3 * i + 2),
                      s_sh + threadIdx.x * PER, cam, a, b, c, rect, radius);
     pv.xy_ab[i] = a;
     pv.c_o_z[i] = b;
@@ -298,10 +303,10 @@ k_project_batch(const float* __restrict__ means, const float* __restrict__ scale
     stage_sh<PER>(sh, sh_aligned, base, n, s_sh, err);
     const int64_t i = base + threadIdx.x;
     if (i >= n) return;
-    const float mx = __ldg(means + 3 * i), my = __ldg(means + 3 * i + 1), mz = __ldg(means + 3 * i + 2);
-    const float o = __ldg(opac + i);
-    const float4 q4 = __ldg(quats + i);
-    const float s0 = __ldg(scales + 3 * i), s1 = __ldg(scales + 3 * i + 1), s2 = __ldg(scales + 3 * i + 2);
+    const float mx = __ldcs(means + 3 * i), my = __ldcs(means + 3 * i + 1), mz = __ldcs(means + 3 * i + 2);
+    const float o = __ldcs(opac + i);
+    const float4 q4 = __ldcs(quats + i);
+    const float s0 = __ldcs(scales + 3 * i), s1 = __ldcs(scales + 3 * i + 1), s2 = __ldcs(scales + 3 * i + 2);
     for (int v = 0; v < bc.nviews; ++v) {
         float4 a, b, c;
         uint2 rect;

@@ -301,11 +301,11 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
     for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += wstride) {
         const int64_t k = c * 32 + lane;
         uint32_t w = 0, g = 0, ya = 0, z = 0;
-        if (k < R) {
-            w = rs_w[k];
-            g = rs_g[k];
-            ya = rs_ya[k];
-            z = rs_z[k];
+        if (k < R) {  // read once: streamed past L2
+            w = __ldcs(rs_w + k);
+            g = __ldcs(rs_g + k);
+            ya = __ldcs(rs_ya + k);
+            z = __ldcs(rs_z + k);
         }
         // inclusive prefix of the widths across the warp
         uint32_t incl = w;
