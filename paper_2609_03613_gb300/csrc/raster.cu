@@ -203,11 +203,12 @@ __device__ __forceinline__ void raster_tile(
     }
     if (inside) {
         const int64_t p = (int64_t)py * a.width + px;
-        out_rgb[3 * p] = fmaf(st.T, a.bg0, st.C0);
-        out_rgb[3 * p + 1] = fmaf(st.T, a.bg1, st.C1);
-        out_rgb[3 * p + 2] = fmaf(st.T, a.bg2, st.C2);
-        out_alpha[p] = 1.0f - st.T;
-        out_last[p] = st.last;
+        // the image is not read again on the device: streaming stores
+        __stcs(out_rgb + 3 * p, fmaf(st.T, a.bg0, st.C0));
+        __stcs(out_rgb + 3 * p + 1, fmaf(st.T, a.bg1, st.C1));
+        __stcs(out_rgb + 3 * p + 2, fmaf(st.T, a.bg2, st.C2));
+        __stcs(out_alpha + p, 1.0f - st.T);
+        __stcs(out_last + p, st.last);
         if (out_T) out_T[p] = st.T;
         if (COUNT) out_ntests[p] = st.ntests;
     }

@@ -161,7 +161,9 @@ __device__ __forceinline__ void load_sort_chunk(const uint64_t* words, int32_t c
     constexpr int BS = TILE * TILE;
     constexpr int NWB = BS / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < len; i += BS) ws.sort[i] = words[c0 + i];
+    // the stream is read once: streamed past L2 (evict first)
+    for (int i = threadIdx.x; i < len; i += BS)
+        ws.sort[i] = __ldcs(reinterpret_cast<const unsigned long long*>(words) + c0 + i);
     if (threadIdx.x == 0) ws.nsort = 0;
     __syncthreads();
     for (int j = bfirst + warp; j < e; j += NWB) {
