@@ -20,11 +20,6 @@
 
 namespace gs {
 
-constexpr int kTbThreads = 512;
-constexpr int kTbWarps = kTbThreads / 32;
-constexpr int kTbCap = 12288;          // entries of a tile sorted in shared memory (96 KB)
-constexpr int kTbWarpSortMax = 512;    // longer bins are sorted by the whole CTA
-
 // ------------------------------------------------------------------ counts
 // Per visible Gaussian: its bin (kept in gbin) and its rect added to layer b.
 __global__ void __launch_bounds__(256)
