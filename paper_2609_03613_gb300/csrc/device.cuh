@@ -144,6 +144,39 @@ __device__ __forceinline__ uint64_t warp_bitonic32(uint64_t v)
 }
 
 
+// 33..64 words a[0..n) sorted ascending by one warp in registers: lane l
+// holds positions l and l + 32 (past n: +infinity, above every word, whose
+// depth bits are those of a finite float), one bitonic network over the 64
+// positions; a stride-32 step pairs the two words of one lane.
+__device__ __forceinline__ void warp_bitonic64(uint64_t* a, int n)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t x0 = a[lane];
+    uint64_t x1 = lane + 32 < n ? a[lane + 32] : ~0ull;
+#pragma unroll
+    for (int k = 2; k <= 64; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j == 32) {  // k = 64: ascending
+                const uint64_t lo = x1 < x0 ? x1 : x0, hi = x1 < x0 ? x0 : x1;
+                x0 = lo;
+                x1 = hi;
+                continue;
+            }
+            const bool lower = (lane & j) == 0;
+            // position i = h * 32 + lane sorts ascending when (i & k) == 0
+            const bool up0 = k == 64 || (lane & k) == 0;
+            const bool up1 = k == 64 || (k < 32 && (lane & k) == 0);
+            const uint64_t o0 = __shfl_xor_sync(0xffffffffu, x0, j);
+            const uint64_t o1 = __shfl_xor_sync(0xffffffffu, x1, j);
+            x0 = (lower == up0) ? (o0 < x0 ? o0 : x0) : (o0 > x0 ? o0 : x0);
+            x1 = (lower == up1) ? (o1 < x1 ? o1 : x1) : (o1 > x1 ? o1 : x1);
+        }
+    }
+    a[lane] = x0;
+    if (lane + 32 < n) a[lane + 32] = x1;
+}
+
 // ------------------------------------------------------------------ tile cull
 // True when no pixel centre of the tile can give alpha >= 1/255 (nor a
 // q < 0 skip would change anything).  Minimum of the quadratic

@@ -151,7 +151,7 @@ struct WalkShared {
 };
 
 // Load the chunk [c0, c0 + len) (bins bfirst..e-1) into ws.sort and sort each
-// of its segments by (depth bits, gid): segments of up to 32 entries in
+// of its segments by (depth bits, gid): segments of up to 64 entries in
 // registers by one warp, up to 256 in shared memory by one warp, longer ones by
 // the whole block.  ws.big[base..] collects the long ones.
 template <int TILE, bool LAZY>
@@ -174,6 +174,8 @@ __device__ __forceinline__ void load_sort_chunk(const uint64_t* words, int32_t c
             uint64_t v = lane < l ? seg[lane] : ~0ull;
             v = warp_bitonic32(v);
             if (lane < l) seg[lane] = v;
+        } else if (l <= 64) {
+            warp_bitonic64(seg, l);
         } else if (l <= 256) {
             bitonic_mem(seg, l, lane, 32, SyncWarp{});
         } else if (lane == 0) {
