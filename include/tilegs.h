@@ -139,7 +139,13 @@ int gs_set_config(gs_ctx* ctx, const gs_config* cfg);
 int gs_get_config(const gs_ctx* ctx, gs_config* cfg);
 
 /* Pre-grow scratch for up to n Gaussians, m_cap entries and an image of
- * width x height (synchronous; allocates). */
+ * width x height (synchronous; allocates).  The reserved capacity also picks
+ * the EXACT path's bin scatter (Alg. 3): from 8192 reserved entries per tile
+ * the row records are grouped by (tile row, bin) and the slots taken with
+ * shared-memory atomics (deep frames), which needs 16 more bytes of scratch
+ * per reserved entry; below that, one global atomic per entry.  Both give the
+ * same stream up to the order inside each (tile, bin) segment, which the
+ * repair sorts. */
 int gs_reserve(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t width, int32_t height);
 
 /* Sticky device error word (synchronises `stream` first; host).  Returns the
