@@ -433,6 +433,52 @@ def test_single_gaussian_and_k1():
         np.testing.assert_array_equal(bits(r["rgb"]), bits(rgb_o))
 
 
+
+def equal_depth_runs_scene():
+    """Nine groups of Gaussians, each group at one bit-identical depth (the
+    camera looks down the z axis, so depth depends on z alone), all inside one
+    tile and too faint for any pixel to terminate: with K = 64 every group is
+    one bin of 2, 31, 32, 33, 47, 63, 64, 65 or 130 entries,
+    on both sides of the in-raster sort's size classes (one word a lane up to
+    32, two up to 64, shared memory up to 256), and every order inside a bin
+    is decided by gid alone."""
+    sizes = [2, 31, 32, 33, 47, 63, 64, 65, 130]
+    rng = np.random.default_rng(83)
+    cam = scenes.tiny_camera()
+    means = []
+    for g, s in enumerate(sizes):
+        z = np.float32(0.4 - 0.09 * g)
+        pix = 136.0 + rng.uniform(-1.5, 1.5, (s, 2))  # around the centre of one tile
+        xy = (pix - cam.cx) * (3.0 - float(z)) / cam.fx
+        means.append(np.column_stack([xy, np.full(s, z)]))
+    means = np.concatenate(means).astype(np.float32)
+    n = means.shape[0]
+    means = means[rng.permutation(n)]  # gids not in depth order
+    sc = scenes.Scene(means, np.full((n, 3), 0.015, np.float32), np.tile(np.array([1, 0, 0, 0], np.float32), (n, 1)),
+                      rng.uniform(0.006, 0.012, n).astype(np.float32), rng.uniform(0, 1, (n, 1, 3)).astype(np.float32), 0)
+    return sc, cam, sizes
+
+
+def test_equal_depth_runs_at_sort_size_boundaries():
+    sc, cam, sizes = equal_depth_runs_scene()
+    proj_o, ent, (off, stream), (rgb_o, a_o, l_o) = O.render(sc, cam)
+    cnt = np.diff(off)
+    t = int(np.argmax(cnt))
+    assert cnt[t] == sum(sizes) and np.count_nonzero(cnt) == 1
+    assert len(np.unique(proj_o["depth"].view(np.uint32))) == len(sizes)
+    assert 1.0 - float(a_o.max()) > 1e-4  # no pixel terminates: every bin is composited
+    for K, lazy in ((64, 1), (16, 1), (64, 0)):
+        r = run_stage_pipeline("exact", sc, cam, K=K, repair_in_raster=lazy)
+        if K == 64:  # one bin a group (with K = 16 two groups share a bin)
+            lens = np.diff(r["offsets"][t * K:(t + 1) * K + 1])
+            assert sorted(int(x) for x in lens if x > 0) == sorted(sizes)
+        kept = assert_culled_stream(r["words"], r["offsets"], K, off, stream, eager=not lazy)
+        assert kept == sum(sizes)
+        np.testing.assert_array_equal(bits(r["rgb"]), bits(rgb_o))
+        np.testing.assert_array_equal(bits(r["alpha"]), bits(a_o))
+        np.testing.assert_array_equal(r["last"], l_o)
+
+
 def test_deterministic_repeat(tiny):
     sc, cam = tiny[0], tiny[1]
     a = run_stage_pipeline("exact", sc, cam, repair_in_raster=0, tile_cull=0)
