@@ -44,8 +44,9 @@ L2_FLUSH_BYTES = 256 << 20
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 300; the reference arm, whose steps are CPU frames: 10)")
+    ap.add_argument("--warmup", type=int, default=None, help="warm-up steps (default 10; reference arm: 3)")
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -61,7 +62,12 @@ def parse_args():
                     help="--profile-frame: render the scene in raster-order-aware (Morton) storage")
     ap.add_argument("--workload", default="mid", choices=["mid", "heavy3m", "heavy6m_4k"],
                     help="--profile-frame: the workload rendered")
-    return ap.parse_args()
+    a = ap.parse_args()
+    if a.steps is None:
+        a.steps = 10 if a.impl == "reference" else 300
+    if a.warmup is None:
+        a.warmup = 3 if a.impl == "reference" else 10
+    return a
 
 
 # --------------------------------------------------------------------- dist
@@ -162,73 +168,84 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- oracle timing (cpu_baseline / reference arm)
-def oracle_frame_estimate(scene, cam, n_sample_tiles=48, seed=7):
-    """Time the CPU oracle on a bounded sample of the frame.
+def bench_config(ws: int) -> dict:
+    """The workload both arms report (identical dicts, so the two JSON lines
+    name the same configuration)."""
+    return {"workload": WORKLOAD_DESC, "gaussians": 1000000, "resolution": "1920x1080", "tile": 16,
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "l2": "GPU steps: flushed between timed steps (256 MiB write outside the timed events)"}
 
-    The per-frame setup (projection of every Gaussian, emission, the per-tile
-    sorted lists) is timed once in full; the compositing is timed on a seeded
-    sample of tiles with all host cores (OpenMP over tiles).  The frame
-    estimate is setup + composite_time * (tiles / sampled tiles)."""
-    import numpy as np
 
+def oracle_frame(scene, cam, threads: int) -> dict:
+    """One whole frame of the CPU oracle, measured, nothing extrapolated:
+    projection, emission and the per-tile (depth, gid) sort (single-threaded
+    code in the oracle), then the compositing of every tile on `threads`
+    OpenMP threads.  Wall-clock seconds of each part."""
     import oracle as O
-    ncores = len(os.sched_getaffinity(0))
-    O.set_threads(ncores)
+    O.set_threads(threads)
     t0 = time.perf_counter()
     proj = O.project(scene, cam)
     ent = O.emit(proj, cam.width, cam.height)
     tx, ty = O.tiles_xy(cam.width, cam.height)
     off, stream = O.sort_tiles(ent, tx * ty)
-    t_setup = time.perf_counter() - t0
-    rng = np.random.default_rng(seed)
-    tiles = rng.choice(tx * ty, size=min(n_sample_tiles, tx * ty), replace=False).astype(np.int32)
     t1 = time.perf_counter()
-    O.composite(proj, off, stream, cam.width, cam.height, tiles=tiles)
-    t_comp = time.perf_counter() - t1
-    frame_s = t_setup + t_comp * (tx * ty) / len(tiles)
-    return dict(frame_s=frame_s, t_setup=t_setup, t_comp=t_comp, n_tiles=int(len(tiles)),
-                total_tiles=int(tx * ty), cores=ncores, entries=int(ent[0].shape[0]))
+    O.composite(proj, off, stream, cam.width, cam.height)
+    t2 = time.perf_counter()
+    return dict(frame_s=t2 - t0, setup_s=t1 - t0, composite_s=t2 - t1, threads=threads,
+                entries=int(ent[0].shape[0]))
+
+
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
 
 
 def cpu_baseline_block(scene, cam):
-    est = oracle_frame_estimate(scene, cam)
+    """The oracle on the full 1080p frame, once on all host cores and once on
+    one thread (the compositing is the part the oracle runs in parallel)."""
     P = cam.width * cam.height
-    return {"value": round(P / est["frame_s"] / 1e6, 6), "unit": "Mpix/s", "cores": est["cores"],
-            "kind": "oracle",
-            "sample": (f"full projection+emission+per-tile sort of the frame ({est['t_setup']:.2f} s, 1 thread) "
-                       f"+ compositing of {est['n_tiles']} seeded tiles of {est['total_tiles']} "
-                       f"({est['t_comp']:.2f} s, {est['cores']} threads), extrapolated to the frame"),
-            "frame_s_est": round(est["frame_s"], 3)}
+    ncores = host_cores()
+    allc = oracle_frame(scene, cam, ncores)
+    one = oracle_frame(scene, cam, 1)
+    return {"value": round(P / allc["frame_s"] / 1e6, 6), "unit": "Mpix/s", "cores": ncores, "kind": "oracle",
+            "sample": (f"one full frame ({allc['entries']} entries, all {cam.width}x{cam.height} pixels), "
+                       f"measured, not extrapolated: projection + emission + per-tile sort single-threaded "
+                       f"(the oracle's code), compositing on {ncores} threads; the same frame is also timed "
+                       f"on 1 thread"),
+            "frame_s_allcores": round(allc["frame_s"], 3),
+            "frame_s_1thread": round(one["frame_s"], 3),
+            "setup_s": round(allc["setup_s"], 3),
+            "composite_s_allcores": round(allc["composite_s"], 3),
+            "composite_s_1thread": round(one["composite_s"], 3),
+            "value_1thread": round(P / one["frame_s"] / 1e6, 6)}
 
 
 def run_reference(args):
-    """The oracle as the reference arm (rank 0 only)."""
+    """The oracle as the reference arm (rank 0 only): every step, warm-up
+    included, is one whole frame of the oracle on all host cores, and its
+    wall-clock time is the step time."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     from paper_2609_03613_gb300 import scenes
     scene, cam = scenes.workload(WORKLOAD)
     P = cam.width * cam.height
+    ncores = host_cores()
     times = []
-    blocks = []
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        est = oracle_frame_estimate(scene, cam, n_sample_tiles=16, seed=100 + i)
-        dt = time.perf_counter() - t0
+        f = oracle_frame(scene, cam, ncores)
         if i >= args.warmup:
-            times.append(est["frame_s"])
-            blocks.append((dt, est))
+            times.append(f["frame_s"])
     frame_s = sum(times) / len(times)
     value = P / frame_s / 1e6
-    est = blocks[-1][1]
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "Mpix/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(frame_s * 1e3, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-           "data": "synthetic",
-           "config": {"workload": WORKLOAD_DESC, "path": "CPU oracle (plain C, float32 spec order)"},
-           "cpu_baseline": {"value": round(value, 6), "unit": "Mpix/s", "cores": est["cores"], "kind": "oracle",
-                            "sample": ("each step: full projection+emission+per-tile sort, compositing of 16 "
-                                       "seeded tiles on all cores, extrapolated to the frame")},
+           "data": "synthetic", "config": bench_config(ws),
+           "path": "CPU oracle (plain C, float32 in the definition's operation order)",
+           "step_s": [round(t, 3) for t in times],
+           "cpu_baseline": {"value": round(value, 6), "unit": "Mpix/s", "cores": ncores, "kind": "oracle",
+                            "sample": ("each step one whole frame, measured: projection + emission + per-tile "
+                                       f"sort single-threaded, compositing of every tile on {ncores} threads")},
            "e2e": {"value": round(value, 6), "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -279,8 +296,8 @@ def run_ours(args):
 
     side = torch.cuda.Stream(device=dev)  # graphs cannot be captured on the legacy stream
 
-    def make(mode, sc_dev=ds):
-        ctx = G.Context(mode)
+    def make(mode, sc_dev=ds, **kw):
+        ctx = G.Context(mode, **kw)
         out = (torch.empty((H, W, 3), device=dev), torch.empty((H, W), device=dev),
                torch.empty((H, W), dtype=torch.int32, device=dev))
         with torch.cuda.stream(side):
@@ -401,20 +418,34 @@ def run_ours(args):
         print(f"op count failed: {e}", file=sys.stderr)
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_ops = n_sm * 128 * sm_mhz * 1e6  # fp32 lanes x clock: instructions / s
-    achieved = ops / (raster_b * 1e-3) if ops else None
+    # FP32 roofline of the dominant kernel as the measurement plan defines it:
+    # 20 FP32 flops per Gaussian test (the exp counted as its FP32 work),
+    # against SMs x 128 FMA lanes x 2 flops x the sampled SM clock
+    flops_per_test = 20
+    peak_flops = n_sm * 128 * 2 * sm_mhz * 1e6
+    flops = flops_per_test * tests if tests else None
+    achieved = flops / (raster_b * 1e-3) if flops else None
     traffic, prof = load_traffic()
     roofline = {"kernel": "k_raster<16,binned>", "bound": "alu",
                 "achieved": round(achieved / 1e12, 4) if achieved else None,
-                "peak": round(peak_ops / 1e12, 4), "unit": "Tinst/s",
-                "frac": round(achieved / peak_ops, 4) if achieved else None,
+                "peak": round(peak_flops / 1e12, 4), "unit": "TFLOP/s",
+                "frac": round(achieved / peak_flops, 4) if achieved else None,
                 "traffic": traffic,
-                "peak_source": (f"{n_sm} SMs x 128 fp32 lanes x {sm_mhz:.0f} MHz (median SM clock sampled "
-                                "during the timed region)"),
-                "ops_per_launch": ops, "tests_per_launch": tests}
-    # the same kernel against its instruction-issue ceiling: warp instructions
-    # per launch from the ncu capture (only while the source is unchanged)
-    # over the live raster time, against 4 schedulers x 1 issue a clock per SM
+                "peak_source": (f"{n_sm} SMs x 128 FP32 FMA lanes x 2 flops x {sm_mhz:.0f} MHz (median SM clock "
+                                "sampled during the timed region)"),
+                "flops_per_test": flops_per_test, "tests_per_launch": tests,
+                "achieved_source": "20 flops x Gaussian tests counted by the raster's instrumented twin, over the "
+                                   "raster's CUDA-event time in un-captured frames"}
+    # the same kernel against the FP32 lanes' instruction rate, with the
+    # compositing definition's own operation count (8 per visit, +17 with
+    # exp, +3 when alpha passes, +4 when applied), and against the warp
+    # schedulers' issue rate (warp instructions per launch from the ncu
+    # capture, only while the source is unchanged)
+    if ops:
+        lane_peak = n_sm * 128 * sm_mhz * 1e6
+        roofline["lane_issue"] = {"achieved": round(ops / (raster_b * 1e-3) / 1e12, 4),
+                                  "peak": round(lane_peak / 1e12, 4), "unit": "T FP32 inst/s",
+                                  "frac": round(ops / (raster_b * 1e-3) / lane_peak, 4), "ops_per_launch": ops}
     winst = prof.get("warp_inst_per_launch") if (prof and traffic is not None) else None
     if winst:
         issue_peak = n_sm * 4 * sm_mhz * 1e6
@@ -422,6 +453,35 @@ def run_ours(args):
         roofline["issue"] = {"achieved": round(issue / 1e9, 2), "peak": round(issue_peak / 1e9, 2),
                              "unit": "G warp-inst/s", "frac": round(issue / issue_peak, 4),
                              "warp_inst_per_launch": winst}
+
+    # what each part of the binned frame buys, stage by stage, on this frame:
+    # the same images from (1) the plain global-sort frame, (2) the global
+    # stream rastered by the binned kernel (tile cull at staging, colour
+    # staging, per-warp masks, early-out), (3) only the culled entries, one
+    # bin per tile, sorted before the raster (their global order), (4) one
+    # bin per tile with the repair in the raster, and (5) the EXACT frame
+    ablation = {"global_plain": {"frame_ms": round(frame_g, 4), "raster_ms": round(raster_g, 4),
+                                 "stages_ms": {k: round(mean(v), 4) for k, v in st_g.items() if mean(v) > 0},
+                                 "entries_sorted": m_g}}
+    for label, mode, kw in (("global_binned_raster", "global", {"tile_cull": 1}),
+                            ("culled_global_order", "exact", {"K": 1, "repair_in_raster": 0}),
+                            ("culled_one_bin_lazy", "exact", {"K": 1})):
+        ctx_a, out_a, m_a = make(mode, **kw)
+        ms_a, _, _, _ = timed(ctx_a, out_a, args.steps, args.warmup)
+        _, st_a, _, _ = timed(ctx_a, out_a, max(20, args.steps // 4), 3, flags=G.RENDER_NO_SYNC)
+        with torch.cuda.stream(side):
+            ctx_a.render(ds, cam, bg, out_a)
+        torch.cuda.synchronize()
+        ablation[label] = {"frame_ms": round(mean(ms_a), 4), "raster_ms": round(mean(st_a["raster"]), 4),
+                           "stages_ms": {k: round(mean(v), 4) for k, v in st_a.items() if mean(v) > 0},
+                           "entries": m_a,
+                           "image_equal_exact": bool(torch.equal(out_a[0], out_b[0])
+                                                     and torch.equal(out_a[2], out_b[2]))}
+        ctx_a.close()
+        del out_a
+    ablation["binned_exact"] = {"frame_ms": round(frame_b, 4), "raster_ms": round(raster_b, 4),
+                                "stages_ms": {k: round(mean(v), 4) for k, v in st_b.items() if mean(v) > 0},
+                                "entries": m_b}
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -570,11 +630,9 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 4), "unit": "Mpix/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(frame_b, 4), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_DESC,
-                   "path": "binned EXACT, K=64, 16x16 tiles, frame replayed as one CUDA graph",
-                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                   "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "entries_per_frame": m_b},
+        "config": bench_config(ws),
+        "path": "binned EXACT, K=64, 16x16 tiles, frame replayed as one CUDA graph",
+        "entries_per_frame": m_b,
         "raster_ms": round(raster_b, 4),
         "raster_ms_source": "CUDA events around the raster kernel on the library stream, un-captured frames",
         "raster_mpix_s": round(P / (raster_b * 1e-3) / 1e6, 3),
@@ -591,6 +649,7 @@ def run_ours(args):
         "frame_ms_min": round(min(ms_b), 4), "frame_ms_median": round(statistics.median(ms_b), 4),
         "frame_ms_without_graph": {"binned": round(mean(ms_b_ng), 4), "global_sort": round(mean(ms_g_ng), 4)},
         "wall_s_timed": round(wall_b, 3),
+        "ablation": ablation,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "train_step": train,
         "planner": planner, "spatial_order": spatial, "batch16": batch, "heavy": heavy,
         "gpu_launches": int(launches),

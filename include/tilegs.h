@@ -100,7 +100,12 @@ typedef struct gs_config {
     float eps;             /* numerical floor (1e-4) */
     float repair_budget_frac; /* B_rep = floor(frac * M) (0.25) */
     int32_t near_shift;    /* 1: bin on z - min(alpha s_max, gamma z) (PAPER default) */
-    int32_t tile_cull;     /* 1: conservative tile-level alpha cull in the binned raster */
+    int32_t tile_cull;     /* 1: conservative tile-level alpha cull in the binned raster
+                              (default).  GLOBAL mode defaults to 0, the plain
+                              baseline raster; GLOBAL with 1 rasters the global
+                              stream with the binned kernel (tile cull at staging,
+                              colour staging, per-warp masks, early-out): the
+                              raster's additions without binning.  Same image. */
     int32_t persistent;    /* 1: binned raster runs persistent CTAs over tiles in
                               descending span order */
     int32_t repair_in_raster; /* EXACT only, 1 (default): gs_sort_or_bin sorts only
@@ -119,6 +124,15 @@ typedef struct gs_config {
                               tile's depth-bin statistics, weights set with
                               gs_planner_set_weights); 0: chunk_cap everywhere.
                               Changes speed only, never the image. */
+    int32_t wait_polls;    /* the most polls of a bounded device-side wait (the
+                              projection's TMA copy of SH coefficients) before it
+                              raises GS_ERR_TIMEOUT; gs_config_default sets
+                              4194304.  0 makes every such wait give up at once
+                              (a test of the error path): the error is raised, the
+                              copy is still drained by a second bounded wait, and
+                              the frame is written.  A block whose copy never
+                              lands writes nothing: after GS_ERR_TIMEOUT the
+                              frame's outputs are not valid. */
 } gs_config;
 
 /* Fill *cfg with the paper's defaults (supplement, default No-GW configuration
@@ -268,10 +282,12 @@ int gs_repair(gs_ctx* ctx, const gs_camera* cam, const int64_t* m_dev, uint64_t*
  * limit: K <= GS_MAX_K (128) split depths and sample_count <= 8192; larger
  * values return GS_ERR_INVALID_ARG before anything is enqueued.
  * The first call on each device resolves the scratch address with
- * cudaGetSymbolAddress; make that first call before any stream capture.
- * Calls cudaMalloc, cudaFree and no allocating routine.  All calls share the
- * scratch, which keeps the last call's contents (each call rewrites every
- * field it reads), so calls that overlap on the GPU race.
+ * cudaGetSymbolAddress (and so does the first call after the device's context
+ * changed, e.g. after cudaDeviceReset); make that first call before any stream
+ * capture.  Calls neither cudaMalloc nor cudaFree nor any other allocating
+ * routine.  All calls share the scratch, which keeps the last call's contents
+ * (each call rewrites every field it reads), so calls that overlap on the GPU
+ * race.
  */
 int gs_depth_range_noalloc(const gs_config* cfg, const void* projected, const float* scales, int64_t n,
                            const gs_camera* cam, const void* isect, int64_t m_cap, const int64_t* m_dev,

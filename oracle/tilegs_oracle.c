@@ -155,6 +155,10 @@ void orc_sh_basis(float x, float y, float z, float* Y)
  *   radius = ceil(3 sqrt(lambda_max)); rect = tiles touched by the
  *   (mean +- radius) square, clamped to the grid; cull if empty;
  *   rgb = max(sum_k Y_k(dir) sh_k + 0.5, 0) with dir = normalize(m - campos).
+ * Non-finite inputs (a reading: the paper assumes trained, finite
+ * parameters and says nothing of others): a Gaussian with a non-finite
+ * mean, scale, quaternion component or opacity is culled, and so is one whose
+ * SH sum is not finite in some channel.
  */
 void orc_project(int64_t n, const float* means, const float* scales, const float* quats,
                  const float* opac, const float* sh, int sh_degree, const float* W,
@@ -186,6 +190,10 @@ void orc_project(int64_t n, const float* means, const float* scales, const float
         visible[i] = 0;
 
         const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+        int finite = isfinite(mx) && isfinite(my) && isfinite(mz) && isfinite(opac[i]);
+        for (int k = 0; k < 4; ++k) finite = finite && isfinite(quats[4 * i + k]);
+        for (int k = 0; k < 3; ++k) finite = finite && isfinite(scales[3 * i + k]);
+        if (!finite) continue;
         const float xc = W[0] * mx + W[1] * my + W[2] * mz + W[3];
         const float yc = W[4] * mx + W[5] * my + W[6] * mz + W[7];
         const float zc = W[8] * mx + W[9] * my + W[10] * mz + W[11];
@@ -265,11 +273,16 @@ void orc_project(int64_t n, const float* means, const float* scales, const float
         if (len > 0.0f) { dx = dx / len; dy = dy / len; dz = dz / len; }
         float Y[16];
         orc_sh_basis(dx, dy, dz, Y);
+        float col[3];
+        int colour_finite = 1;
         for (int ch = 0; ch < 3; ++ch) {
             float acc = Y[0] * sh[(i * ncoef + 0) * 3 + ch];
             for (int k = 1; k < ncoef; ++k) acc = acc + Y[k] * sh[(i * ncoef + k) * 3 + ch];
-            rgb[3 * i + ch] = fmaxf(acc + 0.5f, 0.0f);
+            colour_finite = colour_finite && isfinite(acc);
+            col[ch] = fmaxf(acc + 0.5f, 0.0f);
         }
+        if (!colour_finite) continue;
+        for (int ch = 0; ch < 3; ++ch) rgb[3 * i + ch] = col[ch];
 
         mean2d[2 * i] = px;
         mean2d[2 * i + 1] = py;

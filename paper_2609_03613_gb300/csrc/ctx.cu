@@ -43,11 +43,14 @@ extern "C" void gs_config_default(gs_config* cfg, int32_t mode)
     cfg->eps = 1e-4f;
     cfg->repair_budget_frac = 0.25f;
     cfg->near_shift = (mode == GS_MODE_BINNED_PAPER || mode == GS_MODE_BINNED_NOREPAIR) ? 1 : 0;
-    cfg->tile_cull = 1;
+    // GLOBAL: the plain baseline raster; 1 there rasters the global stream
+    // with the binned kernel's culls (an ablation of the raster's additions)
+    cfg->tile_cull = (mode == GS_MODE_GLOBAL_SORT) ? 0 : 1;
     cfg->persistent = 1;
     cfg->repair_in_raster = (mode == GS_MODE_BINNED_EXACT) ? 1 : 0;
     cfg->chunk_cap = 256;
     cfg->planner = 0;
+    cfg->wait_polls = 1 << 22;
 }
 
 namespace gs {
@@ -66,6 +69,7 @@ int check_config(const gs_config* c)
     if (c->mode == GS_MODE_BINNED_EXACT && c->near_shift) return GS_ERR_INVALID_ARG;
     if (c->chunk_cap != 0 && (c->chunk_cap < 32 || c->chunk_cap > 2048)) return GS_ERR_INVALID_ARG;
     if (c->planner != 0 && c->planner != 1) return GS_ERR_INVALID_ARG;
+    if (c->wait_polls < 0) return GS_ERR_INVALID_ARG;
     return GS_OK;
 }
 
@@ -408,7 +412,7 @@ extern "C" int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, c
     if (n > 0 && (!projected || !stream_words)) return GS_ERR_INVALID_ARG;
     if (offsets_stride < 1 || offsets_stride > GS_MAX_K) return GS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const bool baseline = (ctx->cfg.mode == GS_MODE_GLOBAL_SORT);
+    const bool baseline = baseline_raster(ctx->cfg);
     stage_begin(ctx, GS_STAGE_RASTER, st);
     int r = raster_fwd(ctx, proj_view(const_cast<void*>(projected), n), cam, stream_words, offsets,
                        offsets_stride, bg, rgb, alpha, last, ntests, baseline, st, final_T, tile_end);
@@ -426,7 +430,7 @@ extern "C" int gs_rasterize_fwd_plan(gs_ctx* ctx, const void* projected, int64_t
     if (n > 0 && (!projected || !stream_words)) return GS_ERR_INVALID_ARG;
     if (offsets_stride < 1 || offsets_stride > GS_MAX_K) return GS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const bool baseline = (ctx->cfg.mode == GS_MODE_GLOBAL_SORT);
+    const bool baseline = baseline_raster(ctx->cfg);
     stage_begin(ctx, GS_STAGE_RASTER, st);
     int r = raster_fwd(ctx, proj_view(const_cast<void*>(projected), n), cam, stream_words, offsets, offsets_stride,
                        bg, rgb, alpha, last, nullptr, baseline, st, nullptr, nullptr, plan, tile_cycles);
@@ -601,7 +605,7 @@ int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs
         plan = c->d_plan;
     }
     r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,
-                   c->cfg.mode == GS_MODE_GLOBAL_SORT, st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr,
+                   baseline_raster(c->cfg), st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr,
                    plan, nullptr);
     stage_end(c, GS_STAGE_RASTER, st);
     if (r != GS_OK) return r;

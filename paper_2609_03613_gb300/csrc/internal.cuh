@@ -321,6 +321,10 @@ constexpr int kPlanClasses = 6;
 __host__ __device__ inline int plan_cap(int cls) { return 64 << (cls < 0 ? 0 : cls > 5 ? 5 : cls); }
 // the configured chunk size of the lazy EXACT raster
 inline int chunk_cap(const gs_config& cfg) { return cfg.chunk_cap > 0 ? cfg.chunk_cap : 256; }
+// The plain baseline raster kernel serves GLOBAL mode without the tile cull;
+// every other configuration (GLOBAL with the cull included) uses the binned
+// kernel, which culls at staging when the stream was not culled when built.
+inline bool baseline_raster(const gs_config& cfg) { return cfg.mode == GS_MODE_GLOBAL_SORT && !cfg.tile_cull; }
 // depth range with samples mapped to gids through the per-Gaussian offsets
 int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64_t n, int64_t m_cap,
                      const int64_t* m_dev, const gs_camera* cam, cudaStream_t st);

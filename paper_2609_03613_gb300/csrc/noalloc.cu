@@ -8,6 +8,8 @@
 // this entry point needs no context and no allocation: its scratch (one
 // bin-parameter record) is a file-scope static __device__ array that every GPU
 // loading the library holds until exit.
+#include <cuda.h>  // driver API types only; the functions come from cudaGetDriverEntryPointByVersion
+
 #include <mutex>
 
 #include "internal.cuh"
@@ -19,11 +21,47 @@ static __device__ __align__(256) gs::BinParams g_depth_range_scratch;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+struct ScratchAddr {
+    unsigned long long ctx_id;  // the context the address was resolved in
+    void* addr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique id of the calling thread's current context (0 when there is none
+// yet or the driver cannot say).  Ids are never reused within a process, so
+// a context re-created after a device reset gets a new one.  Called with
+// g_scratch_mu held.
+unsigned long long current_context_id()
+{
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_get_id = reinterpret_cast<CtxGetIdFn>(f);
+        if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (g_ctx_get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 // Device address of the scratch on the current device.  The array's name in
-// host code is only a host-side stand-in, so the address is resolved once per
-// device, with that device current.
+// host code is only a host-side stand-in, so the address is resolved with
+// that device current: once per device, and again whenever the device's
+// current context is a different one (after a device reset the module is
+// loaded anew and the old address is stale).
 int scratch_for_current_device(void** out)
 {
     int dev = 0;
@@ -31,13 +69,16 @@ int scratch_for_current_device(void** out)
     if (e != cudaSuccess) return gs_cuda_fail(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return GS_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long id = current_context_id();
+    ScratchAddr& s = g_scratch[dev];
+    if (!s.addr || id == 0 || s.ctx_id != id) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_depth_range_scratch);
+        e = cudaGetSymbolAddress(&p, g_depth_range_scratch);  // makes the primary context current if needed
         if (e != cudaSuccess || !p) return gs_cuda_fail(e, "cudaGetSymbolAddress");
-        g_scratch_addr[dev] = p;
+        s.addr = p;
+        s.ctx_id = current_context_id();
     }
-    *out = g_scratch_addr[dev];
+    *out = s.addr;
     return GS_OK;
 }
 

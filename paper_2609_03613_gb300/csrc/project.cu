@@ -10,6 +10,10 @@
 //   mean = (fx x/z + cx, fy y/z + cy); radius = ceil(3 sqrt(lambda_max));
 //   rect = tiles met by the (mean +- radius) square, clamped; cull if empty;
 //   rgb = max(sum_k Y_k(dir) sh_k + 0.5, 0), dir = normalize(m - campos).
+// Non-finite inputs (the paper assumes trained, finite parameters): a
+// Gaussian with a non-finite mean, scale, quaternion component or opacity,
+// or whose SH sum is not finite in some channel, is culled, and the kernel
+// raises GS_ERR_NUMERIC in the context's error word.
 // One thread per Gaussian; the block's SH coefficients (contiguous in memory)
 // are staged through shared memory with coalesced float4 loads.  The batched
 // kernel projects each Gaussian for every view of a batch from one read of its
@@ -65,10 +69,24 @@ constexpr int kProjBlock = 64;  // 64 measured 3 % faster than 128 and 192
 // memory.  With a 16-byte aligned array the TMA engine copies the block in one
 // bulk transfer (cp.async.bulk completing on an mbarrier; the multiple-of-16
 // prefix, any 4-byte tail by plain loads); the wait is bounded and reports
-// GS_ERR_TIMEOUT through err.  Otherwise coalesced plain loads.
+// GS_ERR_TIMEOUT through err.  Otherwise coalesced plain loads.  Returns 0
+// (block-uniform) when the copy never completed: the block must then leave
+// without using s_sh.
+constexpr int kDrainPolls = 1 << 22;
+
+__device__ __forceinline__ uint32_t mbar_try_wait(uint32_t sbar)
+{
+    uint32_t done;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(sbar)
+                 : "memory");
+    return done;
+}
+
 template <int PER>
-__device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_aligned, int64_t base, int64_t n,
-                                         float* s_sh, int* err)
+__device__ __forceinline__ int stage_sh(const float* __restrict__ sh, int sh_aligned, int64_t base, int64_t n,
+                                        float* s_sh, int polls, int* err)
 {
     __shared__ __align__(8) uint64_t bar;
     const int cnt = (int)((n - base) < kProjBlock ? (n - base) : kProjBlock);
@@ -98,28 +116,49 @@ __device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_al
             }
         }
         for (int k = (int)(bytes / 4) + threadIdx.x; k < total; k += kProjBlock) s_sh[k] = __ldg(src + k);
-        // bounded wait for phase 0 of the barrier
+        // bounded wait for phase 0 of the barrier: `polls` tries, then
+        // GS_ERR_TIMEOUT and a second bounded wait (the drain) so that the
+        // copy is not left writing into shared memory the block gives up
         uint32_t done = 0;
-        for (int it = 0; it < (1 << 22) && !done; ++it)
-            asm volatile(
-                "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n selp.u32 %0, 1, 0, p;\n}"
-                : "=r"(done)
-                : "r"(sbar)
-                : "memory");
-        if (!done) raise_error(err, GS_ERR_TIMEOUT);
-        __syncthreads();
-        if (threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(sbar) : "memory");
-        return;
+        for (int it = 0; it < polls && !done; ++it) done = mbar_try_wait(sbar);
+        if (!done) {
+            raise_error(err, GS_ERR_TIMEOUT);
+            for (int it = 0; it < kDrainPolls && !done; ++it) done = mbar_try_wait(sbar);
+        }
+        // every thread waited on the same barrier: the block agrees on done;
+        // a barrier whose copy never landed is not invalidated and the block
+        // writes nothing (the frame is invalid after a timeout in any case)
+        const int ok = __syncthreads_and((int)done);
+        if (ok && threadIdx.x == 0) asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(sbar) : "memory");
+        return ok;
     }
     for (int k = threadIdx.x; k < total; k += kProjBlock) s_sh[k] = __ldg(src + k);
     __syncthreads();
+    return 1;
+}
+
+// Bit 31 of the result is set when x is not finite (exponent field all ones).
+__device__ __forceinline__ uint32_t nonfinite_bit(float x)
+{
+    return (__float_as_uint(x) & 0x7f800000u) + 0x00800000u;
+}
+
+// Whether any of a Gaussian's geometric parameters is not finite.
+__device__ __forceinline__ bool geometry_nonfinite(float mx, float my, float mz, float o, float4 q4, float s0,
+                                                   float s1, float s2)
+{
+    const uint32_t f = nonfinite_bit(mx) | nonfinite_bit(my) | nonfinite_bit(mz) | nonfinite_bit(o) |
+                       nonfinite_bit(q4.x) | nonfinite_bit(q4.y) | nonfinite_bit(q4.z) | nonfinite_bit(q4.w) |
+                       nonfinite_bit(s0) | nonfinite_bit(s1) | nonfinite_bit(s2);
+    return (f >> 31) != 0u;
 }
 
 // One Gaussian seen by one camera: the record fields, all zero when culled.
 // (mx, my, mz), o, q4 and (s0, s1, s2) are the Gaussian's parameters, cs its
-// SH coefficients (NC x 3, coefficient-major).
+// SH coefficients (NC x 3, coefficient-major).  Returns true when the SH sum
+// of a Gaussian that reached the colour step was not finite (it is culled).
 template <int DEG>
-__device__ __forceinline__ void project_one(float mx, float my, float mz, float o, float4 q4, float s0, float s1,
+__device__ __forceinline__ bool project_one(float mx, float my, float mz, float o, float4 q4, float s0, float s1,
                                             float s2, const float* cs, const CamArgs& cam, float4& o_xy_ab,
                                             float4& o_c_o_z, float4& o_rgb, uint2& o_rect, int& o_radius)
 {
@@ -130,11 +169,13 @@ __device__ __forceinline__ void project_one(float mx, float my, float mz, float 
     o_rgb = make_float4(0.f, 0.f, 0.f, 0.f);
     o_rect = make_uint2(0u, 0u);
     o_radius = 0;
+    bool bad_colour = false;
     const float xc = W[0] * mx + W[1] * my + W[2] * mz + W[3];
     const float yc = W[4] * mx + W[5] * my + W[6] * mz + W[7];
     const float zc = W[8] * mx + W[9] * my + W[10] * mz + W[11];
     const float qn = sqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
-    bool vis = (zc > cam.near_plane && zc < cam.far_plane) && (o >= 1.0f / 255.0f) && (qn > 0.0f);
+    bool vis = (zc > cam.near_plane && zc < cam.far_plane) && (o >= 1.0f / 255.0f) && (qn > 0.0f) &&
+               !geometry_nonfinite(mx, my, mz, o, q4, s0, s1, s2);
     if (vis) {
         const float w = q4.x / qn, x = q4.y / qn, y = q4.z / qn, z = q4.w / qn;
         float Rq[3][3];
@@ -227,13 +268,16 @@ __device__ __forceinline__ void project_one(float mx, float my, float mz, float 
                 float Y[16];
                 sh_basis(dx, dy, dz, Y);
                 float col[3];
+                uint32_t nf = 0u;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
                     float acc = Y[0] * cs[ch];
 #pragma unroll
                     for (int k = 1; k < NC; ++k) acc = acc + Y[k] * cs[k * 3 + ch];
+                    nf |= nonfinite_bit(acc);
                     col[ch] = fmaxf(acc + 0.5f, 0.0f);
                 }
+                bad_colour = (nf >> 31) != 0u;
                 // conservative tile-cull data (not part of the image math):
                 // tau = ln(255 o) + slack; margin shrinks with the conditioning
                 // of Sigma' to cover float32 cancellation in q.
@@ -244,35 +288,43 @@ __device__ __forceinline__ void project_one(float mx, float my, float mz, float 
                 margin = margin < 0.5f ? 0.0f : margin;
                 const float tau = logf(255.0f * o) + 2e-4f;
 
-                o_xy_ab = make_float4(px, py, ca, cb);
-                o_c_o_z = make_float4(cc, o, zc, tau);
-                o_rgb = make_float4(col[0], col[1], col[2], margin);
-                o_rect = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
-                o_radius = (int)r;
+                if (!bad_colour) {
+                    o_xy_ab = make_float4(px, py, ca, cb);
+                    o_c_o_z = make_float4(cc, o, zc, tau);
+                    o_rgb = make_float4(col[0], col[1], col[2], margin);
+                    o_rect = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16),
+                                        (uint32_t)tx1 | ((uint32_t)ty1 << 16));
+                    o_radius = (int)r;
+                }
             }
         }
     }
+    return bad_colour;
 }
 
 template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
 k_project(const float* __restrict__ means, const float* __restrict__ scales,
           const float4* __restrict__ quats, const float* __restrict__ opac,
-          const float* __restrict__ sh, int sh_aligned, int64_t n, CamArgs cam, ProjView pv, int* err)
+          const float* __restrict__ sh, int sh_aligned, int64_t n, CamArgs cam, ProjView pv, int polls, int* err)
 {
     constexpr int NC = (DEG + 1) * (DEG + 1);
     constexpr int PER = NC * 3;  // floats of SH per Gaussian
     __shared__ __align__(16) float s_sh[kProjBlock * PER];
     const int64_t base = (int64_t)blockIdx.x * kProjBlock;
-    stage_sh<PER>(sh, sh_aligned, base, n, s_sh, err);
+    if (!stage_sh<PER>(sh, sh_aligned, base, n, s_sh, polls, err)) return;
     const int64_t i = base + threadIdx.x;
     if (i >= n) return;
     float4 a, b, c;
     uint2 rect;
     int radius;
-    project_one<DEG>(__ldcs(means + 3 * i), __ldcs(means + 3 * i + 1), __ldcs(means + 3 * i + 2), __ldcs(opac + i),
-                     __ldcs(quats + i), __ldcs(scales + 3 * i), __ldcs(scales + 3 * i + 1), __ldcs(scales + 3 * i + 2),
-                     s_sh + threadIdx.x * PER, cam, a, b, c, rect, radius);
+    const float mx = __ldcs(means + 3 * i), my = __ldcs(means + 3 * i + 1), mz = __ldcs(means + 3 * i + 2);
+    const float o = __ldcs(opac + i);
+    const float4 q4 = __ldcs(quats + i);
+    const float s0 = __ldcs(scales + 3 * i), s1 = __ldcs(scales + 3 * i + 1), s2 = __ldcs(scales + 3 * i + 2);
+    const bool bad = project_one<DEG>(mx, my, mz, o, q4, s0, s1, s2, s_sh + threadIdx.x * PER, cam, a, b, c, rect,
+                                      radius);
+    if (bad || geometry_nonfinite(mx, my, mz, o, q4, s0, s1, s2)) raise_error(err, GS_ERR_NUMERIC);
     pv.xy_ab[i] = a;
     pv.c_o_z[i] = b;
     pv.rgb[i] = c;
@@ -294,24 +346,26 @@ __global__ void __launch_bounds__(kProjBlock)
 k_project_batch(const float* __restrict__ means, const float* __restrict__ scales,
                 const float4* __restrict__ quats, const float* __restrict__ opac,
                 const float* __restrict__ sh, int sh_aligned, int64_t n, const __grid_constant__ BatchCams bc,
-                int* err)
+                int polls, int* err)
 {
     constexpr int NC = (DEG + 1) * (DEG + 1);
     constexpr int PER = NC * 3;
     __shared__ __align__(16) float s_sh[kProjBlock * PER];
     const int64_t base = (int64_t)blockIdx.x * kProjBlock;
-    stage_sh<PER>(sh, sh_aligned, base, n, s_sh, err);
+    if (!stage_sh<PER>(sh, sh_aligned, base, n, s_sh, polls, err)) return;
     const int64_t i = base + threadIdx.x;
     if (i >= n) return;
     const float mx = __ldcs(means + 3 * i), my = __ldcs(means + 3 * i + 1), mz = __ldcs(means + 3 * i + 2);
     const float o = __ldcs(opac + i);
     const float4 q4 = __ldcs(quats + i);
     const float s0 = __ldcs(scales + 3 * i), s1 = __ldcs(scales + 3 * i + 1), s2 = __ldcs(scales + 3 * i + 2);
+    bool bad = geometry_nonfinite(mx, my, mz, o, q4, s0, s1, s2);
     for (int v = 0; v < bc.nviews; ++v) {
         float4 a, b, c;
         uint2 rect;
         int radius;
-        project_one<DEG>(mx, my, mz, o, q4, s0, s1, s2, s_sh + threadIdx.x * PER, bc.cam[v], a, b, c, rect, radius);
+        bad |= project_one<DEG>(mx, my, mz, o, q4, s0, s1, s2, s_sh + threadIdx.x * PER, bc.cam[v], a, b, c, rect,
+                                radius);
         const ProjView& pv = bc.pv[v];
         pv.xy_ab[i] = a;
         pv.c_o_z[i] = b;
@@ -319,6 +373,7 @@ k_project_batch(const float* __restrict__ means, const float* __restrict__ scale
         pv.rect[i] = rect;
         pv.radius[i] = radius;
     }
+    if (bad) raise_error(err, GS_ERR_NUMERIC);
 }
 
 static CamArgs cam_args(const gs_camera* cam, int tile)
@@ -354,13 +409,14 @@ int launch_project_batch(gs_ctx* ctx, const float* means, const float* scales, c
         bc.pv[v] = pvs[v];
     }
     const int aligned = (reinterpret_cast<uintptr_t>(sh) & 15) == 0;
+    const int polls = ctx->cfg.wait_polls;
     const unsigned grid = (unsigned)((n + kProjBlock - 1) / kProjBlock);
     const float4* q4 = reinterpret_cast<const float4*>(quats);
     switch (sh_degree) {
-        case 0: k_project_batch<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, ctx->d_err); break;
-        case 1: k_project_batch<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, ctx->d_err); break;
-        case 2: k_project_batch<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, ctx->d_err); break;
-        default: k_project_batch<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, ctx->d_err); break;
+        case 0: k_project_batch<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, polls, ctx->d_err); break;
+        case 1: k_project_batch<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, polls, ctx->d_err); break;
+        case 2: k_project_batch<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, polls, ctx->d_err); break;
+        default: k_project_batch<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, bc, polls, ctx->d_err); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
@@ -375,13 +431,14 @@ int launch_project(gs_ctx* ctx, const float* means, const float* scales, const f
     if (reinterpret_cast<uintptr_t>(quats) & 15) return GS_ERR_INVALID_ARG;  // float4 loads
     const CamArgs ca = cam_args(cam, ctx->cfg.tile_size);
     const int aligned = (reinterpret_cast<uintptr_t>(sh) & 15) == 0;
+    const int polls = ctx->cfg.wait_polls;
     const unsigned grid = (unsigned)((n + kProjBlock - 1) / kProjBlock);
     const float4* q4 = reinterpret_cast<const float4*>(quats);
     switch (sh_degree) {
-        case 0: k_project<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, ctx->d_err); break;
-        case 1: k_project<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, ctx->d_err); break;
-        case 2: k_project<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, ctx->d_err); break;
-        default: k_project<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, ctx->d_err); break;
+        case 0: k_project<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err); break;
+        case 1: k_project<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err); break;
+        case 2: k_project<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err); break;
+        default: k_project<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());

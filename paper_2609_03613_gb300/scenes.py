@@ -218,6 +218,55 @@ def incoming_grads(height: int, width: int, seed: int = 5):
     return dC, dA
 
 
+def plant_nonfinite(scene: Scene, seed: int = 9, count: int = 48):
+    """A copy of `scene` with non-finite values written into `count` seeded
+    Gaussians, one kind per Gaussian in turn: NaN / +inf / -inf in a mean,
+    scale or quaternion component or in the opacity, a NaN or inf SH
+    coefficient, and (degree >= 2) three finite SH coefficients of 3.3e38
+    whose weighted sum overflows for a camera on the +z axis beyond the scene
+    (the default cameras).  Returns (scene, gids, kinds)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gids = np.sort(rng.choice(scene.n, size=count, replace=False))
+    sc = Scene(scene.means.copy(), scene.scales.copy(), scene.quats.copy(), scene.opacities.copy(),
+               scene.sh.copy(), scene.sh_degree)
+    kinds = ["mean_nan", "mean_inf", "scale_ninf", "scale_nan", "quat_nan", "quat_inf", "opacity_nan",
+             "opacity_inf", "sh_nan", "sh_inf"]
+    if scene.sh_degree >= 2:
+        kinds.append("sh_overflow")
+    used = []
+    for j, g in enumerate(gids):
+        k = kinds[j % len(kinds)]
+        a = int(rng.integers(0, 3))
+        if k == "mean_nan":
+            sc.means[g, a] = np.nan
+        elif k == "mean_inf":
+            sc.means[g, a] = np.inf
+        elif k == "scale_ninf":
+            sc.scales[g, a] = -np.inf
+        elif k == "scale_nan":
+            sc.scales[g, a] = np.nan
+        elif k == "quat_nan":
+            sc.quats[g, a] = np.nan
+        elif k == "quat_inf":
+            sc.quats[g, a + 1] = np.inf
+        elif k == "opacity_nan":
+            sc.opacities[g] = np.nan
+        elif k == "opacity_inf":
+            sc.opacities[g] = np.inf
+        elif k == "sh_nan":
+            sc.sh[g, 0, a] = np.nan
+        elif k == "sh_inf":
+            sc.sh[g, 0, a] = np.inf
+        else:
+            # Y_0, Y_2 (signed as the view direction's z) and Y_6 (positive
+            # along the axis) all weigh their coefficient positively
+            sc.sh[g, 0, a] = 3.3e38
+            sc.sh[g, 2, a] = -3.3e38 if sc.means[g, 2] < 3.0 else 3.3e38
+            sc.sh[g, 6, a] = 3.3e38
+        used.append(k)
+    return sc, gids, used
+
+
 def workload(name: str):
     """Named workloads: returns (scene, camera or list of cameras)."""
     if name == "tiny":

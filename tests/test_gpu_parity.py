@@ -266,13 +266,21 @@ def test_paper_selection_budget_binding_matches_greedy():
     assert used < int(np.where(lens >= 320, lens, 0).sum())  # the budget did bind
 
 
-@pytest.mark.parametrize("mode", ["global", "exact", "exact-eager"])
+@pytest.mark.parametrize("mode", ["global", "global-culled", "exact", "exact-eager", "exact-k1"])
 @pytest.mark.parametrize("tile", [8, 16, 32])
 def test_raster_matches_oracle(tiny, mode, tile):
+    """Every raster configuration the bench's ablation times: the plain global
+    raster, the global stream through the binned kernel (culls at staging),
+    EXACT bins with the repair in the raster or before it, and one bin per
+    tile (the culled entries in global order, sorted before the raster)."""
     sc, cam = tiny[0], tiny[1]
     proj_o, ent, (off, stream), (rgb_o, a_o, l_o) = O.render(sc, cam, tile, bg=(0.1, 0.2, 0.3))
     if mode == "exact-eager":
         ctx = G.Context("exact", tile_size=tile, repair_in_raster=0)
+    elif mode == "exact-k1":
+        ctx = G.Context("exact", tile_size=tile, K=1, repair_in_raster=0)
+    elif mode == "global-culled":
+        ctx = G.Context("global", tile_size=tile, tile_cull=1)
     else:
         ctx = G.Context(mode, tile_size=tile)
     ds, proj, _ = gpu_project(ctx, sc, cam)
@@ -290,7 +298,7 @@ def test_raster_test_counter_matches_oracle(tiny):
     sc, cam = tiny[0], tiny[1]
     proj_o, ent, (off, stream), _ = O.render(sc, cam)
     _, _, _, nt_o = O.composite(proj_o, off, stream, cam.width, cam.height, ntests=True)
-    for mode, cull in (("global", 1), ("exact", 0)):
+    for mode, cull in (("global", 0), ("exact", 0)):
         ctx = G.Context(mode, tile_cull=cull)
         ds, proj, _ = gpu_project(ctx, sc, cam)
         isect, m_cap, m_dev, m = ctx.tile_intersect(proj, sc.n, cam)

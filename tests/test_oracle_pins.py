@@ -327,6 +327,35 @@ def test_transmittance_non_increasing_along_list():
         prev = alpha
 
 
+def test_nonfinite_inputs_are_culled():
+    """Reading of the paper's silence on non-finite parameters: a Gaussian
+    with a non-finite mean, scale, quaternion or opacity, or a non-finite SH
+    sum, is culled.  Pinned against the opacity cull (opacity 0 < 1/255, a
+    different rule): the frame with the planted values equals, bit for bit,
+    the frame with those Gaussians' opacities set to zero, and every other
+    Gaussian projects as before."""
+    cam = scenes.hd_camera(width=480, height=270, f=275.0)
+    for sc0 in (scenes.tiny_scene(4000, 3), scenes.mixture_scene(30000, 11)):
+        bad, gids, kinds = scenes.plant_nonfinite(sc0)
+        ref = scenes.Scene(sc0.means.copy(), sc0.scales.copy(), sc0.quats.copy(), sc0.opacities.copy(),
+                           sc0.sh.copy(), sc0.sh_degree)
+        ref.opacities[gids] = 0.0
+        c = cam if sc0.sh_degree else scenes.tiny_camera()
+        pb, _, _, (rgb_b, a_b, l_b) = O.render(bad, c)
+        pr, _, _, (rgb_r, a_r, l_r) = O.render(ref, c)
+        assert not pb["visible"][gids].any()
+        for k in ("mean2d", "conic", "depth", "radius", "rect", "rgb", "visible"):
+            np.testing.assert_array_equal(pb[k], pr[k])
+        np.testing.assert_array_equal(rgb_b.view(np.uint32), rgb_r.view(np.uint32))
+        np.testing.assert_array_equal(a_b, a_r)
+        np.testing.assert_array_equal(l_b, l_r)
+        assert np.isfinite(rgb_b).all()
+        # the planted Gaussians would be drawn if their values were finite
+        p0 = O.project(sc0, c)
+        assert p0["visible"][gids].sum() >= 4
+    assert "sh_overflow" in kinds
+
+
 def test_composite_brute_force_all_gaussians_low_opacity():
     """With every opacity <= 0.3, a Gaussian outside its tile rectangle has
     alpha < 1/255 everywhere, so per-pixel compositing over ALL Gaussians in
