@@ -575,9 +575,12 @@ def run_ours(args):
         with torch.cuda.stream(side):
             ctx_pl.render(ds, cam, bg, out_pl)
         torch.cuda.synchronize()
-        planner = {"frame_ms": round(mean(ms_pl), 4), "raster_ms": round(mean(st_pl["raster"]), 4),
-                   "frame_ms_fixed": round(frame_b, 4), "raster_ms_fixed": round(raster_b, 4),
-                   "raster_gain": round(1.0 - mean(st_pl["raster"]) / raster_b, 4),
+        planner = {"frame_ms": round(mean(ms_pl), 4), "frame_ms_fixed": round(frame_b, 4),
+                   "frame_gain": round(1.0 - mean(ms_pl) / frame_b, 4),
+                   "stages_ms": {k: round(mean(v), 4) for k, v in st_pl.items() if mean(v) > 0},
+                   "stages_ms_fixed": {k: round(mean(v), 4) for k, v in st_b.items() if mean(v) > 0},
+                   "tiles_to_second_pass": ctx_pl.flagged_tiles(),
+                   "quantile": float(ctx_pl.cfg.planner_quantile),
                    "image_equal_fixed": bool(torch.equal(out_pl[0], out_b[0]) and torch.equal(out_pl[2], out_b[2]))}
 
     # raster-order-aware storage: the same scene with its Gaussians in the
@@ -715,6 +718,8 @@ def heavy_leg(dev, side, flush, frames=10):
             frame = sum(a.elapsed_time(b) for a, b in ev) / frames
             r[label] = {"frame_ms": round(frame, 4), "raster_ms": round(st["raster"], 4),
                         "stages_ms": {k: round(v, 4) for k, v in st.items() if v > 0}}
+            if label == "planner":
+                r[label]["tiles_to_second_pass"] = ctx.flagged_tiles()
             if label != "exact_morton_storage":
                 r["entries_per_frame"] = m
             if ref is None:
@@ -729,6 +734,8 @@ def heavy_leg(dev, side, flush, frames=10):
             del out
             torch.cuda.empty_cache()
         g, e = r["global_sort"], r["exact"]
+        if "planner" in r:
+            r["planner_frame_gain_vs_exact"] = round(1.0 - r["planner"]["frame_ms"] / e["frame_ms"], 4)
         r["speedup_frame_vs_global"] = round(g["frame_ms"] / e["frame_ms"], 3)
         r["speedup_raster_vs_global"] = round(g["raster_ms"] / e["raster_ms"], 3)
         res[name] = r

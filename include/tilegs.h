@@ -119,11 +119,13 @@ typedef struct gs_config {
                               consecutive bins the raster loads and sorts at once
                               (a tile's repair bins; a single longer segment of up
                               to 2048 forms one on its own); 32..2048, 0 = 256 */
-    int32_t planner;       /* EXACT with repair_in_raster, 1: each tile's chunk
-                              size comes from the bin planner (an MLP over the
-                              tile's depth-bin statistics, weights set with
-                              gs_planner_set_weights); 0: chunk_cap everywhere.
-                              Changes speed only, never the image. */
+    int32_t planner;       /* EXACT with repair_in_raster and the tile cull, 1: the
+                              bin planner (an MLP over the tile's depth-bin
+                              statistics, weights set with gs_planner_set_weights)
+                              picks how many of each tile's K bins gs_render builds
+                              in a first pass; tiles that do not terminate within
+                              them are completed by a second pass.  0: every bin
+                              in one pass.  Changes speed only, never the image. */
     int32_t wait_polls;    /* the most polls of a bounded device-side wait (the
                               projection's TMA copy of SH coefficients) before it
                               raises GS_ERR_TIMEOUT; gs_config_default sets
@@ -133,6 +135,9 @@ typedef struct gs_config {
                               the frame is written.  A block whose copy never
                               lands writes nothing: after GS_ERR_TIMEOUT the
                               frame's outputs are not valid. */
+    float planner_quantile; /* the planner's decision: the smallest class whose
+                              cumulative softmax probability reaches this value,
+                              in (0, 1] (gs_config_default: 0.9) */
 } gs_config;
 
 /* Fill *cfg with the paper's defaults (supplement, default No-GW configuration
@@ -170,7 +175,9 @@ int gs_clear_error(gs_ctx* ctx, void* stream);
 /* Per-stage device times of the last gs_render / gs_sort_or_bin call when
  * timing is enabled (host; synchronises).  ms[] receives GS_STAGE_COUNT values. */
 enum { GS_STAGE_PROJECT = 0, GS_STAGE_INTERSECT, GS_STAGE_DEPTH_RANGE, GS_STAGE_BIN,
-       GS_STAGE_REPAIR, GS_STAGE_SORT, GS_STAGE_RASTER, GS_STAGE_COUNT };
+       GS_STAGE_REPAIR, GS_STAGE_SORT, GS_STAGE_RASTER,
+       GS_STAGE_COMPLETE, /* a planned frame's second pass (cfg.planner) */
+       GS_STAGE_COUNT };
 int gs_enable_timing(gs_ctx* ctx, int32_t on);
 int gs_get_stage_times(gs_ctx* ctx, float* ms);
 
@@ -356,26 +363,36 @@ int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_cam
                      const float* dl_drgb, const float* dl_dalpha, void* grad, void* stream);
 
 /*
- * gs_rasterize_fwd with a per-tile chunk plan (EXACT with repair_in_raster):
- * plan [T] (nullable) gives each tile's chunk size class c -- chunks of at
- * most 64 << c entries (c = 0..5) -- in place of cfg.chunk_cap; tile_cycles
- * [T] (nullable) receives each tile's clock64() cycles inside the raster
- * (the planner's training labels).  Other arguments as gs_rasterize_fwd; the
- * image does not depend on the plan.
+ * gs_rasterize_fwd as one pass of a planned frame (EXACT with repair_in_raster):
+ *   plan [T] (nullable: every bin): the number of bins, from each tile's
+ *   front, that this pass walks (values above K count as K).
+ *   flags [T] (nullable): set to 1 for each tile that has a pixel still
+ *   compositing when its planned bins end while later bins hold entries (it
+ *   must be composited again over all its bins), 0 otherwise.
+ *   bins_needed [T] (nullable; requires plan == NULL): the bins each tile
+ *   needs, 1 + the bin holding the last entry any of its pixels visits (the
+ *   stopping entry, or the span's last for a pixel that never stops); 0 for
+ *   an empty tile.  A plan with plan[t] >= bins_needed[t] flags no tile.
+ * Other arguments as gs_rasterize_fwd.  Pixels of tiles that are not flagged
+ * are final.  With flags, a flagged tile's pixels hold the pass's state for
+ * the completing pass: C (no background) in rgb, T in alpha (negative once
+ * the pixel has stopped), last.
  */
 int gs_rasterize_fwd_plan(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
                           uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
                           const float* bg, float* rgb, float* alpha, int32_t* last, const uint8_t* plan,
-                          long long* tile_cycles, void* stream);
+                          uint8_t* flags, int32_t* bins_needed, void* stream);
 
 /* ---------------------------------------------------------------- bin planner */
 /*
  * The learned bin planner (the paper uses one bin count and spacing for every
  * tile, Sec. 5.3, and leaves distribution-dependent settings to future work,
- * Sec. 7).  Per tile, an MLP maps 8 statistics of the tile's culled span and
- * fine-bin counts to a chunk size class: how many consecutive bins the EXACT
- * raster loads, sorts and composites at a time, i.e. the tile's bin count
- * and the split depths where its bins end.  The image never changes.
+ * Sec. 7).  Per tile, an MLP maps 8 statistics of the tile's K depth-bin
+ * counts to a class c: class c < 5 gives the tile's first pass the fewest
+ * bins from its front that hold at least 64 << c entries, class 5 all K.
+ * The class is the smallest whose cumulative softmax probability reaches
+ * cfg.planner_quantile.  The image never changes (gs_render completes every
+ * tile the first pass leaves unfinished).
  *
  * gs_tile_features: features [T][GS_PLAN_FEATURES] (device) of a binned
  *   stream's offsets (stride = K): log1p(n), log1p(max bin), nonempty/K,
@@ -383,7 +400,8 @@ int gs_rasterize_fwd_plan(gs_ctx* ctx, const void* projected, int64_t n, const g
  *   from the first nonempty one), log1p(n/nonempty).
  * gs_planner_set_weights: GS_PLAN_PARAMS floats (host or device; NULL turns
  *   the planner off), packed W1[64][8] b1 W2[64][64] b2 W3[6][64] b3.
- * gs_plan_tiles: plan [T] = argmax class of each tile (device).
+ * gs_plan_tiles: from a binned stream's offsets, plan [T] = each tile's
+ *   first-pass bins and classes [T] (nullable) = its class (device).
  * Training kernels (device buffers, batch B):
  *   gs_mlp_forward: acts [B][128] = (h1, h2), logits [B][6];
  *   gs_mlp_loss_grad: mean softmax cross entropy into loss[0] and its
@@ -394,7 +412,8 @@ int gs_rasterize_fwd_plan(gs_ctx* ctx, const void* projected, int64_t n, const g
 int gs_tile_features(gs_ctx* ctx, const gs_camera* cam, const int32_t* offsets, int32_t stride, float* features,
                      void* stream);
 int gs_planner_set_weights(gs_ctx* ctx, const float* params, void* stream);
-int gs_plan_tiles(gs_ctx* ctx, const float* features, int32_t n_tiles, uint8_t* plan, void* stream);
+int gs_plan_tiles(gs_ctx* ctx, const gs_camera* cam, const int32_t* offsets, int32_t stride, uint8_t* plan,
+                  uint8_t* classes, void* stream);
 int gs_mlp_forward(const float* params, const float* X, int32_t B, float* acts, float* logits, void* stream);
 int gs_mlp_loss_grad(const float* logits, const int32_t* labels, int32_t B, float* dlogits, float* loss,
                      void* stream);
@@ -523,6 +542,10 @@ int64_t gs_batch_last_entry_count(gs_ctx* ctx, int32_t view);
  */
 int gs_batch_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* cams, int32_t n_cams,
                       int32_t tune_tile, int32_t iters, float* best_ms, void* stream);
+
+/* Tiles the last planned gs_render (cfg.planner) left to its second pass
+ * (host; synchronises `stream`); 0 without a planned frame, -1 on error. */
+int32_t gs_last_flagged_tiles(gs_ctx* ctx, void* stream);
 
 /* Entry count of the last gs_render (host; valid after the stream synchronises). */
 int64_t gs_last_entry_count(gs_ctx* ctx);

@@ -12,7 +12,15 @@ What it restates, in float64 numpy, one plain step at a time:
     W1[64][8] b1[64] W2[64][64] b2[64] W3[6][64] b3[6];
   * mean softmax cross entropy and its gradient, backpropagation through the
     network, and one Adam step (Kingma & Ba, 2015: m, v moving averages of the
-    gradient and its square, bias-corrected, step lr * m_hat / (sqrt(v_hat) + eps)).
+    gradient and its square, bias-corrected, step lr * m_hat / (sqrt(v_hat) + eps));
+  * the decision: the smallest class whose cumulative softmax probability
+    reaches the quantile q, and the first-pass bins of a class (class c < 5:
+    the fewest bins from the tile's front holding at least 64 << c entries,
+    all K for class 5);
+  * the training label of a tile: the bins it needs, 1 + the bin holding the
+    last entry any of its pixels visits when compositing its whole list (the
+    stopping entry, or the list's last for a pixel that never stops), and the
+    smallest class whose bins cover them.
 The paper has no planner (it uses one bin count and spacing for every tile,
 Sec. 5.3, and leaves distribution-dependent settings to future work, Sec. 7);
 these definitions are the project's.
@@ -110,6 +118,72 @@ def adam(params, grads, m, v, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     return np.asarray(params, np.float64) - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def plan(params, X):
-    """Argmax class per row (lowest class on ties)."""
-    return np.argmax(forward(params, X)[2], axis=1)
+def decide(logits, q):
+    """Smallest class whose cumulative softmax probability reaches q (the
+    last class when none before it does)."""
+    z = np.asarray(logits, np.float64)
+    e = np.exp(z - z.max(axis=1, keepdims=True))
+    cum = np.cumsum(e, axis=1) / e.sum(axis=1, keepdims=True)
+    hit = cum[:, :C - 1] >= q
+    return np.where(hit.any(axis=1), np.argmax(hit, axis=1), C - 1)
+
+
+def class_bins(offsets, K, n_tiles, classes):
+    """First-pass bins per tile for the given class of each tile."""
+    off = np.asarray(offsets, np.int64)
+    out = np.zeros(n_tiles, np.int64)
+    for t in range(n_tiles):
+        c = int(classes[t])
+        if c >= C - 1:
+            out[t] = K
+            continue
+        cum = off[t * K + 1:t * K + K + 1] - off[t * K]
+        hit = np.nonzero(cum >= (64 << c))[0]
+        out[t] = hit[0] + 1 if len(hit) else K
+    return out
+
+
+def plan(params, X, offsets, K, n_tiles, q=0.9):
+    """(classes, first-pass bins) per tile."""
+    cls = decide(forward(params, X)[2], q)
+    return cls, class_bins(offsets, K, n_tiles, cls)
+
+
+def bins_needed(offsets, K, n_tiles, tile_end):
+    """Bins each tile needs given tile_end[t], the stream position after the
+    last entry any of its pixels visits: 1 + the bin holding tile_end - 1;
+    0 for an empty tile."""
+    off = np.asarray(offsets, np.int64)
+    out = np.zeros(n_tiles, np.int64)
+    for t in range(n_tiles):
+        s0 = off[t * K]
+        e = int(tile_end[t])
+        if e <= s0:
+            continue
+        seg = off[t * K:t * K + K + 1]
+        out[t] = int(np.searchsorted(seg, e - 1, side="right") - 1) + 1
+    return out
+
+
+def tile_end_from_visits(offsets, K, tile, width, height, ntests):
+    """tile_end per tile from the per-pixel visit counts of compositing the
+    tiles' whole lists in order (ntests [H][W]: entries each pixel visited,
+    the stopping one included): the span start plus the largest count."""
+    off = np.asarray(offsets, np.int64)
+    tx = (width + tile - 1) // tile
+    ty = (height + tile - 1) // tile
+    out = np.zeros(tx * ty, np.int64)
+    for t in range(tx * ty):
+        x0, y0 = (t % tx) * tile, (t // tx) * tile
+        blk = ntests[y0:min(y0 + tile, height), x0:min(x0 + tile, width)]
+        out[t] = off[t * K] + (int(blk.max()) if blk.size else 0)
+    return out
+
+
+def label(needed, offsets, K, n_tiles):
+    """Smallest class whose first-pass bins cover the bins a tile needs."""
+    out = np.full(n_tiles, C - 1, np.int64)
+    for c in range(C - 2, -1, -1):
+        b = class_bins(offsets, K, n_tiles, np.full(n_tiles, c))
+        out = np.where(b >= needed, c, out)
+    return out

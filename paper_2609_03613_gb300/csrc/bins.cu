@@ -671,10 +671,12 @@ k_repair_tail(const int32_t* __restrict__ off, const int32_t* __restrict__ tail,
 // thread per segment; most frames have none), then one block per listed
 // segment sorts it -- in shared memory when it fits, else in place.
 __global__ void k_list_long(const int32_t* __restrict__ off, int64_t nseg, int min_len, int32_t* __restrict__ list,
-                            int32_t cap, int* err)
+                            int32_t cap, int* err, const ScatterPass sp, int K, const int32_t* __restrict__ flagged)
 {
+    if (sp.pass == 2 && flagged[0] == 0) return;  // no tile to complete
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseg; q += (int64_t)gridDim.x * blockDim.x) {
         if (off[q + 1] - off[q] < min_len) continue;
+        if (!sp.keep(q / K, (int)(q % K))) continue;
         const int slot = atomicAdd(&list[0], 1);
         if (slot < cap) list[1 + slot] = (int32_t)q;
         else raise_error(err, GS_ERR_CAPACITY);
@@ -723,7 +725,7 @@ int repair(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* words, 
 }
 
 int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* words, const int32_t* offsets,
-               uint8_t* selected_out, int32_t min_len, cudaStream_t st)
+               uint8_t* selected_out, int32_t min_len, cudaStream_t st, int pass)
 {
     const gs_config& c = ctx->cfg;
     const int64_t nseg = (int64_t)n_tiles * c.K;
@@ -755,7 +757,14 @@ int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* wor
         if (nseg > 0) {
             const int64_t want = (nseg + 255) / 256;
             const unsigned g = (unsigned)(want < (int64_t)grid ? want : (int64_t)grid);
-            k_list_long<<<g, 256, 0, st>>>(offsets, nseg, min_len, ctx->d_tail, tail_cap, ctx->d_err);
+            ScatterPass sp;
+            if (pass) {
+                sp.plan = ctx->d_plan;
+                sp.T = n_tiles;
+                sp.pass = pass;
+            }
+            k_list_long<<<g, 256, 0, st>>>(offsets, nseg, min_len, ctx->d_tail, tail_cap, ctx->d_err, sp, c.K,
+                                           pass ? ctx->d_plist : nullptr);
             k_sort_listed<<<(unsigned)ctx->num_sms, 1024, 0, st>>>(offsets, ctx->d_tail, tail_cap, words);
             ctx->launches += 2;
         }

@@ -51,6 +51,7 @@ extern "C" void gs_config_default(gs_config* cfg, int32_t mode)
     cfg->chunk_cap = 256;
     cfg->planner = 0;
     cfg->wait_polls = 1 << 22;
+    cfg->planner_quantile = 0.9f;
 }
 
 namespace gs {
@@ -70,6 +71,7 @@ int check_config(const gs_config* c)
     if (c->chunk_cap != 0 && (c->chunk_cap < 32 || c->chunk_cap > 2048)) return GS_ERR_INVALID_ARG;
     if (c->planner != 0 && c->planner != 1) return GS_ERR_INVALID_ARG;
     if (c->wait_polls < 0) return GS_ERR_INVALID_ARG;
+    if (!(c->planner_quantile > 0.0f && c->planner_quantile <= 1.0f)) return GS_ERR_INVALID_ARG;
     return GS_OK;
 }
 
@@ -423,18 +425,34 @@ extern "C" int gs_rasterize_fwd(gs_ctx* ctx, const void* projected, int64_t n, c
 extern "C" int gs_rasterize_fwd_plan(gs_ctx* ctx, const void* projected, int64_t n, const gs_camera* cam,
                                      uint64_t* stream_words, const int32_t* offsets, int32_t offsets_stride,
                                      const float* bg, float* rgb, float* alpha, int32_t* last, const uint8_t* plan,
-                                     long long* tile_cycles, void* stream)
+                                     uint8_t* flags, int32_t* bins_needed, void* stream)
 {
     if (!ctx || !cam_ok(cam) || n < 0 || !offsets || !bg || !rgb || !alpha || !last)
         return GS_ERR_INVALID_ARG;
     if (n > 0 && (!projected || !stream_words)) return GS_ERR_INVALID_ARG;
     if (offsets_stride < 1 || offsets_stride > GS_MAX_K) return GS_ERR_INVALID_ARG;
+    if (bins_needed && plan) return GS_ERR_INVALID_ARG;
+    if (ctx->cfg.mode != GS_MODE_BINNED_EXACT || !ctx->cfg.repair_in_raster) return GS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const bool baseline = baseline_raster(ctx->cfg);
+    const int32_t T = gs_num_tiles(cam->width, cam->height, ctx->cfg.tile_size);
+    PlanView pl;
+    pl.bins = plan;
+    pl.needed = bins_needed;
+    int r;
+    if (flags) {
+        // the context's flag region (tile flags, then row flags), copied out
+        if ((r = planner_buffers(ctx, T)) != GS_OK) return r;
+        GS_CUDA_TRY(cudaMemsetAsync(ctx->d_plan + T, 0, 2 * (size_t)T, st));
+        GS_CUDA_TRY(cudaMemsetAsync(ctx->d_plist, 0, sizeof(int32_t), st));
+        pl.flag = ctx->d_plan + T;
+        pl.list = ctx->d_plist;
+    }
     stage_begin(ctx, GS_STAGE_RASTER, st);
-    int r = raster_fwd(ctx, proj_view(const_cast<void*>(projected), n), cam, stream_words, offsets, offsets_stride,
-                       bg, rgb, alpha, last, nullptr, baseline, st, nullptr, nullptr, plan, tile_cycles);
+    r = raster_fwd(ctx, proj_view(const_cast<void*>(projected), n), cam, stream_words, offsets, offsets_stride, bg,
+                   rgb, alpha, last, nullptr, false, st, nullptr, nullptr, pl);
     stage_end(ctx, GS_STAGE_RASTER, st);
+    if (r == GS_OK && flags)
+        GS_CUDA_TRY(cudaMemcpyAsync(flags, ctx->d_plan + T, (size_t)T, cudaMemcpyDeviceToDevice, st));
     return r;
 }
 
@@ -497,6 +515,17 @@ extern "C" int64_t gs_last_entry_count(gs_ctx* c) { return c ? c->last_m : -1; }
 
 extern "C" int64_t gs_launch_count(const gs_ctx* c) { return c ? c->launches + batch_launch_count(c) : -1; }
 
+extern "C" int32_t gs_last_flagged_tiles(gs_ctx* c, void* stream)
+{
+    if (!c) return -1;
+    if (!c->d_plist) return 0;
+    int32_t h = 0;
+    if (cudaMemcpyAsync(&h, c->d_plist, sizeof(int32_t), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess ||
+        cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return -1;
+    return h;
+}
+
 extern "C" int64_t gs_last_raster_ops(gs_ctx* c, void* stream)
 {
     if (!c) return -1;
@@ -515,8 +544,11 @@ int gs::planner_buffers(gs_ctx* c, int32_t T)
     if ((r = ensure(&p, &c->feat_cap, (size_t)T * GS_PLAN_FEATURES * 4 + 16)) != GS_OK) return r;
     c->d_feat = (float*)p;
     p = c->d_plan;
-    if ((r = ensure(&p, &c->plan_cap_bytes, (size_t)T + 16)) != GS_OK) return r;
+    if ((r = ensure(&p, &c->plan_cap_bytes, 3 * (size_t)T + 16)) != GS_OK) return r;
     c->d_plan = (uint8_t*)p;
+    p = c->d_plist;
+    if ((r = ensure(&p, &c->plist_cap, ((size_t)T + 1) * 4)) != GS_OK) return r;
+    c->d_plist = (int32_t*)p;
     return GS_OK;
 }
 
@@ -566,13 +598,18 @@ int gs::render_binning(gs_ctx* c, int64_t n, const float* scales, const gs_camer
         r = depth_range_goff(c, pv, scales, n, c->r_m_cap, c->r_m, cam, st);
         stage_end(c, GS_STAGE_DEPTH_RANGE, st);
         if (r != GS_OK) return r;
+        const bool planned = frame_planned(c);
+        if (planned) {
+            if (!c->planner_ready) return GS_ERR_INVALID_ARG;  // gs_planner_set_weights first
+            if ((r = planner_buffers(c, T)) != GS_OK) return r;
+        }
         stage_begin(c, GS_STAGE_BIN, st);
-        r = exact_bins(c, pv, n, cam, true, c->r_m_cap, c->r_m, c->r_stream, c->r_off, st, rows);
+        r = exact_bins(c, pv, n, cam, true, c->r_m_cap, c->r_m, c->r_stream, c->r_off, st, rows, planned);
         stage_end(c, GS_STAGE_BIN, st);
         if (r != GS_OK) return r;
         stage_begin(c, GS_STAGE_REPAIR, st);
         r = repair_min(c, T, c->r_m, c->r_stream, c->r_off, nullptr,
-                       c->cfg.repair_in_raster ? kRasterSortCap + 1 : 2, st);
+                       c->cfg.repair_in_raster ? kRasterSortCap + 1 : 2, st, planned ? 1 : 0);
         stage_end(c, GS_STAGE_REPAIR, st);
     } else {
         r = emit_only(c, pv, n, cam, isect_view(c->r_isect, c->r_m_cap), c->r_m_cap, c->r_m, st);
@@ -597,18 +634,29 @@ int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs
     if (save && (r = render_save_buffers(c, W, H, T)) != GS_OK) return r;
     c->r_saved = 0;
     stage_begin(c, GS_STAGE_RASTER, st);
-    const uint8_t* plan = nullptr;
-    if (c->cfg.planner && c->cfg.mode == GS_MODE_BINNED_EXACT && c->cfg.repair_in_raster) {
-        if (!c->planner_ready) return GS_ERR_INVALID_ARG;  // gs_planner_set_weights first
-        if ((r = planner_buffers(c, T)) != GS_OK) return r;
-        if ((r = plan_frame(c, c->r_off, stride, T, c->d_plan, st)) != GS_OK) return r;
-        plan = c->d_plan;
+    const bool planned = c->cfg.mode == GS_MODE_BINNED_EXACT && frame_planned(c);
+    PlanView pl;
+    if (planned) {
+        pl.bins = c->d_plan;
+        pl.flag = c->d_plan + T;
+        pl.list = c->d_plist;
     }
     r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,
-                   baseline_raster(c->cfg), st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr,
-                   plan, nullptr);
+                   baseline_raster(c->cfg), st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr, pl);
     stage_end(c, GS_STAGE_RASTER, st);
     if (r != GS_OK) return r;
+    if (planned) {
+        // the completing pass: the other bins of the flagged tiles, their long
+        // segments sorted, the tiles composited on from where they stopped
+        stage_begin(c, GS_STAGE_COMPLETE, st);
+        r = exact_scatter_rest(c, n, cam, c->r_m_cap, c->r_m, c->r_stream, c->r_off, st);
+        if (r == GS_OK) r = repair_min(c, T, c->r_m, c->r_stream, c->r_off, nullptr, kRasterSortCap + 1, st, 2);
+        if (r == GS_OK)
+            r = raster_listed(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, c->d_plan,
+                              c->d_plist, st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr);
+        stage_end(c, GS_STAGE_COMPLETE, st);
+        if (r != GS_OK) return r;
+    }
     if (save) {
         c->r_saved = 1;
         c->r_last = d_last;

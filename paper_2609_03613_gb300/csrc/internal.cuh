@@ -244,7 +244,9 @@ struct gs_ctx {
     float* d_planner = nullptr;
     int planner_ready = 0;
     float* d_feat = nullptr; size_t feat_cap = 0;
-    uint8_t* d_plan = nullptr; size_t plan_cap_bytes = 0;
+    uint8_t* d_plan = nullptr; size_t plan_cap_bytes = 0;  // [T] first-pass bins, [T] completion flags, [T] row flags
+    int32_t* d_plist = nullptr; size_t plist_cap = 0;      // [1 + T]: count, then the flagged tiles
+    int32_t* exact_roff = nullptr;  // row-record offsets of the last planned frame's bin construction
     // batched multi-view rendering (gs_render_batch)
     gs::BatchState* batch = nullptr;
     // spatial order of a scene (order.cu)
@@ -261,6 +263,12 @@ struct gs_ctx {
 
 // ------------------------------------------------------------------ internal launchers
 namespace gs {
+// A whole frame of this context runs the planned two passes (EXACT, repair in
+// the raster, tile cull, planner on).
+inline bool frame_planned(const gs_ctx* c)
+{
+    return c->cfg.planner && c->cfg.mode == GS_MODE_BINNED_EXACT && c->cfg.repair_in_raster && c->cfg.tile_cull;
+}
 
 int ensure(void** p, size_t* cap, size_t bytes);
 int check_config(const gs_config* cfg);
@@ -305,20 +313,86 @@ int launch_depth_range_into(const gs_config& c, const ProjView& pv, const float*
 // counts and the expansion, which needs ctx->d_goff -- computed here unless
 // goff_ready).  Segments are left unsorted.
 // rows_ready: count_rows_scan has also written the row-record offsets.
+// With planned (the tile cull on): after the counts, the bin planner sets
+// each tile's first-pass bins (plan_frame) and only entries of those bins are
+// scattered; exact_scatter_rest then places the other entries of the tiles
+// the first raster pass flagged.
 int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, bool goff_ready, int64_t m_cap,
-               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st, bool rows_ready = false);
+               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st, bool rows_ready = false,
+               bool planned = false);
+int exact_scatter_rest(gs_ctx* ctx, int64_t n, const gs_camera* cam, int64_t m_cap, const int64_t* m_dev,
+                       uint64_t* words, const int32_t* offsets, cudaStream_t st);
 // tiles.cu: items of the grouped scatter's count scan (for reserving)
 int64_t group_scan_items(gs_ctx* ctx, int32_t tiles_y, int K);
 // bins.cu: sort segments of length >= min_len (EXACT) or the rule/budget
 // selection (PAPER)
+// pass 1 / 2 (EXACT, long segments only): the segments of the planned
+// frame's first pass (bins below ctx->d_plan) or of its completing pass (the
+// other bins of flagged tiles); 0: every segment
 int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* stream_words, const int32_t* offsets,
-               uint8_t* selected_out, int32_t min_len, cudaStream_t st);
+               uint8_t* selected_out, int32_t min_len, cudaStream_t st, int pass = 0);
 // segments longer than this are sorted before the raster when the raster
 // sorts the segments it reaches
 constexpr int kRasterSortCap = 2048;
-// repair-bin (chunk) size classes of the per-tile plan: 64 << class entries
+// Classes of the bin planner: class c < kPlanClasses - 1 gives a tile's first
+// pass the fewest bins from its front that hold at least plan_entries(c)
+// entries; the last class gives it every bin.
 constexpr int kPlanClasses = 6;
-__host__ __device__ inline int plan_cap(int cls) { return 64 << (cls < 0 ? 0 : cls > 5 ? 5 : cls); }
+__host__ __device__ inline int plan_entries(int cls) { return 64 << cls; }
+// What a planned raster pass reads and writes per tile: bins[t] (nullable:
+// all) is the number of bins walked from the tile's front; a tile that has
+// not terminated when they end while later bins hold entries is flagged
+// (flag[t] = 1, flag[T + tile row] = 1, appended to list = {count,
+// tiles...}) for the completing pass;
+// needed[t] (the counting twin, all bins walked) receives the bins the tile
+// needs: 1 + the bin holding the last entry any pixel visits.
+// Which entries (or segments) a pass of bin construction handles.  pass 0:
+// all; pass 1 (a planned frame's first pass): bins below the tile's planned
+// bins; pass 2 (its completing pass): the other bins of the tiles the first
+// raster pass flagged.
+struct ScatterPass {
+    const uint8_t* plan = nullptr;  // [T] planned bins, [T] flags, then per tile row a flag (any tile of it)
+    int32_t T = 0;
+    int pass = 0;
+    __device__ __forceinline__ bool keep(int64_t t, int b) const
+    {
+        if (pass == 0) return true;
+        const int B = __ldg(plan + t);
+        return pass == 1 ? b < B : (b >= B && __ldg(plan + T + t) != 0);
+    }
+    // whether the completing pass has anything in tile row ty
+    __device__ __forceinline__ bool row_live(int ty) const { return pass != 2 || __ldg(plan + 2 * (int64_t)T + ty) != 0; }
+    // A row record (tile row | first tile << 12 | bin << 24, width) trimmed to
+    // the tiles from the first to the last this pass keeps; width 0 when it
+    // keeps none (the record is skipped whole).
+    __device__ __forceinline__ void trim(uint32_t& ya, uint32_t& w, int tiles_x) const
+    {
+        if (pass == 0 || w == 0u) return;
+        const int b = (int)(ya >> 24), x0 = (int)((ya >> 12) & 0xfffu);
+        const int64_t t0 = (int64_t)(ya & 0xfffu) * tiles_x + x0;
+        int lo = -1, hi = -1;
+        for (int j = 0; j < (int)w; ++j)
+            if (keep(t0 + j, b)) {
+                if (lo < 0) lo = j;
+                hi = j;
+            }
+        if (lo < 0) {
+            w = 0u;
+            return;
+        }
+        ya = (ya & ~(0xfffu << 12)) | ((uint32_t)(x0 + lo) << 12);
+        w = (uint32_t)(hi - lo + 1);
+    }
+};
+// With resume (the completing pass), bins[t] is instead where the walk
+// starts, from the pixel state the first pass left in the outputs.
+struct PlanView {
+    const uint8_t* bins = nullptr;
+    uint8_t* flag = nullptr;
+    int32_t* list = nullptr;
+    int32_t* needed = nullptr;
+    int resume = 0;
+};
 // the configured chunk size of the lazy EXACT raster
 inline int chunk_cap(const gs_config& cfg) { return cfg.chunk_cap > 0 ? cfg.chunk_cap : 256; }
 // The plain baseline raster kernel serves GLOBAL mode without the tile cull;
@@ -333,7 +407,16 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* stream_words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T = nullptr,
-               int32_t* tile_end = nullptr, const uint8_t* plan = nullptr, long long* tile_cycles = nullptr);
+               int32_t* tile_end = nullptr, const PlanView& plan = PlanView());
+// the completing pass of a planned frame: every tile of list (device {count,
+// tiles...}) composited on from the bin where its first pass stopped (plan
+// [T]), from the pixel state that pass left in rgb / alpha / last (EXACT,
+// repair in the raster); a persistent launch that returns at once when the
+// list is empty
+int raster_listed(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* stream_words,
+                  const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha, int32_t* last,
+                  const uint8_t* plan, const int32_t* list, cudaStream_t st, float* final_T = nullptr,
+                  int32_t* tile_end = nullptr);
 
 // one EXACT (repair in the raster, 16x16 tiles) view of a batched raster
 struct RasterView {
@@ -363,8 +446,11 @@ bool camera_ok(const gs_camera* cam);
 int render_buffers(gs_ctx* c, int64_t n, int64_t m_cap, int32_t T);
 int render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T);
 int planner_buffers(gs_ctx* c, int32_t T);
-// planner.cu: features and plan of every tile of a binned stream, one launch
-int plan_frame(gs_ctx* c, const int32_t* offsets, int32_t K, int32_t T, uint8_t* plan, cudaStream_t st);
+// planner.cu: features, class and first-pass bins of every tile of a binned
+// stream in one launch (plan [T] bins; classes [T] nullable); also clears the
+// completion flags (plan + T) and list (c->d_plist) of the frame
+int plan_frame(gs_ctx* c, const int32_t* offsets, int32_t K, int32_t T, uint8_t* plan, uint8_t* classes,
+               cudaStream_t st);
 int render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs_camera* cam, const float* bg,
                          float* d_rgb, float* d_alpha, int32_t* d_last, int32_t flags, cudaStream_t st);
 // the frame up to the raster: intersect, sort or bin, repair (stream and

@@ -1,14 +1,16 @@
 // planner.cu -- K23: the learned bin planner.  The paper uses one bin count
 // and spacing for every tile (Sec. 5.3 ablates K for the whole frame; Sec. 7
 // leaves settings that follow the depth distribution or the resolution to
-// future work); here a small MLP picks,
-// per tile, how the tile's fine depth bins are grouped into repair bins (the
-// chunks the EXACT raster loads, sorts and composites one at a time): a chunk
-// size class c gives chunks of at most 64 << c entries, so it fixes the tile's
-// bin count and the split depths where its bins end.  The image never
-// changes (every chunk's segments are sorted exactly); only the speed does.
+// future work).  Here a small MLP picks, per tile, how many of the tile's K
+// depth bins (the monotone split depths of EXACT mode) the frame builds in
+// its first pass: only the entries of those bins are scattered and
+// composited.  A tile whose pixels have not all terminated when its bins run
+// out, and which has entries in later bins, is completed by a second pass
+// (the rest of its bins scattered, the tile composited again from its
+// front).  So every plan gives the same image; a good plan skips the
+// scattering of entries behind the point where a tile saturates.
 //
-// Features per tile, from its culled span and the K fine-bin counts n_b:
+// Features per tile, from its culled span and the K bin counts n_b:
 //   f0 log1p(n)        n = entries of the tile
 //   f1 log1p(max n_b)
 //   f2 nonempty / K
@@ -19,9 +21,13 @@
 //   f7 log1p(n / nonempty)         mean occupancy of a nonempty bin
 // Network: 8 -> 64 -> 64 -> 6, ReLU, float32; parameters packed as
 //   W1[64][8] b1[64] W2[64][64] b2[64] W3[6][64] b3[6]  (5126 floats).
-// Training runs on the GPU with the kernels below (forward, softmax cross
-// entropy, backward, Adam), on labels the raster itself measures (per-tile
-// cycles of every class, gs_rasterize_fwd_plan).
+// Class c < 5 keeps the fewest bins from the tile's front holding at least
+// 64 << c entries; class 5 keeps all K.  The decision is the smallest class
+// whose cumulative softmax probability reaches the configured quantile q
+// (a calibrated network then needs the second pass for about 1 - q of the
+// tiles).  Training runs on the GPU with the kernels below (forward, softmax
+// cross entropy, backward, Adam) on labels the raster itself logs: each
+// tile's bins needed (the counting raster, gs_rasterize_fwd_plan).
 #include "internal.cuh"
 
 namespace gs {
@@ -32,17 +38,26 @@ static_assert(oB3 + kC == GS_PLAN_PARAMS, "parameter layout");
 static_assert(kC == kPlanClasses, "plan classes");
 
 // The features of tile t, in every lane of the calling warp (K <= GS_MAX_K,
-// so at most 4 bins per lane).
+// so at most 4 bins per lane).  All the tile's offsets are loaded in one
+// round: a lane holds o[b] and o[b + 1] of its bins b = lane + 32 j.
 __device__ __forceinline__ void warp_tile_features(const int32_t* __restrict__ off, int K, int t, float (&f)[kF])
 {
     const int lane = threadIdx.x & 31;
     const int32_t* o = off + (int64_t)t * K;
+    int lo[4], hi[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int b = lane + 32 * j;
+        lo[j] = b < K ? __ldg(o + b) : 0;
+        hi[j] = b < K ? __ldg(o + b + 1) : 0;
+    }
+    const int o0 = __ldg(o), oK = __ldg(o + K);
     int cnt[4];
     int mx = 0, ne = 0, first = K, last = -1;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int b = lane + 32 * j;
-        cnt[j] = b < K ? o[b + 1] - o[b] : 0;
+        cnt[j] = hi[j] - lo[j];
         mx = max(mx, cnt[j]);
         if (cnt[j] > 0) {
             ++ne;
@@ -70,7 +85,7 @@ __device__ __forceinline__ void warp_tile_features(const int32_t* __restrict__ o
         front += __shfl_xor_sync(0xffffffffu, front, s);
         nfirst += __shfl_xor_sync(0xffffffffu, nfirst, s);
     }
-    const int n = o[K] - o[0];
+    const int n = oK - o0;
     const float fk = (float)K;
     f[0] = log1pf((float)n);
     f[1] = log1pf((float)mx);
@@ -99,39 +114,56 @@ __global__ void k_tile_features(const int32_t* __restrict__ off, int K, int T, f
 }
 
 // Inference parameters in shared memory, laid out so that lane l reads
-// consecutive words: W1t[i][j] = W1[j][i], W2t[i][j] = W2[j][i].
-struct PlanShared {
+// consecutive words: W1t[i][j] = W1[j][i], W2t[i][j] = W2[j][i].  The same
+// layout is kept in device memory (written once by gs_planner_set_weights),
+// so a block stages it with contiguous 16-byte copies.
+struct __align__(16) PlanShared {
     float W1t[kF * kH];
     float b1[kH];
     float W2t[kH * kH];
     float b2[kH];
     float W3[kC * kH];
     float b3[kC];
+    float pad[2];
 };
+static_assert(sizeof(PlanShared) % 16 == 0, "16-byte staging");
+constexpr int kPlanLayoutFloats = (int)(sizeof(PlanShared) / 4);
 
-__device__ __forceinline__ void stage_plan_params(const float* __restrict__ P, PlanShared& s)
+// the inference layout of packed parameters P (one block)
+__global__ void k_plan_layout(const float* __restrict__ P, PlanShared* __restrict__ s)
 {
     for (int k = threadIdx.x; k < kF * kH; k += blockDim.x) {
         const int j = k / kF, i = k % kF;
-        s.W1t[i * kH + j] = P[oW1 + k];
+        s->W1t[i * kH + j] = P[oW1 + k];
     }
     for (int k = threadIdx.x; k < kH * kH; k += blockDim.x) {
         const int j = k / kH, i = k % kH;
-        s.W2t[i * kH + j] = P[oW2 + k];
+        s->W2t[i * kH + j] = P[oW2 + k];
     }
     for (int k = threadIdx.x; k < kH; k += blockDim.x) {
-        s.b1[k] = P[oB1 + k];
-        s.b2[k] = P[oB2 + k];
+        s->b1[k] = P[oB1 + k];
+        s->b2[k] = P[oB2 + k];
     }
-    for (int k = threadIdx.x; k < kC * kH; k += blockDim.x) s.W3[k] = P[oW3 + k];
-    for (int k = threadIdx.x; k < kC; k += blockDim.x) s.b3[k] = P[oB3 + k];
+    for (int k = threadIdx.x; k < kC * kH; k += blockDim.x) s->W3[k] = P[oW3 + k];
+    for (int k = threadIdx.x; k < kC; k += blockDim.x) s->b3[k] = P[oB3 + k];
+    if (threadIdx.x < 2) s->pad[threadIdx.x] = 0.0f;
+}
+
+__device__ __forceinline__ void stage_plan_params(const PlanShared* __restrict__ L, PlanShared& s)
+{
+    const float4* src = reinterpret_cast<const float4*>(L);
+    float4* dst = reinterpret_cast<float4*>(&s);
+    constexpr int n4 = kPlanLayoutFloats / 4;
+#pragma unroll 6
+    for (int k = threadIdx.x; k < n4; k += blockDim.x) dst[k] = __ldg(src + k);
     __syncthreads();
 }
 
 // The planner network for one tile by one warp (features in every lane):
 // lane l holds hidden units l and l + 32 of both layers; the logits are warp
-// sums.  Returns the argmax class (lowest on ties) in every lane.
-__device__ __forceinline__ int warp_plan(const PlanShared& P, const float (&f)[kF])
+// sums.  Returns, in every lane, the smallest class whose cumulative softmax
+// probability reaches q.
+__device__ __forceinline__ int warp_plan(const PlanShared& P, const float (&f)[kF], float q)
 {
     const int lane = threadIdx.x & 31;
     float h1[2];
@@ -154,35 +186,75 @@ __device__ __forceinline__ int warp_plan(const PlanShared& P, const float (&f)[k
             a1 = fmaf(P.W2t[i * kH + lane + 32], hi, a1);
         }
     const float h20 = fmaxf(a0, 0.0f), h21 = fmaxf(a1, 0.0f);
-    int best = 0;
-    float zbest = 0.0f;
+    float z[kC];
 #pragma unroll
     for (int c = 0; c < kC; ++c) {
-        float z = fmaf(P.W3[c * kH + lane], h20, P.W3[c * kH + lane + 32] * h21);
+        float v = fmaf(P.W3[c * kH + lane], h20, P.W3[c * kH + lane + 32] * h21);
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) z += __shfl_xor_sync(0xffffffffu, z, s);
-        z += P.b3[c];
-        if (c == 0 || z > zbest) {
-            zbest = z;
-            best = c;
-        }
+        for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+        z[c] = v + P.b3[c];
     }
-    return best;
+    float m = z[0];
+#pragma unroll
+    for (int c = 1; c < kC; ++c) m = fmaxf(m, z[c]);
+    float e[kC], sum = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kC; ++c) {
+        e[c] = expf(z[c] - m);
+        sum += e[c];
+    }
+    int cls = kC - 1;
+    float cum = 0.0f;
+#pragma unroll
+    for (int c = 0; c < kC - 1; ++c) {
+        cum += e[c];
+        if (cls == kC - 1 && cum >= q * sum) cls = c;
+    }
+    return cls;
 }
 
-// features and plan of every tile in one launch (the render path): blocks of
-// 8 warps stage the parameters once and loop over tiles, a warp per tile
-__global__ void __launch_bounds__(256) k_plan_fused(const int32_t* __restrict__ off, int K, int T,
-                                                    const float* __restrict__ params, uint8_t* __restrict__ plan)
+// First-pass bins of class c for the tile whose bin offsets start at o (K + 1
+// of them), in every lane: the fewest bins from the front holding at least
+// plan_entries(c) entries (K if the tile has fewer); K for the last class.
+__device__ __forceinline__ int warp_class_bins(const int32_t* __restrict__ o, int K, int c)
+{
+    if (c >= kC - 1) return K;
+    const int need = plan_entries(c);
+    const int lane = threadIdx.x & 31;
+    const int32_t s0 = o[0];
+    for (int j0 = 0; j0 < K; j0 += 32) {
+        const int b = j0 + lane;
+        const unsigned hit = __ballot_sync(0xffffffffu, b < K && o[b + 1] - s0 >= need);
+        if (hit) return j0 + __ffs(hit);
+    }
+    return K;
+}
+
+// Features, class and first-pass bins of every tile in one launch: blocks
+// of 8 warps stage the parameters once and loop over tiles, a warp per tile.
+// Also clears the frame's completion flags, row flags and list.
+__global__ void __launch_bounds__(256, 8) k_plan_fused(const int32_t* __restrict__ off, int K, int T,
+                                                    const PlanShared* __restrict__ params, float q,
+                                                    uint8_t* __restrict__ plan, uint8_t* __restrict__ classes,
+                                                    uint8_t* __restrict__ flag, int32_t* __restrict__ list)
 {
     __shared__ PlanShared P;
     stage_plan_params(params, P);
+    if (list && blockIdx.x == 0 && threadIdx.x == 0) list[0] = 0;
     const int warps = blockDim.x >> 5;
     for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < T; t += gridDim.x * warps) {
         float f[kF];
         warp_tile_features(off, K, t, f);
-        const int c = warp_plan(P, f);
-        if ((threadIdx.x & 31) == 0) plan[t] = (uint8_t)c;
+        const int c = warp_plan(P, f, q);
+        const int B = warp_class_bins(off + (int64_t)t * K, K, c);
+        if ((threadIdx.x & 31) == 0) {
+            plan[t] = (uint8_t)B;
+            if (classes) classes[t] = (uint8_t)c;
+            if (flag) {
+                flag[t] = 0;
+                flag[T + t] = 0;  // the row flags (tile rows <= T)
+            }
+        }
     }
 }
 
@@ -209,22 +281,6 @@ __device__ __forceinline__ void mlp_logits(const float* __restrict__ P, const fl
         float a = P[oB3 + c];
         for (int i = 0; i < kH; ++i) a = fmaf(P[oW3 + c * kH + i], h2[i], a);
         z[c] = a;
-    }
-}
-
-// inference from given features: one warp per tile
-__global__ void __launch_bounds__(256) k_plan_tiles(const float* __restrict__ params, const float* __restrict__ feat,
-                                                    int T, uint8_t* __restrict__ plan)
-{
-    __shared__ PlanShared P;
-    stage_plan_params(params, P);
-    const int warps = blockDim.x >> 5;
-    for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < T; t += gridDim.x * warps) {
-        float f[kF];
-#pragma unroll
-        for (int i = 0; i < kF; ++i) f[i] = feat[(int64_t)t * kF + i];
-        const int c = warp_plan(P, f);
-        if ((threadIdx.x & 31) == 0) plan[t] = (uint8_t)c;
     }
 }
 
@@ -366,12 +422,23 @@ extern "C" int gs_tile_features(gs_ctx* c, const gs_camera* cam, const int32_t* 
 }
 
 namespace gs {
-int plan_frame(gs_ctx* c, const int32_t* offsets, int32_t K, int32_t T, uint8_t* plan, cudaStream_t st)
+// device copy of the planner: the packed parameters, then (16-byte aligned)
+// their inference layout
+constexpr size_t kPlannerLayoutOffset = ((GS_PLAN_PARAMS + 3) / 4) * 4;
+constexpr size_t kPlannerDeviceFloats = kPlannerLayoutOffset + kPlanLayoutFloats;
+static PlanShared* planner_layout(gs_ctx* c) { return reinterpret_cast<PlanShared*>(c->d_planner + kPlannerLayoutOffset); }
+
+int plan_frame(gs_ctx* c, const int32_t* offsets, int32_t K, int32_t T, uint8_t* plan, uint8_t* classes,
+               cudaStream_t st)
 {
     if (!c->planner_ready) return GS_ERR_INVALID_ARG;
     if (T <= 0) return GS_OK;
-    const int grid = min((T + 7) / 8, c->num_sms * 4);
-    k_plan_fused<<<(unsigned)grid, 256, 0, st>>>(offsets, K, T, c->d_planner, plan);
+    // about one tile a warp: each warp's loads of its tile's offsets are one
+    // dependent chain, so parallelism over tiles, not fewer weight stagings,
+    // sets the time
+    const int grid = min((T + 7) / 8, c->num_sms * 8);
+    k_plan_fused<<<(unsigned)grid, 256, 0, st>>>(offsets, K, T, planner_layout(c), c->cfg.planner_quantile, plan, classes,
+                                                 plan + T, c->d_plist);
     c->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -388,23 +455,33 @@ extern "C" int gs_planner_set_weights(gs_ctx* c, const float* params, void* stre
     if (!c->d_planner) {
         void* p = nullptr;
         size_t cap = 0;
-        const int r = ensure(&p, &cap, GS_PLAN_PARAMS * sizeof(float));
+        const int r = ensure(&p, &cap, kPlannerDeviceFloats * sizeof(float));
         if (r != GS_OK) return r;
         c->d_planner = (float*)p;
     }
     GS_CUDA_TRY(cudaMemcpyAsync(c->d_planner, params, GS_PLAN_PARAMS * sizeof(float), cudaMemcpyDefault,
                                 (cudaStream_t)stream));
+    k_plan_layout<<<1, 256, 0, (cudaStream_t)stream>>>(c->d_planner, planner_layout(c));
+    GS_CUDA_TRY(cudaGetLastError());
+    // 20 KB of parameters per block: let as many blocks share an SM as its
+    // threads allow (the kernel's time is its tiles' load latency)
+    GS_CUDA_TRY(cudaFuncSetAttribute(k_plan_fused, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared));
     c->planner_ready = 1;
     return GS_OK;
 }
 
-extern "C" int gs_plan_tiles(gs_ctx* c, const float* features, int32_t n_tiles, uint8_t* plan, void* stream)
+extern "C" int gs_plan_tiles(gs_ctx* c, const gs_camera* cam, const int32_t* offsets, int32_t stride, uint8_t* plan,
+                             uint8_t* classes, void* stream)
 {
-    if (!c || !features || !plan || n_tiles < 0) return GS_ERR_INVALID_ARG;
+    if (!c || !cam || !offsets || !plan || stride < 1 || stride > GS_MAX_K) return GS_ERR_INVALID_ARG;
     if (!c->planner_ready) return GS_ERR_INVALID_ARG;
-    if (n_tiles == 0) return GS_OK;
-    const int grid = min((n_tiles + 7) / 8, c->num_sms * 4);
-    k_plan_tiles<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(c->d_planner, features, n_tiles, plan);
+    const int T = gs_num_tiles(cam->width, cam->height, c->cfg.tile_size);
+    if (T <= 0) return GS_ERR_INVALID_ARG;
+    const int grid = min((T + 7) / 8, c->num_sms * 8);
+    k_plan_fused<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(offsets, stride, T, planner_layout(c),
+                                                                   c->cfg.planner_quantile, plan, classes, nullptr,
+                                                                   nullptr);
     c->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;

@@ -32,6 +32,7 @@ namespace gs {
 struct PixelState {
     float T, C0, C1, C2;
     int32_t last, ntests;
+    int32_t stop;  // counting twin: stream position of the entry that stopped the pixel
     unsigned long long ops;
     bool done;
 };
@@ -89,7 +90,7 @@ __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_en
                                             RasterShared<TILE, BASELINE>& sh, const float4* __restrict__ xy_ab,
                                             const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
                                             int cullmode, int tx, int ty, float pxc, float pyc, PixelState& st,
-                                            bool checked = false)
+                                            bool checked, int32_t base)
 {
     using SH = RasterShared<TILE, BASELINE>;
     constexpr int BS = SH::BS, BATCH = SH::BATCH;
@@ -110,7 +111,10 @@ __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_en
                     const float4 gb = sh.b[k];
                     const float dx = ga.x - pxc, dy = ga.y - pyc;
                     const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
-                    if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st)) break;
+                    if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st)) {
+                        if (COUNT) st.stop = base + b0 + k;
+                        break;
+                    }
                 }
             } else {
                 // two entries a round: both q first (independent), then the
@@ -124,15 +128,21 @@ __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_en
                     const float dx1 = ga1.x - pxc, dy1 = ga1.y - pyc;
                     const float q0 = fmaf(dx0, fmaf(ga0.z, dx0, ga0.w * dy0), (gb0.x * dy0) * dy0);
                     const float q1 = fmaf(dx1, fmaf(ga1.z, dx1, ga1.w * dy1), (gb1.x * dy1) * dy1);
-                    if (composite_entry<BASELINE, COUNT>(q0, ga0, gb0, sh, k0, rgbv, st)) break;
-                    if (composite_entry<BASELINE, COUNT>(q1, ga1, gb1, sh, k1, rgbv, st)) break;
+                    if (composite_entry<BASELINE, COUNT>(q0, ga0, gb0, sh, k0, rgbv, st)) {
+                        if (COUNT) st.stop = base + b0 + k0;
+                        break;
+                    }
+                    if (composite_entry<BASELINE, COUNT>(q1, ga1, gb1, sh, k1, rgbv, st)) {
+                        if (COUNT) st.stop = base + b0 + k1;
+                        break;
+                    }
                 }
                 if (!st.done && i < nk) {
                     const int k = sh.list[warp][i];
                     const float4 ga = sh.a[k], gb = sh.b[k];
                     const float dx = ga.x - pxc, dy = ga.y - pyc;
                     const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
-                    composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st);
+                    if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st) && COUNT) st.stop = base + b0 + k;
                 }
             }
         }
@@ -149,10 +159,10 @@ struct FwdSpan {
     int cullmode, tx, ty;
     float pxc, pyc;
     PixelState& st;
-    __device__ __forceinline__ int32_t operator()(const uint64_t* src, int32_t n, bool checked = false)
+    __device__ __forceinline__ int32_t operator()(const uint64_t* src, int32_t n, bool checked, int32_t base)
     {
         return raster_span<TILE, BASELINE, COUNT>(src, n, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st,
-                                                  checked);
+                                                  checked, base);
     }
     __device__ __forceinline__ bool done() const { return st.done; }
 };
@@ -170,7 +180,7 @@ __device__ __forceinline__ void raster_tile(
     const int32_t* __restrict__ off, const RasterArgs& a, int cullmode, float* __restrict__ out_rgb,
     float* __restrict__ out_alpha, int32_t* __restrict__ out_last, int32_t* __restrict__ out_ntests,
     unsigned long long* __restrict__ ops_total, float* __restrict__ out_T, int32_t* __restrict__ out_end,
-    const uint8_t* __restrict__ plan, int default_cap, long long* __restrict__ tile_cycles)
+    const PlanView& pl, int cap)
 {
     const int tx = t % a.tiles_x, ty = t / a.tiles_x;
     const int lx = WarpBlocks<TILE>::lx(), ly = WarpBlocks<TILE>::ly();
@@ -187,22 +197,77 @@ __device__ __forceinline__ void raster_tile(
     st.C0 = st.C1 = st.C2 = 0.0f;
     st.last = -1;
     st.ntests = 0;
+    st.stop = -1;
     st.ops = 0;
     st.done = !inside;
 
-    long long c_start = 0;
-    if (tile_cycles && threadIdx.x == 0) c_start = clock64();
-    const int cap = plan ? plan_cap(plan[t]) : default_cap;
+    const int K = a.stride;
+    int kbegin = 0, kend = K;
+    if (pl.bins) {
+        const int B = min((int)pl.bins[t], K);
+        if (pl.resume) kbegin = B;
+        else kend = B;
+    }
+    const int64_t p = (int64_t)py * a.width + px;
+    if (pl.resume && inside) {
+        // the first pass's state: C in rgb, T in alpha (negative once the
+        // pixel stopped), last
+        const float Ts = out_alpha[p];
+        st.T = fabsf(Ts);
+        st.done = signbit(Ts);
+        st.C0 = out_rgb[3 * p];
+        st.C1 = out_rgb[3 * p + 1];
+        st.C2 = out_rgb[3 * p + 2];
+        st.last = out_last[p];
+    }
     FwdSpan<TILE, BASELINE, COUNT> span{sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty, pxc, pyc, st};
     // saving for the backward: the sorted chunks go back into the stream
-    const int32_t end = walk_tile<TILE, LAZY>(words, off, t, a.stride, cap, ws, span, out_end ? words : nullptr);
+    const int32_t end =
+        walk_tile<TILE, LAZY>(words, off, t, K, kbegin, kend, cap, ws, span, out_end ? words : nullptr);
     if (out_end && threadIdx.x == 0) out_end[t] = end;
-    if (tile_cycles) {
-        __syncthreads();
-        if (threadIdx.x == 0) tile_cycles[t] = clock64() - c_start;
+    bool unfinished = false;
+    if (pl.flag && kend < K) {
+        // a planned first pass: a tile with a pixel still compositing when its
+        // bins ran out, and entries in later bins, is left to the completing
+        // pass with its pixels' state in the outputs
+        const bool all_done = __syncthreads_count(st.done) == TILE * TILE;
+        unfinished = !all_done && off[(int64_t)t * K + K] > off[(int64_t)t * K + kend];
+        if (unfinished && threadIdx.x == 0) {
+            pl.flag[t] = 1;
+            pl.flag[a.n_tiles + ty] = 1;
+            pl.list[1 + atomicAdd(&pl.list[0], 1)] = t;
+        }
     }
-    if (inside) {
-        const int64_t p = (int64_t)py * a.width + px;
+    if (COUNT && pl.needed) {
+        // the bins the tile needs: through the one holding the last entry any
+        // pixel visits (a pixel that never stops visits the whole span)
+        __shared__ int32_t s_end;
+        const int32_t s0 = off[(int64_t)t * K], s1 = off[(int64_t)t * K + K];
+        if (threadIdx.x == 0) s_end = s0;
+        __syncthreads();
+        if (inside) atomicMax(&s_end, st.done ? st.stop + 1 : s1);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int need = 0;
+            if (s_end > s0) {
+                int lo = 0, hi = K - 1;  // the last bin starting at or before s_end - 1
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (off[(int64_t)t * K + mid] <= s_end - 1) lo = mid;
+                    else hi = mid - 1;
+                }
+                need = lo + 1;
+            }
+            pl.needed[t] = need;
+        }
+    }
+    if (inside && unfinished) {
+        out_rgb[3 * p] = st.C0;
+        out_rgb[3 * p + 1] = st.C1;
+        out_rgb[3 * p + 2] = st.C2;
+        out_alpha[p] = st.done ? -st.T : st.T;
+        out_last[p] = st.last;
+    } else if (inside) {
         // the image is not read again on the device: streaming stores
         __stcs(out_rgb + 3 * p, fmaf(st.T, a.bg0, st.C0));
         __stcs(out_rgb + 3 * p + 1, fmaf(st.T, a.bg1, st.C1));
@@ -210,7 +275,7 @@ __device__ __forceinline__ void raster_tile(
         __stcs(out_alpha + p, 1.0f - st.T);
         __stcs(out_last + p, st.last);
         if (out_T) out_T[p] = st.T;
-        if (COUNT) out_ntests[p] = st.ntests;
+        if (COUNT && out_ntests) out_ntests[p] = st.ntests;
     }
     if (COUNT) {
         // block reduction of the op count, one atomic per block
@@ -230,14 +295,37 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
          uint64_t* words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
          float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
          int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total, float* __restrict__ out_T,
-         int32_t* __restrict__ out_end, const uint8_t* __restrict__ plan, int default_cap,
-         long long* __restrict__ tile_cycles)
+         int32_t* __restrict__ out_end, const PlanView pl, int cap)
 {
     __shared__ RasterShared<TILE, BASELINE> sh;
     __shared__ WalkShared<LAZY> ws;
     raster_tile<TILE, BASELINE, COUNT, LAZY>(blockIdx.x, sh, ws, xy_ab, c_o_z, rgbv, words, off, a, cullmode, out_rgb,
-                                             out_alpha, out_last, out_ntests, ops_total, out_T, out_end, plan,
-                                             default_cap, tile_cycles);
+                                             out_alpha, out_last, out_ntests, ops_total, out_T, out_end, pl, cap);
+}
+
+// The completing pass of a planned frame: persistent blocks take the listed
+// tiles ({count, tiles...}) one at a time and composite each on from the bin
+// where its first pass stopped, from the pixel state that pass left.
+template <int TILE>
+__global__ void __launch_bounds__(TILE * TILE, TILE == 16 ? 5 : 1)
+k_raster_listed(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, const float4* __restrict__ rgbv,
+                uint64_t* words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
+                float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
+                float* __restrict__ out_T, int32_t* __restrict__ out_end, const uint8_t* __restrict__ plan,
+                const int32_t* __restrict__ list, int cap)
+{
+    __shared__ RasterShared<TILE, false> sh;
+    __shared__ WalkShared<true> ws;
+    PlanView pl;
+    pl.bins = plan;
+    pl.resume = 1;
+    const int32_t nl = list[0];
+    for (int32_t k = blockIdx.x; k < nl; k += gridDim.x) {
+        const int t = list[1 + k];
+        raster_tile<TILE, false, false, true>(t, sh, ws, xy_ab, c_o_z, rgbv, words, off, a, cullmode, out_rgb,
+                                              out_alpha, out_last, nullptr, nullptr, out_T, out_end, pl, cap);
+        __syncthreads();  // the next tile reuses the shared memory
+    }
 }
 
 // Several views in one persistent launch: blocks take (view, tile) work items
@@ -321,7 +409,7 @@ k_raster_views(const __grid_constant__ ViewRasterSet vs, const int32_t* __restri
         const ViewRasterSet::View& V = vs.v[view_of(vs, item)];
         raster_tile<TILE, false, false, LAZY>(item - V.item0, sh, ws, V.xy_ab, V.c_o_z, V.rgbv, V.words, V.off, V.a,
                                               V.cullmode, V.rgb, V.alpha, V.last, nullptr, nullptr, nullptr, nullptr,
-                                              nullptr, V.cap, nullptr);
+                                              PlanView(), V.cap);
     }
 }
 
@@ -329,13 +417,12 @@ template <int TILE>
 static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cudaStream_t st, const ProjView& pv,
                         uint64_t* words, const int32_t* off, const RasterArgs& a, int cull, float* rgb,
                         float* alpha, int32_t* last, int32_t* ntests, unsigned long long* ops, float* final_T,
-                        int32_t* tile_end, const uint8_t* plan, int cap, long long* cycles)
+                        int32_t* tile_end, const PlanView& pl, int cap)
 {
     constexpr int BS = TILE * TILE;
 #define GS_RASTER_LAUNCH(B, CNT, LZ)                                                                        \
     k_raster<TILE, B, CNT, LZ><<<grid, BS, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, (B) ? 0 : cull, \
-                                                   rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap,     \
-                                                   cycles)
+                                                   rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap)
     if (baseline) {
         if (count) GS_RASTER_LAUNCH(true, true, false);
         else GS_RASTER_LAUNCH(true, false, false);
@@ -352,7 +439,7 @@ static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cud
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T, int32_t* tile_end,
-               const uint8_t* plan, long long* tile_cycles)
+               const PlanView& pl)
 {
     const int tile = ctx->cfg.tile_size;
     RasterArgs a;
@@ -365,7 +452,7 @@ int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* 
     a.bg1 = bg[1];
     a.bg2 = bg[2];
     const int cull = ctx->cfg.tile_cull ? 1 : 0;
-    const bool count = ntests != nullptr;
+    const bool count = ntests != nullptr || pl.needed != nullptr;
     const bool lazy = !baseline && ctx->cfg.mode == GS_MODE_BINNED_EXACT && ctx->cfg.repair_in_raster;
     // EXACT streams are culled when they are built: no second tile test at
     // staging, only the per-warp strip mask
@@ -376,9 +463,37 @@ int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* 
     unsigned long long* ops = reinterpret_cast<unsigned long long*>(ctx->d_ops);
     if (count) GS_CUDA_TRY(cudaMemsetAsync(ops, 0, sizeof(unsigned long long), st));
     switch (tile) {
-        case 8: launch_tile<8>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap, tile_cycles); break;
-        case 32: launch_tile<32>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap, tile_cycles); break;
-        default: launch_tile<16>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, plan, cap, tile_cycles); break;
+        case 8: launch_tile<8>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
+        case 32: launch_tile<32>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
+        default: launch_tile<16>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
+    }
+    ctx->launches += 1;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int raster_listed(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* words, const int32_t* offsets,
+                  int32_t stride, const float* bg, float* rgb, float* alpha, int32_t* last, const uint8_t* plan,
+                  const int32_t* list, cudaStream_t st, float* final_T, int32_t* tile_end)
+{
+    const int tile = ctx->cfg.tile_size;
+    RasterArgs a;
+    a.width = cam->width;
+    a.height = cam->height;
+    a.tiles_x = (cam->width + tile - 1) / tile;
+    a.n_tiles = gs_num_tiles(cam->width, cam->height, tile);
+    a.stride = stride;
+    a.bg0 = bg[0];
+    a.bg1 = bg[1];
+    a.bg2 = bg[2];
+    if (a.n_tiles == 0) return GS_OK;
+    // EXACT streams are culled when built: the strip mask only
+    const int cull = ctx->cfg.tile_cull ? 2 : 0;
+    const int cap = chunk_cap(ctx->cfg);
+    switch (tile) {
+        case 8: k_raster_listed<8><<<(unsigned)ctx->num_sms, 64, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, offsets, a, cull, rgb, alpha, last, final_T, tile_end, plan, list, cap); break;
+        case 32: k_raster_listed<32><<<(unsigned)ctx->num_sms, 1024, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, offsets, a, cull, rgb, alpha, last, final_T, tile_end, plan, list, cap); break;
+        default: k_raster_listed<16><<<(unsigned)ctx->num_sms * 5, 256, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, offsets, a, cull, rgb, alpha, last, final_T, tile_end, plan, list, cap); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());

@@ -151,9 +151,13 @@ struct WalkShared {
 };
 
 // Load the chunk [c0, c0 + len) (bins bfirst..e-1) into ws.sort and sort each
-// of its segments by (depth bits, gid): segments of up to 64 entries in
-// registers by one warp, up to 256 in shared memory by one warp, longer ones by
-// the whole block.  ws.big[base..] collects the long ones.
+// of its segments by (depth bits, gid).  A chunk of at most one entry per
+// thread is sorted by rank: each thread counts the smaller words of its own
+// segment (the words are distinct, their low half being the gid), so one
+// pass of comparisons and one scatter place every word.  Longer chunks: each
+// segment of up to 64 entries in registers by one warp, up to 256 in shared
+// memory by one warp, longer ones by the whole block (ws.big[base..] collects
+// the long ones).
 template <int TILE, bool LAZY>
 __device__ __forceinline__ void load_sort_chunk(const uint64_t* words, int32_t c0, int32_t len,
                                                 int bfirst, int e, WalkShared<LAZY>& ws, int base = 0)
@@ -161,6 +165,31 @@ __device__ __forceinline__ void load_sort_chunk(const uint64_t* words, int32_t c
     constexpr int BS = TILE * TILE;
     constexpr int NWB = BS / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (len <= BS) {
+        // one entry a thread: its rank in its segment is the segment start
+        // plus the number of smaller words there (words are unique: gid)
+        const int i = threadIdx.x;
+        uint64_t key = 0;
+        if (i < len) key = __ldcs(reinterpret_cast<const unsigned long long*>(words) + c0 + i);
+        if (i < len) ws.sort[i] = key;
+        __syncthreads();
+        int r = 0;
+        if (i < len) {
+            int lo = bfirst, hi = e - 1;  // the last bin starting at or before i
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (ws.off[mid] - c0 <= i) lo = mid;
+                else hi = mid - 1;
+            }
+            const int s0 = ws.off[lo] - c0, s1 = ws.off[lo + 1] - c0;
+            r = s0;
+            for (int j = s0; j < s1; ++j) r += ws.sort[j] < key ? 1 : 0;
+        }
+        __syncthreads();
+        if (i < len) ws.sort[r] = key;
+        __syncthreads();
+        return;
+    }
     // the stream is read once: streamed past L2 (evict first)
     for (int i = threadIdx.x; i < len; i += BS)
         ws.sort[i] = __ldcs(reinterpret_cast<const unsigned long long*>(words) + c0 + i);
@@ -191,38 +220,41 @@ __device__ __forceinline__ void load_sort_chunk(const uint64_t* words, int32_t c
 }
 
 // Walk tile t's span of the stream front to back, handing runs of entries to
-// span(src, n) (returns -1 after consuming all n, or, block-uniformly, the
-// offset within the run at which every pixel of the tile had terminated;
-// span.done() is the calling thread's termination flag).
-// Not LAZY: one run, the span [off[t*K], off[(t+1)*K]).  LAZY: chunks of
+// span(src, n, checked, base) (src[0] is stream position base; returns -1
+// after consuming all n, or, block-uniformly, the offset within the run at
+// which every pixel of the tile had terminated; span.done() is the calling
+// thread's termination flag).  Only bins [kbegin, kend) of the tile's K are
+// walked (a planned frame's passes; 0, K: the whole span).
+// Not LAZY: one run, [off[t*K], off[t*K + kend]).  LAZY: chunks of
 // consecutive segments of at most `cap` entries (a single segment of up to
 // kRasterSortCap entries forms a chunk of its own) are loaded into shared
-// memory and every segment of the chunk is sorted (small ones by one warp
-// each, long ones by the whole block); a segment longer than kRasterSortCap
-// was sorted before the raster and is handed over in place.  The chunks are
-// the tile's repair bins: `cap` sets their count and their split depths (the
-// bin boundaries where a chunk ends).
-// Returns the stream index at which the walk ended: the tile's span end, or
-// the position (in the composited order) where every pixel had terminated.
-// With writeback (the stream itself), every sorted chunk is also stored back
-// in place, so the tile's composited prefix is left in (depth, gid) order.
+// memory and every segment of the chunk is sorted; a segment longer than
+// kRasterSortCap was sorted before the raster and is handed over in place.
+// The chunks are the tile's repair bins.  ws.off holds all K + 1 bin offsets
+// of the tile on return (LAZY).
+// Returns the stream index at which the walk ended: the end of the walked
+// bins, or the position (in the composited order) where every pixel had
+// terminated.  With writeback (the stream itself), every sorted chunk is also
+// stored back in place, so the tile's composited prefix is left in (depth,
+// gid) order.
 template <int TILE, bool LAZY, class Span>
 __device__ __forceinline__ int32_t walk_tile(const uint64_t* words, const int32_t* __restrict__ off, int t, int K,
-                                             int cap, WalkShared<LAZY>& ws, Span& span, uint64_t* writeback = nullptr)
+                                             int kbegin, int kend, int cap, WalkShared<LAZY>& ws, Span& span,
+                                             uint64_t* writeback = nullptr)
 {
     constexpr int BS = TILE * TILE;
     if (!LAZY) {
-        const int32_t s0 = off[(int64_t)t * K], s1 = off[(int64_t)(t + 1) * K];
-        const int32_t r = span(words + s0, s1 - s0);
+        const int32_t s0 = off[(int64_t)t * K + kbegin], s1 = off[(int64_t)t * K + kend];
+        const int32_t r = span(words + s0, s1 - s0, false, s0);
         return r < 0 ? s1 : s0 + r;
     }
     for (int b = threadIdx.x; b <= K; b += BS) ws.off[b] = off[(int64_t)t * K + b];
     __syncthreads();
-    int b = 0;
-    while (b < K) {
+    int b = kbegin;
+    while (b < kend) {
         const int32_t c0 = ws.off[b];
         if (ws.off[b + 1] - c0 > kRasterSortCap) {  // sorted before the raster
-            const int32_t r = span(words + c0, ws.off[b + 1] - c0);
+            const int32_t r = span(words + c0, ws.off[b + 1] - c0, false, c0);
             if (r >= 0) return c0 + r;
             ++b;
             continue;
@@ -233,9 +265,9 @@ __device__ __forceinline__ int32_t walk_tile(const uint64_t* words, const int32_
         int e = b + 1;
         {
             const int lane = threadIdx.x & 31;
-            for (int j0 = b + 1; j0 < K; j0 += 32) {
+            for (int j0 = b + 1; j0 < kend; j0 += 32) {
                 const int j = j0 + lane;
-                const int fit = __popc(__ballot_sync(0xffffffffu, j < K && ws.off[j + 1] - c0 <= cap));
+                const int fit = __popc(__ballot_sync(0xffffffffu, j < kend && ws.off[j + 1] - c0 <= cap));
                 e += fit;
                 if (fit < 32) break;
             }
@@ -248,10 +280,10 @@ __device__ __forceinline__ int32_t walk_tile(const uint64_t* words, const int32_
         load_sort_chunk<TILE>(words, c0, len, bfirst, e, ws);  // ends with a block barrier
         if (writeback)
             for (int i = threadIdx.x; i < len; i += BS) writeback[c0 + i] = ws.sort[i];
-        const int32_t r = span(ws.sort, len, true);  // termination just counted above
+        const int32_t r = span(ws.sort, len, true, c0);  // termination just counted above
         if (r >= 0) return c0 + r;
     }
-    return ws.off[K];
+    return ws.off[kend];
 }
 
 // The walk of walk_tile in reverse over the entries before stream index

@@ -286,9 +286,10 @@ __global__ void __launch_bounds__(256)
 k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ rs_w,
                    const uint32_t* __restrict__ rs_z, const int32_t* __restrict__ roff, int64_t n, int tiles_x, int K,
                    const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ cur,
-                   uint64_t* __restrict__ words)
+                   uint64_t* __restrict__ words, const ScatterPass sp, const int32_t* __restrict__ flagged)
 {
     if (*m_dev > m_cap) return;
+    if (sp.pass == 2 && flagged[0] == 0) return;  // no tile to complete
     const int64_t R = roff[n];
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (R + 31) / 32;
@@ -296,11 +297,14 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
     for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += wstride) {
         const int64_t k = c * 32 + lane;
         uint32_t w = 0, g = 0, ya = 0, z = 0;
-        if (k < R) {  // read once: streamed past L2
-            w = __ldcs(rs_w + k);
-            g = __ldcs(rs_g + k);
+        if (k < R) {  // read once: streamed past L2 (a planned first pass reads them again later)
             ya = __ldcs(rs_ya + k);
-            z = __ldcs(rs_z + k);
+            if (sp.row_live((int)(ya & 0xfffu))) {  // the completing pass skips rows with no flagged tile
+                w = __ldcs(rs_w + k);
+                g = __ldcs(rs_g + k);
+                z = __ldcs(rs_z + k);
+                sp.trim(ya, w, tiles_x);  // a planned pass: only the tiles it keeps
+            }
         }
         // inclusive prefix of the widths across the warp
         uint32_t incl = w;
@@ -331,15 +335,30 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
                 live[u] = e < total;
                 if (live[u]) {
                     const int ty = (int)(oya & 0xfffu), tx = (int)((oya >> 12) & 0xfffu) + (int)(e - oex);
-                    const int64_t qi = ((int64_t)ty * tiles_x + tx) * K + (oya >> 24);
-                    p[u] = atomicAdd(&cur[qi], 1);
-                    word[u] = ((uint64_t)oz << 32) | og;
+                    const int64_t t = (int64_t)ty * tiles_x + tx;
+                    live[u] = sp.keep(t, (int)(oya >> 24));
+                    if (live[u]) {
+                        p[u] = atomicAdd(&cur[t * K + (oya >> 24)], 1);
+                        word[u] = ((uint64_t)oz << 32) | og;
+                    }
                 }
             }
 #pragma unroll
             for (int u = 0; u < kScatterInFlight; ++u)
                 if (live[u]) words[p[u]] = word[u];
         }
+    }
+}
+
+// The completing pass's cursors: those of every flagged tile start at its
+// segment offsets (the first pass placed none of the bins it leaves).
+__global__ void k_flagged_cursors(const int32_t* __restrict__ list, const int32_t* __restrict__ offsets, int K,
+                                  int32_t* __restrict__ cur)
+{
+    const int32_t nl = list[0];
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nl * K; i += gridDim.x * blockDim.x) {
+        const int64_t q = (int64_t)list[1 + i / K] * K + i % K;
+        cur[q] = offsets[q];
     }
 }
 
@@ -372,7 +391,8 @@ __device__ __forceinline__ int group_key(uint32_t ya, int K) { return (int)(ya &
 // pass 1: H[key * C + c] = non-empty records of slice c with that key
 __global__ void __launch_bounds__(kGroupThreads)
 k_group_count(const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ rs_w, const int32_t* __restrict__ roff,
-              int64_t n, int K, int nkeys, const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ H)
+              int64_t n, int K, int nkeys, const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ H,
+              const ScatterPass sp, int tiles_x)
 {
     extern __shared__ int32_t s_h[];
     const int C = gridDim.x, c = blockIdx.x;
@@ -381,8 +401,11 @@ k_group_count(const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ r
     if (*m_dev <= m_cap) {
         int64_t r0, r1;
         record_slice(roff[n], C, c, &r0, &r1);
-        for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x)
-            if (rs_w[k] != 0u) atomicAdd(&s_h[group_key(rs_ya[k], K)], 1);
+        for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
+            uint32_t w = rs_w[k], ya = rs_ya[k];
+            sp.trim(ya, w, tiles_x);
+            if (w != 0u) atomicAdd(&s_h[group_key(ya, K)], 1);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < nkeys; i += blockDim.x) H[(int64_t)i * C + c] = s_h[i];
@@ -395,7 +418,7 @@ __global__ void __launch_bounds__(kGroupThreads)
 k_group_write(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya,
               const uint32_t* __restrict__ rs_w, const uint32_t* __restrict__ rs_z, const int32_t* __restrict__ roff,
               int64_t n, int K, int nkeys, const int64_t* __restrict__ m_dev, int64_t m_cap,
-              const int32_t* __restrict__ Hs, uint4* __restrict__ list)
+              const int32_t* __restrict__ Hs, uint4* __restrict__ list, const ScatterPass sp, int tiles_x)
 {
     extern __shared__ int32_t s_h[];  // [nkeys] next slot, from the slice's base
     const int C = gridDim.x, c = blockIdx.x;
@@ -405,9 +428,9 @@ k_group_write(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs
     int64_t r0, r1;
     record_slice(roff[n], C, c, &r0, &r1);
     for (int64_t k = r0 + threadIdx.x; k < r1; k += blockDim.x) {
-        const uint32_t w = rs_w[k];
+        uint32_t w = rs_w[k], ya = rs_ya[k];
+        sp.trim(ya, w, tiles_x);
         if (w == 0u) continue;
-        const uint32_t ya = rs_ya[k];
         list[atomicAdd(&s_h[group_key(ya, K)], 1)] = make_uint4(rs_g[k], ya, w, rs_z[k]);
     }
 }
@@ -420,21 +443,30 @@ constexpr int kScatterGroupThreads = 1024;
 __global__ void __launch_bounds__(kScatterGroupThreads)
 k_scatter_groups(const uint4* __restrict__ list, const int32_t* __restrict__ Hs, int C,
                  const int32_t* __restrict__ offsets, int tiles_x, int K, const int64_t* __restrict__ m_dev,
-                 int64_t m_cap, uint64_t* __restrict__ words)
+                 int64_t m_cap, uint64_t* __restrict__ words, const ScatterPass sp,
+                 const int32_t* __restrict__ flagged)
 {
     extern __shared__ int32_t s_cur[];  // [tiles_x]
     const int key = blockIdx.x;
     if (*m_dev > m_cap) return;
+    if (sp.pass == 2 && flagged[0] == 0) return;  // no tile to complete
     const int ty = key / K, b = key - ty * K;
     const int32_t L0 = Hs[(int64_t)key * C], L1 = Hs[(int64_t)(key + 1) * C];
     if (L1 <= L0) return;
-    for (int x = threadIdx.x; x < tiles_x; x += blockDim.x) s_cur[x] = offsets[((int64_t)ty * tiles_x + x) * K + b];
-    __syncthreads();
+    int any = 0;
+    for (int x = threadIdx.x; x < tiles_x; x += blockDim.x) {
+        const int64_t t = (int64_t)ty * tiles_x + x;
+        s_cur[x] = offsets[t * K + b];
+        any |= sp.keep(t, b) ? 1 : 0;
+    }
+    // a planned pass skips the groups no tile of the row takes in this pass
+    if (!__syncthreads_or(any)) return;
     for (int32_t i = L0 + (int32_t)threadIdx.x; i < L1; i += (int32_t)blockDim.x) {
         const uint4 rec = list[i];
         const uint64_t word = ((uint64_t)rec.w << 32) | rec.x;
         const int a = (int)((rec.y >> 12) & 0xfffu);
         for (int j = 0; j < (int)rec.z; ++j) {
+            if (!sp.keep((int64_t)ty * tiles_x + a + j, b)) continue;
             const int32_t slot = atomicAdd(&s_cur[a + j], 1);
             words[slot] = word;
         }
@@ -587,8 +619,69 @@ int exact_bins_reserve(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t tiles_x, i
     return r;
 }
 
+// The record scatter of the tile-cull path, for one pass (grouped by (tile
+// row, bin) on deep frames, else per-entry global cursors, `cur` being
+// initialised from the offsets before the first pass).
+static int exact_scatter(gs_ctx* ctx, const ExactScratch& v, int64_t n, int32_t tiles_x, int32_t tiles_y, int K,
+                         int64_t m_cap, const int64_t* m_dev, uint64_t* words, const int32_t* offsets,
+                         const ScatterPass& sp, cudaStream_t st)
+{
+    const int64_t T = (int64_t)tiles_x * tiles_y;
+    const int nkeys = tiles_y * K;
+    const unsigned g_sm = (unsigned)ctx->num_sms * 8;
+    const int32_t* flagged = sp.pass ? ctx->d_plist : nullptr;
+    if (n <= 0) return GS_OK;
+    if (sp.pass != 2 && grouped_scatter(m_cap, T) && nkeys <= kMaxGroupKeys) {
+        // records grouped by (tile row, bin), then cursors in shared memory
+        // (a planned first pass groups only the records it keeps)
+        const int C = group_slices(ctx->num_sms);
+        const size_t hsm = (size_t)nkeys * 4;
+        k_group_count<<<(unsigned)C, kGroupThreads, hsm, st>>>(v.rs_ya, v.rs_w, v.roff, n, K, nkeys, m_dev, m_cap,
+                                                                v.H, sp, tiles_x);
+        ctx->launches += 1;
+        int r;
+        if ((r = scan_impl(ctx, LoadI32{v.H}, (int64_t)nkeys * C, v.Hs, nullptr, st)) != GS_OK) return r;
+        k_group_write<<<(unsigned)C, kGroupThreads, hsm, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, K, nkeys,
+                                                                m_dev, m_cap, v.Hs, v.list, sp, tiles_x);
+        k_scatter_groups<<<(unsigned)nkeys, kScatterGroupThreads, (size_t)tiles_x * 4, st>>>(
+            v.list, v.Hs, C, offsets, tiles_x, K, m_dev, m_cap, words, sp, flagged);
+        ctx->launches += 2;
+    } else {
+        // per-entry cursors in global memory: all of them from the offsets
+        // before a first pass, those of the flagged tiles before the
+        // completing pass (few entries: no grouping)
+        if (sp.pass != 2) {
+            GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)T * K * 4, cudaMemcpyDeviceToDevice, st));
+        } else {
+            k_flagged_cursors<<<(unsigned)ctx->num_sms * 2, 256, 0, st>>>(flagged, offsets, K, v.cur);
+            ctx->launches += 1;
+        }
+        k_bin_scatter_rows<<<g_sm * 2, 256, 0, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, tiles_x, K, m_dev,
+                                                     m_cap, v.cur, words, sp, flagged);
+        ctx->launches += 1;
+    }
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}
+
+int exact_scatter_rest(gs_ctx* ctx, int64_t n, const gs_camera* cam, int64_t m_cap, const int64_t* m_dev,
+                       uint64_t* words, const int32_t* offsets, cudaStream_t st)
+{
+    const int tile = ctx->cfg.tile_size, K = ctx->cfg.K;
+    const int32_t tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
+    ExactScratch v;
+    exact_scratch(ctx, n, m_cap, tiles_x, tiles_y, K, &v);
+    v.roff = ctx->exact_roff;  // the first pass's row records (the fused scan's offsets on the render path)
+    ScatterPass sp;
+    sp.plan = ctx->d_plan;
+    sp.T = tiles_x * tiles_y;
+    sp.pass = 2;
+    return exact_scatter(ctx, v, n, tiles_x, tiles_y, K, m_cap, m_dev, words, offsets, sp, st);
+}
+
 int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, bool goff_ready, int64_t m_cap,
-               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st, bool rows_ready)
+               const int64_t* m_dev, uint64_t* words, int32_t* offsets, cudaStream_t st, bool rows_ready,
+               bool planned)
 {
     const int tile = ctx->cfg.tile_size, K = ctx->cfg.K;
     const int32_t tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
@@ -625,26 +718,17 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
         if ((r = scan_impl(ctx, LoadPlainCount{v.cur}, nseg, offsets, nullptr, st)) != GS_OK) return r;
         k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1, ctx->d_err);
         ctx->launches += 1;
-        const int nkeys = tiles_y * K;
-        if (n > 0 && grouped_scatter(m_cap, T) && nkeys <= kMaxGroupKeys) {
-            // records grouped by (tile row, bin), then cursors in shared memory
-            const int C = group_slices(ctx->num_sms);
-            const size_t hsm = (size_t)nkeys * 4;
-            k_group_count<<<(unsigned)C, kGroupThreads, hsm, st>>>(v.rs_ya, v.rs_w, v.roff, n, K, nkeys, m_dev, m_cap,
-                                                                    v.H);
-            ctx->launches += 1;
-            if ((r = scan_impl(ctx, LoadI32{v.H}, (int64_t)nkeys * C, v.Hs, nullptr, st)) != GS_OK) return r;
-            k_group_write<<<(unsigned)C, kGroupThreads, hsm, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, K,
-                                                                    nkeys, m_dev, m_cap, v.Hs, v.list);
-            k_scatter_groups<<<(unsigned)nkeys, kScatterGroupThreads, (size_t)tiles_x * 4, st>>>(
-                v.list, v.Hs, C, offsets, tiles_x, K, m_dev, m_cap, words);
-            ctx->launches += 2;
-        } else if (n > 0) {
-            GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)nseg * 4, cudaMemcpyDeviceToDevice, st));
-            k_bin_scatter_rows<<<g_sm * 2, 256, 0, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, tiles_x, K,
-                                                         m_dev, m_cap, v.cur, words);
-            ctx->launches += 1;
+        ScatterPass sp;
+        if (planned) {
+            ctx->exact_roff = v.roff;
+            // the bin planner sets each tile's first-pass bins from the counts
+            if ((r = plan_frame(ctx, offsets, K, (int32_t)T, ctx->d_plan, nullptr, st)) != GS_OK) return r;
+            sp.plan = ctx->d_plan;
+            sp.T = (int32_t)T;
+            sp.pass = 1;
         }
+        if ((r = exact_scatter(ctx, v, n, tiles_x, tiles_y, K, m_cap, m_dev, words, offsets, sp, st)) != GS_OK)
+            return r;
     } else {
         // whole rects per bin layer: four atomics per Gaussian, 2D prefix sums
         if (!goff_ready && (r = count_scan(ctx, pv, n, v.total, st)) != GS_OK) return r;

@@ -4,21 +4,24 @@ Data (one "render" = one seeded scene and camera, EXACT mode, K = 64):
   * the frame's binned stream is built once (projection, tile intersection,
     depth range, bins);
   * gs_tile_features gives each tile's 8 features;
-  * the raster runs once per chunk class c = 0..5 with every tile forced to c
-    (gs_rasterize_fwd_plan) and records each tile's clock64() cycles, `reps`
-    times; the label of a tile is the class of its smallest median cycles
-    (softmax cross entropy on these labels saved more cycles on a held-out
-    split than an expected-cost loss or labels that keep the default class
-    within a few percent).
-Training: mini-batch Adam on the GPU, entirely through the library's own
-kernels (gs_mlp_forward, gs_mlp_loss_grad, gs_mlp_backward, gs_adam_step).
-Feature standardisation is folded into the first layer afterwards, so the
-inference kernel takes raw features.
+  * the counting raster (gs_rasterize_fwd_plan) logs each tile's bins
+    needed: 1 + the bin holding the last entry any of its pixels visits;
+  * the label of a tile is the smallest class whose first-pass bins (class
+    c < 5: the fewest bins from the front holding 64 << c entries; class 5:
+    all) cover the bins it needs.
+Training: mini-batch Adam on softmax cross entropy, on the GPU, entirely
+through the library's own kernels (gs_mlp_forward, gs_mlp_loss_grad,
+gs_mlp_backward, gs_adam_step).  Feature standardisation is folded into the
+first layer afterwards, so the inference kernel takes raw features.  At
+inference the planner takes the smallest class whose cumulative probability
+reaches cfg.planner_quantile.
 
     python -m paper_2609_03613_gb300.planner_train --out planner_weights.npy
 
-writes the float32 parameters (GS_PLAN_PARAMS values) and prints a summary.
-The committed `planner_weights.npy` next to this file was written this way.
+writes the float32 parameters (GS_PLAN_PARAMS values) and prints a summary,
+with a held-out evaluation of whole frames (planned against every bin in one
+pass).  The committed `planner_weights.npy` next to this file was written
+this way.
 """
 from __future__ import annotations
 
@@ -37,11 +40,18 @@ WEIGHTS = os.path.join(HERE, "planner_weights.npy")
 
 
 def training_renders(n_scenes, views_per_scene, scene_seed0, cam_seed0, sizes=(300_000, 600_000, 1_000_000)):
-    """(scene, camera) pairs: scenes of the mid workload's distribution, cameras
-    on spheres around them with resolutions 512^2 .. 1080p."""
+    """(scene, camera) pairs: scenes of the mid workload's distribution, half
+    the cameras on spheres around them (resolutions 512^2 .. 1080p), half
+    inside one of their dense clusters (deep tiles, like the heavy
+    workloads)."""
     for i in range(n_scenes):
-        sc = scenes.mixture_scene(sizes[i % len(sizes)], scene_seed0 + i)
-        for cam in scenes.batch_cameras(views_per_scene, cam_seed0 + 97 * i):
+        seed = scene_seed0 + i
+        sc = scenes.mixture_scene(sizes[i % len(sizes)], seed)
+        cams = scenes.batch_cameras(views_per_scene - views_per_scene // 2, cam_seed0 + 97 * i)
+        for j in range(views_per_scene // 2):
+            w, h = scenes.BATCH_RESOLUTIONS[(i + j) % len(scenes.BATCH_RESOLUTIONS)]
+            cams.append(scenes.heavy_camera(seed, cam_seed0 + 97 * i + 50 + j, w, h, w * (1100.0 / 1920.0)))
+        for cam in cams:
             yield sc, cam
 
 
@@ -52,38 +62,52 @@ def frame(ctx, ds, cam):
     return proj, words, offsets
 
 
-def log_tiles(ctx, ds, cam, reps=3):
-    """features [T][8] (numpy) and median cycles [T][6] (numpy) of one render."""
+def class_bins(off, K, c):
+    """First-pass bins of class c for every tile (off: [T*K + 1] numpy)."""
+    T = (len(off) - 1) // K
+    if c >= G.PLAN_CLASSES - 1:
+        return np.full(T, K, np.int64)
+    o = off[:T * K + 1].astype(np.int64)
+    cum = o[1:].reshape(T, K) - o[0:T * K:K][:, None]
+    hit = cum >= (64 << c)
+    return np.where(hit.any(axis=1), np.argmax(hit, axis=1) + 1, K)
+
+
+def labels_of(needed, off, K):
+    """Smallest class whose first-pass bins cover each tile's bins needed."""
+    y = np.full(len(needed), G.PLAN_CLASSES - 1, np.int64)
+    for c in range(G.PLAN_CLASSES - 2, -1, -1):
+        y = np.where(class_bins(off, K, c) >= needed, c, y)
+    return y
+
+
+def log_tiles(ctx, ds, cam):
+    """features [T][8], labels [T] and offsets (numpy) of one render."""
     import torch
     proj, words, offsets = frame(ctx, ds, cam)
     feat = ctx.tile_features(cam, offsets)
-    T = feat.shape[0]
-    cyc = np.zeros((reps, G.PLAN_CLASSES, T))
-    for r in range(reps):
-        for c in range(G.PLAN_CLASSES):
-            plan = torch.full((T,), c, dtype=torch.uint8, device=feat.device)
-            _, _, _, cy = ctx.rasterize_fwd_plan(proj, ds.n, cam, words, offsets, plan=plan, cycles=True)
-            cyc[r, c] = cy.cpu().numpy()
+    needed = ctx.rasterize_fwd_plan(proj, ds.n, cam, words, offsets, needed=True)[4]
     torch.cuda.synchronize()
-    return feat.cpu().numpy(), np.median(cyc, axis=0).T
+    off = offsets.cpu().numpy().astype(np.int64)
+    return feat.cpu().numpy(), labels_of(needed.cpu().numpy(), off, ctx.stride), off
 
 
-def collect(renders, reps=3):
+def collect(renders):
     import torch
     ctx = G.Context("exact")
-    feats, cycles = [], []
+    feats, labels = [], []
     last_sc, ds = None, None
     for sc, cam in renders:
         if sc is not last_sc:
             ds = G.DeviceScene.from_numpy(sc)
             last_sc = sc
-        f, c = log_tiles(ctx, ds, cam, reps)
+        f, y, _ = log_tiles(ctx, ds, cam)
         keep = f[:, 0] > 0.0  # tiles with entries
         feats.append(f[keep])
-        cycles.append(c[keep])
+        labels.append(y[keep])
     assert ctx.error() == 0
     torch.cuda.synchronize()
-    return np.concatenate(feats), np.concatenate(cycles)
+    return np.concatenate(feats), np.concatenate(labels)
 
 
 def init_params(seed):
@@ -134,47 +158,50 @@ def train(X, y, epochs=20, batch=4096, lr=3e-3, seed=0):
     return fold_standardisation(P.cpu().numpy(), mu, sd), hist
 
 
-def labels_of(cycles, default_class=2, margin=0.0):
-    """argmin class per tile; with margin > 0, tiles whose best class is within
-    `margin` of the default's cycles keep the default."""
-    best = np.argmin(cycles, axis=1)
-    dflt = cycles[:, default_class]
-    keep_default = cycles[np.arange(len(best)), best] >= (1.0 - margin) * dflt
-    return np.where(keep_default, default_class, best)
-
-
-def evaluate(params, renders, iters=20):
-    """Raster ms per render with the planner's per-tile plan and with the
-    fixed chunk size (every tile class 2 = the default 256 entries), on the
-    same stream; images compared bit for bit.  Returns a list of
-    (fixed_ms, planned_ms)."""
+def evaluate(params, renders, iters=10, q=0.9):
+    """Whole frames (gs_render, un-captured, stage events) of each held-out
+    render with the planner (two passes) and with every bin in one pass;
+    images compared bit for bit.  Returns per render a dict of frame and
+    bin-stage ms for both, and the tiles the planner left to the second
+    pass."""
     import torch
-    ctx = G.Context("exact")
-    ctx.set_planner_weights(torch.from_numpy(params))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    fixed = G.Context("exact")
+    planned = G.Context("exact", planner=1, planner_quantile=q)
+    planned.set_planner_weights(torch.from_numpy(params))
     out = []
     last_sc, ds = None, None
     for sc, cam in renders:
         if sc is not last_sc:
             ds = G.DeviceScene.from_numpy(sc)
             last_sc = sc
-        proj, words, offsets = frame(ctx, ds, cam)
-        plan = ctx.plan_tiles(ctx.tile_features(cam, offsets))
-        ref = ctx.rasterize_fwd_plan(proj, ds.n, cam, words, offsets)
-        got = ctx.rasterize_fwd_plan(proj, ds.n, cam, words, offsets, plan=plan)
-        assert all(torch.equal(a, b) for a, b in zip(ref[:3], got[:3]))
-        ms = []
-        for p in (None, plan):
-            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
+        a = fixed.render(ds, cam)
+        b = planned.render(ds, cam)
+        torch.cuda.synchronize()
+        assert all(torch.equal(x, y) for x, y in zip(a, b))
+        r = {}
+        for name, ctx in (("fixed", fixed), ("planned", planned)):
+            ctx.enable_timing(True)
+            ev, st = [], {}
             for i in range(iters):
                 flush.zero_()
-                ev[i][0].record()
-                ctx.rasterize_fwd_plan(proj, ds.n, cam, words, offsets, plan=p)
-                ev[i][1].record()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                ctx.render(ds, cam, flags=G.RENDER_NO_SYNC)
+                e1.record()
+                for k, v in ctx.stage_times().items():
+                    st.setdefault(k, []).append(v)
+                ev.append((e0, e1))
             torch.cuda.synchronize()
-            ms.append(float(np.median([a.elapsed_time(b) for a, b in ev])))
-        out.append(tuple(ms))
-    assert ctx.error() == 0
+            fr = [a.elapsed_time(b) for a, b in ev]
+            ctx.enable_timing(False)
+            r[name] = {"frame_ms": float(np.median(fr)), "bin_ms": float(np.median(st["bin"])),
+                       "complete_ms": float(np.median(st["complete"]))}
+        T = G.n_tiles(cam.width, cam.height, 16)
+        r["flagged"] = int(planned.flagged_tiles())
+        r["tiles"] = T
+        out.append(r)
+    assert fixed.error() == 0 and planned.error() == 0
     return out
 
 
@@ -183,32 +210,26 @@ def main():
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--scenes", type=int, default=20)
     ap.add_argument("--views", type=int, default=10)
-    ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--epochs", type=int, default=20)
-    ap.add_argument("--dump", default=None, help="npz of a 300k-tile sample of the logged data")
+    ap.add_argument("--quantile", type=float, default=0.9)
     args = ap.parse_args()
     t0 = time.time()
-    X, cyc = collect(training_renders(args.scenes, args.views, 7000, 20000), args.reps)
+    X, y = collect(training_renders(args.scenes, args.views, 7000, 20000))
     t1 = time.time()
-    y = labels_of(cyc)
     params, hist = train(X, y, epochs=args.epochs)
     t2 = time.time()
     np.save(args.out, params)
-    if args.dump:
-        rng = np.random.Generator(np.random.PCG64(1))
-        sel = rng.choice(len(y), min(len(y), 300_000), replace=False)
-        np.savez_compressed(args.dump, X=X[sel].astype(np.float32), cycles=cyc[sel].astype(np.float32))
     counts = np.bincount(y, minlength=G.PLAN_CLASSES)
-    perfect = 1.0 - cyc[np.arange(len(y)), np.argmin(cyc, axis=1)].sum() / cyc[:, 2].sum()
-    held = evaluate(params, training_renders(4, 5, 9000, 30000))
-    fixed, planned = np.array(held).T
+    held = evaluate(params, training_renders(4, 4, 9000, 30000), q=args.quantile)
+    fx = sum(h["fixed"]["frame_ms"] for h in held)
+    pl = sum(h["planned"]["frame_ms"] for h in held)
     print(json.dumps({"samples": int(len(y)), "label_counts": counts.tolist(),
-                      "cycles_sum_gain_if_perfect_vs_class2": round(float(perfect), 4),
                       "loss_first_batch_per_epoch": [round(h, 4) for h in hist],
-                      "held_out_raster_ms_fixed": round(float(fixed.sum()), 4),
-                      "held_out_raster_ms_planned": round(float(planned.sum()), 4),
-                      "held_out_gain": round(float(1.0 - planned.sum() / fixed.sum()), 4),
-                      "held_out_per_render": [[round(a, 4), round(b, 4)] for a, b in held],
+                      "held_out_frame_ms_fixed": round(fx, 4), "held_out_frame_ms_planned": round(pl, 4),
+                      "held_out_gain": round(1.0 - pl / fx, 4),
+                      "held_out_flagged_tiles": [h["flagged"] for h in held],
+                      "held_out_tiles": [h["tiles"] for h in held],
+                      "held_out_per_render": held,
                       "collect_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1), "out": args.out}))
 
 

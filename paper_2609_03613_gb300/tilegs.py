@@ -22,7 +22,7 @@ ERRORS = {1: "invalid argument", 2: "entry capacity exceeded", 3: "CUDA runtime 
 
 MODE_GLOBAL_SORT, MODE_BINNED_EXACT, MODE_BINNED_PAPER, MODE_BINNED_NOREPAIR = 0, 1, 2, 3
 MODES = {"global": 0, "exact": 1, "paper": 2, "norepair": 3}
-STAGES = ["project", "intersect", "depth_range", "bin", "repair", "sort", "raster"]
+STAGES = ["project", "intersect", "depth_range", "bin", "repair", "sort", "raster", "complete"]
 MAX_K = 128
 MAX_VIEWS = 32
 PLAN_FEATURES, PLAN_HIDDEN, PLAN_CLASSES = 8, 64, 6
@@ -43,7 +43,7 @@ EXPORTS = [
     "gs_render_batch", "gs_batch_set_view_config", "gs_batch_get_view_config", "gs_batch_last_entry_count",
     "gs_batch_autotune", "gs_rasterize_fwd_plan", "gs_tile_features", "gs_planner_set_weights", "gs_plan_tiles",
     "gs_mlp_forward", "gs_mlp_loss_grad", "gs_mlp_backward", "gs_adam_step", "gs_spatial_order",
-    "gs_gather_rows",
+    "gs_gather_rows", "gs_last_flagged_tiles",
 ]
 
 
@@ -63,7 +63,8 @@ class GsConfig(C.Structure):
                 ("pad", C.c_float), ("near_alpha", C.c_float), ("near_gamma", C.c_float),
                 ("eps", C.c_float), ("repair_budget_frac", C.c_float), ("near_shift", C.c_int32),
                 ("tile_cull", C.c_int32), ("persistent", C.c_int32), ("repair_in_raster", C.c_int32),
-                ("chunk_cap", C.c_int32), ("planner", C.c_int32), ("wait_polls", C.c_int32)]
+                ("chunk_cap", C.c_int32), ("planner", C.c_int32), ("wait_polls", C.c_int32),
+                ("planner_quantile", C.c_float)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -125,6 +126,7 @@ def lib():
         "gs_last_entry_count": (i64, [vp]),
         "gs_launch_count": (i64, [vp]),
         "gs_last_raster_ops": (i64, [vp, vp]),
+        "gs_last_flagged_tiles": (i32, [vp, vp]),
         "gs_depth_range_noalloc": (C.c_int, [C.POINTER(GsConfig), vp, vp, i64, C.POINTER(GsCamera), vp, i64,
                                              vp, vp, vp]),
         "gs_grad2d_bytes": (sz, [i64]),
@@ -135,10 +137,10 @@ def lib():
         "gs_batch_get_view_config": (C.c_int, [vp, i32, C.POINTER(GsConfig)]),
         "gs_batch_last_entry_count": (i64, [vp, i32]),
         "gs_rasterize_fwd_plan": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32, C.POINTER(C.c_float),
-                                            vp, vp, vp, vp, vp, vp]),
+                                            vp, vp, vp, vp, vp, vp, vp]),
         "gs_tile_features": (C.c_int, [vp, C.POINTER(GsCamera), vp, i32, vp, vp]),
         "gs_planner_set_weights": (C.c_int, [vp, vp, vp]),
-        "gs_plan_tiles": (C.c_int, [vp, vp, i32, vp, vp]),
+        "gs_plan_tiles": (C.c_int, [vp, C.POINTER(GsCamera), vp, i32, vp, vp, vp]),
         "gs_mlp_forward": (C.c_int, [vp, vp, i32, vp, vp, vp]),
         "gs_mlp_loss_grad": (C.c_int, [vp, vp, i32, vp, vp, vp]),
         "gs_mlp_backward": (C.c_int, [vp, vp, vp, vp, i32, vp, vp, vp]),
@@ -445,24 +447,28 @@ class Context:
         return grad
 
     # ------------------------------------------------------------- bin planner
-    def rasterize_fwd_plan(self, projected, n, cam, words, offsets, plan=None, cycles=False, stride=None,
-                           bg=(0.0, 0.0, 0.0)):
-        """(rgb, alpha, last, tile_cycles or None) with an optional per-tile
-        chunk-class plan (uint8 [T])."""
+    def rasterize_fwd_plan(self, projected, n, cam, words, offsets, plan=None, flags=False, needed=False,
+                           stride=None, bg=(0.0, 0.0, 0.0)):
+        """One pass of a planned frame: (rgb, alpha, last, flags or None,
+        bins_needed or None).  plan: uint8 [T] bins walked per tile (None:
+        all); flags: also return the tiles left for a completing pass;
+        needed: also return each tile's bins needed (requires plan=None)."""
         import torch
         dev = projected.device
         H, W = int(cam.height), int(cam.width)
+        T = n_tiles(W, H, self.cfg.tile_size)
         rgb = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
         alpha = torch.empty((H, W), dtype=torch.float32, device=dev)
         last = torch.empty((H, W), dtype=torch.int32, device=dev)
-        cyc = (torch.zeros(n_tiles(W, H, self.cfg.tile_size), dtype=torch.int64, device=dev) if cycles else None)
+        fl = torch.empty(T, dtype=torch.uint8, device=dev) if flags else None
+        nd = torch.empty(T, dtype=torch.int32, device=dev) if needed else None
         bgv = (C.c_float * 3)(*[float(x) for x in bg])
         c = gs_camera(cam)
         check(lib().gs_rasterize_fwd_plan(self.h, _ptr(projected), n, C.byref(c), _ptr(words), _ptr(offsets),
                                           self.stride if stride is None else int(stride), bgv, _ptr(rgb),
-                                          _ptr(alpha), _ptr(last), _ptr(plan), _ptr(cyc), _stream()),
+                                          _ptr(alpha), _ptr(last), _ptr(plan), _ptr(fl), _ptr(nd), _stream()),
               "gs_rasterize_fwd_plan")
-        return rgb, alpha, last, cyc
+        return rgb, alpha, last, fl, nd
 
     def tile_features(self, cam, offsets, stride=None):
         import torch
@@ -485,12 +491,17 @@ class Context:
         self._planner_params = p  # kept alive until the copy has run
         check(lib().gs_planner_set_weights(self.h, _ptr(p), _stream()), "gs_planner_set_weights")
 
-    def plan_tiles(self, features):
+    def plan_tiles(self, cam, offsets, stride=None):
+        """(plan, classes): each tile's first-pass bins and planner class
+        (uint8 [T] each) from a binned stream's offsets."""
         import torch
-        plan = torch.empty(features.shape[0], dtype=torch.uint8, device=features.device)
-        check(lib().gs_plan_tiles(self.h, _ptr(features), int(features.shape[0]), _ptr(plan), _stream()),
-              "gs_plan_tiles")
-        return plan
+        T = n_tiles(cam.width, cam.height, self.cfg.tile_size)
+        plan = torch.empty(T, dtype=torch.uint8, device=offsets.device)
+        cls = torch.empty(T, dtype=torch.uint8, device=offsets.device)
+        c = gs_camera(cam)
+        check(lib().gs_plan_tiles(self.h, C.byref(c), _ptr(offsets), self.stride if stride is None else int(stride),
+                                  _ptr(plan), _ptr(cls), _stream()), "gs_plan_tiles")
+        return plan, cls
 
     # ------------------------------------------------------------- scene order
     def spatial_order(self, means):
@@ -578,6 +589,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(lib().gs_launch_count(self.h))
+
+    def flagged_tiles(self) -> int:
+        """Tiles the last planned render left to its second pass."""
+        return int(lib().gs_last_flagged_tiles(self.h, _stream()))
 
     def last_raster_ops(self) -> int:
         return int(lib().gs_last_raster_ops(self.h, _stream()))

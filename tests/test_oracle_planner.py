@@ -1,7 +1,8 @@
 """Pins for the planner oracle (oracle/planner.py): the tile features on
 hand-made bin histograms, the network's gradient by central finite
 differences, the cross-entropy gradient and its closed form at uniform
-logits, and Adam's first step (update = -lr g / (|g| + eps)).
+logits, Adam's first step (update = -lr g / (|g| + eps)), and the decision
+rule, class-to-bins map and training label on hand-computed cases.
 None of these runs the CUDA path."""
 import math
 
@@ -80,9 +81,63 @@ def test_adam_first_step_closed_form():
     np.testing.assert_allclose(v, 0.001 * g * g)
 
 
-def test_plan_is_argmax_with_lowest_class_on_ties():
+def test_plan_of_a_bias_only_network():
+    """Zero weights: every tile gets the classes of the output bias alone.
+    Bias (0, 0, log 2, -50, ...) has cumulative probabilities .25 .5 1 ...,
+    so q = 0.5 picks class 1 and q = 0.9 class 2, whatever the features."""
     P = np.zeros(PL.N_PARAMS)
     W1, b1, W2, b2, W3, b3 = PL.unpack(P)
-    b3 = np.array([0.0, 1.0, 1.0, -1.0, 0.5, 1.0])
+    b3 = np.array([0.0, 0.0, math.log(2.0), -50.0, -50.0, -50.0])
     P2 = PL.pack(W1, b1, W2, b2, W3, b3)
-    assert list(PL.plan(P2, np.zeros((2, PL.F)))) == [1, 1]
+    K = 8
+    off = _offsets([np.array([10, 0, 60, 0, 100, 500, 0, 30]), np.zeros(K, int)])
+    X = PL.tile_features(off, K, 2)
+    cls, bins = PL.plan(P2, X, off, K, 2, q=0.5)
+    assert cls.tolist() == [1, 1] and bins.tolist() == [5, 8]
+    cls, bins = PL.plan(P2, X, off, K, 2, q=0.9)
+    assert cls.tolist() == [2, 2] and bins.tolist() == [6, 8]
+
+
+def test_decision_rule_by_hand():
+    # softmax of (0, 0, log 2, ...) etc.: cumulative probabilities by hand
+    z = np.array([[0.0, 0.0, math.log(2.0), -50.0, -50.0, -50.0],   # p = .25 .25 .5 ~0 ~0 ~0
+                  [-50.0, -50.0, -50.0, -50.0, -50.0, 0.0],       # all mass on class 5
+                  [0.0] * 6])                                    # uniform: cum = (c+1)/6
+    np.testing.assert_array_equal(PL.decide(z, 0.5), [1, 5, 2])
+    np.testing.assert_array_equal(PL.decide(z, 0.9), [2, 5, 5])   # 5/6 < 0.9 -> class 5
+    np.testing.assert_array_equal(PL.decide(z, 0.2), [0, 5, 1])
+
+
+def test_class_bins_by_hand():
+    K = 8
+    t0 = np.array([10, 0, 60, 0, 100, 500, 0, 30])   # cumulative 10 10 70 70 170 670 670 700
+    t1 = np.zeros(K, int)                            # empty: never reaches -> K
+    t2 = np.array([3000, 0, 0, 0, 0, 0, 0, 1])       # the first bin alone holds 3000
+    off = _offsets([t0, t1, t2])
+    for c, want in ((0, [3, 8, 1]), (1, [5, 8, 1]), (2, [6, 8, 1]), (3, [6, 8, 1]), (4, [8, 8, 1]),
+                    (5, [8, 8, 8])):
+        np.testing.assert_array_equal(PL.class_bins(off, K, 3, [c] * 3), want, err_msg=str(c))
+
+
+def test_bins_needed_and_label_by_hand():
+    K = 8
+    t0 = np.array([10, 0, 60, 0, 100, 500, 0, 30])
+    off = _offsets([t0, np.zeros(K, int)])
+    # tile 0 spans [0, 700): an end inside bin 2 ([10, 70)) needs 3 bins
+    assert PL.bins_needed(off, K, 2, [40, 700]).tolist() == [3, 0]
+    assert PL.bins_needed(off, K, 2, [70, 700]).tolist() == [3, 0]   # the last visit is entry 69
+    assert PL.bins_needed(off, K, 2, [71, 700]).tolist() == [5, 0]   # entry 70 sits in bin 4 ([70, 170))
+    assert PL.bins_needed(off, K, 2, [700, 700]).tolist() == [8, 0]
+    need = np.array([3, 0])
+    # class 0 keeps 3 bins (64 entries reached in bin 2): it covers 3 bins
+    assert PL.label(need, off, K, 2).tolist() == [0, 0]
+    assert PL.label(np.array([5, 0]), off, K, 2).tolist() == [1, 0]
+    assert PL.label(np.array([6, 0]), off, K, 2).tolist() == [2, 0]
+    assert PL.label(np.array([8, 0]), off, K, 2).tolist() == [4, 0]
+
+
+def test_tile_end_from_visits_by_hand():
+    # a 2x1 tile grid of 2x2 tiles on a 3x2 image (ragged right column)
+    off = np.array([0, 5, 9])
+    nt = np.array([[1, 4, 2], [0, 3, 1]])
+    np.testing.assert_array_equal(PL.tile_end_from_visits(off, 1, 2, 3, 2, nt), [4, 7])
