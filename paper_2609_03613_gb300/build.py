@@ -65,7 +65,10 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
                     sys.stderr.write(res.stdout + res.stderr)
                 if res.returncode != 0:
                     raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if jobs or not os.path.exists(LIB):
+    # relink also when an object is newer than the library (a failed link
+    # leaves the previous library in place)
+    lib_t = os.path.getmtime(LIB) if os.path.exists(LIB) else -1.0
+    if jobs or lib_t < 0 or any(os.path.getmtime(o) > lib_t for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         res = subprocess.run(cmd, capture_output=True, text=True)

@@ -3,12 +3,13 @@
 //   * one projection launch for all views: each Gaussian's parameters and SH
 //     coefficients are read from HBM once and projected for every view
 //     (k_project_batch);
-//   * each view's intersect / bin / repair runs on its own stream, forked
-//     from and joined back into the caller's stream, so small views and the
-//     tails of large ones overlap on the 152 SMs;
-//   * one persistent raster launch composites every view's tiles (blocks take
-//     (view, tile) items from a counter) when all views are EXACT with 16x16
-//     tiles; otherwise each view's raster runs on its stream;
+//   * the views that are EXACT with the repair in the raster, 16x16 tiles, the
+//     tile cull and no planner form one group binned as a single frame of
+//     V n items (batch_bins.cu): one launch per stage for all of them, on the
+//     caller's stream, then one persistent raster launch composites all their
+//     tiles (blocks take (view, tile) items from a counter, longest first);
+//   * every other view runs the whole-frame pipeline on its own stream,
+//     forked from and joined back into the caller's stream;
 //   * with GS_RENDER_GRAPH the whole batch (fork, V pipelines, join) is one
 //     CUDA graph, replayed while the arguments stay the same;
 //   * per-view tile size and bin count come from gs_batch_autotune, which
@@ -36,6 +37,12 @@ struct BatchState {
     int32_t* d_counter = nullptr;  // schedule of the persistent multi-view raster (65 int32)
     int32_t* d_order = nullptr;    // its work items, longest tiles first
     size_t order_cap = 0;
+    // the group of views binned together (batch_bins.cu)
+    gs_ctx* group = nullptr;                  // its scratch, stream and offsets, error word
+    GroupViews* gview = nullptr;              // its view table
+    int64_t* h_group_m = nullptr;             // pinned: per-view entry counts of the last batch
+    int group_pos[kMaxBatchViews];            // position of view v in the group, -1: not in it
+    int ngroup = 0;
 };
 
 void batch_destroy(gs_ctx* c)
@@ -51,6 +58,9 @@ void batch_destroy(gs_ctx* c)
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->d_counter) cudaFree(b->d_counter);
     if (b->d_order) cudaFree(b->d_order);
+    if (b->group) gs_destroy(b->group);
+    if (b->gview) group_views_free(b->gview);
+    if (b->h_group_m) cudaFreeHost(b->h_group_m);
     delete b;
     c->batch = nullptr;
 }
@@ -58,6 +68,10 @@ void batch_destroy(gs_ctx* c)
 int batch_error(gs_ctx* c, cudaStream_t st)
 {
     if (!c->batch) return GS_OK;
+    if (c->batch->group) {
+        const int e = gs_get_error(c->batch->group, st);
+        if (e != GS_OK) return e;
+    }
     for (int v = 0; v < kMaxBatchViews; ++v)
         if (c->batch->views[v]) {
             const int e = gs_get_error(c->batch->views[v], st);
@@ -69,6 +83,10 @@ int batch_error(gs_ctx* c, cudaStream_t st)
 int batch_clear_error(gs_ctx* c, cudaStream_t st)
 {
     if (!c->batch) return GS_OK;
+    if (c->batch->group) {
+        const int e = gs_clear_error(c->batch->group, st);
+        if (e != GS_OK) return e;
+    }
     for (int v = 0; v < kMaxBatchViews; ++v)
         if (c->batch->views[v]) {
             const int e = gs_clear_error(c->batch->views[v], st);
@@ -82,11 +100,16 @@ static BatchState* batch_state(gs_ctx* c)
     if (!c->batch) {
         BatchState* b = new BatchState();
         if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaMalloc(&b->d_counter, 65 * sizeof(int32_t)) != cudaSuccess) {
+            cudaMalloc(&b->d_counter, 65 * sizeof(int32_t)) != cudaSuccess ||
+            cudaMallocHost(&b->h_group_m, kMaxBatchViews * sizeof(int64_t)) != cudaSuccess ||
+            !(b->gview = group_views_new())) {
             if (b->fork) cudaEventDestroy(b->fork);
+            if (b->d_counter) cudaFree(b->d_counter);
+            if (b->h_group_m) cudaFreeHost(b->h_group_m);
             delete b;
             return nullptr;
         }
+        for (int v = 0; v < kMaxBatchViews; ++v) b->group_pos[v] = -1;
         c->batch = b;
     }
     return c->batch;
@@ -121,10 +144,58 @@ static int view_ctx(gs_ctx* c, int v, gs_ctx** out)
 int64_t batch_launch_count(const gs_ctx* c)
 {
     int64_t s = 0;
-    if (c->batch)
+    if (c->batch) {
         for (int v = 0; v < kMaxBatchViews; ++v)
             if (c->batch->views[v]) s += c->batch->views[v]->launches;
+        if (c->batch->group) s += c->batch->group->launches;
+    }
     return s;
+}
+
+// Whether two view configurations may share a group: every field but the
+// bin count.
+static bool same_but_k(gs_config a, gs_config b)
+{
+    a.K = b.K = 0;
+    return memcmp(&a, &b, sizeof(gs_config)) == 0;
+}
+
+static bool groupable(const gs_config& cfg)
+{
+    return cfg.mode == GS_MODE_BINNED_EXACT && cfg.repair_in_raster && cfg.tile_size == 16 && cfg.tile_cull &&
+           !cfg.planner;
+}
+
+// The group: the groupable views whose configuration equals (but for K) the
+// first groupable view's; its context carries that configuration.
+static int batch_group(gs_ctx* c, const gs_scene* sc, const gs_camera* cams, int nv)
+{
+    BatchState* b = c->batch;
+    gs_camera gcams[kMaxBatchViews];
+    int32_t gk[kMaxBatchViews];
+    int first = -1;
+    b->ngroup = 0;
+    for (int v = 0; v < kMaxBatchViews; ++v) b->group_pos[v] = -1;
+    for (int v = 0; v < nv; ++v) {
+        const gs_config& cfg = view_config(c, v);
+        if (!groupable(cfg)) continue;
+        if (first < 0) first = v;
+        else if (!same_but_k(cfg, view_config(c, first))) continue;
+        b->group_pos[v] = b->ngroup;
+        gcams[b->ngroup] = cams[v];
+        gk[b->ngroup] = cfg.K;
+        ++b->ngroup;
+    }
+    if (b->ngroup == 0) return GS_OK;
+    const gs_config& gcfg = view_config(c, first);
+    int r;
+    if (!b->group) {
+        if ((r = gs_create(&b->group, &gcfg)) != GS_OK) return r;
+    } else if (memcmp(&b->group->cfg, &gcfg, sizeof(gs_config)) != 0 && (r = gs_set_config(b->group, &gcfg)) != GS_OK) {
+        return r;
+    }
+    group_views_set(b->gview, sc->n, b->ngroup, gcams, gk);
+    return group_reserve(b->group, b->gview, b->group->r_m_cap > 0 ? b->group->r_m_cap : 1);
 }
 
 // Device buffers of every view, allocated outside any capture.
@@ -145,8 +216,17 @@ static int batch_buffers(gs_ctx* c, const gs_scene* sc, const gs_camera* cams, i
         gs_ctx* vc;
         int r = view_ctx(c, v, &vc);
         if (r != GS_OK) return r;
+    }
+    {
+        const int r = batch_group(c, sc, cams, nv);
+        if (r != GS_OK) return r;
+    }
+    for (int v = 0; v < nv; ++v) {
+        gs_ctx* vc = c->batch->views[v];
+        int r;
         const int32_t T = gs_num_tiles(cams[v].width, cams[v].height, vc->cfg.tile_size);
-        if ((r = render_buffers(vc, sc->n, vc->r_m_cap > 0 ? vc->r_m_cap : 1, T)) != GS_OK) return r;
+        if (c->batch->group_pos[v] < 0 && (r = render_buffers(vc, sc->n, vc->r_m_cap > 0 ? vc->r_m_cap : 1, T)) != GS_OK)
+            return r;
         if (!last || !last[v]) {
             const size_t px = (size_t)cams[v].width * cams[v].height;
             void* p = vc->r_out;
@@ -166,58 +246,79 @@ static int batch_impl(gs_ctx* c, const gs_scene* sc, const gs_camera* cams, int 
     BatchState* b = c->batch;
     const int64_t n = sc->n;
     int r;
-    // one projection launch per kMaxBatchViews views, on the caller's stream
+    gs_ctx* gc = b->group;
+    const ProjView big = b->ngroup > 0 ? proj_view(gc->r_proj, n * b->ngroup) : ProjView();
+    // one projection launch for all views, on the caller's stream: a group
+    // view's records at items [p n, (p+1) n) of the group's buffer
     {
         ProjView pvs[kMaxBatchViews];
         int tiles[kMaxBatchViews];
         for (int v = 0; v < nv; ++v) {
-            pvs[v] = proj_view(b->views[v]->r_proj, n);
+            const int p = b->group_pos[v];
+            if (p >= 0) {
+                ProjView x = big;
+                x.xy_ab += p * n;
+                x.c_o_z += p * n;
+                x.rgb += p * n;
+                x.rect += p * n;
+                x.radius += p * n;
+                pvs[v] = x;
+            } else {
+                pvs[v] = proj_view(b->views[v]->r_proj, n);
+            }
             tiles[v] = b->views[v]->cfg.tile_size;
         }
         r = launch_project_batch(c, sc->means, sc->scales, sc->quats, sc->opacities, sc->sh, sc->sh_degree, n, nv,
                                  cams, tiles, pvs, st);
         if (r != GS_OK) return r;
     }
-    // views that are EXACT with the repair in the raster, 16x16 tiles and no
-    // plan: their binning runs on their streams and all their tiles are
-    // composited by one persistent raster launch after the join (other views
-    // run their own raster on their stream)
+    // the views outside the group: the whole-frame pipeline on their streams
     GS_CUDA_TRY(cudaEventRecord(b->fork, st));
-    RasterView rv[kMaxBatchViews];
-    int nfused = 0;
+    bool forked[kMaxBatchViews] = {};
     for (int v = 0; v < nv; ++v) {
+        if (b->group_pos[v] >= 0) continue;
         gs_ctx* vc = b->views[v];
         cudaStream_t vs = b->streams[v];
         GS_CUDA_TRY(cudaStreamWaitEvent(vs, b->fork, 0));
         vc->capturing = c->capturing;
         int32_t* d_last = (last && last[v]) ? last[v] : reinterpret_cast<int32_t*>(vc->r_out);
-        const gs_config& vcfg = vc->cfg;
-        const bool fused = vcfg.mode == GS_MODE_BINNED_EXACT && vcfg.repair_in_raster && vcfg.tile_size == 16 &&
-                           !vcfg.planner;
-        if (fused) {
-            r = render_binning(vc, n, sc->scales, cams + v, flags, vs);
-            RasterView& x = rv[nfused++];
-            x.pv = proj_view(vc->r_proj, n);
-            x.cam = cams[v];
-            x.words = vc->r_stream;
-            x.offsets = vc->r_off;
-            x.stride = vc->cfg.K;
-            for (int k = 0; k < 3; ++k) x.bg[k] = bg[k];
-            x.cull = vc->cfg.tile_cull;
-            x.cap = chunk_cap(vc->cfg);
-            x.rgb = rgb[v];
-            x.alpha = alpha[v];
-            x.last = d_last;
-        } else {
-            r = render_after_project(vc, n, sc->scales, cams + v, bg, rgb[v], alpha[v], d_last, flags, vs);
-        }
+        r = render_after_project(vc, n, sc->scales, cams + v, bg, rgb[v], alpha[v], d_last, flags, vs);
         vc->capturing = 0;
         if (r != GS_OK) return r;
         GS_CUDA_TRY(cudaMemcpyAsync(vc->h_m + 1, vc->r_m, sizeof(int64_t), cudaMemcpyDeviceToHost, vs));
         GS_CUDA_TRY(cudaEventRecord(b->join[v], vs));
-        GS_CUDA_TRY(cudaStreamWaitEvent(st, b->join[v], 0));
+        forked[v] = true;
     }
-    if (nfused > 0) return raster_views(c, rv, nfused, b->d_counter, b->d_order, st);
+    // the group: its binning as one frame on the caller's stream, then one
+    // persistent raster launch over all its views' tiles
+    if (b->ngroup > 0) {
+        gc->capturing = c->capturing;
+        r = group_binning(gc, b->gview, flags, b->h_group_m, st);
+        gc->capturing = 0;
+        if (r != GS_OK) return r;
+        RasterView rv[kMaxBatchViews];
+        int k = 0;
+        for (int v = 0; v < nv; ++v) {
+            const int p = b->group_pos[v];
+            if (p < 0) continue;
+            RasterView& x = rv[k++];
+            x.pv = big;
+            x.cam = cams[v];
+            x.words = gc->r_stream;
+            x.offsets = gc->r_off + group_seg_base(b->gview, p);
+            x.stride = b->views[v]->cfg.K;
+            for (int q = 0; q < 3; ++q) x.bg[q] = bg[q];
+            x.cull = gc->cfg.tile_cull;
+            x.cap = chunk_cap(gc->cfg);
+            x.rgb = rgb[v];
+            x.alpha = alpha[v];
+            x.last = (last && last[v]) ? last[v] : reinterpret_cast<int32_t*>(b->views[v]->r_out);
+            x.gid_base = (int32_t)(p * n);
+        }
+        if ((r = raster_views(c, rv, k, b->d_counter, b->d_order, st)) != GS_OK) return r;
+    }
+    for (int v = 0; v < nv; ++v)
+        if (forked[v]) GS_CUDA_TRY(cudaStreamWaitEvent(st, b->join[v], 0));
     return GS_OK;
 }
 
@@ -261,6 +362,7 @@ extern "C" int gs_batch_get_view_config(gs_ctx* c, int32_t view, gs_config* cfg)
 extern "C" int64_t gs_batch_last_entry_count(gs_ctx* c, int32_t view)
 {
     if (!c || !c->batch || view < 0 || view >= kMaxBatchViews || !c->batch->views[view]) return -1;
+    if (c->batch->group_pos[view] >= 0) return c->batch->h_group_m[c->batch->group_pos[view]];
     return c->batch->views[view]->h_m[1];
 }
 
@@ -284,7 +386,8 @@ extern "C" int gs_render_batch(gs_ctx* c, const gs_scene* sc, const gs_camera* c
     // graph: capacity must have been sized by an earlier call without NO_SYNC
     if (!stream) return GS_ERR_INVALID_ARG;
     for (int v = 0; v < n_cams; ++v)
-        if (b->views[v]->r_m_cap <= 1) return GS_ERR_INVALID_ARG;
+        if (b->group_pos[v] < 0 && b->views[v]->r_m_cap <= 1) return GS_ERR_INVALID_ARG;
+    if (b->ngroup > 0 && b->group->r_m_cap <= 1) return GS_ERR_INVALID_ARG;
     std::vector<unsigned char> key;
     auto put = [&key](const void* p, size_t nbytes) {
         const unsigned char* q = static_cast<const unsigned char*>(p);
@@ -303,6 +406,13 @@ extern "C" int gs_render_batch(gs_ctx* c, const gs_scene* sc, const gs_camera* c
         put(ptrs, sizeof(ptrs));
         put(&vc->r_m_cap, sizeof(vc->r_m_cap));
         put(&vc->cfg, sizeof(gs_config));
+    }
+    if (b->group) {
+        const gs_ctx* gc = b->group;
+        const void* gptr[] = {gc->r_proj, gc->r_stream, gc->r_off, gc->d_tiles, gc->d_goff, gc->d_scan, gc->d_tail};
+        put(gptr, sizeof(gptr));
+        put(&gc->r_m_cap, sizeof(gc->r_m_cap));
+        put(b->group_pos, sizeof(b->group_pos));
     }
     put(&flags, sizeof(flags));
     put(&c->device, sizeof(c->device));

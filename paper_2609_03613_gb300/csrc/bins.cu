@@ -7,83 +7,17 @@
 //   K13 repair selection        (Sec. 3.5 rule table; supplement "Selective
 //                                repair selection and local exact sorting")
 //   K14 segment sorts by the baseline key (depth bits, gid)
-#include "device.cuh"
+#include "depth_range.cuh"
 
 namespace gs {
 
-// ------------------------------------------------------------------ depth range
-constexpr int kDrThreads = 1024;
-constexpr int kDrMaxS = 8192;
-
-struct DrArgs {
-    float near_plane, far_plane;
-    int S;
-    int near_shift;
-    float near_alpha, near_gamma;
-    float p_lo, p_hi, pad, eps;
-    int K;
-};
-
-__device__ __forceinline__ float zkey_of(float z, const float* __restrict__ scales, uint32_t g, float a, float gm)
-{
-    const float s0 = __ldg(scales + 3 * (size_t)g), s1 = __ldg(scales + 3 * (size_t)g + 1),
-                s2 = __ldg(scales + 3 * (size_t)g + 2);
-    const float smax = fmaxf(fmaxf(s0, s1), s2);
-    return z - fminf(a * smax, gm * z);
-}
-
-__device__ __forceinline__ int64_t rank_of(float p, int64_t n)
-{
-    int64_t k = (int64_t)ceil((double)p / 100.0 * (double)n);
-    if (k < 1) k = 1;
-    if (k > n) k = n;
-    return k;
-}
-
-// Bin parameters from [zmin, zmax]: z'min = max(zmin, eps),
-// z'max = max(zmax, z'min + 1e-6), lmin/lmax their logs, and K-1 log-spaced
-// split depths exp(lmin + (lmax - lmin) k/K), kept non-decreasing.
-__device__ void write_bin_params(BinParams* bp, float zmin, float zmax, int K, float eps, int nsamples)
-{
-    __shared__ float s_l[2];
-    if (threadIdx.x == 0) {
-        const float zmn = fmaxf(zmin, eps);
-        const float zmx = fmaxf(zmax, zmn + 1e-6f);
-        s_l[0] = spec_log(zmn);
-        s_l[1] = spec_log(zmx);
-        bp->zmin = zmin;
-        bp->zmax = zmax;
-        bp->lmin = s_l[0];
-        bp->lmax = s_l[1];
-        bp->K = K;
-        bp->nsamples = nsamples;
-    }
-    __syncthreads();
-    __shared__ float s_split[GS_MAX_K];
-    const float lmin = s_l[0], lmax = s_l[1];
-    for (int k = 1 + threadIdx.x; k < K; k += blockDim.x) {
-        const float t = (float)k / (float)K;
-        s_split[k - 1] = spec_exp(lmin + (lmax - lmin) * t);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int k = 1; k < K - 1; ++k)
-            if (s_split[k] < s_split[k - 1]) s_split[k] = s_split[k - 1];
-    __syncthreads();
-    for (int k = threadIdx.x; k < K - 1; k += blockDim.x) bp->splits[k] = s_split[k];
-}
+// ------------------------------------------------------------------ depth range: depth_range.cuh
 
 // Sample j of the emission order -> gid, from the materialised entries ...
 struct GidFromIsect {
     const uint32_t* gid;
     __device__ uint32_t operator()(int64_t, int64_t j) const { return gid[j]; }
 };
-// ... or from a per-sample gid array filled by k_sample_gids.
-struct GidFromSamples {
-    const uint32_t* gid;  // indexed by sample number
-    __device__ uint32_t operator()(int64_t i, int64_t) const { return gid[i]; }
-};
-
 // Sample i of S' = min(S, M) is entry j = floor(i M / S') of the emission
 // order.  Gaussian g owns entries [goff[g], goff[g+1]), so its samples are the
 // i with goff[g] <= floor(i M / S') < goff[g+1], i.e.
@@ -115,163 +49,12 @@ k_sample_gids(const int32_t* __restrict__ goff, int64_t n, const int64_t* __rest
     }
 }
 
-// Rank search of one radix pass, by one warp: the digit d whose cumulative
-// count first reaches k (k >= 1), and k minus the counts below d, written by
-// the one lane that returns true.  Lane l holds digits 8l .. 8l+7.
-__device__ __forceinline__ bool warp_digit_select(const uint32_t* __restrict__ h, int64_t k, uint32_t* dsel,
-                                                  int64_t* krem)
-{
-    const int lane = threadIdx.x & 31;
-    uint32_t c[8], sum = 0;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        c[j] = h[8 * lane + j];
-        sum += c[j];
-    }
-    uint32_t incl = sum;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += u;
-    }
-    const unsigned hit = __ballot_sync(0xffffffffu, (int64_t)incl >= k);
-    const int L = hit ? __ffs(hit) - 1 : 31;
-    const uint32_t before = __shfl_sync(0xffffffffu, incl - sum, L);
-    if (lane == L) {
-        int64_t kk = k - (int64_t)before;
-        uint32_t d = 8u * L + 7u;
-        for (int j = 0; j < 8; ++j) {
-            if ((int64_t)c[j] >= kk) {
-                d = 8u * L + j;
-                break;
-            }
-            kk -= c[j];
-        }
-        *dsel = d;
-        *krem = kk;
-    }
-    return lane == L;
-}
-
 template <class GidOf>
 __global__ void __launch_bounds__(kDrThreads)
 k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales, GidOf gid_of,
               const int64_t* __restrict__ m_dev, int64_t m_cap, DrArgs a, BinParams* bp)
 {
-    __shared__ uint32_t s_v[kDrMaxS];
-    __shared__ int s_n;
-    __shared__ uint32_t s_h[2][256];
-    __shared__ uint32_t s_pref[2];
-    __shared__ int64_t s_k[2];
-    __shared__ int s_low;
-    if (threadIdx.x == 0) s_n = 0;
-    __syncthreads();
-    const int64_t M = live_count(m_dev, m_cap);
-    const int64_t ns = M < (int64_t)a.S ? M : (int64_t)a.S;
-    const float lo_clamp = fmaxf(a.near_plane, a.eps);
-    // every sample's gid, then every depth (and scale) gathered at once, so
-    // the dependent loads cost two round trips rather than two per round
-    constexpr int kPer = kDrMaxS / kDrThreads;
-    uint32_t gk[kPer];
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-        const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
-        gk[r] = i < ns ? gid_of(i, (i * M) / ns) : 0u;
-    }
-    float zk[kPer];
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-        const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
-        float z = 0.0f;
-        if (i < ns) {
-            z = c_o_z[gk[r]].z;
-            if (a.near_shift) z = zkey_of(z, scales, gk[r], a.near_alpha, a.near_gamma);
-        }
-        zk[r] = z;
-    }
-    // the positive keys, compacted with one shared atomic per warp and round
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-        const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
-        const float z = zk[r];
-        const bool keep = i < ns && z > 0.0f;
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        const int lane = threadIdx.x & 31;
-        int base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&s_n, __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep) s_v[base + __popc(bal & ((1u << lane) - 1u))] = __float_as_uint(fminf(fmaxf(z, lo_clamp), a.far_plane));
-    }
-    __syncthreads();
-    const int n = s_n;
-    float zmin, zmax;
-    if (n == 0) {
-        zmin = lo_clamp;
-        zmax = a.far_plane;
-    } else {
-        // the bits every sample shares (those of the block's min and max)
-        // need no pass: start below the highest bit where samples differ
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        uint32_t lo_v = 0xffffffffu, hi_v = 0u;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            lo_v = min(lo_v, s_v[i]);
-            hi_v = max(hi_v, s_v[i]);
-        }
-        lo_v = __reduce_min_sync(0xffffffffu, lo_v);
-        hi_v = __reduce_max_sync(0xffffffffu, hi_v);
-        if (lane == 0) {
-            s_h[0][warp] = lo_v;
-            s_h[1][warp] = hi_v;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const int nw = blockDim.x >> 5;
-            lo_v = __reduce_min_sync(0xffffffffu, lane < nw ? s_h[0][lane] : 0xffffffffu);
-            hi_v = __reduce_max_sync(0xffffffffu, lane < nw ? s_h[1][lane] : 0u);
-            if (lane == 0) {
-                const int cp = lo_v == hi_v ? 32 : __clz(lo_v ^ hi_v);
-                const uint32_t top = cp == 32 ? 0xffffffffu : (cp == 0 ? 0u : ~(0xffffffffu >> cp));
-                s_pref[0] = s_pref[1] = lo_v & top;
-                s_k[0] = rank_of(a.p_lo, n);
-                s_k[1] = rank_of(a.p_hi, n);
-                s_low = 32 - cp;  // bits still to select
-            }
-        }
-        __syncthreads();
-        const int low = s_low;
-        uint32_t mask = low >= 32 ? 0u : ~((1u << low) - 1u);
-        // radix select (positive floats: bit order = value order), <= 8 bits a pass
-        for (int hi_bit = low; hi_bit > 0; hi_bit -= 8) {
-            const int shift = hi_bit > 8 ? hi_bit - 8 : 0;
-            const uint32_t dmask = (1u << (hi_bit - shift)) - 1u;
-            for (int d = threadIdx.x; d < 512; d += blockDim.x) s_h[d >> 8][d & 255] = 0u;
-            __syncthreads();
-            const uint32_t p0 = s_pref[0], p1 = s_pref[1];
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const uint32_t v = s_v[i];
-                const uint32_t dg = (v >> shift) & dmask;
-                if ((v & mask) == p0) atomicAdd(&s_h[0][dg], 1u);
-                if ((v & mask) == p1) atomicAdd(&s_h[1][dg], 1u);
-            }
-            __syncthreads();
-            if (warp < 2) {
-                uint32_t dsel = 0u;
-                int64_t krem = 0;
-                if (warp_digit_select(s_h[warp], s_k[warp], &dsel, &krem)) {
-                    s_k[warp] = krem;
-                    s_pref[warp] |= dsel << shift;
-                }
-            }
-            mask |= dmask << shift;
-            __syncthreads();
-        }
-        const float zlo = __uint_as_float(s_pref[0]);
-        const float zhi = __uint_as_float(s_pref[1]);
-        const float span = fmaxf(zhi - zlo, 1e-6f);
-        zmin = fmaxf(a.near_plane, zlo - a.pad * span);
-        zmax = fminf(a.far_plane, zhi + a.pad * span);
-    }
-    write_bin_params(bp, zmin, zmax, a.K, a.eps, n);
+    depth_range_block(c_o_z, scales, gid_of, live_count(m_dev, m_cap), a, bp);
 }
 
 __global__ void k_bin_params_from(const float* __restrict__ zrange, int K, float eps, BinParams* bp)
@@ -716,6 +499,23 @@ __global__ void k_fill_selected(const int32_t* __restrict__ off, int64_t nseg, c
         else if (mode == GS_MODE_BINNED_PAPER) v = sel[q] && l >= 2;
         out[q] = v;
     }
+}
+
+int sort_long_segments(gs_ctx* ctx, int64_t nseg, const int32_t* offsets, uint64_t* words, int32_t min_len,
+                       cudaStream_t st)
+{
+    if (nseg <= 0) return GS_OK;
+    int r;
+    const int32_t tail_cap = tail_capacity(nseg);
+    if ((r = bins_reserve(ctx, 1, nseg)) != GS_OK) return r;
+    GS_CUDA_TRY(cudaMemsetAsync(ctx->d_tail, 0, 4, st));
+    const int64_t want = (nseg + 255) / 256, grid = (int64_t)ctx->num_sms * 8;
+    k_list_long<<<(unsigned)(want < grid ? want : grid), 256, 0, st>>>(offsets, nseg, min_len, ctx->d_tail, tail_cap,
+                                                                        ctx->d_err, ScatterPass(), 1, nullptr);
+    k_sort_listed<<<(unsigned)ctx->num_sms, 1024, 0, st>>>(offsets, ctx->d_tail, tail_cap, words);
+    ctx->launches += 2;
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
 }
 
 int repair(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* words, const int32_t* offsets,

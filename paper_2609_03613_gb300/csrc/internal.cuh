@@ -288,6 +288,9 @@ int count_scan(gs_ctx* ctx, const ProjView& pv, int64_t n, int64_t* m_dev, cudaS
 int count_rows_scan(gs_ctx* ctx, const ProjView& pv, int64_t n, int64_t* m_dev, cudaStream_t st);
 int32_t* rows_offsets(gs_ctx* ctx, int64_t n);
 int64_t* rows_total(gs_ctx* ctx, int64_t n);
+// scratch of the per-Gaussian offsets and of the scans (intersect.cu)
+int goff_reserve(gs_ctx* ctx, int64_t n);
+int scan_reserve(gs_ctx* ctx, int64_t n);
 int emit_only(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam, const IsectView& is,
               int64_t m_cap, const int64_t* m_dev, cudaStream_t st);
 
@@ -331,6 +334,10 @@ int64_t group_scan_items(gs_ctx* ctx, int32_t tiles_y, int K);
 // other bins of flagged tiles); 0: every segment
 int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* stream_words, const int32_t* offsets,
                uint8_t* selected_out, int32_t min_len, cudaStream_t st, int pass = 0);
+// sort every segment of a flat segment array [nseg] longer than min_len - 1
+// entries (the segments the raster cannot sort in shared memory)
+int sort_long_segments(gs_ctx* ctx, int64_t nseg, const int32_t* offsets, uint64_t* words, int32_t min_len,
+                       cudaStream_t st);
 // segments longer than this are sorted before the raster when the raster
 // sorts the segments it reaches
 constexpr int kRasterSortCap = 2048;
@@ -430,6 +437,7 @@ struct RasterView {
     float* rgb;
     float* alpha;
     int32_t* last;
+    int32_t gid_base;  // stream words hold gid_base + the view's gid (a batch group's shared records)
 };
 // all views' tiles in one persistent launch, longest tiles first
 // (sched: 65 device int32; order: one int32 per tile of all views)
@@ -463,6 +471,22 @@ constexpr int kMaxBatchViews = GS_MAX_VIEWS;
 int launch_project_batch(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
                          const float* opac, const float* sh, int32_t sh_degree, int64_t n, int nviews,
                          const gs_camera* cams, const int* tiles, const ProjView* pvs, cudaStream_t st);
+
+// batch_bins.cu: EXACT binning of a group of views as one frame of V n items
+// (records of view v at items [v n, (v+1) n) of the group context's
+// projected buffer); the view table is opaque here
+struct GroupViews;
+GroupViews* group_views_new();
+void group_views_free(GroupViews* gv);
+// fill the table for views of n Gaussians with cameras cams[0..nv) and bin
+// counts K[0..nv); returns the group's total (tile, bin) segments
+int64_t group_views_set(GroupViews* gv, int64_t n, int nv, const gs_camera* cams, const int32_t* K);
+int64_t group_seg_base(const GroupViews* gv, int v);
+int group_reserve(gs_ctx* gc, const GroupViews* gv, int64_t m_cap);
+// intersect, depth range, bins and the long-segment sort of every view of the
+// group (stream and offsets in gc->r_stream, gc->r_off); per-view entry
+// counts copied to the pinned host array h_m_views [nv]
+int group_binning(gs_ctx* gc, const GroupViews* gv, int32_t flags, int64_t* h_m_views, cudaStream_t st);
 
 // batch.cu: per-context batch state (sub-contexts, streams, graph)
 struct BatchState;

@@ -273,7 +273,7 @@ __device__ __forceinline__ void raster_tile(
         __stcs(out_rgb + 3 * p + 1, fmaf(st.T, a.bg1, st.C1));
         __stcs(out_rgb + 3 * p + 2, fmaf(st.T, a.bg2, st.C2));
         __stcs(out_alpha + p, 1.0f - st.T);
-        __stcs(out_last + p, st.last);
+        __stcs(out_last + p, st.last >= 0 ? st.last - a.gid_base : st.last);
         if (out_T) out_T[p] = st.T;
         if (COUNT && out_ntests) out_ntests[p] = st.ntests;
     }
@@ -528,6 +528,7 @@ int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* sched, i
         V.rgb = r.rgb;
         V.alpha = r.alpha;
         V.last = r.last;
+        V.a.gid_base = r.gid_base;
         V.item0 = total;
         total += V.a.n_tiles;
     }

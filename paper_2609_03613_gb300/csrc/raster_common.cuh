@@ -16,6 +16,7 @@ namespace gs {
 struct RasterArgs {
     int width, height, tiles_x, n_tiles, stride;
     float bg0, bg1, bg2;
+    int32_t gid_base = 0;  // stream words hold gid_base + gid (the last-id output subtracts it)
 };
 
 template <int TILE, bool BASELINE>

@@ -1,7 +1,10 @@
-// scan.cuh -- device-wide exclusive scan of int64-valued items given by a
-// load functor: two kernels without inter-block waits (reduce per block, the
-// last block to finish scanning the block sums -> per-block rescan with the
-// prefix), all in int64 so an overflowing total is detected instead of
+// scan.cuh -- device-wide exclusive scan of items given by a load functor, in
+// one pass: each block takes a ticket (its place in the scan, so every block
+// it waits for has already started), scans its tile of 4096 items, publishes
+// its total, and looks back over its predecessors' published totals and
+// prefixes (decoupled look-back: D. Merrill and M. Garland, "Single-pass
+// Parallel Prefix Scan with Decoupled Look-back", 2016) with bounded waits.
+// Totals are carried in int64, so an overflowing total is detected instead of
 // wrapping.
 #pragma once
 
@@ -42,40 +45,6 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* s_wa
     return warp_prefix + incl - v;
 }
 
-// Exclusive scan of sums[0..nb) in place by one block; sums[nb] = grand total.
-__device__ __forceinline__ void scan_sums_body(int64_t* sums, int64_t nb)
-{
-    __shared__ int64_t s_warp[kScanThreads / 32];
-    int64_t carry = 0;
-    for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
-        const int64_t i = b0 + threadIdx.x;
-        const int64_t v = i < nb ? __ldcg(sums + i) : 0;  // written by other blocks: read at L2
-        int64_t total;
-        const int64_t ex = block_exclusive_scan(v, s_warp, &total);
-        if (i < nb) sums[i] = carry + ex;
-        carry += total;
-    }
-    if (threadIdx.x == 0) sums[nb] = carry;
-}
-
-// Called by every block after it stored its block sum(s): the last block to
-// arrive (a counter, reset by that block) scans the sums; no block waits for
-// another.  Returns true in the block that did the scan.
-__device__ __forceinline__ bool last_block_scans(unsigned int* done, int64_t* sa, int64_t* sb)
-{
-    __shared__ bool s_last;
-    __threadfence();  // this thread's sum store is visible device-wide ...
-    __syncthreads();  // ... before the block counts itself done
-    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (!s_last) return false;
-    __threadfence();
-    scan_sums_body(sa, gridDim.x);
-    if (sb) scan_sums_body(sb, gridDim.x);
-    if (threadIdx.x == 0) *done = 0u;  // ready for the next scan on the stream
-    return true;
-}
-
 struct LoadI32 {
     const int32_t* p;
     __device__ int64_t operator()(int64_t i) const { return p[i]; }
@@ -106,37 +75,6 @@ struct LoadRectCountRows {
     }
 };
 
-// Block sums: every item of the block's tile loaded at once (coalesced,
-// all in flight), summed, then reduced across the block.
-template <class Load>
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Load ld, int64_t n, int64_t* sums, unsigned int* done)
-{
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int64_t v[kScanItems];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-        v[k] = i < n ? ld(i) : 0;
-    }
-    int64_t acc = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) acc += v[k];
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
-    __shared__ int64_t s_warp[kScanThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) s_warp[warp] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int64_t t = 0;
-#pragma unroll
-        for (int w = 0; w < kScanThreads / 32; ++w) t += s_warp[w];
-        sums[blockIdx.x] = t;
-    }
-    last_block_scans(done, sums, nullptr);
-}
-
-
 // The block tile's items move between the striped order of coalesced global
 // accesses (item k*256 + t in thread t's slot k) and the blocked order of the
 // per-thread serial scan (item 16t + k) through shared memory, one padding
@@ -144,163 +82,146 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Load ld, int64_t n
 constexpr int kScanPadded = kScanTile + kScanTile / 32;
 __device__ __forceinline__ int scan_pad(int j) { return j + (j >> 5); }
 
-__device__ __forceinline__ void striped_to_blocked(int64_t (&v)[kScanItems], int64_t* sm)
+// ------------------------------------------------------------------ one pass
+// A block's published word: status in the top two bits (0 not yet, A its
+// total, P its inclusive prefix), the value below (< 2^62).
+constexpr uint64_t kScanFlagA = 1ull << 62, kScanFlagP = 2ull << 62, kScanFlagMask = 3ull << 62;
+constexpr int kLookbackPolls = 1 << 22;
+
+// The exclusive prefix of block bid from the words of its predecessors, by
+// one warp (in every lane): windows of 32 predecessors, each lane waiting
+// (bounded; GS_ERR_TIMEOUT when it runs out) for its word, the values summed
+// back to the nearest inclusive prefix.
+__device__ __forceinline__ int64_t scan_lookback(const volatile uint64_t* flags, int64_t bid, int* err)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t prefix = 0;
+    for (int64_t j = bid - 1; j >= 0; j -= 32) {
+        const int64_t idx = j - lane;
+        uint64_t w = 0;
+        if (idx >= 0) {
+            int it = 0;
+            do {
+                w = flags[idx];
+            } while ((w & kScanFlagMask) == 0 && ++it < kLookbackPolls);
+            if ((w & kScanFlagMask) == 0) raise_error(err, GS_ERR_TIMEOUT);
+        }
+        const unsigned pmask = __ballot_sync(0xffffffffu, idx >= 0 && (w & kScanFlagMask) == kScanFlagP);
+        const int stop = pmask ? __ffs(pmask) - 1 : 31;  // the nearest predecessor with a prefix
+        int64_t val = (idx >= 0 && lane <= stop) ? (int64_t)(w & ~kScanFlagMask) : 0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) val += __shfl_xor_sync(0xffffffffu, val, d);
+        prefix += val;
+        if (pmask) break;
+    }
+    return prefix;
+}
+
+// Exclusive scan of the block tile's items in int32 (striped in, striped
+// out): blocked transposition through shared memory, serial scan per thread,
+// one block scan; returns the tile's total.
+__device__ __forceinline__ int64_t scan_tile32(int32_t (&v)[kScanItems], int32_t* sm, int64_t* s_warp)
 {
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) sm[scan_pad(k * kScanThreads + threadIdx.x)] = v[k];
     __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) v[k] = sm[scan_pad(threadIdx.x * kScanItems + k)];
-    __syncthreads();
-}
-
-__device__ __forceinline__ void blocked_to_striped(int64_t (&v)[kScanItems], int64_t* sm)
-{
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) sm[scan_pad(threadIdx.x * kScanItems + k)] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) v[k] = sm[scan_pad(k * kScanThreads + threadIdx.x)];
-    __syncthreads();
-}
-
-// Exclusive scan of the block tile's items (striped in, striped out), offset
-// by `base`: blocked transposition, serial scan per thread, one block scan.
-__device__ __forceinline__ void scan_tile_striped(int64_t (&v)[kScanItems], int64_t base, int64_t* sm,
-                                                  int64_t* s_warp)
-{
-    striped_to_blocked(v, sm);
-    int64_t run = 0;
+    int32_t run = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        const int64_t x = v[k];
+        const int32_t x = sm[scan_pad(threadIdx.x * kScanItems + k)];
         v[k] = run;
         run += x;
     }
     int64_t total;
-    const int64_t off = base + block_exclusive_scan(run, s_warp, &total);
+    const int32_t off = (int32_t)block_exclusive_scan(run, s_warp, &total);
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) v[k] += off;
-    blocked_to_striped(v, sm);
+    for (int k = 0; k < kScanItems; ++k) sm[scan_pad(threadIdx.x * kScanItems + k)] = v[k] + off;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) v[k] = sm[scan_pad(k * kScanThreads + threadIdx.x)];
+    __syncthreads();
+    return total;
 }
 
-// Per-block rescan.  out[i] (int32) = exclusive prefix; out[n] = total.  The
-// int64 total goes to total64.  A total >= 2^31 raises GS_ERR_CAPACITY and
-// leaves out[] unwritten.  Same tile partition as k_scan_reduce, so the
-// block's prefix from the sums applies; loads and stores are coalesced.
-template <class Load>
+// NC channels of item values (one load gives all of them), each scanned into
+// its own output; out[n] = total unless it exceeds INT32_MAX - 1 (then
+// GS_ERR_CAPACITY and the outputs are not valid); totals[c] receives the
+// int64 total.  Per-item values and a tile's total must fit in int32.
+template <int NC, class Load>
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_down(Load ld, int64_t n, const int64_t* sums, int64_t nb, int32_t* out, int64_t* total64, int* err)
+k_scan_onepass(Load ld, int64_t n, uint64_t* flags, int64_t nb, unsigned int* ticket, int32_t* out0, int32_t* out1,
+               int64_t* tot0, int64_t* tot1, int* err)
 {
+    __shared__ int32_t s_tile[kScanPadded];
     __shared__ int64_t s_warp[kScanThreads / 32];
-    __shared__ int64_t s_tile[kScanPadded];
-    const int64_t grand = sums[nb];
-    if (grand > (int64_t)INT32_MAX - 1) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            raise_error(err, GS_ERR_CAPACITY);
-            if (total64) *total64 = grand;
-        }
-        return;
-    }
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int64_t v[kScanItems];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-        v[k] = i < n ? ld(i) : 0;
-    }
-    scan_tile_striped(v, sums[blockIdx.x], s_tile, s_warp);
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-        if (i < n) out[i] = (int32_t)v[k];
-    }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        out[n] = (int32_t)grand;
-        if (total64) *total64 = grand;
-    }
-}
-
-// ------------------------------------------------------------------ two scans in one pass
-// Two exclusive scans of per-item values produced by one load (for example a
-// rect's tile count and its row count): ld(i, a, b).  The same kernels, each
-// carrying both values; sums hold [nb + 1] entries per scan.
-template <class Load2>
-__global__ void __launch_bounds__(kScanThreads) k_scan2_reduce(Load2 ld, int64_t n, int64_t* sa, int64_t* sb,
-                                                               unsigned int* done)
-{
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int64_t acc_a = 0, acc_b = 0;
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-        int64_t x = 0, y = 0;
-        if (i < n) ld(i, x, y);
-        acc_a += x;
-        acc_b += y;
-    }
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        acc_a += __shfl_down_sync(0xffffffffu, acc_a, d);
-        acc_b += __shfl_down_sync(0xffffffffu, acc_b, d);
-    }
-    __shared__ int64_t s_warp[2][kScanThreads / 32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        s_warp[0][warp] = acc_a;
-        s_warp[1][warp] = acc_b;
+    __shared__ int64_t s_pre[NC];
+    __shared__ int64_t s_bid;
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        s_bid = t;
+        if ((int64_t)t == nb - 1) *ticket = 0u;  // every ticket is out: ready for the next scan
     }
     __syncthreads();
-    if (threadIdx.x < 2) {
-        int64_t t = 0;
+    const int64_t bid = s_bid;
+    const int64_t base = bid * kScanTile;
+    int32_t v[NC][kScanItems];
 #pragma unroll
-        for (int w = 0; w < kScanThreads / 32; ++w) t += s_warp[threadIdx.x][w];
-        (threadIdx.x ? sb : sa)[blockIdx.x] = t;
+    for (int k = 0; k < kScanItems; ++k) {
+        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+        int64_t x[2] = {0, 0};
+        if (i < n) ld.load(i, x);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[c][k] = (int32_t)x[c];
     }
-    last_block_scans(done, sa, sb);
+    int64_t agg[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) agg[c] = scan_tile32(v[c], s_tile, s_warp);
+    volatile uint64_t* vf = flags;
+    if (threadIdx.x == 0)
+        for (int c = 0; c < NC; ++c) vf[c * nb + bid] = (bid == 0 ? kScanFlagP : kScanFlagA) | (uint64_t)agg[c];
+    if (threadIdx.x < 32) {
+        for (int c = 0; c < NC; ++c) {
+            const int64_t pre = bid > 0 ? scan_lookback(vf + c * nb, bid, err) : 0;
+            if (threadIdx.x == 0) {
+                if (bid > 0) vf[c * nb + bid] = kScanFlagP | (uint64_t)(pre + agg[c]);
+                s_pre[c] = pre;
+            }
+        }
+    }
+    __syncthreads();
+    int32_t* outs[2] = {out0, out1};
+    int64_t* tots[2] = {tot0, tot1};
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int64_t pre = s_pre[c];
+        const bool over = pre + agg[c] > (int64_t)INT32_MAX - 1;
+        if (over) {
+            if (threadIdx.x == 0) raise_error(err, GS_ERR_CAPACITY);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kScanItems; ++k) {
+                const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
+                if (i < n) outs[c][i] = (int32_t)(pre + v[c][k]);
+            }
+        }
+        if (bid == nb - 1 && threadIdx.x == 0) {
+            if (!over) outs[c][n] = (int32_t)(pre + agg[c]);
+            if (tots[c]) *tots[c] = pre + agg[c];
+        }
+    }
 }
 
+// one-value and two-value loads for the one-pass kernel
+template <class Load>
+struct Load1 {
+    Load ld;
+    __device__ void load(int64_t i, int64_t (&x)[2]) const { x[0] = ld(i); }
+};
 template <class Load2>
-__global__ void __launch_bounds__(kScanThreads)
-k_scan2_down(Load2 ld, int64_t n, const int64_t* sa, const int64_t* sb, int64_t nb, int32_t* oa, int64_t* ta,
-             int32_t* ob, int64_t* tb, int* err)
-{
-    __shared__ int64_t s_warp[kScanThreads / 32];
-    __shared__ int64_t s_tile[kScanPadded];
-    const int64_t ga = sa[nb], gb = sb[nb];
-    if (ga > (int64_t)INT32_MAX - 1 || gb > (int64_t)INT32_MAX - 1) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            raise_error(err, GS_ERR_CAPACITY);
-            if (ta) *ta = ga;
-            if (tb) *tb = gb;
-        }
-        return;
-    }
-    const int64_t base = (int64_t)blockIdx.x * kScanTile;
-    int64_t va[kScanItems], vb[kScanItems];
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-        va[k] = vb[k] = 0;
-        if (i < n) ld(i, va[k], vb[k]);
-    }
-    scan_tile_striped(va, sa[blockIdx.x], s_tile, s_warp);
-    scan_tile_striped(vb, sb[blockIdx.x], s_tile, s_warp);
-#pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-        if (i < n) {
-            oa[i] = (int32_t)va[k];
-            ob[i] = (int32_t)vb[k];
-        }
-    }
-    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-        oa[n] = (int32_t)ga;
-        ob[n] = (int32_t)gb;
-        if (ta) *ta = ga;
-        if (tb) *tb = gb;
-    }
-}
+struct Load2v {
+    Load2 ld;
+    __device__ void load(int64_t i, int64_t (&x)[2]) const { ld(i, x[0], x[1]); }
+};
 
 template <class Load2>
 static inline int scan2_impl(gs_ctx* ctx, Load2 ld, int64_t n, int32_t* oa, int64_t* ta, int32_t* ob, int64_t* tb,
@@ -309,11 +230,10 @@ static inline int scan2_impl(gs_ctx* ctx, Load2 ld, int64_t n, int32_t* oa, int6
     const int64_t nb = n > 0 ? (n + kScanTile - 1) / kScanTile : 1;
     int r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)2 * (nb + 1) * sizeof(int64_t));
     if (r != GS_OK) return r;
-    int64_t* sa = static_cast<int64_t*>(ctx->d_scan);
-    int64_t* sb = sa + nb + 1;
-    k_scan2_reduce<Load2><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sa, sb, ctx->d_scan_done);
-    k_scan2_down<Load2><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sa, sb, nb, oa, ta, ob, tb, ctx->d_err);
-    ctx->launches += 2;
+    GS_CUDA_TRY(cudaMemsetAsync(ctx->d_scan, 0, (size_t)2 * nb * sizeof(uint64_t), st));
+    k_scan_onepass<2, Load2v<Load2>><<<(unsigned)nb, kScanThreads, 0, st>>>(
+        Load2v<Load2>{ld}, n, static_cast<uint64_t*>(ctx->d_scan), nb, ctx->d_scan_done, oa, ob, ta, tb, ctx->d_err);
+    ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
@@ -322,15 +242,15 @@ template <class Load>
 static inline int scan_impl(gs_ctx* ctx, Load ld, int64_t n, int32_t* out, int64_t* total64, cudaStream_t st)
 {
     const int64_t nb = n > 0 ? (n + kScanTile - 1) / kScanTile : 1;
-    int r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)(nb + 1) * sizeof(int64_t));
+    int r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)2 * (nb + 1) * sizeof(int64_t));
     if (r != GS_OK) return r;
-    int64_t* sums = static_cast<int64_t*>(ctx->d_scan);
-    k_scan_reduce<Load><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sums, ctx->d_scan_done);
-    k_scan_down<Load><<<(unsigned)nb, kScanThreads, 0, st>>>(ld, n, sums, nb, out, total64, ctx->d_err);
-    ctx->launches += 2;
+    GS_CUDA_TRY(cudaMemsetAsync(ctx->d_scan, 0, (size_t)nb * sizeof(uint64_t), st));
+    k_scan_onepass<1, Load1<Load>><<<(unsigned)nb, kScanThreads, 0, st>>>(
+        Load1<Load>{ld}, n, static_cast<uint64_t*>(ctx->d_scan), nb, ctx->d_scan_done, out, nullptr, total64, nullptr,
+        ctx->d_err);
+    ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
-
 
 }  // namespace gs
