@@ -27,6 +27,7 @@ __global__ void __launch_bounds__(256)
 k_sample_gids(const int32_t* __restrict__ goff, int64_t n, const int64_t* __restrict__ m_dev, int64_t m_cap, int S,
               uint32_t* __restrict__ out)
 {
+    grid_dependency_sync();
     const int64_t M = live_count(m_dev, m_cap);
     if (M <= 0) return;
     const uint64_t ns = (uint64_t)(M < (int64_t)S ? M : (int64_t)S);
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(kDrThreads)
 k_depth_range(const float4* __restrict__ c_o_z, const float* __restrict__ scales, GidOf gid_of,
               const int64_t* __restrict__ m_dev, int64_t m_cap, DrArgs a, BinParams* bp)
 {
+    grid_dependency_sync();
     depth_range_block(c_o_z, scales, gid_of, live_count(m_dev, m_cap), a, bp);
 }
 
@@ -78,7 +80,7 @@ int depth_range(gs_ctx* ctx, const ProjView& pv, const float* scales, const Isec
     a.pad = c.pad;
     a.eps = c.eps;
     a.K = c.K;
-    k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, GidFromIsect{is.gid}, m_dev, m_cap, a, ctx->d_bp);
+    GS_CUDA_TRY(launch_k(ctx, k_depth_range<GidFromIsect>, 1, kDrThreads, 0, st, pv.c_o_z, scales, GidFromIsect{is.gid}, m_dev, m_cap, a, ctx->d_bp));
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -134,9 +136,9 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
     int r = samples_reserve(ctx);
     if (r != GS_OK) return r;
     if (n > 0)
-        k_sample_gids<<<(unsigned)ctx->num_sms * 4, 256, 0, st>>>(ctx->d_goff, n, m_dev, m_cap, a.S, ctx->d_samples);
-    k_depth_range<<<1, kDrThreads, 0, st>>>(pv.c_o_z, scales, GidFromSamples{ctx->d_samples}, m_dev, m_cap, a,
-                                             ctx->d_bp);
+        GS_CUDA_TRY(launch_k(ctx, k_sample_gids, (unsigned)ctx->num_sms * 4, 256, 0, st, ctx->d_goff, n, m_dev, m_cap, a.S, ctx->d_samples));
+    GS_CUDA_TRY(launch_k(ctx, k_depth_range<GidFromSamples>, 1, kDrThreads, 0, st, pv.c_o_z, scales, GidFromSamples{ctx->d_samples}, m_dev, m_cap, a,
+                                             ctx->d_bp));
     ctx->launches += 2;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -456,6 +458,7 @@ k_repair_tail(const int32_t* __restrict__ off, const int32_t* __restrict__ tail,
 __global__ void k_list_long(const int32_t* __restrict__ off, int64_t nseg, int min_len, int32_t* __restrict__ list,
                             int32_t cap, int* err, const ScatterPass sp, int K, const int32_t* __restrict__ flagged)
 {
+    grid_dependency_sync();
     if (sp.pass == 2 && flagged[0] == 0) return;  // no tile to complete
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseg; q += (int64_t)gridDim.x * blockDim.x) {
         if (off[q + 1] - off[q] < min_len) continue;
@@ -470,6 +473,7 @@ __global__ void __launch_bounds__(1024)
 k_sort_listed(const int32_t* __restrict__ off, const int32_t* __restrict__ list, int32_t cap,
               uint64_t* __restrict__ words)
 {
+    grid_dependency_sync();
     __shared__ uint64_t s_buf[kRpCtaCap];
     const int nl = min(list[0], cap);
     for (int k = blockIdx.x; k < nl; k += gridDim.x) {
@@ -510,9 +514,9 @@ int sort_long_segments(gs_ctx* ctx, int64_t nseg, const int32_t* offsets, uint64
     if ((r = bins_reserve(ctx, 1, nseg)) != GS_OK) return r;
     GS_CUDA_TRY(cudaMemsetAsync(ctx->d_tail, 0, 4, st));
     const int64_t want = (nseg + 255) / 256, grid = (int64_t)ctx->num_sms * 8;
-    k_list_long<<<(unsigned)(want < grid ? want : grid), 256, 0, st>>>(offsets, nseg, min_len, ctx->d_tail, tail_cap,
-                                                                        ctx->d_err, ScatterPass(), 1, nullptr);
-    k_sort_listed<<<(unsigned)ctx->num_sms, 1024, 0, st>>>(offsets, ctx->d_tail, tail_cap, words);
+    GS_CUDA_TRY(launch_k(ctx, k_list_long, (unsigned)(want < grid ? want : grid), 256, 0, st, offsets, nseg, min_len, ctx->d_tail, tail_cap,
+                                                                        ctx->d_err, ScatterPass(), 1, nullptr));
+    GS_CUDA_TRY(launch_k(ctx, k_sort_listed, (unsigned)ctx->num_sms, 1024, 0, st, offsets, ctx->d_tail, tail_cap, words));
     ctx->launches += 2;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -563,9 +567,9 @@ int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* wor
                 sp.T = n_tiles;
                 sp.pass = pass;
             }
-            k_list_long<<<g, 256, 0, st>>>(offsets, nseg, min_len, ctx->d_tail, tail_cap, ctx->d_err, sp, c.K,
-                                           pass ? ctx->d_plist : nullptr);
-            k_sort_listed<<<(unsigned)ctx->num_sms, 1024, 0, st>>>(offsets, ctx->d_tail, tail_cap, words);
+            GS_CUDA_TRY(launch_k(ctx, k_list_long, g, 256, 0, st, offsets, nseg, min_len, ctx->d_tail, tail_cap, ctx->d_err, sp, c.K,
+                                           pass ? ctx->d_plist : nullptr));
+            GS_CUDA_TRY(launch_k(ctx, k_sort_listed, (unsigned)ctx->num_sms, 1024, 0, st, offsets, ctx->d_tail, tail_cap, words));
             ctx->launches += 2;
         }
     } else if (n_tiles > 0)

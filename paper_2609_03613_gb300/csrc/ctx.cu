@@ -52,6 +52,7 @@ extern "C" void gs_config_default(gs_config* cfg, int32_t mode)
     cfg->planner = 0;
     cfg->wait_polls = 1 << 22;
     cfg->planner_quantile = 0.9f;
+    cfg->pdl = 1;
 }
 
 namespace gs {
@@ -72,6 +73,7 @@ int check_config(const gs_config* c)
     if (c->planner != 0 && c->planner != 1) return GS_ERR_INVALID_ARG;
     if (c->wait_polls < 0) return GS_ERR_INVALID_ARG;
     if (!(c->planner_quantile > 0.0f && c->planner_quantile <= 1.0f)) return GS_ERR_INVALID_ARG;
+    if (c->pdl != 0 && c->pdl != 1) return GS_ERR_INVALID_ARG;
     return GS_OK;
 }
 
@@ -133,6 +135,7 @@ extern "C" int gs_create(gs_ctx** out, const gs_config* cfg)
     if (cudaMalloc(&c->d_ops, sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
     if (cudaMalloc(&c->d_scan_done, sizeof(unsigned int)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
     cudaMemset(c->d_scan_done, 0, sizeof(unsigned int));
+    if (raster_bwd_prepare() != GS_OK) { gs_destroy(c); return GS_ERR_CUDA; }
     if (cudaMallocHost(&c->h_m, 2 * sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
     c->ev_ok = 1;
     for (int s = 0; s < GS_STAGE_COUNT; ++s) {

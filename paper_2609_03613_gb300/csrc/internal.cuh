@@ -96,6 +96,22 @@ __device__ inline void raise_error(int* err, int code)
     if (err) atomicCAS(err, 0, code);
 }
 
+// ------------------------------------------------------------------ programmatic dependent launch
+// A kernel launched by launch_k() on a context with cfg.pdl may be scheduled
+// while its predecessor in the stream still runs (the predecessor's blocks
+// signal it once they have all started).  Every such kernel calls
+// grid_dependency_sync() first, in every thread, before any memory access:
+// the wait returns once the predecessor grid has completed and its writes are
+// visible -- and since every kernel of the chain waits the same way, so have
+// all earlier ones -- and the signal then lets this kernel's own successor be
+// scheduled behind its last blocks.  Launched the ordinary way, both are
+// no-ops.
+__device__ __forceinline__ void grid_dependency_sync()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ elementary functions
 // exp by Cody-Waite range reduction and a degree-7 Taylor polynomial (W. J.
 // Cody and W. Waite, "Software Manual for the Elementary Functions", 1980):
@@ -263,6 +279,29 @@ struct gs_ctx {
 
 // ------------------------------------------------------------------ internal launchers
 namespace gs {
+// Launch of a frame kernel (one that starts with grid_dependency_sync()):
+// with programmatic stream serialization when the context allows it and is
+// not recording stage times (an event between two overlapped kernels would
+// not bound either of them).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(const gs_ctx* ctx, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                            cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = block;
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    if (ctx->cfg.pdl && !ctx->timing) {
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+    }
+    return cudaLaunchKernelEx(&lc, kern, static_cast<KArgs>(args)...);
+}
+
 // A whole frame of this context runs the planned two passes (EXACT, repair in
 // the raster, tile cull, planner on).
 inline bool frame_planned(const gs_ctx* c)
@@ -444,6 +483,7 @@ struct RasterView {
 int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* sched, int32_t* order, cudaStream_t st);
 
 // raster_bwd.cu
+int raster_bwd_prepare();
 int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
                int32_t stride, const float* bg, const int32_t* last, const float* final_T,
                const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, const GradView& gv,

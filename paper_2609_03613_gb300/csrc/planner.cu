@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(256, 8) k_plan_fused(const int32_t* __restrict
                                                     uint8_t* __restrict__ plan, uint8_t* __restrict__ classes,
                                                     uint8_t* __restrict__ flag, int32_t* __restrict__ list)
 {
+    grid_dependency_sync();
     __shared__ PlanShared P;
     stage_plan_params(params, P);
     if (list && blockIdx.x == 0 && threadIdx.x == 0) list[0] = 0;
@@ -437,8 +438,8 @@ int plan_frame(gs_ctx* c, const int32_t* offsets, int32_t K, int32_t T, uint8_t*
     // dependent chain, so parallelism over tiles, not fewer weight stagings,
     // sets the time
     const int grid = min((T + 7) / 8, c->num_sms * 8);
-    k_plan_fused<<<(unsigned)grid, 256, 0, st>>>(offsets, K, T, planner_layout(c), c->cfg.planner_quantile, plan, classes,
-                                                 plan + T, c->d_plist);
+    GS_CUDA_TRY(launch_k(c, k_plan_fused, (unsigned)grid, 256, 0, st, offsets, K, T, planner_layout(c), c->cfg.planner_quantile, plan, classes,
+                                                 plan + T, c->d_plist));
     c->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -479,9 +480,9 @@ extern "C" int gs_plan_tiles(gs_ctx* c, const gs_camera* cam, const int32_t* off
     const int T = gs_num_tiles(cam->width, cam->height, c->cfg.tile_size);
     if (T <= 0) return GS_ERR_INVALID_ARG;
     const int grid = min((T + 7) / 8, c->num_sms * 8);
-    k_plan_fused<<<(unsigned)grid, 256, 0, (cudaStream_t)stream>>>(offsets, stride, T, planner_layout(c),
+    GS_CUDA_TRY(launch_k(c, k_plan_fused, (unsigned)grid, 256, 0, (cudaStream_t)stream, offsets, stride, T, planner_layout(c),
                                                                    c->cfg.planner_quantile, plan, classes, nullptr,
-                                                                   nullptr);
+                                                                   nullptr));
     c->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;

@@ -308,6 +308,7 @@ k_project(const float* __restrict__ means, const float* __restrict__ scales,
           const float4* __restrict__ quats, const float* __restrict__ opac,
           const float* __restrict__ sh, int sh_aligned, int64_t n, CamArgs cam, ProjView pv, int polls, int* err)
 {
+    grid_dependency_sync();
     constexpr int NC = (DEG + 1) * (DEG + 1);
     constexpr int PER = NC * 3;  // floats of SH per Gaussian
     __shared__ __align__(16) float s_sh[kProjBlock * PER];
@@ -435,10 +436,10 @@ int launch_project(gs_ctx* ctx, const float* means, const float* scales, const f
     const unsigned grid = (unsigned)((n + kProjBlock - 1) / kProjBlock);
     const float4* q4 = reinterpret_cast<const float4*>(quats);
     switch (sh_degree) {
-        case 0: k_project<0><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err); break;
-        case 1: k_project<1><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err); break;
-        case 2: k_project<2><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err); break;
-        default: k_project<3><<<grid, kProjBlock, 0, st>>>(means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err); break;
+        case 0: GS_CUDA_TRY(launch_k(ctx, k_project<0>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err)); break;
+        case 1: GS_CUDA_TRY(launch_k(ctx, k_project<1>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err)); break;
+        case 2: GS_CUDA_TRY(launch_k(ctx, k_project<2>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err)); break;
+        default: GS_CUDA_TRY(launch_k(ctx, k_project<3>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err)); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());

@@ -297,6 +297,7 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
          int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total, float* __restrict__ out_T,
          int32_t* __restrict__ out_end, const PlanView pl, int cap)
 {
+    grid_dependency_sync();
     __shared__ RasterShared<TILE, BASELINE> sh;
     __shared__ WalkShared<LAZY> ws;
     raster_tile<TILE, BASELINE, COUNT, LAZY>(blockIdx.x, sh, ws, xy_ab, c_o_z, rgbv, words, off, a, cullmode, out_rgb,
@@ -314,6 +315,7 @@ k_raster_listed(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o
                 float* __restrict__ out_T, int32_t* __restrict__ out_end, const uint8_t* __restrict__ plan,
                 const int32_t* __restrict__ list, int cap)
 {
+    grid_dependency_sync();
     __shared__ RasterShared<TILE, false> sh;
     __shared__ WalkShared<true> ws;
     PlanView pl;
@@ -414,15 +416,16 @@ k_raster_views(const __grid_constant__ ViewRasterSet vs, const int32_t* __restri
 }
 
 template <int TILE>
-static void launch_tile(bool baseline, bool count, bool lazy, unsigned grid, cudaStream_t st, const ProjView& pv,
-                        uint64_t* words, const int32_t* off, const RasterArgs& a, int cull, float* rgb,
-                        float* alpha, int32_t* last, int32_t* ntests, unsigned long long* ops, float* final_T,
-                        int32_t* tile_end, const PlanView& pl, int cap)
+static cudaError_t launch_tile(const gs_ctx* ctx, bool baseline, bool count, bool lazy, unsigned grid,
+                               cudaStream_t st, const ProjView& pv, uint64_t* words, const int32_t* off,
+                               const RasterArgs& a, int cull, float* rgb, float* alpha, int32_t* last,
+                               int32_t* ntests, unsigned long long* ops, float* final_T, int32_t* tile_end,
+                               const PlanView& pl, int cap)
 {
     constexpr int BS = TILE * TILE;
-#define GS_RASTER_LAUNCH(B, CNT, LZ)                                                                        \
-    k_raster<TILE, B, CNT, LZ><<<grid, BS, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, (B) ? 0 : cull, \
-                                                   rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap)
+#define GS_RASTER_LAUNCH(B, CNT, LZ)                                                                          \
+    return launch_k(ctx, k_raster<TILE, B, CNT, LZ>, grid, BS, 0, st, pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, \
+                    (B) ? 0 : cull, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap)
     if (baseline) {
         if (count) GS_RASTER_LAUNCH(true, true, false);
         else GS_RASTER_LAUNCH(true, false, false);
@@ -462,11 +465,13 @@ int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* 
     if (grid == 0) return GS_OK;
     unsigned long long* ops = reinterpret_cast<unsigned long long*>(ctx->d_ops);
     if (count) GS_CUDA_TRY(cudaMemsetAsync(ops, 0, sizeof(unsigned long long), st));
+    cudaError_t e;
     switch (tile) {
-        case 8: launch_tile<8>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
-        case 32: launch_tile<32>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
-        default: launch_tile<16>(baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
+        case 8: e = launch_tile<8>(ctx, baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
+        case 32: e = launch_tile<32>(ctx, baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
+        default: e = launch_tile<16>(ctx, baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
     }
+    GS_CUDA_TRY(e);
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -491,9 +496,9 @@ int raster_listed(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_
     const int cull = ctx->cfg.tile_cull ? 2 : 0;
     const int cap = chunk_cap(ctx->cfg);
     switch (tile) {
-        case 8: k_raster_listed<8><<<(unsigned)ctx->num_sms, 64, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, offsets, a, cull, rgb, alpha, last, final_T, tile_end, plan, list, cap); break;
-        case 32: k_raster_listed<32><<<(unsigned)ctx->num_sms, 1024, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, offsets, a, cull, rgb, alpha, last, final_T, tile_end, plan, list, cap); break;
-        default: k_raster_listed<16><<<(unsigned)ctx->num_sms * 5, 256, 0, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, offsets, a, cull, rgb, alpha, last, final_T, tile_end, plan, list, cap); break;
+        case 8: GS_CUDA_TRY(launch_k(ctx, k_raster_listed<8>, (unsigned)ctx->num_sms, 64, 0, st, pv.xy_ab, pv.c_o_z, pv.rgb, words, offsets, a, cull, rgb, alpha, last, final_T, tile_end, plan, list, cap)); break;
+        case 32: GS_CUDA_TRY(launch_k(ctx, k_raster_listed<32>, (unsigned)ctx->num_sms, 1024, 0, st, pv.xy_ab, pv.c_o_z, pv.rgb, words, offsets, a, cull, rgb, alpha, last, final_T, tile_end, plan, list, cap)); break;
+        default: GS_CUDA_TRY(launch_k(ctx, k_raster_listed<16>, (unsigned)ctx->num_sms * 5, 256, 0, st, pv.xy_ab, pv.c_o_z, pv.rgb, words, offsets, a, cull, rgb, alpha, last, final_T, tile_end, plan, list, cap)); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());

@@ -146,12 +146,15 @@ __device__ __forceinline__ int64_t scan_tile32(int32_t (&v)[kScanItems], int32_t
 // NC channels of item values (one load gives all of them), each scanned into
 // its own output; out[n] = total unless it exceeds INT32_MAX - 1 (then
 // GS_ERR_CAPACITY and the outputs are not valid); totals[c] receives the
-// int64 total.  Per-item values and a tile's total must fit in int32.
+// int64 total.  dup0, when given, receives a second copy of channel 0's
+// items 0..n-1 (it may be the load's own source: a block writes only the
+// items it has read).  Per-item values and a tile's total must fit in int32.
 template <int NC, class Load>
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_onepass(Load ld, int64_t n, uint64_t* flags, int64_t nb, unsigned int* ticket, int32_t* out0, int32_t* out1,
-               int64_t* tot0, int64_t* tot1, int* err)
+               int64_t* tot0, int64_t* tot1, int* err, int32_t* dup0)
 {
+    grid_dependency_sync();
     __shared__ int32_t s_tile[kScanPadded];
     __shared__ int64_t s_warp[kScanThreads / 32];
     __shared__ int64_t s_pre[NC];
@@ -201,7 +204,10 @@ k_scan_onepass(Load ld, int64_t n, uint64_t* flags, int64_t nb, unsigned int* ti
 #pragma unroll
             for (int k = 0; k < kScanItems; ++k) {
                 const int64_t i = base + (int64_t)k * kScanThreads + threadIdx.x;
-                if (i < n) outs[c][i] = (int32_t)(pre + v[c][k]);
+                if (i < n) {
+                    outs[c][i] = (int32_t)(pre + v[c][k]);
+                    if (c == 0 && dup0) dup0[i] = (int32_t)(pre + v[c][k]);
+                }
             }
         }
         if (bid == nb - 1 && threadIdx.x == 0) {
@@ -231,23 +237,25 @@ static inline int scan2_impl(gs_ctx* ctx, Load2 ld, int64_t n, int32_t* oa, int6
     int r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)2 * (nb + 1) * sizeof(int64_t));
     if (r != GS_OK) return r;
     GS_CUDA_TRY(cudaMemsetAsync(ctx->d_scan, 0, (size_t)2 * nb * sizeof(uint64_t), st));
-    k_scan_onepass<2, Load2v<Load2>><<<(unsigned)nb, kScanThreads, 0, st>>>(
-        Load2v<Load2>{ld}, n, static_cast<uint64_t*>(ctx->d_scan), nb, ctx->d_scan_done, oa, ob, ta, tb, ctx->d_err);
+    GS_CUDA_TRY(launch_k(ctx, (k_scan_onepass<2, Load2v<Load2>>), (unsigned)nb, kScanThreads, 0, st, 
+        Load2v<Load2>{ld}, n, static_cast<uint64_t*>(ctx->d_scan), nb, ctx->d_scan_done, oa, ob, ta, tb, ctx->d_err,
+        static_cast<int32_t*>(nullptr)));
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
 }
 
 template <class Load>
-static inline int scan_impl(gs_ctx* ctx, Load ld, int64_t n, int32_t* out, int64_t* total64, cudaStream_t st)
+static inline int scan_impl(gs_ctx* ctx, Load ld, int64_t n, int32_t* out, int64_t* total64, cudaStream_t st,
+                            int32_t* dup = nullptr)
 {
     const int64_t nb = n > 0 ? (n + kScanTile - 1) / kScanTile : 1;
     int r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)2 * (nb + 1) * sizeof(int64_t));
     if (r != GS_OK) return r;
     GS_CUDA_TRY(cudaMemsetAsync(ctx->d_scan, 0, (size_t)nb * sizeof(uint64_t), st));
-    k_scan_onepass<1, Load1<Load>><<<(unsigned)nb, kScanThreads, 0, st>>>(
+    GS_CUDA_TRY(launch_k(ctx, (k_scan_onepass<1, Load1<Load>>), (unsigned)nb, kScanThreads, 0, st, 
         Load1<Load>{ld}, n, static_cast<uint64_t*>(ctx->d_scan), nb, ctx->d_scan_done, out, nullptr, total64, nullptr,
-        ctx->d_err);
+        ctx->d_err, dup));
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;

@@ -103,6 +103,7 @@ k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict
             int32_t* __restrict__ Drow, int64_t layer, uint8_t* __restrict__ gbin, uint32_t* __restrict__ rs_g,
             uint32_t* __restrict__ rs_ya, uint32_t* __restrict__ rs_w, uint32_t* __restrict__ rs_z)
 {
+    grid_dependency_sync();
     __shared__ float s_split[GS_MAX_K];
     for (int k = threadIdx.x; k < K - 1; k += blockDim.x) s_split[k] = bp->splits[k];
     __syncthreads();
@@ -176,6 +177,7 @@ k_row_spans(const uint2* __restrict__ rect, int64_t n, const int32_t* __restrict
 __global__ void __launch_bounds__(1024)
 k_layer_rows_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y, int64_t layer)
 {
+    grid_dependency_sync();
     const int W1 = tiles_x + 1;
     int32_t* L = D + (int64_t)blockIdx.x * layer;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -210,6 +212,7 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
                    const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ cur,
                    uint64_t* __restrict__ words, const ScatterPass sp, const int32_t* __restrict__ flagged)
 {
+    grid_dependency_sync();
     if (*m_dev > m_cap) return;
     if (sp.pass == 2 && flagged[0] == 0) return;  // no tile to complete
     const int64_t R = roff[n];
@@ -277,6 +280,7 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
 __global__ void k_flagged_cursors(const int32_t* __restrict__ list, const int32_t* __restrict__ offsets, int K,
                                   int32_t* __restrict__ cur)
 {
+    grid_dependency_sync();
     const int32_t nl = list[0];
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nl * K; i += gridDim.x * blockDim.x) {
         const int64_t q = (int64_t)list[1 + i / K] * K + i % K;
@@ -316,6 +320,7 @@ k_group_count(const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ r
               int64_t n, int K, int nkeys, const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ H,
               const ScatterPass sp, int tiles_x)
 {
+    grid_dependency_sync();
     extern __shared__ int32_t s_h[];
     const int C = gridDim.x, c = blockIdx.x;
     for (int i = threadIdx.x; i < nkeys; i += blockDim.x) s_h[i] = 0;
@@ -342,6 +347,7 @@ k_group_write(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs
               int64_t n, int K, int nkeys, const int64_t* __restrict__ m_dev, int64_t m_cap,
               const int32_t* __restrict__ Hs, uint4* __restrict__ list, const ScatterPass sp, int tiles_x)
 {
+    grid_dependency_sync();
     extern __shared__ int32_t s_h[];  // [nkeys] next slot, from the slice's base
     const int C = gridDim.x, c = blockIdx.x;
     if (*m_dev > m_cap) return;
@@ -368,6 +374,7 @@ k_scatter_groups(const uint4* __restrict__ list, const int32_t* __restrict__ Hs,
                  int64_t m_cap, uint64_t* __restrict__ words, const ScatterPass sp,
                  const int32_t* __restrict__ flagged)
 {
+    grid_dependency_sync();
     extern __shared__ int32_t s_cur[];  // [tiles_x]
     const int key = blockIdx.x;
     if (*m_dev > m_cap) return;
@@ -441,6 +448,7 @@ __global__ void __launch_bounds__(256)
 k_transpose_counts(const int32_t* __restrict__ D, int tiles_x, int tiles_y, int K, int64_t layer,
                    int32_t* __restrict__ C)
 {
+    grid_dependency_sync();
     __shared__ int32_t s[32][33];
     const int y = blockIdx.z;
     const int x0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
@@ -478,6 +486,7 @@ struct LoadLayerCount {
 __global__ void k_zero_if_over(const int64_t* __restrict__ m_dev, int64_t m_cap, int32_t* __restrict__ off, int64_t nq,
                                int* err)
 {
+    grid_dependency_sync();
     if (*m_dev <= m_cap) return;  // over capacity: empty stream, nothing out of bounds downstream
     if (blockIdx.x == 0 && threadIdx.x == 0) raise_error(err, GS_ERR_CAPACITY);
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x)
@@ -541,45 +550,55 @@ int exact_bins_reserve(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t tiles_x, i
     return r;
 }
 
+// Whether a first-pass scatter takes the grouped path (records grouped by
+// (tile row, bin), cursors in shared memory) rather than per-entry global
+// cursors.
+static bool grouped_path(int64_t m_cap, int32_t tiles_x, int32_t tiles_y, int K)
+{
+    return grouped_scatter(m_cap, (int64_t)tiles_x * tiles_y) && tiles_y * K <= kMaxGroupKeys;
+}
+
 // The record scatter of the tile-cull path, for one pass (grouped by (tile
 // row, bin) on deep frames, else per-entry global cursors, `cur` being
-// initialised from the offsets before the first pass).
+// initialised from the offsets before the first pass -- unless the offsets'
+// scan already wrote them there, cur_ready).
 static int exact_scatter(gs_ctx* ctx, const ExactScratch& v, int64_t n, int32_t tiles_x, int32_t tiles_y, int K,
                          int64_t m_cap, const int64_t* m_dev, uint64_t* words, const int32_t* offsets,
-                         const ScatterPass& sp, cudaStream_t st)
+                         const ScatterPass& sp, cudaStream_t st, bool cur_ready = false)
 {
     const int64_t T = (int64_t)tiles_x * tiles_y;
     const int nkeys = tiles_y * K;
     const unsigned g_sm = (unsigned)ctx->num_sms * 8;
     const int32_t* flagged = sp.pass ? ctx->d_plist : nullptr;
     if (n <= 0) return GS_OK;
-    if (sp.pass != 2 && grouped_scatter(m_cap, T) && nkeys <= kMaxGroupKeys) {
+    if (sp.pass != 2 && grouped_path(m_cap, tiles_x, tiles_y, K)) {
         // records grouped by (tile row, bin), then cursors in shared memory
         // (a planned first pass groups only the records it keeps)
         const int C = group_slices(ctx->num_sms);
         const size_t hsm = (size_t)nkeys * 4;
-        k_group_count<<<(unsigned)C, kGroupThreads, hsm, st>>>(v.rs_ya, v.rs_w, v.roff, n, K, nkeys, m_dev, m_cap,
-                                                                v.H, sp, tiles_x);
+        GS_CUDA_TRY(launch_k(ctx, k_group_count, (unsigned)C, kGroupThreads, hsm, st, v.rs_ya, v.rs_w, v.roff, n, K, nkeys, m_dev, m_cap,
+                                                                v.H, sp, tiles_x));
         ctx->launches += 1;
         int r;
         if ((r = scan_impl(ctx, LoadI32{v.H}, (int64_t)nkeys * C, v.Hs, nullptr, st)) != GS_OK) return r;
-        k_group_write<<<(unsigned)C, kGroupThreads, hsm, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, K, nkeys,
-                                                                m_dev, m_cap, v.Hs, v.list, sp, tiles_x);
-        k_scatter_groups<<<(unsigned)nkeys, kScatterGroupThreads, (size_t)tiles_x * 4, st>>>(
-            v.list, v.Hs, C, offsets, tiles_x, K, m_dev, m_cap, words, sp, flagged);
+        GS_CUDA_TRY(launch_k(ctx, k_group_write, (unsigned)C, kGroupThreads, hsm, st, v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, K, nkeys,
+                                                                m_dev, m_cap, v.Hs, v.list, sp, tiles_x));
+        GS_CUDA_TRY(launch_k(ctx, k_scatter_groups, (unsigned)nkeys, kScatterGroupThreads, (size_t)tiles_x * 4, st, 
+            v.list, v.Hs, C, offsets, tiles_x, K, m_dev, m_cap, words, sp, flagged));
         ctx->launches += 2;
     } else {
         // per-entry cursors in global memory: all of them from the offsets
         // before a first pass, those of the flagged tiles before the
         // completing pass (few entries: no grouping)
         if (sp.pass != 2) {
-            GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)T * K * 4, cudaMemcpyDeviceToDevice, st));
+            if (!cur_ready)
+                GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)T * K * 4, cudaMemcpyDeviceToDevice, st));
         } else {
-            k_flagged_cursors<<<(unsigned)ctx->num_sms * 2, 256, 0, st>>>(flagged, offsets, K, v.cur);
+            GS_CUDA_TRY(launch_k(ctx, k_flagged_cursors, (unsigned)ctx->num_sms * 2, 256, 0, st, flagged, offsets, K, v.cur));
             ctx->launches += 1;
         }
-        k_bin_scatter_rows<<<g_sm * 2, 256, 0, st>>>(v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, tiles_x, K, m_dev,
-                                                     m_cap, v.cur, words, sp, flagged);
+        GS_CUDA_TRY(launch_k(ctx, k_bin_scatter_rows, g_sm * 2, 256, 0, st, v.rs_g, v.rs_ya, v.rs_w, v.rs_z, v.roff, n, tiles_x, K, m_dev,
+                                                     m_cap, v.cur, words, sp, flagged));
         ctx->launches += 1;
     }
     GS_CUDA_TRY(cudaGetLastError());
@@ -628,17 +647,20 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
         CullArgs ca{pv.xy_ab, pv.c_o_z, pv.rgb, tile};
         const int64_t warps = (n + 31) / 32;
         if (warps > 0)
-            k_row_spans<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(pv.rect, n, v.roff, ca, tiles_x, ctx->d_bp, K,
+            GS_CUDA_TRY(launch_k(ctx, k_row_spans, (unsigned)((warps + 7) / 8), 256, 0, st, pv.rect, n, v.roff, ca, tiles_x, ctx->d_bp, K,
                                                                      m_dev, m_cap, v.D, rlayer, v.gbin, v.rs_g,
-                                                                     v.rs_ya, v.rs_w, v.rs_z);
-        k_layer_rows_prefix<<<(unsigned)K, 1024, 0, st>>>(v.D, tiles_x, tiles_y, rlayer);
+                                                                     v.rs_ya, v.rs_w, v.rs_z));
+        GS_CUDA_TRY(launch_k(ctx, k_layer_rows_prefix, (unsigned)K, 1024, 0, st, v.D, tiles_x, tiles_y, rlayer));
         // the counts tile-major (the cursor array serves as the staging copy;
-        // it is rewritten with the offsets below), then a coalesced scan
-        k_transpose_counts<<<dim3((unsigned)((tiles_x + 31) / 32), (unsigned)((K + 31) / 32), (unsigned)tiles_y), 256, 0,
-                             st>>>(v.D, tiles_x, tiles_y, K, rlayer, v.cur);
+        // the scan rewrites it with the offsets when the per-entry scatter
+        // will start its cursors there), then a coalesced scan
+        GS_CUDA_TRY(launch_k(ctx, k_transpose_counts, dim3((unsigned)((tiles_x + 31) / 32), (unsigned)((K + 31) / 32), (unsigned)tiles_y), 256, 0, st, v.D, tiles_x, tiles_y, K, rlayer, v.cur));
         ctx->launches += 3;
-        if ((r = scan_impl(ctx, LoadPlainCount{v.cur}, nseg, offsets, nullptr, st)) != GS_OK) return r;
-        k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1, ctx->d_err);
+        const bool cur_ready = n > 0 && !grouped_path(m_cap, tiles_x, tiles_y, K);
+        if ((r = scan_impl(ctx, LoadPlainCount{v.cur}, nseg, offsets, nullptr, st, cur_ready ? v.cur : nullptr)) !=
+            GS_OK)
+            return r;
+        GS_CUDA_TRY(launch_k(ctx, k_zero_if_over, g_sm, 256, 0, st, m_dev, m_cap, offsets, nseg + 1, ctx->d_err));
         ctx->launches += 1;
         ScatterPass sp;
         if (planned) {
@@ -649,7 +671,8 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
             sp.T = (int32_t)T;
             sp.pass = 1;
         }
-        if ((r = exact_scatter(ctx, v, n, tiles_x, tiles_y, K, m_cap, m_dev, words, offsets, sp, st)) != GS_OK)
+        if ((r = exact_scatter(ctx, v, n, tiles_x, tiles_y, K, m_cap, m_dev, words, offsets, sp, st, cur_ready)) !=
+            GS_OK)
             return r;
     } else {
         // whole rects per bin layer: four atomics per Gaussian, 2D prefix sums
@@ -660,7 +683,7 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
         if ((r = scan_impl(ctx, LoadLayerCount{v.D, K, tiles_x, tiles_x + 1, (int64_t)layer}, nseg, offsets, nullptr,
                            st)) != GS_OK)
             return r;
-        k_zero_if_over<<<g_sm, 256, 0, st>>>(m_dev, m_cap, offsets, nseg + 1, ctx->d_err);
+        GS_CUDA_TRY(launch_k(ctx, k_zero_if_over, g_sm, 256, 0, st, m_dev, m_cap, offsets, nseg + 1, ctx->d_err));
         GS_CUDA_TRY(cudaMemcpyAsync(v.cur, offsets, (size_t)nseg * 4, cudaMemcpyDeviceToDevice, st));
         const int64_t warps = (n + 31) / 32;
         if (warps > 0)

@@ -64,7 +64,7 @@ class GsConfig(C.Structure):
                 ("eps", C.c_float), ("repair_budget_frac", C.c_float), ("near_shift", C.c_int32),
                 ("tile_cull", C.c_int32), ("persistent", C.c_int32), ("repair_in_raster", C.c_int32),
                 ("chunk_cap", C.c_int32), ("planner", C.c_int32), ("wait_polls", C.c_int32),
-                ("planner_quantile", C.c_float)]
+                ("planner_quantile", C.c_float), ("pdl", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
