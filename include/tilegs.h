@@ -140,12 +140,12 @@ typedef struct gs_config {
                               in (0, 1] (gs_config_default: 0.9) */
     int32_t pdl;           /* 1 (gs_config_default): the kernels of a frame are
                               launched with programmatic stream serialization, so
-                              each one's blocks are scheduled while its
-                              predecessor's last blocks run (every such kernel
-                              waits for its predecessor's completion before it
-                              touches memory).  0: ordinary launches.  Frames
-                              that record stage times (gs_enable_timing) use
-                              ordinary launches.  Changes speed only. */
+                              each one is set up while its predecessor drains
+                              (every such kernel waits for its predecessor's
+                              completion before it touches memory).  0: ordinary
+                              launches.  Frames that record stage times
+                              (gs_enable_timing) use ordinary launches.  Changes
+                              speed only. */
 } gs_config;
 
 /* Fill *cfg with the paper's defaults (supplement, default No-GW configuration

@@ -25,9 +25,10 @@ struct GidFromIsect {
 // One thread per Gaussian (coalesced reads of goff; empty Gaussians own none).
 __global__ void __launch_bounds__(256)
 k_sample_gids(const int32_t* __restrict__ goff, int64_t n, const int64_t* __restrict__ m_dev, int64_t m_cap, int S,
-              uint32_t* __restrict__ out)
+              uint32_t* __restrict__ out, FrameZero fz)
 {
     grid_dependency_sync();
+    frame_zero(fz);  // the frame's bin-stage counts, later scan flags, repair counter
     const int64_t M = live_count(m_dev, m_cap);
     if (M <= 0) return;
     const uint64_t ns = (uint64_t)(M < (int64_t)S ? M : (int64_t)S);
@@ -135,8 +136,15 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
     a.K = c.K;
     int r = samples_reserve(ctx);
     if (r != GS_OK) return r;
-    if (n > 0)
-        GS_CUDA_TRY(launch_k(ctx, k_sample_gids, (unsigned)ctx->num_sms * 4, 256, 0, st, ctx->d_goff, n, m_dev, m_cap, a.S, ctx->d_samples));
+    if (n > 0) {
+        FrameZero late;
+        for (int k = 0; k < 3; ++k) {
+            late.p[k] = ctx->late_p[k];
+            late.n[k] = ctx->late_n[k];
+            ctx->late_p[k] = nullptr;
+        }
+        GS_CUDA_TRY(launch_k(ctx, k_sample_gids, (unsigned)ctx->num_sms * 4, 256, 0, st, ctx->d_goff, n, m_dev, m_cap, a.S, ctx->d_samples, late));
+    }
     GS_CUDA_TRY(launch_k(ctx, k_depth_range<GidFromSamples>, 1, kDrThreads, 0, st, pv.c_o_z, scales, GidFromSamples{ctx->d_samples}, m_dev, m_cap, a,
                                              ctx->d_bp));
     ctx->launches += 2;
@@ -556,7 +564,9 @@ int repair_min(gs_ctx* ctx, int32_t n_tiles, const int64_t* m_dev, uint64_t* wor
     }
     const int32_t tail_cap = tail_capacity(nseg);
     if ((r = bins_reserve(ctx, 1, nseg)) != GS_OK) return r;
-    GS_CUDA_TRY(cudaMemsetAsync(ctx->d_tail, 0, 4, st));
+    if (!(ctx->zeroed_tail == ctx->d_tail && ctx->zeroed_tail_bytes == ctx->tail_cap))
+        GS_CUDA_TRY(cudaMemsetAsync(ctx->d_tail, 0, 4, st));
+    ctx->zeroed_tail = nullptr;  // zeroed by the frame's first kernel once, for this call
     if (c.mode == GS_MODE_BINNED_EXACT && min_len > kRpWarpCap) {
         if (nseg > 0) {
             const int64_t want = (nseg + 255) / 256;

@@ -271,7 +271,7 @@ static bool cam_ok(const gs_camera* cam) { return camera_ok(cam); }
 namespace gs {
 int launch_project(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
                    const float* opac, const float* sh, int32_t sh_degree, int64_t n,
-                   const gs_camera* cam, const ProjView& pv, cudaStream_t st);
+                   const gs_camera* cam, const ProjView& pv, cudaStream_t st, const FrameZero& fz = FrameZero());
 int launch_emit(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
                 const IsectView& is, int64_t m_cap, int64_t* m_dev, cudaStream_t st);
 }  // namespace gs
@@ -716,13 +716,25 @@ static int render_impl(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, cons
     }
     if ((r = render_buffers(c, n, c->r_m_cap > 0 ? c->r_m_cap : 1, T)) != GS_OK) return r;
     ProjView pv = proj_view(c->r_proj, n);
+    frame_zero_reset(c);
     if (n > 0) {
+        // the projection and the depth-range sampling also zero what the
+        // frame's later kernels count into (EXACT with the tile cull), so no
+        // memset sits between kernels
+        FrameZero fz;
+        if (c->cfg.mode == GS_MODE_BINNED_EXACT && c->cfg.tile_cull &&
+            (r = exact_frame_zero(c, n, cam, c->r_m_cap, &fz)) != GS_OK)
+            return r;
         stage_begin(c, GS_STAGE_PROJECT, st);
-        r = launch_project(c, means, scales, quats, opac, sh, sc->sh_degree, n, cam, pv, st);
+        r = launch_project(c, means, scales, quats, opac, sh, sc->sh_degree, n, cam, pv, st, fz);
         stage_end(c, GS_STAGE_PROJECT, st);
-        if (r != GS_OK) return r;
+        if (r != GS_OK) {
+            frame_zero_reset(c);
+            return r;
+        }
     }
     r = render_after_project(c, n, scales, cam, bg, d_rgb, d_alpha, d_last, flags, st);
+    frame_zero_reset(c);
     if (r != GS_OK) return r;
     if (flags & GS_RENDER_HOST_OUTPUTS) {
         const size_t px = (size_t)W * H;
@@ -760,6 +772,10 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
         int64_t m_cap;
         gs_config cfg;
         int timing, device, flags;
+        // the internal scratch the captured kernels address (a grown buffer
+        // is a new allocation: the graph is captured again)
+        const void* scratch[14];
+        size_t scratch_bytes[10];
     } key;
     if (flags & GS_RENDER_SAVE) {
         // allocate outside the capture
@@ -787,6 +803,15 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
     key.flags = flags;
     key.saved_T = c->r_T;
     key.saved_end = c->r_tend;
+    const void* scratch[] = {c->d_scan, c->d_goff, c->d_keys[0], c->d_keys[1], c->d_vals[0], c->d_vals[1],
+                             c->d_hist, c->d_count, c->d_bin, c->d_sel, c->d_tail, c->d_tiles, c->d_samples,
+                             c->d_plan};
+    const size_t scratch_bytes[] = {c->scan_bytes, c->goff_cap, c->sort_cap, c->hist_cap, c->count_cap,
+                                    c->bin_cap, c->sel_cap, c->tail_cap, c->tiles_cap, c->samples_cap};
+    static_assert(sizeof(scratch) == sizeof(key.scratch) && sizeof(scratch_bytes) == sizeof(key.scratch_bytes),
+                  "graph key scratch");
+    memcpy(key.scratch, scratch, sizeof(scratch));
+    memcpy(key.scratch_bytes, scratch_bytes, sizeof(scratch_bytes));
     static_assert(sizeof(Key) <= sizeof(c->gkey), "graph key");
     if (!(c->gexec && c->gkey_len == sizeof(Key) && memcmp(c->gkey, &key, sizeof(Key)) == 0)) {
         if (c->gexec) {

@@ -1,10 +1,8 @@
 // intersect.cu -- K3 tile intersection (Sec. 3.1: one record per covered
 // tile) and the device-wide exclusive scans it and the binning use.
 //
-// Scan (scan.cuh): two kernels without inter-block waits (reduce per block,
-// the last block scanning the block sums -> per-block rescan with the
-// prefix), all in int64 so an overflowing total is detected instead of
-// wrapping.
+// Scan (scan.cuh): one pass with decoupled look-back and bounded waits,
+// totals in int64 so an overflowing total is detected instead of wrapping.
 #include "device.cuh"
 #include "scan.cuh"
 
@@ -143,7 +141,12 @@ int reserve_internal(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t width, int32
     int64_t nscan = n > nseg ? n : nseg;
     const int64_t ngroup = group_scan_items(ctx, tiles_y, GS_MAX_K);
     if (ngroup > nscan) nscan = ngroup;
-    if ((r = scan_reserve(ctx, nscan)) != GS_OK) return r;
+    // a frame's scan-flag arena (the row-count scan's two channels, the
+    // offsets scan, the grouped scatter's scan) and, past it, the flags of
+    // any one further scan
+    auto blocks = [](int64_t items) { return items > 0 ? (items + kScanTile - 1) / kScanTile : 1; };
+    const int64_t words = 2 * blocks(n) + blocks(nseg) + blocks(ngroup) + 2 * blocks(nscan) + 4;
+    if ((r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)words * sizeof(uint64_t))) != GS_OK) return r;
     if ((r = goff_reserve(ctx, n)) != GS_OK) return r;
     if ((r = samples_reserve(ctx)) != GS_OK) return r;
     if (ctx->cfg.mode == GS_MODE_GLOBAL_SORT) return sort_reserve(ctx, m_cap);

@@ -306,9 +306,11 @@ template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
 k_project(const float* __restrict__ means, const float* __restrict__ scales,
           const float4* __restrict__ quats, const float* __restrict__ opac,
-          const float* __restrict__ sh, int sh_aligned, int64_t n, CamArgs cam, ProjView pv, int polls, int* err)
+          const float* __restrict__ sh, int sh_aligned, int64_t n, CamArgs cam, ProjView pv, int polls, int* err,
+          FrameZero fz)
 {
     grid_dependency_sync();
+    frame_zero(fz);  // the frame's first scan's flags
     constexpr int NC = (DEG + 1) * (DEG + 1);
     constexpr int PER = NC * 3;  // floats of SH per Gaussian
     __shared__ __align__(16) float s_sh[kProjBlock * PER];
@@ -426,7 +428,7 @@ int launch_project_batch(gs_ctx* ctx, const float* means, const float* scales, c
 
 int launch_project(gs_ctx* ctx, const float* means, const float* scales, const float* quats,
                    const float* opac, const float* sh, int32_t sh_degree, int64_t n,
-                   const gs_camera* cam, const ProjView& pv, cudaStream_t st)
+                   const gs_camera* cam, const ProjView& pv, cudaStream_t st, const FrameZero& fz)
 {
     if (n <= 0) return GS_OK;
     if (reinterpret_cast<uintptr_t>(quats) & 15) return GS_ERR_INVALID_ARG;  // float4 loads
@@ -436,10 +438,10 @@ int launch_project(gs_ctx* ctx, const float* means, const float* scales, const f
     const unsigned grid = (unsigned)((n + kProjBlock - 1) / kProjBlock);
     const float4* q4 = reinterpret_cast<const float4*>(quats);
     switch (sh_degree) {
-        case 0: GS_CUDA_TRY(launch_k(ctx, k_project<0>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err)); break;
-        case 1: GS_CUDA_TRY(launch_k(ctx, k_project<1>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err)); break;
-        case 2: GS_CUDA_TRY(launch_k(ctx, k_project<2>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err)); break;
-        default: GS_CUDA_TRY(launch_k(ctx, k_project<3>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err)); break;
+        case 0: GS_CUDA_TRY(launch_k(ctx, k_project<0>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err, fz)); break;
+        case 1: GS_CUDA_TRY(launch_k(ctx, k_project<1>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err, fz)); break;
+        case 2: GS_CUDA_TRY(launch_k(ctx, k_project<2>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err, fz)); break;
+        default: GS_CUDA_TRY(launch_k(ctx, k_project<3>, grid, kProjBlock, 0, st, means, scales, q4, opac, sh, aligned, n, ca, pv, polls, ctx->d_err, fz)); break;
     }
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());

@@ -229,17 +229,37 @@ struct Load2v {
     __device__ void load(int64_t i, int64_t (&x)[2]) const { ld(i, x[0], x[1]); }
 };
 
+// The flag words of one scan of nw words: the next piece of the frame's
+// pre-zeroed arena, or (no arena, or the arena is spent) words past the arena
+// cleared here.
+static inline int scan_flags(gs_ctx* ctx, int64_t nw, uint64_t** flags, cudaStream_t st)
+{
+    if (ctx->scan_arena > 0 && ctx->scan_bytes != ctx->scan_arena_bytes) ctx->scan_arena = 0;  // reallocated
+    if (ctx->scan_arena > 0 && ctx->scan_used + nw <= ctx->scan_arena) {
+        *flags = static_cast<uint64_t*>(ctx->d_scan) + ctx->scan_used;
+        ctx->scan_used += nw;
+        return GS_OK;
+    }
+    const size_t bytes = ctx->scan_bytes;
+    int r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)(ctx->scan_arena + nw + 2) * sizeof(uint64_t));
+    if (r != GS_OK) return r;
+    if (ctx->scan_bytes != bytes) ctx->scan_arena = 0;
+    *flags = static_cast<uint64_t*>(ctx->d_scan) + ctx->scan_arena;
+    GS_CUDA_TRY(cudaMemsetAsync(*flags, 0, (size_t)nw * sizeof(uint64_t), st));
+    return GS_OK;
+}
+
 template <class Load2>
 static inline int scan2_impl(gs_ctx* ctx, Load2 ld, int64_t n, int32_t* oa, int64_t* ta, int32_t* ob, int64_t* tb,
                              cudaStream_t st)
 {
     const int64_t nb = n > 0 ? (n + kScanTile - 1) / kScanTile : 1;
-    int r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)2 * (nb + 1) * sizeof(int64_t));
+    uint64_t* flags;
+    int r = scan_flags(ctx, 2 * nb, &flags, st);
     if (r != GS_OK) return r;
-    GS_CUDA_TRY(cudaMemsetAsync(ctx->d_scan, 0, (size_t)2 * nb * sizeof(uint64_t), st));
-    GS_CUDA_TRY(launch_k(ctx, (k_scan_onepass<2, Load2v<Load2>>), (unsigned)nb, kScanThreads, 0, st, 
-        Load2v<Load2>{ld}, n, static_cast<uint64_t*>(ctx->d_scan), nb, ctx->d_scan_done, oa, ob, ta, tb, ctx->d_err,
-        static_cast<int32_t*>(nullptr)));
+    GS_CUDA_TRY(launch_k(ctx, (k_scan_onepass<2, Load2v<Load2>>), (unsigned)nb, kScanThreads, 0, st,
+                         Load2v<Load2>{ld}, n, flags, nb, ctx->d_scan_done, oa, ob, ta, tb, ctx->d_err,
+                         static_cast<int32_t*>(nullptr)));
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;
@@ -250,12 +270,11 @@ static inline int scan_impl(gs_ctx* ctx, Load ld, int64_t n, int32_t* out, int64
                             int32_t* dup = nullptr)
 {
     const int64_t nb = n > 0 ? (n + kScanTile - 1) / kScanTile : 1;
-    int r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)2 * (nb + 1) * sizeof(int64_t));
+    uint64_t* flags;
+    int r = scan_flags(ctx, nb, &flags, st);
     if (r != GS_OK) return r;
-    GS_CUDA_TRY(cudaMemsetAsync(ctx->d_scan, 0, (size_t)nb * sizeof(uint64_t), st));
-    GS_CUDA_TRY(launch_k(ctx, (k_scan_onepass<1, Load1<Load>>), (unsigned)nb, kScanThreads, 0, st, 
-        Load1<Load>{ld}, n, static_cast<uint64_t*>(ctx->d_scan), nb, ctx->d_scan_done, out, nullptr, total64, nullptr,
-        ctx->d_err, dup));
+    GS_CUDA_TRY(launch_k(ctx, (k_scan_onepass<1, Load1<Load>>), (unsigned)nb, kScanThreads, 0, st, Load1<Load>{ld}, n,
+                         flags, nb, ctx->d_scan_done, out, nullptr, total64, nullptr, ctx->d_err, dup));
     ctx->launches += 1;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;

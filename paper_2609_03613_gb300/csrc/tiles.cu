@@ -605,6 +605,50 @@ static int exact_scatter(gs_ctx* ctx, const ExactScratch& v, int64_t n, int32_t 
     return GS_OK;
 }
 
+// The regions a frame of the tile-cull EXACT path needs zeroed, so that no
+// memset sits between its kernels: the frame's scan-flag arena (the row-count
+// scan, the offsets scan and, on deep frames, the grouped scatter's count
+// scan), the bin stage's difference counts, the repair's long-segment
+// counter.  The projection (*fz) clears the row-count scan's flags, the
+// depth-range sampling (ctx->late_*) the rest.  Reserves the scratch they
+// live in.
+int exact_frame_zero(gs_ctx* ctx, int64_t n, const gs_camera* cam, int64_t m_cap, FrameZero* fz)
+{
+    const int tile = ctx->cfg.tile_size, K = ctx->cfg.K;
+    const int32_t tiles_x = (cam->width + tile - 1) / tile, tiles_y = (cam->height + tile - 1) / tile;
+    const int64_t T = (int64_t)tiles_x * tiles_y, nseg = T * K;
+    int r;
+    if ((r = exact_bins_reserve(ctx, n, m_cap, tiles_x, tiles_y, K)) != GS_OK) return r;
+    if ((r = bins_reserve(ctx, 1, nseg)) != GS_OK) return r;
+    ExactScratch v;
+    exact_scratch(ctx, n, m_cap, tiles_x, tiles_y, K, &v);
+    auto blocks = [](int64_t items) { return items > 0 ? (items + kScanTile - 1) / kScanTile : 1; };
+    int64_t words = 2 * blocks(n) + blocks(nseg);
+    if (grouped_path(m_cap, tiles_x, tiles_y, K))
+        words += blocks((int64_t)tiles_y * K * group_slices(ctx->num_sms));
+    if ((size_t)(words + 2) * sizeof(uint64_t) > ctx->scan_bytes) {
+        if (ctx->capturing) return GS_OK;  // no allocation inside a capture: the scans clear their own flags
+        if ((r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)(words + 2) * sizeof(uint64_t))) != GS_OK) return r;
+    }
+    const int64_t w2 = 2 * blocks(n);  // the row-count scan's flags: cleared by the projection
+    fz->p[0] = static_cast<int32_t*>(ctx->d_scan);
+    fz->n[0] = 2 * w2;
+    ctx->late_p[0] = v.D;
+    ctx->late_n[0] = (int64_t)(tiles_x + 1) * (tiles_y + 1) * K;
+    ctx->late_p[1] = static_cast<int32_t*>(ctx->d_scan) + 2 * w2;
+    ctx->late_n[1] = 2 * (words - w2);
+    ctx->late_p[2] = ctx->d_tail;
+    ctx->late_n[2] = 1;
+    ctx->scan_arena = words;
+    ctx->scan_used = 0;
+    ctx->scan_arena_bytes = ctx->scan_bytes;
+    ctx->zeroed_D = v.D;
+    ctx->zeroed_D_bytes = ctx->tiles_cap;
+    ctx->zeroed_tail = ctx->d_tail;
+    ctx->zeroed_tail_bytes = ctx->tail_cap;
+    return GS_OK;
+}
+
 int exact_scatter_rest(gs_ctx* ctx, int64_t n, const gs_camera* cam, int64_t m_cap, const int64_t* m_dev,
                        uint64_t* words, const int32_t* offsets, cudaStream_t st)
 {
@@ -633,7 +677,9 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
     exact_scratch(ctx, n, m_cap, tiles_x, tiles_y, K, &v);
     const size_t layer = (size_t)(tiles_x + 1) * (tiles_y + 1);
     if (tiles_x > 4096 || tiles_y > 4096) return GS_ERR_INVALID_ARG;  // row-record packing
-    GS_CUDA_TRY(cudaMemsetAsync(v.D, 0, layer * K * 4, st));
+    if (!(ctx->zeroed_D == v.D && ctx->zeroed_D_bytes == ctx->tiles_cap))
+        GS_CUDA_TRY(cudaMemsetAsync(v.D, 0, layer * K * 4, st));
+    ctx->zeroed_D = nullptr;  // zeroed by the frame's first kernel once, for this call
     const unsigned g_sm = (unsigned)ctx->num_sms * 8;
     if (ctx->cfg.tile_cull) {
         // rows of every rect, each row's culled span, per-row difference counts
