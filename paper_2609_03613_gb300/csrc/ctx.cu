@@ -135,7 +135,7 @@ extern "C" int gs_create(gs_ctx** out, const gs_config* cfg)
     if (cudaMalloc(&c->d_ops, sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
     if (cudaMalloc(&c->d_scan_done, sizeof(unsigned int)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
     cudaMemset(c->d_scan_done, 0, sizeof(unsigned int));
-    if (raster_bwd_prepare() != GS_OK) { gs_destroy(c); return GS_ERR_CUDA; }
+    if (raster_bwd_prepare() != GS_OK || bin_offsets_prepare() != GS_OK) { gs_destroy(c); return GS_ERR_CUDA; }
     if (cudaMallocHost(&c->h_m, 2 * sizeof(int64_t)) != cudaSuccess) { gs_destroy(c); return GS_ERR_NO_MEMORY; }
     c->ev_ok = 1;
     for (int s = 0; s < GS_STAGE_COUNT; ++s) {

@@ -540,6 +540,8 @@ int raster_views(gs_ctx* ctx, const RasterView* views, int nv, int32_t* sched, i
 
 // raster_bwd.cu
 int raster_bwd_prepare();
+// tiles.cu
+int bin_offsets_prepare();
 int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
                int32_t stride, const float* bg, const int32_t* last, const float* final_T,
                const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, const GradView& gv,

@@ -145,7 +145,7 @@ int reserve_internal(gs_ctx* ctx, int64_t n, int64_t m_cap, int32_t width, int32
     // offsets scan, the grouped scatter's scan) and, past it, the flags of
     // any one further scan
     auto blocks = [](int64_t items) { return items > 0 ? (items + kScanTile - 1) / kScanTile : 1; };
-    const int64_t words = 2 * blocks(n) + blocks(nseg) + blocks(ngroup) + 2 * blocks(nscan) + 4;
+    const int64_t words = 2 * blocks(n) + blocks(nseg) + tiles_y + blocks(ngroup) + 2 * blocks(nscan) + 4;
     if ((r = ensure(&ctx->d_scan, &ctx->scan_bytes, (size_t)words * sizeof(uint64_t))) != GS_OK) return r;
     if ((r = goff_reserve(ctx, n)) != GS_OK) return r;
     if ((r = samples_reserve(ctx)) != GS_OK) return r;

@@ -465,6 +465,120 @@ k_transpose_counts(const int32_t* __restrict__ D, int tiles_x, int tiles_y, int 
     }
 }
 
+// The (tile, bin) segment offsets from the layered row differences
+// D[b][ty][x] in one pass, tile-major (t = ty tiles_x + x, bins inside): one
+// block per tile row (taken in ticket order) forms its counts by a prefix
+// along x per bin, scans them in tile-major order, finds the rows before it
+// by decoupled look-back over the rows' published totals (bounded waits),
+// and writes offsets and, when given, the scatter cursors.  Over capacity
+// (or past INT32_MAX) every offset is written 0 and GS_ERR_CAPACITY raised,
+// so nothing downstream reads out of bounds.  Replaces a per-layer prefix,
+// a transposition, a device-wide scan and the over-capacity pass.
+constexpr int kOffThreads = 1024;
+constexpr size_t kOffMaxSmem = 160 * 1024;
+__host__ __device__ inline size_t bin_offsets_smem(int tiles_x, int K) { return (size_t)tiles_x * (K + 1) * 4; }
+
+__global__ void __launch_bounds__(kOffThreads)
+k_bin_offsets(const int32_t* __restrict__ D, int tiles_x, int tiles_y, int K, int64_t layer,
+              const int64_t* __restrict__ m_dev, int64_t m_cap, uint64_t* flags, unsigned int* ticket,
+              int32_t* __restrict__ off, int32_t* __restrict__ cur, int* err)
+{
+    grid_dependency_sync();
+    extern __shared__ int32_t s_c[];  // [tiles_x][K + 1]: counts, then exclusive offsets in the row
+    __shared__ int32_t s_warp[kOffThreads / 32];
+    __shared__ int64_t s_pre;
+    __shared__ int s_row;
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(ticket, 1u);
+        s_row = (int)t;
+        if ((int)t == tiles_y - 1) *ticket = 0u;  // every ticket is out: ready for the next scan
+    }
+    __syncthreads();
+    const int ty = s_row;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int KP = K + 1;
+    // counts: per bin, the inclusive prefix of the row's differences
+    for (int b = warp; b < K; b += kOffThreads / 32) {
+        const int32_t* row = D + (int64_t)b * layer + (int64_t)ty * (tiles_x + 1);
+        int32_t carry = 0;
+        for (int x0 = 0; x0 < tiles_x; x0 += 32) {
+            const int x = x0 + lane;
+            int32_t v = x < tiles_x ? row[x] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t u = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d) v += u;
+            }
+            if (x < tiles_x) s_c[x * KP + b] = carry + v;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    // the row's exclusive scan in tile-major order: a run of items a thread
+    const int items = tiles_x * K;
+    const int per = (items + kOffThreads - 1) / kOffThreads;
+    const int j0 = threadIdx.x * per;
+    int32_t run = 0;
+    {
+        int x = j0 / K, b = j0 - (j0 / K) * K;
+        for (int k = 0; k < per && j0 + k < items; ++k) {
+            run += s_c[x * KP + b];
+            if (++b == K) { b = 0; ++x; }
+        }
+    }
+    int32_t incl = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += u;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = s_warp[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += u;
+        }
+        s_warp[lane] = w;  // inclusive warp totals
+    }
+    __syncthreads();
+    const int64_t total = s_warp[kOffThreads / 32 - 1];
+    int32_t e = (warp > 0 ? s_warp[warp - 1] : 0) + incl - run;
+    {
+        int x = j0 / K, b = j0 - (j0 / K) * K;
+        for (int k = 0; k < per && j0 + k < items; ++k) {
+            const int32_t c = s_c[x * KP + b];
+            s_c[x * KP + b] = e;
+            e += c;
+            if (++b == K) { b = 0; ++x; }
+        }
+    }
+    // the rows before: publish this row's total, look back over theirs
+    volatile uint64_t* vf = flags;
+    if (threadIdx.x == 0) vf[ty] = (ty == 0 ? kScanFlagP : kScanFlagA) | (uint64_t)total;
+    if (warp == 0) {
+        const int64_t pre = ty > 0 ? scan_lookback(vf, ty, err) : 0;
+        if (lane == 0) {
+            if (ty > 0) vf[ty] = kScanFlagP | (uint64_t)(pre + total);
+            s_pre = pre;
+        }
+    }
+    __syncthreads();
+    const int64_t pre = s_pre;
+    const bool over = *m_dev > m_cap || pre + total > (int64_t)INT32_MAX - 1;
+    if (over && threadIdx.x == 0) raise_error(err, GS_ERR_CAPACITY);
+    const int64_t base = (int64_t)ty * items;
+    for (int j = threadIdx.x; j < items; j += kOffThreads) {
+        const int x = j / K, b = j - x * K;
+        const int32_t v = over ? 0 : (int32_t)(pre + s_c[x * KP + b]);
+        off[base + j] = v;
+        if (cur) cur[base + j] = v;
+    }
+    if (ty == tiles_y - 1 && threadIdx.x == 0) off[(int64_t)tiles_y * items] = over ? 0 : (int32_t)(pre + total);
+}
+
 struct LoadPlainCount {
     const int32_t* C;
     __device__ int64_t operator()(int64_t q) const { return C[q]; }
@@ -623,7 +737,7 @@ int exact_frame_zero(gs_ctx* ctx, int64_t n, const gs_camera* cam, int64_t m_cap
     ExactScratch v;
     exact_scratch(ctx, n, m_cap, tiles_x, tiles_y, K, &v);
     auto blocks = [](int64_t items) { return items > 0 ? (items + kScanTile - 1) / kScanTile : 1; };
-    int64_t words = 2 * blocks(n) + blocks(nseg);
+    int64_t words = 2 * blocks(n) + (blocks(nseg) > tiles_y ? blocks(nseg) : tiles_y);
     if (grouped_path(m_cap, tiles_x, tiles_y, K))
         words += blocks((int64_t)tiles_y * K * group_slices(ctx->num_sms));
     if ((size_t)(words + 2) * sizeof(uint64_t) > ctx->scan_bytes) {
@@ -646,6 +760,15 @@ int exact_frame_zero(gs_ctx* ctx, int64_t n, const gs_camera* cam, int64_t m_cap
     ctx->zeroed_D_bytes = ctx->tiles_cap;
     ctx->zeroed_tail = ctx->d_tail;
     ctx->zeroed_tail_bytes = ctx->tail_cap;
+    return GS_OK;
+}
+
+// The one-pass offsets kernel takes up to kOffMaxSmem of dynamic shared
+// memory (tile rows of up to kOffMaxSmem / 4 / (K + 1) tiles): set once per
+// context, on its device.
+int bin_offsets_prepare()
+{
+    GS_CUDA_TRY(cudaFuncSetAttribute(k_bin_offsets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOffMaxSmem));
     return GS_OK;
 }
 
@@ -696,18 +819,34 @@ int exact_bins(gs_ctx* ctx, const ProjView& pv, int64_t n, const gs_camera* cam,
             GS_CUDA_TRY(launch_k(ctx, k_row_spans, (unsigned)((warps + 7) / 8), 256, 0, st, pv.rect, n, v.roff, ca, tiles_x, ctx->d_bp, K,
                                                                      m_dev, m_cap, v.D, rlayer, v.gbin, v.rs_g,
                                                                      v.rs_ya, v.rs_w, v.rs_z));
-        GS_CUDA_TRY(launch_k(ctx, k_layer_rows_prefix, (unsigned)K, 1024, 0, st, v.D, tiles_x, tiles_y, rlayer));
-        // the counts tile-major (the cursor array serves as the staging copy;
-        // the scan rewrites it with the offsets when the per-entry scatter
-        // will start its cursors there), then a coalesced scan
-        GS_CUDA_TRY(launch_k(ctx, k_transpose_counts, dim3((unsigned)((tiles_x + 31) / 32), (unsigned)((K + 31) / 32), (unsigned)tiles_y), 256, 0, st, v.D, tiles_x, tiles_y, K, rlayer, v.cur));
-        ctx->launches += 3;
-        const bool cur_ready = n > 0 && !grouped_path(m_cap, tiles_x, tiles_y, K);
-        if ((r = scan_impl(ctx, LoadPlainCount{v.cur}, nseg, offsets, nullptr, st, cur_ready ? v.cur : nullptr)) !=
-            GS_OK)
-            return r;
-        GS_CUDA_TRY(launch_k(ctx, k_zero_if_over, g_sm, 256, 0, st, m_dev, m_cap, offsets, nseg + 1, ctx->d_err));
         ctx->launches += 1;
+        // the per-entry scatter starts its cursors at the offsets
+        const bool cur_ready = n > 0 && !grouped_path(m_cap, tiles_x, tiles_y, K);
+        const size_t osm = bin_offsets_smem(tiles_x, K);
+        if (osm <= kOffMaxSmem) {
+            // one pass: counts, tile-major scan, look-back over tile rows
+            uint64_t* flags;
+            if ((r = scan_flags(ctx, tiles_y, &flags, st)) != GS_OK) return r;
+            GS_CUDA_TRY(launch_k(ctx, k_bin_offsets, (unsigned)tiles_y, kOffThreads, osm, st, v.D, tiles_x, tiles_y,
+                                 K, rlayer, m_dev, m_cap, flags, ctx->d_scan_done, offsets,
+                                 cur_ready ? v.cur : nullptr, ctx->d_err));
+            ctx->launches += 1;
+        } else {
+            // rows too wide for one block's shared memory: per-layer prefix,
+            // the counts tile-major (the cursor array serves as the staging
+            // copy; the scan rewrites it with the offsets when the per-entry
+            // scatter will start its cursors there), a coalesced scan
+            GS_CUDA_TRY(launch_k(ctx, k_layer_rows_prefix, (unsigned)K, 1024, 0, st, v.D, tiles_x, tiles_y, rlayer));
+            GS_CUDA_TRY(launch_k(ctx, k_transpose_counts,
+                                 dim3((unsigned)((tiles_x + 31) / 32), (unsigned)((K + 31) / 32), (unsigned)tiles_y),
+                                 256, 0, st, v.D, tiles_x, tiles_y, K, rlayer, v.cur));
+            ctx->launches += 2;
+            if ((r = scan_impl(ctx, LoadPlainCount{v.cur}, nseg, offsets, nullptr, st, cur_ready ? v.cur : nullptr)) !=
+                GS_OK)
+                return r;
+            GS_CUDA_TRY(launch_k(ctx, k_zero_if_over, g_sm, 256, 0, st, m_dev, m_cap, offsets, nseg + 1, ctx->d_err));
+            ctx->launches += 1;
+        }
         ScatterPass sp;
         if (planned) {
             ctx->exact_roff = v.roff;

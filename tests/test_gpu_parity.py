@@ -430,6 +430,24 @@ def test_ragged_image_and_giant_gaussian(mode, K, lazy, cull):
     np.testing.assert_array_equal(r["last"], l_o)
 
 
+@pytest.mark.parametrize("width", [1000, 2700])
+def test_wide_tile_rows_offsets_paths(width):
+    """The (tile, bin) offsets are built one tile row a block when a row's
+    counts fit the block's shared memory, else by per-layer prefix,
+    transposition and a device-wide scan: 8-pixel tiles and 128 bins over a
+    1000-pixel row (125 tiles) take the first, over 2700 pixels (338 tiles x
+    129 words > 160 KB) the second.  Both give the oracle's image; the stream
+    is the oracle's culled subset, segment by segment."""
+    sc = scenes.tiny_scene(30000, 71)
+    cam = scenes.Camera(scenes.look_at((0, 0, 2.6)), 700.0, 700.0, width / 2 - 0.5, 23.5, width, 48)
+    _, _, (off, stream), (rgb_o, _, l_o) = O.render(sc, cam, tile=8)
+    r = run_stage_pipeline("exact", sc, cam, K=128, tile=8, repair_in_raster=0, tile_cull=1)
+    kept = assert_culled_stream(r["words"], r["offsets"], 128, off, stream, eager=True)
+    assert 0 < kept <= stream.shape[0]
+    np.testing.assert_array_equal(bits(r["rgb"]), bits(rgb_o))
+    np.testing.assert_array_equal(r["last"], l_o)
+
+
 def test_single_gaussian_and_k1():
     sc = scenes.Scene(np.zeros((1, 3), np.float32), np.full((1, 3), 0.05, np.float32),
                       np.array([[1, 0, 0, 0]], np.float32), np.array([0.9], np.float32),
