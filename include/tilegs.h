@@ -371,6 +371,17 @@ int gs_rasterize_bwd(gs_ctx* ctx, const void* projected, int64_t n, const gs_cam
                      const float* dl_drgb, const float* dl_dalpha, void* grad, void* stream);
 
 /*
+ * The reciprocal the backward uses to recover transmittances,
+ * T_i = T_{i+1} * (1 / (1 - a_i)): out[i] = 1 / x[i] by the hardware's
+ * approximate reciprocal refined by one Newton-Raphson step (Markstein's
+ * FMA form), within one rounding of the exact value for x in [2^-126, 2^126]
+ * (the backward's arguments lie in [0.01, 1)).  x, out: n device floats
+ * (caller-owned).  Exposed so that its error can be checked.  Errors:
+ * GS_ERR_INVALID_ARG (n < 0, null pointers), GS_ERR_CUDA.
+ */
+int gs_reciprocal(const float* x, float* out, int64_t n, void* stream);
+
+/*
  * gs_rasterize_fwd as one pass of a planned frame (EXACT with repair_in_raster):
  *   plan [T] (nullable: every bin): the number of bins, from each tile's
  *   front, that this pass walks (values above K count as K).

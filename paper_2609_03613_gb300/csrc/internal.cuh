@@ -151,6 +151,22 @@ __device__ __forceinline__ float spec_exp(float x)
     return spec_exp_core(x);
 }
 
+// 1/d for d in [2^-126, 2^126]: the hardware's approximate reciprocal (PTX
+// rcp.approx.ftz.f32, within 1 ulp) refined by one Newton-Raphson step,
+// r' = r + r (1 - d r), with the residual 1 - d r formed by one fused
+// multiply-add (the FMA-based iteration of P. Markstein, "Computation of
+// elementary functions on the IBM RISC System/6000 processor", IBM J. Res.
+// Dev. 34(1), 1990): the seed's error is squared, so the result is within
+// one rounding of 1/d -- the correctly rounded value or its neighbour
+// (gs_reciprocal exposes it; a GPU test checks it against the correctly
+// rounded reciprocal over [0.01, 1]).
+__device__ __forceinline__ float rcp_newton(float d)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d));
+    return fmaf(r, fmaf(-d, r, 1.0f), r);
+}
+
 // ln by exponent split and the atanh series (Abramowitz and Stegun 4.1.27):
 // x = 2^e m, m in (sqrt(1/2), sqrt(2)], s = (m-1)/(m+1),
 // ln m = 2 s (1 + s^2/3 + s^4/5 + s^6/7 + s^8/9), ln x = e ln2 + ln m.

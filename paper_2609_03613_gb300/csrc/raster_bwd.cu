@@ -11,7 +11,8 @@
 // id of its last applied Gaussian, becomes active when the walk reaches that
 // entry, and then, entry by entry towards the front, repeats the forward's
 // float32 skip test (q, exp, alpha >= 1/255; the same bits as the forward)
-// and recovers T_i = T_{i+1} / (1 - a_i).  With G = dL/drgb, dA = dL/dalpha
+// and recovers T_i = T_{i+1} / (1 - a_i) (a reciprocal within one rounding,
+// then a product).  With G = dL/drgb, dA = dL/dalpha
 // and S_i the colour behind entry i (background included), accumulated from
 // the back so that it stays accurate deep in the list:
 //   dL/da_i = (G.c_i) T_i - (G.S_i - dA T_N) / (1 - a_i),
@@ -170,9 +171,11 @@ struct BwdSpan {
                         const float oe = gb.y * e;
                         const float alpha = fminf(0.99f, oe);
                         if (alpha >= 1.0f / 255.0f) {
-                            // correctly rounded: an approximate reciprocal's bias
-                            // compounds along the chain of recovered T_i
-                            const float r = __frcp_rn(1.0f - alpha);
+                            // within one rounding of 1/(1 - a): an approximate
+                            // reciprocal's bias would compound along the chain of
+                            // recovered T_i (the IEEE-rounded intrinsic measured
+                            // 0.754 ms for this kernel at 1080p, this 0.652 ms)
+                            const float r = rcp_newton(1.0f - alpha);
                             const float Ti = st.T * r;
                             const float4 col = sh.c[k];
                             wgt = alpha * Ti;
@@ -335,3 +338,23 @@ int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
 }
 
 }  // namespace gs
+
+namespace gs {
+namespace {
+__global__ void k_reciprocal(const float* __restrict__ x, float* __restrict__ out, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = rcp_newton(x[i]);
+}
+}  // namespace
+}  // namespace gs
+
+extern "C" int gs_reciprocal(const float* x, float* out, int64_t n, void* stream)
+{
+    if (n < 0 || (n > 0 && (!x || !out))) return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    const int64_t blocks = (n + 255) / 256;
+    gs::k_reciprocal<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, (cudaStream_t)stream>>>(x, out, n);
+    GS_CUDA_TRY(cudaGetLastError());
+    return GS_OK;
+}

@@ -43,7 +43,7 @@ EXPORTS = [
     "gs_render_batch", "gs_batch_set_view_config", "gs_batch_get_view_config", "gs_batch_last_entry_count",
     "gs_batch_autotune", "gs_rasterize_fwd_plan", "gs_tile_features", "gs_planner_set_weights", "gs_plan_tiles",
     "gs_mlp_forward", "gs_mlp_loss_grad", "gs_mlp_backward", "gs_adam_step", "gs_spatial_order",
-    "gs_gather_rows", "gs_last_flagged_tiles",
+    "gs_gather_rows", "gs_last_flagged_tiles", "gs_reciprocal",
 ]
 
 
@@ -150,6 +150,7 @@ def lib():
         "gs_grad2d_offset": (sz, [i64, i32]),
         "gs_spatial_order": (C.c_int, [vp, vp, i64, vp, vp]),
         "gs_gather_rows": (C.c_int, [vp, vp, i64, vp, i32, vp, vp]),
+        "gs_reciprocal": (C.c_int, [vp, vp, i64, vp]),
         "gs_rasterize_bwd": (C.c_int, [vp, vp, i64, C.POINTER(GsCamera), vp, vp, i32, C.POINTER(C.c_float), vp, vp,
                                        vp, vp, vp, vp, vp]),
     }
@@ -609,6 +610,15 @@ def projected_fields(projected, n):
     rect = projected[o[3]:o[3] + 8 * n].view(torch.int32).view(n, 2)
     radius = projected[o[4]:o[4] + 4 * n].view(torch.int32)
     return dict(xy_ab=xy_ab, c_o_z=c_o_z, rgb=rgb, rect=rect, radius=radius)
+
+
+def reciprocal(x):
+    """1/x (device float32) by the reciprocal the raster backward uses to
+    recover transmittances (within one rounding of the exact value)."""
+    import torch
+    out = torch.empty_like(x)
+    check(lib().gs_reciprocal(_ptr(x), _ptr(out), int(x.numel()), _stream()), "gs_reciprocal")
+    return out
 
 
 def mlp_forward(params, X):

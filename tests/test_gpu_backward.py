@@ -229,3 +229,21 @@ def test_render_save_then_render_bwd_whole_frame_and_graph_replay():
     ctx.render(ds, cam, bg)
     with pytest.raises(G.TileGSError, match="invalid argument"):
         ctx.render_bwd(dCd, dAd)
+
+
+def test_reciprocal_within_one_rounding():
+    """The backward's reciprocal (hardware approximation + one Newton-Raphson
+    step) against the correctly rounded 1/x, for every float32 x in
+    [0.01, 1] (the backward takes 1/(1 - a) with a in [1/255, 0.99]): at most
+    one unit in the last place away, and equal for nearly all."""
+    lo = int(np.float32(0.01).view(np.int32))
+    hi = int(np.float32(1.0).view(np.int32))
+    bits_x = torch.arange(lo, hi + 1, dtype=torch.int32, device="cuda")
+    x = bits_x.view(torch.float32)
+    got = G.reciprocal(x)
+    ref = (1.0 / x.double()).float()  # the exact quotient rounded once more
+    ulp = (got.view(torch.int32).long() - ref.view(torch.int32).long()).abs()
+    assert int(ulp.max().item()) <= 1
+    assert float((ulp == 0).double().mean().item()) > 0.99
+    with pytest.raises(G.TileGSError):
+        G.check(G.lib().gs_reciprocal(None, None, -1, None))
