@@ -155,7 +155,8 @@ extern "C" int gs_destroy(gs_ctx* c)
                     c->d_vals[1], c->d_hist, c->d_count, c->d_bin, c->d_bp, c->d_sel, c->d_tail,
                     c->d_tiles_order, c->d_tile_counter, c->r_proj, c->r_isect, c->r_stream,
                     c->r_off, c->r_m, c->r_scene, c->r_out, c->d_ops, c->d_tiles, c->d_samples,
-                    c->r_T, c->r_tend, c->d_planner, c->d_feat, c->d_plan, c->d_order_ws, c->d_scan_done};
+                    c->r_T, c->r_tend, c->r_wend, c->d_planner, c->d_feat, c->d_plan, c->d_plist,
+                    c->d_order_ws, c->d_scan_done};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (c->h_m) cudaFreeHost(c->h_m);
@@ -565,6 +566,10 @@ int gs::render_save_buffers(gs_ctx* c, int32_t W, int32_t H, int32_t T)
     p = c->r_tend;
     if ((r = ensure(&p, &c->r_tend_cap, (size_t)T * 4 + 4)) != GS_OK) return r;
     c->r_tend = (int32_t*)p;
+    p = c->r_wend;
+    const int ts = c->cfg.tile_size;
+    if ((r = ensure(&p, &c->r_wend_cap, (size_t)T * (ts * ts / 32) * 4 + 4)) != GS_OK) return r;
+    c->r_wend = (int32_t*)p;
     return GS_OK;
 }
 
@@ -644,8 +649,11 @@ int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs
         pl.flag = c->d_plan + T;
         pl.list = c->d_plist;
     }
+    // per-warp ends for the backward (a planned frame's completing pass
+    // resumes pixels whose stops it does not know: tile ends only)
+    int32_t* wend = save && !planned ? c->r_wend : nullptr;
     r = raster_fwd(c, pv, cam, c->r_stream, c->r_off, stride, bg, d_rgb, d_alpha, d_last, nullptr,
-                   baseline_raster(c->cfg), st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr, pl);
+                   baseline_raster(c->cfg), st, save ? c->r_T : nullptr, save ? c->r_tend : nullptr, pl, wend);
     stage_end(c, GS_STAGE_RASTER, st);
     if (r != GS_OK) return r;
     if (planned) {
@@ -662,6 +670,7 @@ int gs::render_after_project(gs_ctx* c, int64_t n, const float* scales, const gs
     }
     if (save) {
         c->r_saved = 1;
+        c->r_wend_valid = wend != nullptr;
         c->r_last = d_last;
         c->r_n = n;
         c->r_cam = *cam;
@@ -768,7 +777,7 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
         gs_scene sc;
         gs_camera cam;
         float bg[3];
-        void *rgb, *alpha, *last, *proj, *isect, *stream, *off, *scene_copy, *out, *saved_T, *saved_end;
+        void *rgb, *alpha, *last, *proj, *isect, *stream, *off, *scene_copy, *out, *saved_T, *saved_end, *saved_wend;
         int64_t m_cap;
         gs_config cfg;
         int timing, device, flags;
@@ -803,6 +812,7 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
     key.flags = flags;
     key.saved_T = c->r_T;
     key.saved_end = c->r_tend;
+    key.saved_wend = c->r_wend;
     const void* scratch[] = {c->d_scan, c->d_goff, c->d_keys[0], c->d_keys[1], c->d_vals[0], c->d_vals[1],
                              c->d_hist, c->d_count, c->d_bin, c->d_sel, c->d_tail, c->d_tiles, c->d_samples,
                              c->d_plan};
@@ -839,6 +849,7 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
         c->glaunches = c->launches - l0;
         c->launches = l0;
         c->g_last = c->r_last;  // the last-id buffer the captured frame writes
+        c->g_wend_valid = c->r_wend_valid;
         memcpy(c->gkey, &key, sizeof(Key));
         c->gkey_len = sizeof(Key);
     }
@@ -848,6 +859,7 @@ extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, co
     if (flags & GS_RENDER_SAVE) {
         // the replayed frame is the captured one: its saved state is current
         c->r_saved = 1;
+        c->r_wend_valid = c->g_wend_valid;
         c->r_last = c->g_last;
         c->r_n = sc->n;
         c->r_cam = *cam;
@@ -867,5 +879,6 @@ extern "C" int gs_render_bwd(gs_ctx* c, const float* dl_drgb, const float* dl_da
     if (n == 0) return GS_OK;
     const int32_t stride = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : c->cfg.K;
     return raster_bwd(c, proj_view(c->r_proj, n), &c->r_cam, c->r_stream, c->r_off, stride, c->r_bg, c->r_last,
-                      c->r_T, c->r_tend, dl_drgb, dl_dalpha, grad_view(grad, n), st);
+                      c->r_T, c->r_tend, dl_drgb, dl_dalpha, grad_view(grad, n), st,
+                      c->r_wend_valid ? c->r_wend : nullptr);
 }

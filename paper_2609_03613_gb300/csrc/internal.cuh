@@ -275,6 +275,8 @@ struct gs_ctx {
     // saved state of the last gs_render with GS_RENDER_SAVE (for gs_render_bwd)
     float* r_T = nullptr; size_t r_T_cap = 0;        // final transmittance [H,W]
     int32_t* r_tend = nullptr; size_t r_tend_cap = 0; // per-tile end of the compositing [T]
+    int32_t* r_wend = nullptr; size_t r_wend_cap = 0; // per-warp end of the compositing [T][warps]
+    int r_wend_valid = 0;                             // the saved frame wrote r_wend
     const int32_t* r_last = nullptr;                  // the last-id buffer that render wrote (device)
     int64_t r_n = -1;                                 // Gaussian count of that render
     gs_camera r_cam;
@@ -289,6 +291,7 @@ struct gs_ctx {
     size_t gkey_len = 0;
     int64_t glaunches = 0;
     const int32_t* g_last = nullptr;  // last-id buffer of the captured frame
+    int g_wend_valid = 0;             // the captured frame writes per-warp ends
     int capturing = 0;
     // bin planner (planner.cu): MLP parameters, per-frame features and plan
     float* d_planner = nullptr;
@@ -525,7 +528,7 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* stream_words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T = nullptr,
-               int32_t* tile_end = nullptr, const PlanView& plan = PlanView());
+               int32_t* tile_end = nullptr, const PlanView& plan = PlanView(), int32_t* warp_end = nullptr);
 // the completing pass of a planned frame: every tile of list (device {count,
 // tiles...}) composited on from the bin where its first pass stopped (plan
 // [T]), from the pixel state that pass left in rgb / alpha / last (EXACT,
@@ -561,7 +564,7 @@ int bin_offsets_prepare();
 int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
                int32_t stride, const float* bg, const int32_t* last, const float* final_T,
                const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, const GradView& gv,
-               cudaStream_t st);
+               cudaStream_t st, const int32_t* warp_end = nullptr);
 
 // ctx.cu: whole-frame pieces the batched render reuses
 bool camera_ok(const gs_camera* cam);

@@ -32,7 +32,7 @@ namespace gs {
 struct PixelState {
     float T, C0, C1, C2;
     int32_t last, ntests;
-    int32_t stop;  // counting twin: stream position of the entry that stopped the pixel
+    int32_t stop;  // stream position of the entry that stopped the pixel
     unsigned long long ops;
     bool done;
 };
@@ -112,7 +112,7 @@ __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_en
                     const float dx = ga.x - pxc, dy = ga.y - pyc;
                     const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
                     if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st)) {
-                        if (COUNT) st.stop = base + b0 + k;
+                        st.stop = base + b0 + k;
                         break;
                     }
                 }
@@ -129,11 +129,11 @@ __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_en
                     const float q0 = fmaf(dx0, fmaf(ga0.z, dx0, ga0.w * dy0), (gb0.x * dy0) * dy0);
                     const float q1 = fmaf(dx1, fmaf(ga1.z, dx1, ga1.w * dy1), (gb1.x * dy1) * dy1);
                     if (composite_entry<BASELINE, COUNT>(q0, ga0, gb0, sh, k0, rgbv, st)) {
-                        if (COUNT) st.stop = base + b0 + k0;
+                        st.stop = base + b0 + k0;
                         break;
                     }
                     if (composite_entry<BASELINE, COUNT>(q1, ga1, gb1, sh, k1, rgbv, st)) {
-                        if (COUNT) st.stop = base + b0 + k1;
+                        st.stop = base + b0 + k1;
                         break;
                     }
                 }
@@ -142,7 +142,7 @@ __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_en
                     const float4 ga = sh.a[k], gb = sh.b[k];
                     const float dx = ga.x - pxc, dy = ga.y - pyc;
                     const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
-                    if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st) && COUNT) st.stop = base + b0 + k;
+                    if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st)) st.stop = base + b0 + k;
                 }
             }
         }
@@ -180,7 +180,7 @@ __device__ __forceinline__ void raster_tile(
     const int32_t* __restrict__ off, const RasterArgs& a, int cullmode, float* __restrict__ out_rgb,
     float* __restrict__ out_alpha, int32_t* __restrict__ out_last, int32_t* __restrict__ out_ntests,
     unsigned long long* __restrict__ ops_total, float* __restrict__ out_T, int32_t* __restrict__ out_end,
-    const PlanView& pl, int cap)
+    const PlanView& pl, int cap, int32_t* __restrict__ out_wend = nullptr)
 {
     const int tx = t % a.tiles_x, ty = t / a.tiles_x;
     const int lx = WarpBlocks<TILE>::lx(), ly = WarpBlocks<TILE>::ly();
@@ -225,6 +225,15 @@ __device__ __forceinline__ void raster_tile(
     const int32_t end =
         walk_tile<TILE, LAZY>(words, off, t, K, kbegin, kend, cap, ws, span, out_end ? words : nullptr);
     if (out_end && threadIdx.x == 0) out_end[t] = end;
+    if (out_wend) {
+        // per warp, the stream position past the entry that stopped its last
+        // pixel (the tile's end when one of its pixels never stopped): the
+        // backward has nothing to do for the warp at or beyond it
+        const int32_t wv = !inside ? INT32_MIN : (st.done ? st.stop + 1 : end);
+        const int32_t m = __reduce_max_sync(0xffffffffu, wv);
+        if ((threadIdx.x & 31) == 0)
+            out_wend[(int64_t)t * (TILE * TILE / 32) + (threadIdx.x >> 5)] = m == INT32_MIN ? 0 : min(m, end);
+    }
     bool unfinished = false;
     if (pl.flag && kend < K) {
         // a planned first pass: a tile with a pixel still compositing when its
@@ -295,13 +304,14 @@ k_raster(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z, con
          uint64_t* words, const int32_t* __restrict__ off, RasterArgs a, int cullmode,
          float* __restrict__ out_rgb, float* __restrict__ out_alpha, int32_t* __restrict__ out_last,
          int32_t* __restrict__ out_ntests, unsigned long long* __restrict__ ops_total, float* __restrict__ out_T,
-         int32_t* __restrict__ out_end, const PlanView pl, int cap)
+         int32_t* __restrict__ out_end, const PlanView pl, int cap, int32_t* __restrict__ out_wend)
 {
     grid_dependency_sync();
     __shared__ RasterShared<TILE, BASELINE> sh;
     __shared__ WalkShared<LAZY> ws;
     raster_tile<TILE, BASELINE, COUNT, LAZY>(blockIdx.x, sh, ws, xy_ab, c_o_z, rgbv, words, off, a, cullmode, out_rgb,
-                                             out_alpha, out_last, out_ntests, ops_total, out_T, out_end, pl, cap);
+                                             out_alpha, out_last, out_ntests, ops_total, out_T, out_end, pl, cap,
+                                             out_wend);
 }
 
 // The completing pass of a planned frame: persistent blocks take the listed
@@ -420,12 +430,12 @@ static cudaError_t launch_tile(const gs_ctx* ctx, bool baseline, bool count, boo
                                cudaStream_t st, const ProjView& pv, uint64_t* words, const int32_t* off,
                                const RasterArgs& a, int cull, float* rgb, float* alpha, int32_t* last,
                                int32_t* ntests, unsigned long long* ops, float* final_T, int32_t* tile_end,
-                               const PlanView& pl, int cap)
+                               const PlanView& pl, int cap, int32_t* warp_end)
 {
     constexpr int BS = TILE * TILE;
 #define GS_RASTER_LAUNCH(B, CNT, LZ)                                                                          \
     return launch_k(ctx, k_raster<TILE, B, CNT, LZ>, grid, BS, 0, st, pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, \
-                    (B) ? 0 : cull, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap)
+                    (B) ? 0 : cull, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap, warp_end)
     if (baseline) {
         if (count) GS_RASTER_LAUNCH(true, true, false);
         else GS_RASTER_LAUNCH(true, false, false);
@@ -442,7 +452,7 @@ static cudaError_t launch_tile(const gs_ctx* ctx, bool baseline, bool count, boo
 int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* words,
                const int32_t* offsets, int32_t stride, const float* bg, float* rgb, float* alpha,
                int32_t* last, int32_t* ntests, bool baseline, cudaStream_t st, float* final_T, int32_t* tile_end,
-               const PlanView& pl)
+               const PlanView& pl, int32_t* warp_end)
 {
     const int tile = ctx->cfg.tile_size;
     RasterArgs a;
@@ -467,9 +477,9 @@ int raster_fwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, uint64_t* 
     if (count) GS_CUDA_TRY(cudaMemsetAsync(ops, 0, sizeof(unsigned long long), st));
     cudaError_t e;
     switch (tile) {
-        case 8: e = launch_tile<8>(ctx, baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
-        case 32: e = launch_tile<32>(ctx, baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
-        default: e = launch_tile<16>(ctx, baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap); break;
+        case 8: e = launch_tile<8>(ctx, baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap, warp_end); break;
+        case 32: e = launch_tile<32>(ctx, baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap, warp_end); break;
+        default: e = launch_tile<16>(ctx, baseline, count, lazy, grid, st, pv, words, offsets, a, cull_here, rgb, alpha, last, ntests, ops, final_T, tile_end, pl, cap, warp_end); break;
     }
     GS_CUDA_TRY(e);
     ctx->launches += 1;

@@ -84,6 +84,7 @@ struct BwdSpan {
     float pxc, pyc;  // this lane's pixel centre
     float bxc, byc;  // centre of the warp block's first pixel
     GradState& st;
+    int32_t wend;    // span-relative: the warp has nothing to do at or beyond it
 
     // The first n rows of the buffer -> the nine sums of each row's entry ->
     // its gradients (row s: the entry's batch slot in lane s's `kslot`).
@@ -154,9 +155,12 @@ struct BwdSpan {
             const int cnt = stage_batch<TILE, false>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
             __syncthreads();
             // the entries this warp's strip mask admits, walked back to front
-            const int nk = warp_strip_list<TILE>(sh, cnt);
+            // from the last one before the warp's end
+            const int nk = b0 < wend ? warp_strip_list<TILE>(sh, cnt) : 0;
+            int i0 = nk - 1;
+            while (i0 >= 0 && b0 + sh.list[warp][i0] >= wend) --i0;
             int nrow = 0, kslot = 0;
-            for (int i = nk - 1; i >= 0; --i) {
+            for (int i = i0; i >= 0; --i) {
                 const int k = sh.list[warp][i];
                 const float4 gb = sh.b[k];
                 if (!st.active) st.active = __float_as_uint(gb.w) == st.last;
@@ -228,7 +232,7 @@ k_raster_bwd(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z,
              const int32_t* __restrict__ last, const float* __restrict__ final_T,
              const int32_t* __restrict__ tile_end, const float* __restrict__ dl_drgb,
              const float* __restrict__ dl_dalpha, float4* __restrict__ g_xy_ab, float4* __restrict__ g_c_o_z,
-             float4* __restrict__ g_rgb)
+             float4* __restrict__ g_rgb, const int32_t* __restrict__ warp_end)
 {
     using SH = RasterShared<TILE, false>;
     using WB = WarpBlocks<TILE>;
@@ -272,20 +276,34 @@ k_raster_bwd(const float4* __restrict__ xy_ab, const float4* __restrict__ c_o_z,
     const float bxc = (float)(px - (lane & 7)) + 0.5f, byc = (float)(py - (lane >> 3)) + 0.5f;
     __syncwarp();
 
+    // the walk ends where the forward's tile ended, or (per-warp ends saved)
+    // where the last of its warps ended; each warp skips what lies past its
+    // own end (every one of its pixels had stopped before)
+    const int32_t s0 = off[(int64_t)t * a.stride];
+    int32_t end = tile_end[t], wend = end;
+    if (warp_end) {
+        __shared__ int32_t s_end;
+        wend = min(warp_end[(int64_t)t * NWT + warp], end);
+        if (threadIdx.x == 0) s_end = s0;
+        __syncthreads();
+        if (lane == 0) atomicMax(&s_end, wend);
+        __syncthreads();
+        end = s_end;
+    }
     BwdSpan<TILE, SLOTS> span{sh, rows[warp], gpix + warp * 32, xy_ab, c_o_z, rgbv, g_xy_ab, g_c_o_z, g_rgb,
-                              cullmode, tx, ty, (float)px + 0.5f, (float)py + 0.5f, bxc, byc, st};
-    walk_tile_rev(words, off, t, a.stride, tile_end[t], span);
+                              cullmode, tx, ty, (float)px + 0.5f, (float)py + 0.5f, bxc, byc, st, wend - s0};
+    walk_tile_rev(words, off, t, a.stride, end, span);
 }
 
 template <int TILE>
 int launch_bwd(unsigned grid, cudaStream_t st, const ProjView& pv, const uint64_t* words, const int32_t* off,
                const RasterArgs& a, int cull, const int32_t* last, const float* final_T, const int32_t* tile_end,
-               const float* dl_drgb, const float* dl_dalpha, const GradView& gv)
+               const float* dl_drgb, const float* dl_dalpha, const GradView& gv, const int32_t* warp_end)
 {
     constexpr size_t dyn = bwd_dyn_smem<TILE>();
     k_raster_bwd<TILE><<<grid, TILE * TILE, dyn, st>>>(pv.xy_ab, pv.c_o_z, pv.rgb, words, off, a, cull, last,
                                                       final_T, tile_end, dl_drgb, dl_dalpha, gv.xy_ab, gv.c_o_z,
-                                                      gv.rgb);
+                                                      gv.rgb, warp_end);
     return GS_OK;
 }
 
@@ -307,7 +325,7 @@ int raster_bwd_prepare()
 int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint64_t* words, const int32_t* offsets,
                int32_t stride, const float* bg, const int32_t* last, const float* final_T,
                const int32_t* tile_end, const float* dl_drgb, const float* dl_dalpha, const GradView& gv,
-               cudaStream_t st)
+               cudaStream_t st, const int32_t* warp_end)
 {
     const int tile = ctx->cfg.tile_size;
     RasterArgs a;
@@ -327,9 +345,9 @@ int raster_bwd(gs_ctx* ctx, const ProjView& pv, const gs_camera* cam, const uint
     if (grid == 0) return GS_OK;
     int r;
     switch (tile) {
-        case 8: r = launch_bwd<8>(grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
-        case 32: r = launch_bwd<32>(grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
-        default: r = launch_bwd<16>(grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv); break;
+        case 8: r = launch_bwd<8>(grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv, warp_end); break;
+        case 32: r = launch_bwd<32>(grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv, warp_end); break;
+        default: r = launch_bwd<16>(grid, st, pv, words, offsets, a, cull, last, final_T, tile_end, dl_drgb, dl_dalpha, gv, warp_end); break;
     }
     if (r != GS_OK) return r;
     ctx->launches += 1;
