@@ -61,11 +61,14 @@ struct WarpBlocks {
     __device__ static int ly() { return ((threadIdx.x >> 5) / COLS) * 4 + ((threadIdx.x & 31) >> 3); }
 };
 
-// Warp mask of an entry: bit w is set when the entry's alpha >= 1/255 ellipse
-// (the tile cull's bound tau / margin, widened as there) has a bounding box
-// that reaches warp w's 8 x 4 block of the tile (origin x0, y0): the box is
-// |d| <= sqrt(4 q' tp / D) per axis (q' the other axis' coefficient,
-// D = 4 a/2 c/2 - b^2), so a warp never skips a pixel the entry can reach.
+// Warp mask of an entry: bit w is set when the entry's alpha >= 1/255
+// ellipse (the tile cull's bound Q(d) <= tau / margin, d = mean - pixel
+// centre, widened as there) reaches a pixel centre of warp w's 8 x 4 block of
+// the tile (origin x0, y0).  Per band of four pixel rows the ellipse's
+// x-extent over the band's centre rows (the row-span geometry of the bin
+// stage: band ends and the ellipse's leftmost / rightmost points) is widened
+// by 5e-3 relative + 0.05 px and tested against each block's centre columns,
+// so a warp never skips a pixel the entry can reach.
 template <int TILE>
 __device__ __forceinline__ uint32_t strip_mask(float mx, float my, float ha, float hb, float hc, float tau,
                                                float margin, float x0, float y0)
@@ -77,19 +80,34 @@ __device__ __forceinline__ uint32_t strip_mask(float mx, float my, float ha, flo
     const float D = 4.0f * ha * hc - hb * hb;
     const float tp = tau / margin;
     if (!(D > 0.0f) || !(tp > 0.0f)) return all;
-    const float dymax = sqrtf(4.0f * ha * tp / D) * (1.0f + 5e-3f) + 0.05f;
-    const float dxmax = sqrtf(4.0f * hc * tp / D) * (1.0f + 5e-3f) + 0.05f;
-    // pixel rows / columns (centres origin + i + 0.5) within the box
-    const float rlo = fmaxf(ceilf(my - dymax - y0 - 0.5f), 0.0f);
-    const float rhi = fminf(floorf(my + dymax - y0 - 0.5f), (float)(TILE - 1));
-    const float clo = fmaxf(ceilf(mx - dxmax - x0 - 0.5f), 0.0f);
-    const float chi = fminf(floorf(mx + dxmax - x0 - 0.5f), (float)(TILE - 1));
-    if (rlo > rhi || clo > chi) return 0u;
-    const int by0 = (int)rlo / 4, by1 = (int)rhi / 4, bx0 = (int)clo / 8, bx1 = (int)chi / 8;
-    uint32_t cols = 0u;
-    for (int bx = bx0; bx <= bx1; ++bx) cols |= 1u << bx;
+    const float a4tp = 4.0f * ha * tp;
+    const float dymax = sqrtf(a4tp / D) * (1.0f + 5e-3f) + 0.05f;
+    const float ext = sqrtf(4.0f * hc * tp / D);
+    const float dyl = hb * ext / (2.0f * hc);  // dy of the leftmost point (dx = -ext)
+    const float inv2ha = 1.0f / (2.0f * ha);
     uint32_t m = 0u;
-    for (int by = by0; by <= by1; ++by) m |= cols << (by * WB::COLS);
+#pragma unroll
+    for (int by = 0; by < WB::ROWS; ++by) {
+        float yl = my - (y0 + (float)(4 * by) + 3.5f), yh = my - (y0 + (float)(4 * by) + 0.5f);
+        yl = yl - (0.05f + 5e-3f * fabsf(yl));
+        yh = yh + (0.05f + 5e-3f * fabsf(yh));
+        const float ya = fmaxf(yl, -dymax), yb = fminf(yh, dymax);
+        if (ya > yb) continue;  // the band misses the ellipse
+        float s_a, s_b;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(s_a) : "f"(fmaxf(0.0f, a4tp - D * ya * ya)));
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(s_b) : "f"(fmaxf(0.0f, a4tp - D * yb * yb)));
+        const float La = (-hb * ya - s_a) * inv2ha, Lb = (-hb * yb - s_b) * inv2ha;
+        const float Ra = (-hb * ya + s_a) * inv2ha, Rb = (-hb * yb + s_b) * inv2ha;
+        float dxmin = (dyl >= ya && dyl <= yb) ? -ext : fminf(La, Lb);
+        float dxmax = (-dyl >= ya && -dyl <= yb) ? ext : fmaxf(Ra, Rb);
+        dxmin = dxmin - (0.05f + 5e-3f * fabsf(dxmin));
+        dxmax = dxmax + (0.05f + 5e-3f * fabsf(dxmax));
+        // pixel centres x with mx - x in [dxmin, dxmax]
+        const float xlo = mx - dxmax - x0, xhi = mx - dxmin - x0;
+#pragma unroll
+        for (int bx = 0; bx < WB::COLS; ++bx)
+            if (xlo <= (float)(8 * bx) + 7.5f && xhi >= (float)(8 * bx) + 0.5f) m |= 1u << (by * WB::COLS + bx);
+    }
     return m & all;
 }
 

@@ -65,8 +65,11 @@ __device__ __forceinline__ void row_span(float mx, const RowGeom& g, int ty, int
         *b = *a;  // the band misses the ellipse
         return;
     }
-    const float s_a = sqrtf(fmaxf(0.0f, g.a4tp - g.D * ya * ya));
-    const float s_b = sqrtf(fmaxf(0.0f, g.a4tp - g.D * yb * yb));
+    // the hardware's approximate square root (relative error below 2^-22):
+    // the widening below is 5e-3 relative + 0.05 px
+    float s_a, s_b;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(s_a) : "f"(fmaxf(0.0f, g.a4tp - g.D * ya * ya)));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(s_b) : "f"(fmaxf(0.0f, g.a4tp - g.D * yb * yb)));
     const float La = (-g.hb * ya - s_a) * g.inv2ha, Lb = (-g.hb * yb - s_b) * g.inv2ha;
     const float Ra = (-g.hb * ya + s_a) * g.inv2ha, Rb = (-g.hb * yb + s_b) * g.inv2ha;
     float dxmin = (g.dyl >= ya && g.dyl <= yb) ? -g.ext : fminf(La, Lb);
