@@ -68,7 +68,9 @@ struct WarpBlocks {
 // x-extent over the band's centre rows (the row-span geometry of the bin
 // stage: band ends and the ellipse's leftmost / rightmost points) is widened
 // by 5e-3 relative + 0.05 px and tested against each block's centre columns,
-// so a warp never skips a pixel the entry can reach.
+// so a warp never skips a pixel the entry can reach.  The geometry takes the
+// hardware's approximate division and square root (relative errors near
+// 2^-22, far inside the widening).
 template <int TILE>
 __device__ __forceinline__ uint32_t strip_mask(float mx, float my, float ha, float hb, float hc, float tau,
                                                float margin, float x0, float y0)
@@ -78,13 +80,16 @@ __device__ __forceinline__ uint32_t strip_mask(float mx, float my, float ha, flo
     const uint32_t all = NWT >= 32 ? 0xffffffffu : ((1u << NWT) - 1u);
     if (!(margin > 0.0f)) return all;
     const float D = 4.0f * ha * hc - hb * hb;
-    const float tp = tau / margin;
+    const float tp = __fdividef(tau, margin);
     if (!(D > 0.0f) || !(tp > 0.0f)) return all;
     const float a4tp = 4.0f * ha * tp;
-    const float dymax = sqrtf(a4tp / D) * (1.0f + 5e-3f) + 0.05f;
-    const float ext = sqrtf(4.0f * hc * tp / D);
-    const float dyl = hb * ext / (2.0f * hc);  // dy of the leftmost point (dx = -ext)
-    const float inv2ha = 1.0f / (2.0f * ha);
+    const float iD = __fdividef(1.0f, D);
+    float dymax, ext;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(dymax) : "f"(a4tp * iD));
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(ext) : "f"(4.0f * hc * tp * iD));
+    dymax = dymax * (1.0f + 5e-3f) + 0.05f;
+    const float dyl = hb * ext * __fdividef(1.0f, 2.0f * hc);  // dy of the leftmost point (dx = -ext)
+    const float inv2ha = __fdividef(1.0f, 2.0f * ha);
     uint32_t m = 0u;
 #pragma unroll
     for (int by = 0; by < WB::ROWS; ++by) {
