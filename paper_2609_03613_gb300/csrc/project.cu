@@ -302,6 +302,29 @@ __device__ __forceinline__ bool project_one(float mx, float my, float mz, float 
     return bad_colour;
 }
 
+// A Gaussian's parameters other than its SH coefficients (streamed: the
+// scene is read once a frame).
+struct GaussParams {
+    float mx = 0.f, my = 0.f, mz = 0.f, o = 0.f, s0 = 0.f, s1 = 0.f, s2 = 0.f;
+    float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f);
+};
+
+__device__ __forceinline__ GaussParams load_params(const float* __restrict__ means, const float* __restrict__ scales,
+                                                   const float4* __restrict__ quats, const float* __restrict__ opac,
+                                                   int64_t i)
+{
+    GaussParams g;
+    g.mx = __ldcs(means + 3 * i);
+    g.my = __ldcs(means + 3 * i + 1);
+    g.mz = __ldcs(means + 3 * i + 2);
+    g.o = __ldcs(opac + i);
+    g.q4 = __ldcs(quats + i);
+    g.s0 = __ldcs(scales + 3 * i);
+    g.s1 = __ldcs(scales + 3 * i + 1);
+    g.s2 = __ldcs(scales + 3 * i + 2);
+    return g;
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(kProjBlock)
 k_project(const float* __restrict__ means, const float* __restrict__ scales,
@@ -315,16 +338,18 @@ k_project(const float* __restrict__ means, const float* __restrict__ scales,
     constexpr int PER = NC * 3;  // floats of SH per Gaussian
     __shared__ __align__(16) float s_sh[kProjBlock * PER];
     const int64_t base = (int64_t)blockIdx.x * kProjBlock;
-    if (!stage_sh<PER>(sh, sh_aligned, base, n, s_sh, polls, err)) return;
     const int64_t i = base + threadIdx.x;
+    // the Gaussian's other parameters are loaded before the wait for the SH
+    // copy: both round trips overlap
+    GaussParams gp;
+    if (i < n) gp = load_params(means, scales, quats, opac, i);
+    if (!stage_sh<PER>(sh, sh_aligned, base, n, s_sh, polls, err)) return;
     if (i >= n) return;
     float4 a, b, c;
     uint2 rect;
     int radius;
-    const float mx = __ldcs(means + 3 * i), my = __ldcs(means + 3 * i + 1), mz = __ldcs(means + 3 * i + 2);
-    const float o = __ldcs(opac + i);
-    const float4 q4 = __ldcs(quats + i);
-    const float s0 = __ldcs(scales + 3 * i), s1 = __ldcs(scales + 3 * i + 1), s2 = __ldcs(scales + 3 * i + 2);
+    const float mx = gp.mx, my = gp.my, mz = gp.mz, o = gp.o, s0 = gp.s0, s1 = gp.s1, s2 = gp.s2;
+    const float4 q4 = gp.q4;
     const bool bad = project_one<DEG>(mx, my, mz, o, q4, s0, s1, s2, s_sh + threadIdx.x * PER, cam, a, b, c, rect,
                                       radius);
     if (bad || geometry_nonfinite(mx, my, mz, o, q4, s0, s1, s2)) raise_error(err, GS_ERR_NUMERIC);
@@ -355,13 +380,13 @@ k_project_batch(const float* __restrict__ means, const float* __restrict__ scale
     constexpr int PER = NC * 3;
     __shared__ __align__(16) float s_sh[kProjBlock * PER];
     const int64_t base = (int64_t)blockIdx.x * kProjBlock;
-    if (!stage_sh<PER>(sh, sh_aligned, base, n, s_sh, polls, err)) return;
     const int64_t i = base + threadIdx.x;
+    GaussParams gp;
+    if (i < n) gp = load_params(means, scales, quats, opac, i);
+    if (!stage_sh<PER>(sh, sh_aligned, base, n, s_sh, polls, err)) return;
     if (i >= n) return;
-    const float mx = __ldcs(means + 3 * i), my = __ldcs(means + 3 * i + 1), mz = __ldcs(means + 3 * i + 2);
-    const float o = __ldcs(opac + i);
-    const float4 q4 = __ldcs(quats + i);
-    const float s0 = __ldcs(scales + 3 * i), s1 = __ldcs(scales + 3 * i + 1), s2 = __ldcs(scales + 3 * i + 2);
+    const float mx = gp.mx, my = gp.my, mz = gp.mz, o = gp.o, s0 = gp.s0, s1 = gp.s1, s2 = gp.s2;
+    const float4 q4 = gp.q4;
     bool bad = geometry_nonfinite(mx, my, mz, o, q4, s0, s1, s2);
     for (int v = 0; v < bc.nviews; ++v) {
         float4 a, b, c;
