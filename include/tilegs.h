@@ -554,10 +554,15 @@ int64_t gs_batch_last_entry_count(gs_ctx* ctx, int32_t view);
  * count K (32, 64, 128; binned modes) by timing `iters` whole frames of that
  * view for every candidate (CUDA events on `stream`, synchronous), and set
  * them with gs_batch_set_view_config.  best_ms: HOST [n_cams] (nullable), the
- * chosen candidates' mean frame times.  K never changes an EXACT image; the
- * tile size can, for Gaussians that reach alpha >= 1/255 outside their 3-sigma
- * square (opacity above ~0.35), because their tile rectangles differ.
- * Allocates (temporary contexts and output buffers).
+ * chosen candidates' mean frame times.  With tune_tile, when a view's
+ * fastest tile size is not 16 (so it would leave the group of views binned
+ * and rasterised together), the assignment of each view's fastest candidate
+ * and that of each view's fastest 16 x 16 candidate are also timed as whole
+ * batches (`iters` gs_render_batch calls each) and the faster is kept.  K
+ * never changes an EXACT image; the tile size can, for Gaussians that reach
+ * alpha >= 1/255 outside their 3-sigma square (opacity above ~0.35), because
+ * their tile rectangles differ.  Allocates (temporary contexts and output
+ * buffers).
  */
 int gs_batch_autotune(gs_ctx* ctx, const gs_scene* scene, const gs_camera* cams, int32_t n_cams,
                       int32_t tune_tile, int32_t iters, float* best_ms, void* stream);

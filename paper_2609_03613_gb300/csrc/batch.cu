@@ -448,6 +448,41 @@ extern "C" int gs_render_batch(gs_ctx* c, const gs_scene* sc, const gs_camera* c
     return GS_OK;
 }
 
+// Mean time of `iters` batches of the views with configurations cfgs (after
+// one sizing batch and one warm batch), for the autotuner; outputs go to
+// temporary buffers.
+static int time_batch(gs_ctx* c, const gs_scene* sc, const gs_camera* cams, int nv, const gs_config* cfgs, int iters,
+                      cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st, float* ms_out)
+{
+    const float zero_bg[3] = {0.0f, 0.0f, 0.0f};
+    float* rgb[kMaxBatchViews] = {};
+    float* alpha[kMaxBatchViews] = {};
+    int status = GS_OK;
+    for (int v = 0; v < nv && status == GS_OK; ++v) {
+        const size_t px = (size_t)cams[v].width * cams[v].height;
+        if (cudaMalloc(&rgb[v], px * 12) != cudaSuccess || cudaMalloc(&alpha[v], px * 4) != cudaSuccess)
+            status = GS_ERR_NO_MEMORY;
+        if (status == GS_OK) status = gs_batch_set_view_config(c, v, &cfgs[v]);
+    }
+    if (status == GS_OK) status = gs_render_batch(c, sc, cams, nv, zero_bg, rgb, alpha, nullptr, 0, st);
+    if (status == GS_OK)
+        status = gs_render_batch(c, sc, cams, nv, zero_bg, rgb, alpha, nullptr, GS_RENDER_NO_SYNC, st);
+    if (status == GS_OK && cudaEventRecord(e0, st) != cudaSuccess) status = GS_ERR_CUDA;
+    for (int i = 0; i < iters && status == GS_OK; ++i)
+        status = gs_render_batch(c, sc, cams, nv, zero_bg, rgb, alpha, nullptr, GS_RENDER_NO_SYNC, st);
+    float ms = 0.0f;
+    if (status == GS_OK && (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        status = GS_ERR_CUDA;
+    if (status == GS_OK && gs_get_error(c, st) != GS_OK) status = GS_ERR_CAPACITY;
+    for (int v = 0; v < nv; ++v) {
+        if (rgb[v]) cudaFree(rgb[v]);
+        if (alpha[v]) cudaFree(alpha[v]);
+    }
+    *ms_out = ms / (float)iters;
+    return status;
+}
+
 extern "C" int gs_batch_autotune(gs_ctx* c, const gs_scene* sc, const gs_camera* cams, int32_t n_cams,
                                  int32_t tune_tile, int32_t iters, float* best_ms, void* stream)
 {
@@ -458,6 +493,8 @@ extern "C" int gs_batch_autotune(gs_ctx* c, const gs_scene* sc, const gs_camera*
     static const int ks[3] = {64, 32, 128};
     const int ntile = tune_tile ? 3 : 1;
     const int nk = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : 3;
+    gs_config choice[kMaxBatchViews], choice16[kMaxBatchViews];
+    float t16[kMaxBatchViews];
     cudaEvent_t e0, e1;
     GS_CUDA_TRY(cudaEventCreate(&e0));
     GS_CUDA_TRY(cudaEventCreate(&e1));
@@ -473,6 +510,9 @@ extern "C" int gs_batch_autotune(gs_ctx* c, const gs_scene* sc, const gs_camera*
         gs_config best = c->cfg;
         float best_t = 3.4e38f;
         const gs_config base = (c->batch && c->batch->has_cfg[v]) ? c->batch->vcfg[v] : c->cfg;
+        // the best candidate that keeps 16 x 16 tiles (the views binned as one group)
+        gs_config best16 = base;
+        float best16_t = 3.4e38f;
         for (int it = 0; it < ntile && status == GS_OK; ++it)
             for (int ik = 0; ik < nk && status == GS_OK; ++ik) {
                 gs_config cfg = base;
@@ -499,6 +539,10 @@ extern "C" int gs_batch_autotune(gs_ctx* c, const gs_scene* sc, const gs_camera*
                     best_t = ms / iters;
                     best = cfg;
                 }
+                if (status == GS_OK && cfg.tile_size == 16 && ms / iters < best16_t) {
+                    best16_t = ms / iters;
+                    best16 = cfg;
+                }
             }
         if (d_rgb) cudaFree(d_rgb);
         if (d_alpha) cudaFree(d_alpha);
@@ -506,7 +550,28 @@ extern "C" int gs_batch_autotune(gs_ctx* c, const gs_scene* sc, const gs_camera*
         if (status == GS_OK) {
             status = gs_batch_set_view_config(c, v, &best);
             if (best_ms) best_ms[v] = best_t;
+            choice[v] = best;
+            choice16[v] = best16.tile_size == 16 && best16_t < 3.4e38f ? best16 : best;
+            t16[v] = best16_t < 3.4e38f ? best16_t : best_t;
         }
+    }
+    // a view whose fastest tile size is not 16 leaves the group of views
+    // binned and rasterised together; whether that pays is a property of the
+    // batch, so the two assignments are timed as whole batches
+    bool differ = false;
+    for (int v = 0; v < n_cams && status == GS_OK; ++v)
+        differ = differ || memcmp(&choice[v], &choice16[v], sizeof(gs_config)) != 0;
+    if (status == GS_OK && tune_tile && differ) {
+        float ms_a = 0.0f, ms_b = 0.0f;
+        status = time_batch(c, sc, cams, n_cams, choice, iters, e0, e1, st, &ms_a);
+        if (status == GS_OK) status = time_batch(c, sc, cams, n_cams, choice16, iters, e0, e1, st, &ms_b);
+        if (status == GS_OK && ms_b < ms_a)
+            for (int v = 0; v < n_cams && status == GS_OK; ++v) {
+                status = gs_batch_set_view_config(c, v, &choice16[v]);
+                if (best_ms) best_ms[v] = t16[v];
+            }
+        else if (status == GS_OK)
+            for (int v = 0; v < n_cams && status == GS_OK; ++v) status = gs_batch_set_view_config(c, v, &choice[v]);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
