@@ -515,7 +515,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            ctx_e.render(hs, cam, bg, hout, flags=flags)  # returns after the outputs landed
+            # the warm-up sized the entry buffers: no mid-frame entry-count
+            # read-back (a capacity overflow would raise GS_ERR_CAPACITY)
+            ctx_e.render(hs, cam, bg, hout, flags=flags | G.RENDER_NO_SYNC)  # returns after the outputs landed
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
