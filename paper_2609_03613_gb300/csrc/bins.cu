@@ -15,6 +15,7 @@ namespace gs {
 
 // Sample j of the emission order -> gid, from the materialised entries ...
 struct GidFromIsect {
+    static constexpr bool kKeys = false;
     const uint32_t* gid;
     __device__ uint32_t operator()(int64_t, int64_t j) const { return gid[j]; }
 };
@@ -22,10 +23,12 @@ struct GidFromIsect {
 // order.  Gaussian g owns entries [goff[g], goff[g+1]), so its samples are the
 // i with goff[g] <= floor(i M / S') < goff[g+1], i.e.
 // i in [ceil(goff[g] S' / M), ceil(goff[g+1] S' / M)) -- exact in integers.
-// One thread per Gaussian (coalesced reads of goff; empty Gaussians own none).
+// One thread per Gaussian (coalesced reads of goff; empty Gaussians own none),
+// which writes its samples' key (depth or near-shifted key, float bits).
 __global__ void __launch_bounds__(256)
-k_sample_gids(const int32_t* __restrict__ goff, int64_t n, const int64_t* __restrict__ m_dev, int64_t m_cap, int S,
-              uint32_t* __restrict__ out, FrameZero fz)
+k_sample_keys(const int32_t* __restrict__ goff, int64_t n, const int64_t* __restrict__ m_dev, int64_t m_cap, int S,
+              uint32_t* __restrict__ out, FrameZero fz, const float4* __restrict__ c_o_z,
+              const float* __restrict__ scales, DrArgs dr)
 {
     grid_dependency_sync();
     frame_zero(fz);  // the frame's bin-stage counts, later scan flags, repair counter
@@ -47,7 +50,11 @@ k_sample_gids(const int32_t* __restrict__ goff, int64_t n, const int64_t* __rest
         const int64_t a = goff[g], b = goff[g + 1];
         if (b <= a) continue;
         const uint64_t i0 = ceil_div((uint64_t)a), i1 = ceil_div((uint64_t)b);
-        for (uint64_t i = i0; i < i1 && i < ns; ++i) out[i] = (uint32_t)g;
+        if (i0 >= i1 || i0 >= ns) continue;
+        // the samples' key, gathered here by many blocks rather than by the
+        // one block that selects
+        const uint32_t key = __float_as_uint(sample_key(c_o_z, scales, (uint32_t)g, dr));
+        for (uint64_t i = i0; i < i1 && i < ns; ++i) out[i] = key;
     }
 }
 
@@ -143,10 +150,11 @@ int depth_range_goff(gs_ctx* ctx, const ProjView& pv, const float* scales, int64
             late.n[k] = ctx->late_n[k];
             ctx->late_p[k] = nullptr;
         }
-        GS_CUDA_TRY(launch_k(ctx, k_sample_gids, (unsigned)ctx->num_sms * 4, 256, 0, st, ctx->d_goff, n, m_dev, m_cap, a.S, ctx->d_samples, late));
+        GS_CUDA_TRY(launch_k(ctx, k_sample_keys, (unsigned)ctx->num_sms * 4, 256, 0, st, ctx->d_goff, n, m_dev,
+                             m_cap, a.S, ctx->d_samples, late, pv.c_o_z, scales, a));
     }
-    GS_CUDA_TRY(launch_k(ctx, k_depth_range<GidFromSamples>, 1, kDrThreads, 0, st, pv.c_o_z, scales, GidFromSamples{ctx->d_samples}, m_dev, m_cap, a,
-                                             ctx->d_bp));
+    GS_CUDA_TRY(launch_k(ctx, k_depth_range<KeyFromSamples>, 1, kDrThreads, 0, st, pv.c_o_z, scales,
+                         KeyFromSamples{ctx->d_samples}, m_dev, m_cap, a, ctx->d_bp));
     ctx->launches += 2;
     GS_CUDA_TRY(cudaGetLastError());
     return GS_OK;

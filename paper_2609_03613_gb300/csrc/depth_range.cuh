@@ -69,11 +69,29 @@ __device__ __forceinline__ void write_bin_params(BinParams* bp, float zmin, floa
     for (int k = threadIdx.x; k < K - 1; k += blockDim.x) bp->splits[k] = s_split[k];
 }
 
-// ... or from a per-sample gid array filled by k_sample_gids.
+// ... or from a per-sample gid array (the batched views' sampling).
 struct GidFromSamples {
+    static constexpr bool kKeys = false;
     const uint32_t* gid;  // indexed by sample number
     __device__ uint32_t operator()(int64_t i, int64_t) const { return gid[i]; }
 };
+
+// ... or the samples' keys themselves (depth, or the near-shifted key, as
+// float bits), gathered by the wide sampling kernel.
+struct KeyFromSamples {
+    static constexpr bool kKeys = true;
+    const uint32_t* key;  // indexed by sample number
+    __device__ uint32_t operator()(int64_t i, int64_t) const { return key[i]; }
+};
+
+// The key of Gaussian g's depth sample: its depth, or the near-shifted key.
+__device__ __forceinline__ float sample_key(const float4* __restrict__ c_o_z, const float* __restrict__ scales,
+                                            uint32_t g, const DrArgs& a)
+{
+    float z = c_o_z[g].z;
+    if (a.near_shift) z = zkey_of(z, scales, g, a.near_alpha, a.near_gamma);
+    return z;
+}
 
 // Rank search of one radix pass, by one warp: the digit d whose cumulative
 // count first reaches k (k >= 1), and k minus the counts below d, written by
@@ -132,27 +150,33 @@ __device__ __forceinline__ void depth_range_block(const float4* __restrict__ c_o
     __syncthreads();
     const int64_t ns = M < (int64_t)a.S ? M : (int64_t)a.S;
     const float lo_clamp = fmaxf(a.near_plane, a.eps);
-    // every sample's gid, then every depth (and scale) gathered at once, so
-    // the dependent loads cost two round trips rather than two per round
+    // every sample's key: read (the sampling kernel gathered them), or its
+    // gid then its depth (and scale) gathered at once, so the dependent loads
+    // cost two round trips rather than two per round
     constexpr int kPer = kDrMaxS / kDrThreads;
-    uint32_t gk[kPer];
-#pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-        const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
-        gk[r] = i < ns ? gid_of(i, (i * M) / ns) : 0u;
-    }
     float zk[kPer];
+    if constexpr (GidOf::kKeys) {
 #pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-        const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
-        float z = 0.0f;
-        if (i < ns) {
-            z = c_o_z[gk[r]].z;
-            if (a.near_shift) z = zkey_of(z, scales, gk[r], a.near_alpha, a.near_gamma);
+        for (int r = 0; r < kPer; ++r) {
+            const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
+            zk[r] = i < ns ? __uint_as_float(gid_of(i, 0)) : 0.0f;
         }
-        zk[r] = z;
+    } else {
+        uint32_t gk[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
+            gk[r] = i < ns ? gid_of(i, (i * M) / ns) : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
+            zk[r] = i < ns ? sample_key(c_o_z, scales, gk[r], a) : 0.0f;
+        }
     }
-    // the positive keys, compacted with one shared atomic per warp and round
+    // the positive keys, clamped, compacted with one shared atomic per warp
+    // and round; their minimum and maximum on the way
+    uint32_t lo_v = 0xffffffffu, hi_v = 0u;
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
         const int64_t i = (int64_t)r * kDrThreads + threadIdx.x;
@@ -163,7 +187,12 @@ __device__ __forceinline__ void depth_range_block(const float4* __restrict__ c_o
         int base = 0;
         if (lane == 0 && bal) base = atomicAdd(&s_n, __popc(bal));
         base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep) s_v[base + __popc(bal & ((1u << lane) - 1u))] = __float_as_uint(fminf(fmaxf(z, lo_clamp), a.far_plane));
+        if (keep) {
+            const uint32_t v = __float_as_uint(fminf(fmaxf(z, lo_clamp), a.far_plane));
+            s_v[base + __popc(bal & ((1u << lane) - 1u))] = v;
+            lo_v = min(lo_v, v);
+            hi_v = max(hi_v, v);
+        }
     }
     __syncthreads();
     const int n = s_n;
@@ -175,11 +204,6 @@ __device__ __forceinline__ void depth_range_block(const float4* __restrict__ c_o
         // the bits every sample shares (those of the block's min and max)
         // need no pass: start below the highest bit where samples differ
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        uint32_t lo_v = 0xffffffffu, hi_v = 0u;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            lo_v = min(lo_v, s_v[i]);
-            hi_v = max(hi_v, s_v[i]);
-        }
         lo_v = __reduce_min_sync(0xffffffffu, lo_v);
         hi_v = __reduce_max_sync(0xffffffffu, hi_v);
         if (lane == 0) {

@@ -258,7 +258,7 @@ struct gs_ctx {
     size_t tail_cap = 0;
     int32_t* d_tiles = nullptr;   // tile-count difference grid, tile offsets, cursors
     size_t tiles_cap = 0;
-    uint32_t* d_samples = nullptr; // depth-range sample gids
+    uint32_t* d_samples = nullptr; // depth-range samples (their keys as float bits)
     size_t samples_cap = 0;
     int32_t* d_tiles_order = nullptr;  // persistent raster tile order
     int32_t* d_tile_counter = nullptr;
