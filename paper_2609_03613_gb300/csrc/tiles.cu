@@ -202,10 +202,10 @@ k_layer_rows_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y, int64_t l
 // 32nd entry, finds its lane by a binary search over the prefix (and which of
 // that lane's two records by the first one's width) and takes a slot in the
 // entry's (tile, bin) segment -- the cursors start at the segment offsets, so
-// the atomic returns the slot itself; eight entries per lane are in flight
-// (the kernel waits on its atomics' return: one record a lane and four in
-// flight measured 4.5 us slower at 1080p, four records and sixteen slower
-// still at 105 registers).  The records carry the Gaussian's bin and depth
+// the atomic returns the slot itself; twelve entries per lane are in flight
+// (the kernel waits on its atomics' return: at 1080p one record a lane and
+// four in flight measured 6.9 us slower, eight in flight 2.4 us slower,
+// sixteen (89 registers) 27 us slower, four records a lane slower still).  The records carry the Gaussian's bin and depth
 // bits, so nothing is gathered.
 __global__ void __launch_bounds__(256)
 k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ rs_w,
@@ -216,7 +216,7 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
     grid_dependency_sync();
     if (*m_dev > m_cap) return;
     if (sp.pass == 2 && flagged[0] == 0) return;  // no tile to complete
-    constexpr int IF = 8;  // entries a lane has in flight
+    constexpr int IF = 12;  // entries a lane has in flight
     const int64_t R = roff[n];
     const int lane = threadIdx.x & 31;
     const int64_t nchunks = (R + 63) / 64;  // 64 records a warp and round: two a lane
