@@ -198,15 +198,23 @@ k_layer_rows_prefix(int32_t* __restrict__ D, int tiles_x, int tiles_y, int64_t l
 }
 
 // Warp-cooperative over the entries of 64 consecutive row records, two a
-// lane: a warp scans the lanes' record widths, then each lane takes every
-// 32nd entry, finds its lane by a binary search over the prefix (and which of
-// that lane's two records by the first one's width) and takes a slot in the
+// lane: a warp scans the lanes' record widths and keeps its records (gid,
+// tile row | first tile | bin, depth bits, first entry) in shared memory;
+// then, a window of 384 entries at a time, each record marks the window's
+// entries that are its own in a per-warp owner map, and each lane takes
+// every 32nd entry, reads its record through the map and takes a slot in the
 // entry's (tile, bin) segment -- the cursors start at the segment offsets, so
-// the atomic returns the slot itself; twelve entries per lane are in flight
-// (the kernel waits on its atomics' return: at 1080p one record a lane and
-// four in flight measured 6.9 us slower, eight in flight 2.4 us slower,
-// sixteen (89 registers) 27 us slower, four records a lane slower still).  The records carry the Gaussian's bin and depth
-// bits, so nothing is gathered.
+// the atomic returns the slot itself.  Twelve entries per lane are in flight:
+// the kernel waits on its atomics' returns.  Measured at 1080p against a
+// binary search over the warp's prefix with the fields shuffled from the
+// owning lane: one record a lane and four in flight 13.6 us slower, two
+// records and twelve in flight 6.7 us slower (short-scoreboard stalls on
+// the shuffles); with the owner map, four records a lane were slower.  The
+// records carry the Gaussian's bin and depth bits, so nothing is gathered.
+constexpr int kScatRL = 2;                 // row records a lane
+constexpr int kScatIF = 12;                // entries a lane has in flight
+constexpr int kScatWin = 32 * kScatIF;     // entries a warp places a round
+
 __global__ void __launch_bounds__(256)
 k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict__ rs_ya, const uint32_t* __restrict__ rs_w,
                    const uint32_t* __restrict__ rs_z, const int32_t* __restrict__ roff, int64_t n, int tiles_x, int K,
@@ -214,18 +222,24 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
                    uint64_t* __restrict__ words, const ScatterPass sp, const int32_t* __restrict__ flagged)
 {
     grid_dependency_sync();
+    // per warp: its 64 records {gid, tile row | first tile | bin, depth bits,
+    // first entry}, and for a round's window of entries the record of each
+    __shared__ uint4 s_rec[8][32 * kScatRL];
+    __shared__ uint8_t s_own[8][kScatWin];
     if (*m_dev > m_cap) return;
     if (sp.pass == 2 && flagged[0] == 0) return;  // no tile to complete
-    constexpr int IF = 12;  // entries a lane has in flight
     const int64_t R = roff[n];
-    const int lane = threadIdx.x & 31;
-    const int64_t nchunks = (R + 63) / 64;  // 64 records a warp and round: two a lane
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint4* rec = s_rec[warp];
+    uint8_t* own = s_own[warp];
+    const int64_t nchunks = (R + 32 * kScatRL - 1) / (32 * kScatRL);
     const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nchunks; c += wstride) {
-        uint32_t w[2] = {0, 0}, g[2] = {0, 0}, ya[2] = {0, 0}, z[2] = {0, 0};
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp; c < nchunks; c += wstride) {
+        uint32_t w[kScatRL], g[kScatRL], ya[kScatRL], z[kScatRL];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int64_t k = c * 64 + 2 * lane + h;
+        for (int h = 0; h < kScatRL; ++h) {
+            w[h] = g[h] = ya[h] = z[h] = 0;
+            const int64_t k = c * (32 * kScatRL) + kScatRL * lane + h;
             if (k < R) {  // read once: streamed past L2
                 ya[h] = __ldcs(rs_ya + k);
                 w[h] = __ldcs(rs_w + k);
@@ -235,56 +249,57 @@ k_bin_scatter_rows(const uint32_t* __restrict__ rs_g, const uint32_t* __restrict
                 else w[h] = 0;
             }
         }
-        // inclusive prefix of the lanes' two widths across the warp
-        const uint32_t wl = w[0] + w[1];
+        uint32_t wl = 0;
+#pragma unroll
+        for (int h = 0; h < kScatRL; ++h) wl += w[h];
         uint32_t incl = wl;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const uint32_t u = __shfl_up_sync(0xffffffffu, incl, d);
             if (lane >= d) incl += u;
         }
-        const uint32_t excl = incl - wl;
         const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-        for (uint32_t e0 = 0; e0 < total; e0 += 32 * IF) {
-            int32_t p[IF];
-            uint64_t word[IF];
-            bool live[IF];
+        uint32_t st[kScatRL];
+        st[0] = incl - wl;
 #pragma unroll
-            for (int u = 0; u < IF; ++u) {
+        for (int h = 1; h < kScatRL; ++h) st[h] = st[h - 1] + w[h - 1];
+#pragma unroll
+        for (int h = 0; h < kScatRL; ++h) rec[kScatRL * lane + h] = make_uint4(g[h], ya[h], z[h], st[h]);
+        for (uint32_t e0 = 0; e0 < total; e0 += kScatWin) {
+            // each record marks the entries of this window that are its own
+#pragma unroll
+            for (int h = 0; h < kScatRL; ++h) {
+                const uint32_t lo = st[h] > e0 ? st[h] : e0;
+                const uint32_t end = st[h] + w[h], wend = e0 + kScatWin;
+                const uint32_t hi = end < wend ? end : wend;
+                for (uint32_t x = lo; x < hi; ++x) own[x - e0] = (uint8_t)(kScatRL * lane + h);
+            }
+            __syncwarp();
+            int32_t p[kScatIF];
+            uint64_t word[kScatIF];
+            bool live[kScatIF];
+#pragma unroll
+            for (int u = 0; u < kScatIF; ++u) {
                 const uint32_t e = e0 + 32 * u + lane;
-                // owner lane: the last whose exclusive prefix is <= e; then
-                // its first record, or its second past the first's width
-                int o = 0;
-#pragma unroll
-                for (int s = 16; s > 0; s >>= 1) {
-                    const uint32_t v = __shfl_sync(0xffffffffu, excl, (o + s) & 31);
-                    if (o + s < 32 && v <= e) o += s;
-                }
-                const uint32_t oex = __shfl_sync(0xffffffffu, excl, o);
-                const uint32_t ow0 = __shfl_sync(0xffffffffu, w[0], o);
-                const bool second = e >= oex + ow0;
-                // both records' fields come over, the receiver picks (the
-                // choice is the receiving lane's, not the sender's)
-                const uint32_t og0 = __shfl_sync(0xffffffffu, g[0], o), og1 = __shfl_sync(0xffffffffu, g[1], o);
-                const uint32_t oya0 = __shfl_sync(0xffffffffu, ya[0], o), oya1 = __shfl_sync(0xffffffffu, ya[1], o);
-                const uint32_t oz0 = __shfl_sync(0xffffffffu, z[0], o), oz1 = __shfl_sync(0xffffffffu, z[1], o);
-                const uint32_t og = second ? og1 : og0, oya = second ? oya1 : oya0, oz = second ? oz1 : oz0;
                 live[u] = e < total;
                 if (live[u]) {
-                    const uint32_t off = e - oex - (second ? ow0 : 0u);
-                    const int ty = (int)(oya & 0xfffu), tx = (int)((oya >> 12) & 0xfffu) + (int)off;
+                    const uint4 r = rec[own[e - e0]];
+                    const uint32_t oya = r.y;
+                    const int ty = (int)(oya & 0xfffu), tx = (int)((oya >> 12) & 0xfffu) + (int)(e - r.w);
                     const int64_t t = (int64_t)ty * tiles_x + tx;
                     live[u] = sp.keep(t, (int)(oya >> 24));
                     if (live[u]) {
                         p[u] = atomicAdd(&cur[t * K + (oya >> 24)], 1);
-                        word[u] = ((uint64_t)oz << 32) | og;
+                        word[u] = ((uint64_t)r.z << 32) | r.x;
                     }
                 }
             }
 #pragma unroll
-            for (int u = 0; u < IF; ++u)
+            for (int u = 0; u < kScatIF; ++u)
                 if (live[u]) words[p[u]] = word[u];
+            __syncwarp();  // the window's owner map is read before the next one is written
         }
+        __syncwarp();  // the records are read before the next chunk's are written
     }
 }
 
