@@ -55,6 +55,8 @@ def test_defaults_match_paper_tables(G):
     assert cfg.repair_budget_frac == pytest.approx(gold["repair"]["budget_frac"])
     assert cfg.near_shift == 1 and cfg.tile_size == 16
     assert G.default_config("exact").near_shift == 0
+    # frame kernels launched with programmatic dependent launch by default
+    assert G.default_config("exact").pdl == 1 and G.default_config("global").pdl == 1
 
 
 def test_host_layout_helpers(G):
@@ -73,7 +75,7 @@ def test_host_layout_helpers(G):
 def test_invalid_config_rejected_before_any_cuda_call(G):
     L = G.lib()
     for bad in (dict(K=0), dict(K=G.MAX_K + 1), dict(tile_size=12), dict(sample_count=9000),
-                dict(mode=7)):
+                dict(mode=7), dict(pdl=2), dict(pdl=-1)):
         cfg = G.default_config("exact")
         for k, v in bad.items():
             setattr(cfg, k, v)

@@ -344,6 +344,36 @@ def test_render_entry_point(tiny, mode):
         np.testing.assert_array_equal(last, l_o)
 
 
+@pytest.mark.parametrize("mode", ["exact", "global"])
+def test_launch_modes_change_nothing(tiny, mode):
+    """Programmatic dependent launch on or off, the frame graph-replayed or
+    launched kernel by kernel, with stage timing (ordinary launches) or
+    without: every frame is the oracle's, bit for bit."""
+    sc, cam = tiny[0], tiny[1]
+    rgb_o, _, l_o = tiny[6]
+    ds = G.DeviceScene.from_numpy(sc)
+    side = torch.cuda.Stream()
+    for pdl in (1, 0):
+        ctx = G.Context(mode, pdl=pdl)
+        H, W = cam.height, cam.width
+        out = (torch.empty((H, W, 3), device="cuda"), torch.empty((H, W), device="cuda"),
+               torch.empty((H, W), dtype=torch.int32, device="cuda"))
+        with torch.cuda.stream(side):
+            ctx.render(ds, cam, (0.0, 0.0, 0.0), out)  # sizes the scratch
+        torch.cuda.synchronize()
+        ctx.reserve(sc.n, ctx.last_entry_count() + 1024, W, H)
+        for flags, timing in ((G.RENDER_NO_SYNC, False), (G.RENDER_NO_SYNC, True),
+                              (G.RENDER_NO_SYNC | G.RENDER_GRAPH, False)):
+            ctx.enable_timing(timing)
+            for _ in range(2):
+                with torch.cuda.stream(side):
+                    ctx.render(ds, cam, (0.0, 0.0, 0.0), out, flags=flags)
+                torch.cuda.synchronize()
+                assert ctx.error() == 0
+                np.testing.assert_array_equal(bits(out[0].cpu().numpy()), bits(rgb_o))
+                np.testing.assert_array_equal(out[2].cpu().numpy(), l_o)
+
+
 def test_render_host_buffers(tiny):
     sc, cam = tiny[0], tiny[1]
     rgb_o = tiny[6][0]
