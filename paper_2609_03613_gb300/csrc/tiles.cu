@@ -563,13 +563,14 @@ k_bin_offsets(const int32_t* __restrict__ D, int tiles_x, int tiles_y, int K, in
     if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
     if (warp == 0) {
-        int32_t w = s_warp[lane];
+        constexpr int NW = kOffThreads / 32;
+        int32_t w = lane < NW ? s_warp[lane] : 0;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int32_t u = __shfl_up_sync(0xffffffffu, w, d);
             if (lane >= d) w += u;
         }
-        s_warp[lane] = w;  // inclusive warp totals
+        if (lane < NW) s_warp[lane] = w;  // inclusive warp totals
     }
     __syncthreads();
     const int64_t total = s_warp[kOffThreads / 32 - 1];
