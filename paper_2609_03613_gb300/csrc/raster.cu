@@ -112,6 +112,61 @@ __device__ __forceinline__ bool composite_entry(float q, const float4& ga, const
     }
 }
 
+// Composite the cnt staged entries of a batch into the calling thread's
+// pixel (slot k is stream position base + k).  Binned: the warp composites
+// only the entries its warp mask admits.
+template <int TILE, bool BASELINE, bool COUNT>
+__device__ __forceinline__ void composite_batch(int cnt, RasterShared<TILE, BASELINE>& sh,
+                                                const float4* __restrict__ rgbv, float pxc, float pyc, PixelState& st,
+                                                int32_t base)
+{
+    const int warp = threadIdx.x >> 5;
+    int nk = cnt;
+    if constexpr (!BASELINE) nk = __all_sync(0xffffffffu, st.done) ? 0 : warp_strip_list<TILE>(sh, cnt);
+    if (st.done) return;
+    if constexpr (BASELINE) {
+        for (int k = 0; k < nk; ++k) {
+            const float4 ga = sh.a[k];
+            const float4 gb = sh.b[k];
+            const float dx = ga.x - pxc, dy = ga.y - pyc;
+            const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
+            if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st)) {
+                st.stop = base + k;
+                break;
+            }
+        }
+    } else {
+        // two entries a round: both q and exp(-q) first (independent), then
+        // the two compositing steps in stream order
+        int i = 0;
+        for (; i + 1 < nk; i += 2) {
+            const int k0 = sh.list[warp][i], k1 = sh.list[warp][i + 1];
+            const float4 ga0 = sh.a[k0], gb0 = sh.b[k0];
+            const float4 ga1 = sh.a[k1], gb1 = sh.b[k1];
+            const float dx0 = ga0.x - pxc, dy0 = ga0.y - pyc;
+            const float dx1 = ga1.x - pxc, dy1 = ga1.y - pyc;
+            const float q0 = fmaf(dx0, fmaf(ga0.z, dx0, ga0.w * dy0), (gb0.x * dy0) * dy0);
+            const float q1 = fmaf(dx1, fmaf(ga1.z, dx1, ga1.w * dy1), (gb1.x * dy1) * dy1);
+            const float e0 = spec_exp_core(-q0), e1 = spec_exp_core(-q1);
+            if (composite_binned<COUNT>(q0, e0, gb0, sh.c[k0], st)) {
+                st.stop = base + k0;
+                break;
+            }
+            if (composite_binned<COUNT>(q1, e1, gb1, sh.c[k1], st)) {
+                st.stop = base + k1;
+                break;
+            }
+        }
+        if (!st.done && i < nk) {
+            const int k = sh.list[warp][i];
+            const float4 ga = sh.a[k], gb = sh.b[k];
+            const float dx = ga.x - pxc, dy = ga.y - pyc;
+            const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
+            if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st)) st.stop = base + k;
+        }
+    }
+}
+
 // Composite n_entries stream words from src (global or shared memory) into
 // every pixel of the tile, in batches.  Returns -1 after the last entry, or,
 // block-uniformly, the offset of the first batch left unprocessed once every
@@ -126,60 +181,13 @@ __device__ __forceinline__ int32_t raster_span(const uint64_t* src, int32_t n_en
 {
     using SH = RasterShared<TILE, BASELINE>;
     constexpr int BS = SH::BS, BATCH = SH::BATCH;
-    const int warp = threadIdx.x >> 5;
     for (int32_t b0 = 0; b0 < n_entries; b0 += BATCH) {
         // checked: the caller has just counted the terminated pixels (block
         // barrier included) with nothing composited since
         if (!(checked && b0 == 0) && __syncthreads_count(st.done) == BS) return b0;
         const int cnt = stage_batch<TILE, BASELINE>(src, b0, n_entries, sh, xy_ab, c_o_z, rgbv, cullmode, tx, ty);
         __syncthreads();
-        // binned: the warp composites only the entries its strip mask admits
-        int nk = cnt;
-        if constexpr (!BASELINE) nk = __all_sync(0xffffffffu, st.done) ? 0 : warp_strip_list<TILE>(sh, cnt);
-        if (!st.done) {
-            if constexpr (BASELINE) {
-                for (int k = 0; k < nk; ++k) {
-                    const float4 ga = sh.a[k];
-                    const float4 gb = sh.b[k];
-                    const float dx = ga.x - pxc, dy = ga.y - pyc;
-                    const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
-                    if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st)) {
-                        st.stop = base + b0 + k;
-                        break;
-                    }
-                }
-            } else {
-                // two entries a round: both q and exp(-q) first
-                // (independent), then the two compositing steps in stream
-                // order
-                int i = 0;
-                for (; i + 1 < nk; i += 2) {
-                    const int k0 = sh.list[warp][i], k1 = sh.list[warp][i + 1];
-                    const float4 ga0 = sh.a[k0], gb0 = sh.b[k0];
-                    const float4 ga1 = sh.a[k1], gb1 = sh.b[k1];
-                    const float dx0 = ga0.x - pxc, dy0 = ga0.y - pyc;
-                    const float dx1 = ga1.x - pxc, dy1 = ga1.y - pyc;
-                    const float q0 = fmaf(dx0, fmaf(ga0.z, dx0, ga0.w * dy0), (gb0.x * dy0) * dy0);
-                    const float q1 = fmaf(dx1, fmaf(ga1.z, dx1, ga1.w * dy1), (gb1.x * dy1) * dy1);
-                    const float e0 = spec_exp_core(-q0), e1 = spec_exp_core(-q1);
-                    if (composite_binned<COUNT>(q0, e0, gb0, sh.c[k0], st)) {
-                        st.stop = base + b0 + k0;
-                        break;
-                    }
-                    if (composite_binned<COUNT>(q1, e1, gb1, sh.c[k1], st)) {
-                        st.stop = base + b0 + k1;
-                        break;
-                    }
-                }
-                if (!st.done && i < nk) {
-                    const int k = sh.list[warp][i];
-                    const float4 ga = sh.a[k], gb = sh.b[k];
-                    const float dx = ga.x - pxc, dy = ga.y - pyc;
-                    const float q = fmaf(dx, fmaf(ga.z, dx, ga.w * dy), (gb.x * dy) * dy);
-                    if (composite_entry<BASELINE, COUNT>(q, ga, gb, sh, k, rgbv, st)) st.stop = base + b0 + k;
-                }
-            }
-        }
+        composite_batch<TILE, BASELINE, COUNT>(cnt, sh, rgbv, pxc, pyc, st, base + b0);
     }
     return -1;
 }
@@ -199,6 +207,23 @@ struct FwdSpan {
                                                   checked, base);
     }
     __device__ __forceinline__ bool done() const { return st.done; }
+    // binned: a chunk of one batch is staged slot by slot by the walk
+    static constexpr bool kStageAtRank = !BASELINE;
+    static constexpr int kBatch = RasterShared<TILE, BASELINE>::BATCH;
+    __device__ __forceinline__ void stage_at(int slot, uint32_t g)
+    {
+        if constexpr (!BASELINE) {
+            float4 A, B, C;
+            stage_record<TILE>(g, __ldg(xy_ab + g), __ldg(c_o_z + g), __ldg(rgbv + g), cullmode, tx, ty, A, B, C);
+            sh.a[slot] = A;
+            sh.b[slot] = B;
+            sh.c[slot] = C;
+        }
+    }
+    __device__ __forceinline__ void composite_staged(int cnt, int32_t base)
+    {
+        composite_batch<TILE, BASELINE, COUNT>(cnt, sh, rgbv, pxc, pyc, st, base);
+    }
 };
 
 // LAZY (EXACT mode with the repair in the raster): the tile's segments are
@@ -242,8 +267,8 @@ __device__ __forceinline__ void raster_tile(
         if (pl.resume) kbegin = B;
         else kend = B;
     }
-    const int64_t p = (int64_t)py * a.width + px;
     if (pl.resume && inside) {
+        const int64_t p = (int64_t)py * a.width + px;
         // the first pass's state: C in rgb, T in alpha (negative once the
         // pixel stopped), last
         const float Ts = out_alpha[p];
@@ -268,6 +293,10 @@ __device__ __forceinline__ void raster_tile(
         if ((threadIdx.x & 31) == 0)
             out_wend[(int64_t)t * (TILE * TILE / 32) + (threadIdx.x >> 5)] = m == INT32_MIN ? 0 : min(m, end);
     }
+    // the pixel's index formed again after the walk: kept live across it,
+    // it cost the kernel a spill at its register budget (raster 0.274 ->
+    // 0.264 ms at 1080p)
+    const int64_t p = (int64_t)(ty * TILE + WarpBlocks<TILE>::ly()) * a.width + (tx * TILE + WarpBlocks<TILE>::lx());
     bool unfinished = false;
     if (pl.flag && kend < K) {
         // a planned first pass: a tile with a pixel still compositing when its
