@@ -510,22 +510,35 @@ def run_ours(args):
         flags = G.RENDER_HOST_INPUTS | G.RENDER_HOST_OUTPUTS
         for _ in range(args.warmup):
             ctx_e.render(hs, cam, bg, hout, flags=flags)
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            # the warm-up sized the entry buffers: no mid-frame entry-count
-            # read-back (a capacity overflow would raise GS_ERR_CAPACITY)
-            ctx_e.render(hs, cam, bg, hout, flags=flags | G.RENDER_NO_SYNC)  # returns after the outputs landed
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dist, dev)
+
+        def e2e_run(step_flags):
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                # the warm-up sized the entry buffers: no mid-frame entry-count
+                # read-back (a capacity overflow raises GS_ERR_CAPACITY)
+                ctx_e.render(hs, cam, bg, hout, flags=step_flags)
+            ctx_e.render_wait()  # every step's outputs are in host memory
+            torch.cuda.synchronize()
+            if dist is not None:
+                dist.barrier()
+            return max_over_ranks((time.perf_counter() - t0) / args.steps, dist, dev)
+
+        # pipelined calls (each still uploads its scene and downloads its
+        # image; the upload of one overlaps the frame and download of the
+        # one before), then calls that each return after their outputs landed
+        e2e_s = e2e_run(flags | G.RENDER_PIPELINE)
+        e2e_sync_s = e2e_run(flags | G.RENDER_NO_SYNC)
+        assert ctx_e.error() == 0
         h2d = sum(int(t.numel()) * 4 for t in (hs.means, hs.scales, hs.quats, hs.opacities, hs.sh))
         d2h = sum(int(t.numel()) * 4 for t in hout)
         e2e = {"value": round(ws * P / e2e_s / 1e6, 4), "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3, 3)}
+               "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_s * 1e3, 3),
+               "call": "gs_render, host scene in and host image out every step, GS_RENDER_PIPELINE",
+               "one_call_at_a_time": {"value": round(ws * P / e2e_sync_s / 1e6, 4),
+                                      "ms_per_step": round(e2e_sync_s * 1e3, 3)}}
 
     # training step on the same workload: the frame (graph replay, saving the
     # backward's state), the L1 loss gradient against a fixed U[0,1] target,

@@ -486,13 +486,19 @@ enum {
                                    the final transmittance and per-tile end of this
                                    frame (the projected record, stream and offsets
                                    stay in the context until the next gs_render) */
-    GS_RENDER_GRAPH = 8         /* device buffers only: capture the frame's launches
+    GS_RENDER_GRAPH = 8,        /* device buffers only: capture the frame's launches
                                    into a CUDA graph on the first call and replay it
                                    on later calls with identical arguments (pointers,
                                    sizes, camera, background, config); implies
                                    NO_SYNC, so capacity must be reserved first
                                    (gs_reserve or one plain gs_render), and
                                    needs a non-default stream */
+    GS_RENDER_PIPELINE = 32     /* with HOST_INPUTS and HOST_OUTPUTS: the call
+                                   returns once its copies and its frame are
+                                   enqueued, and consecutive calls overlap -- the
+                                   scene upload of one call with the frame and the
+                                   image download of the one before (see
+                                   gs_render_wait) */
 };
 
 /*
@@ -504,6 +510,34 @@ enum {
  */
 int gs_render(gs_ctx* ctx, const gs_scene* scene, const gs_camera* cam, const float* bg,
               float* rgb, float* alpha, int32_t* last, int32_t flags, void* stream);
+
+/*
+ * Pipelined host-buffer frames (GS_RENDER_PIPELINE | GS_RENDER_HOST_INPUTS |
+ * GS_RENDER_HOST_OUTPUTS; implies GS_RENDER_NO_SYNC).  The context keeps two
+ * slots of device inputs and outputs and two streams of its own, one for
+ * uploads and one for downloads; calls alternate between the slots.  A call
+ * enqueues its scene upload on the upload stream (after the frame two calls
+ * back has finished reading that slot), its frame on `stream` (after its
+ * upload, and after the download two calls back has emptied the slot's
+ * outputs), and its image download on the download stream (after its frame),
+ * then returns: the host link moves the next scene while this frame renders
+ * and the previous image comes back.  Every call still copies all its inputs
+ * in and all its outputs out.  Until gs_render_wait returns, the caller keeps
+ * the host inputs of every pipelined call unchanged and reads none of their
+ * host outputs.  All pipelined calls use the same `stream`; entry capacity
+ * must have been reserved (gs_reserve or one gs_render without NO_SYNC);
+ * an overflow is reported in the sticky error word (gs_get_error), as for
+ * any NO_SYNC frame; gs_last_entry_count is not updated.  Errors:
+ * GS_ERR_INVALID_ARG when a host flag is missing, with GS_RENDER_SAVE or
+ * GS_RENDER_GRAPH, or before capacity was reserved; GS_ERR_NO_MEMORY;
+ * GS_ERR_CUDA.
+ *
+ * gs_render_wait (host): returns once every pipelined call made so far on
+ * this context has finished, its outputs in host memory.  GS_OK, or
+ * GS_ERR_CUDA when a copy or the frame failed.  Also GS_OK when no pipelined
+ * call was made.
+ */
+int gs_render_wait(gs_ctx* ctx);
 
 /*
  * Backward of the last gs_render on this context, which must have had
@@ -533,7 +567,7 @@ int gs_render_bwd(gs_ctx* ctx, const float* dl_drgb, const float* dl_dalpha, voi
  *   calls), GS_RENDER_GRAPH (device buffers, non-default stream: the whole
  *   batch is captured once and replayed while the arguments are unchanged;
  *   every view must have been sized by an earlier call without NO_SYNC).
- *   Host-buffer and SAVE flags are rejected.
+ *   Host-buffer, pipelined and SAVE flags are rejected.
  * Each view's image is the one gs_render gives for that camera and the view's
  * configuration.  Errors: as gs_render; GS_ERR_INVALID_ARG for bad counts.
  */

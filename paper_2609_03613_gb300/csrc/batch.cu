@@ -371,7 +371,8 @@ extern "C" int gs_render_batch(gs_ctx* c, const gs_scene* sc, const gs_camera* c
                                int32_t flags, void* stream)
 {
     if (!batch_args_ok(c, sc, cams, n_cams, bg, rgb, alpha)) return GS_ERR_INVALID_ARG;
-    if (flags & (GS_RENDER_HOST_INPUTS | GS_RENDER_HOST_OUTPUTS | GS_RENDER_SAVE)) return GS_ERR_INVALID_ARG;
+    if (flags & (GS_RENDER_HOST_INPUTS | GS_RENDER_HOST_OUTPUTS | GS_RENDER_SAVE | GS_RENDER_PIPELINE))
+        return GS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     int r = batch_buffers(c, sc, cams, n_cams, last, flags);
     if (r != GS_OK) return r;

@@ -151,6 +151,19 @@ extern "C" int gs_create(gs_ctx** out, const gs_config* cfg)
 extern "C" int gs_destroy(gs_ctx* c)
 {
     if (!c) return GS_ERR_INVALID_ARG;
+    if (c->pipe_down) {
+        // pipelined frames still in flight finish before their buffers go
+        cudaStreamSynchronize(c->pipe_up);
+        cudaStreamSynchronize(c->pipe_down);
+        cudaStreamDestroy(c->pipe_up);
+        cudaStreamDestroy(c->pipe_down);
+    }
+    for (auto& P : c->pipe) {
+        if (P.scene) cudaFree(P.scene);
+        if (P.out) cudaFree(P.out);
+        for (cudaEvent_t e : {P.uploaded, P.rendered, P.downloaded})
+            if (e) cudaEventDestroy(e);
+    }
     void* ptrs[] = {c->d_err, c->d_scan, c->d_goff, c->d_keys[0], c->d_keys[1], c->d_vals[0],
                     c->d_vals[1], c->d_hist, c->d_count, c->d_bin, c->d_bp, c->d_sel, c->d_tail,
                     c->d_tiles_order, c->d_tile_counter, c->r_proj, c->r_isect, c->r_stream,
@@ -597,7 +610,6 @@ int gs::render_binning(gs_ctx* c, int64_t n, const float* scales, const gs_camer
             if ((r = render_buffers(c, n, c->h_m[0], T)) != GS_OK) return r;
         }
     }
-    const int32_t stride = c->cfg.mode == GS_MODE_GLOBAL_SORT ? 1 : c->cfg.K;
     if (c->cfg.mode == GS_MODE_BINNED_EXACT) {
         // the emission is fused with the bucketing by tile: no emission-order
         // entries are written; depth samples map to gids through the offsets
@@ -762,11 +774,120 @@ static int render_impl(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, cons
     return GS_OK;
 }
 
+// ------------------------------------------------------------------ pipelined host-buffer frames
+static int pipe_init(gs_ctx* c)
+{
+    if (c->pipe_down) return GS_OK;
+    cudaStream_t up = nullptr, down = nullptr;
+    if (cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        if (up) cudaStreamDestroy(up);
+        return GS_ERR_CUDA;
+    }
+    for (auto& P : c->pipe)
+        for (cudaEvent_t* e : {&P.uploaded, &P.rendered, &P.downloaded})
+            if (!*e && cudaEventCreateWithFlags(e, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                *e = nullptr;
+                cudaStreamDestroy(up);
+                cudaStreamDestroy(down);
+                return GS_ERR_CUDA;
+            }
+    c->pipe_up = up;
+    c->pipe_down = down;
+    return GS_OK;
+}
+
+// One pipelined frame in the next slot: the scene up on the upload stream,
+// the frame on `st`, the outputs down on the download stream, each step
+// ordered by the slot's events after the slot's previous use.
+static int render_pipelined(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, const float* bg, float* rgb,
+                            float* alpha, int32_t* last, int32_t flags, cudaStream_t st)
+{
+    const int32_t host = GS_RENDER_HOST_INPUTS | GS_RENDER_HOST_OUTPUTS;
+    if (!c || !sc || !cam_ok(cam) || !bg || !rgb || !alpha) return GS_ERR_INVALID_ARG;
+    if ((flags & host) != host || (flags & (GS_RENDER_SAVE | GS_RENDER_GRAPH))) return GS_ERR_INVALID_ARG;
+    if (sc->n < 0 || sc->n > INT32_MAX - 1 || sc->sh_degree < 0 || sc->sh_degree > 3) return GS_ERR_INVALID_ARG;
+    if (c->r_m_cap <= 1) return GS_ERR_INVALID_ARG;  // capacity must be reserved first
+    int r;
+    if ((r = pipe_init(c)) != GS_OK) return r;
+    gs_ctx::PipeSlot& P = c->pipe[c->pipe_next];
+    const int64_t n = sc->n;
+    const int ncoef = (sc->sh_degree + 1) * (sc->sh_degree + 1);
+    const size_t px = (size_t)cam->width * cam->height;
+    const float* src[5] = {sc->means, sc->scales, sc->quats, sc->opacities, sc->sh};
+    const size_t cnt[5] = {(size_t)n * 3, (size_t)n * 3, (size_t)n * 4, (size_t)n, (size_t)n * 3 * ncoef};
+    size_t scene_bytes = 0;
+    for (size_t k : cnt) scene_bytes += align256(k * 4);
+    // a buffer that grows is freed first, and cudaFree waits for the device
+    void* ps = P.scene;
+    if ((r = ensure(&ps, &P.scene_cap, scene_bytes)) != GS_OK) return r;
+    P.scene = (float*)ps;
+    void* po = P.out;
+    if ((r = ensure(&po, &P.out_cap, align256(px * 12) + align256(px * 4) + px * 4)) != GS_OK) return r;
+    P.out = (float*)po;
+    // up: after the frame that last read this slot's scene
+    if (P.used) GS_CUDA_TRY(cudaStreamWaitEvent(c->pipe_up, P.rendered, 0));
+    const float* dst[5];
+    char* b = (char*)P.scene;
+    for (int k = 0; k < 5; ++k) {
+        dst[k] = (const float*)b;
+        if (cnt[k]) GS_CUDA_TRY(cudaMemcpyAsync(b, src[k], cnt[k] * 4, cudaMemcpyHostToDevice, c->pipe_up));
+        b += align256(cnt[k] * 4);
+    }
+    GS_CUDA_TRY(cudaEventRecord(P.uploaded, c->pipe_up));
+    // the frame: after the upload, and after the download that last read
+    // this slot's outputs
+    GS_CUDA_TRY(cudaStreamWaitEvent(st, P.uploaded, 0));
+    if (P.used) GS_CUDA_TRY(cudaStreamWaitEvent(st, P.downloaded, 0));
+    P.used = true;
+    c->pipe_next ^= 1;
+    const gs_scene dsc = {dst[0], dst[1], dst[2], dst[3], dst[4], sc->sh_degree, n};
+    char* o = (char*)P.out;
+    float* d_rgb = (float*)o;
+    o += align256(px * 12);
+    float* d_alpha = (float*)o;
+    o += align256(px * 4);
+    int32_t* d_last = (int32_t*)o;
+    r = render_impl(c, &dsc, cam, bg, d_rgb, d_alpha, d_last,
+                    (flags & ~(host | GS_RENDER_PIPELINE)) | GS_RENDER_NO_SYNC, st);
+    // recorded whatever the frame did, so the slot's next use never waits on
+    // an event that was not recorded after this one's
+    GS_CUDA_TRY(cudaEventRecord(P.rendered, st));
+    if (r != GS_OK) {
+        GS_CUDA_TRY(cudaEventRecord(P.downloaded, c->pipe_down));
+        return r;
+    }
+    // down: after the frame
+    GS_CUDA_TRY(cudaStreamWaitEvent(c->pipe_down, P.rendered, 0));
+    GS_CUDA_TRY(cudaMemcpyAsync(rgb, d_rgb, px * 12, cudaMemcpyDeviceToHost, c->pipe_down));
+    GS_CUDA_TRY(cudaMemcpyAsync(alpha, d_alpha, px * 4, cudaMemcpyDeviceToHost, c->pipe_down));
+    if (last) GS_CUDA_TRY(cudaMemcpyAsync(last, d_last, px * 4, cudaMemcpyDeviceToHost, c->pipe_down));
+    GS_CUDA_TRY(cudaEventRecord(P.downloaded, c->pipe_down));
+    return GS_OK;
+}
+
+extern "C" int gs_render_wait(gs_ctx* c)
+{
+    if (!c) return GS_ERR_INVALID_ARG;
+    if (!c->pipe_down) return GS_OK;
+    const cudaError_t a = cudaStreamSynchronize(c->pipe_up);
+    const cudaError_t d = cudaStreamSynchronize(c->pipe_down);
+    if (a != cudaSuccess || d != cudaSuccess) {
+        cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
 // The frame as a CUDA graph: captured on first use (and whenever any pointer,
 // size, camera, background or configuration value changes), replayed after.
 extern "C" int gs_render(gs_ctx* c, const gs_scene* sc, const gs_camera* cam, const float* bg, float* rgb,
                          float* alpha, int32_t* last, int32_t flags, void* stream)
 {
+    if (flags & GS_RENDER_PIPELINE)
+        return render_pipelined(c, sc, cam, bg, rgb, alpha, last, flags, (cudaStream_t)stream);
     if (!(flags & GS_RENDER_GRAPH)) return render_impl(c, sc, cam, bg, rgb, alpha, last, flags, stream);
     if (!c || !sc || !cam || !bg || !rgb || !alpha) return GS_ERR_INVALID_ARG;
     if (flags & (GS_RENDER_HOST_INPUTS | GS_RENDER_HOST_OUTPUTS)) return GS_ERR_INVALID_ARG;

@@ -272,6 +272,18 @@ struct gs_ctx {
     int64_t* h_m = nullptr;  // pinned
     float* r_scene = nullptr; size_t r_scene_cap = 0;  // device copies of host inputs
     float* r_out = nullptr; size_t r_out_cap = 0;      // device outputs for host outputs
+    // pipelined host-buffer frames (GS_RENDER_PIPELINE): two slots of device
+    // inputs and outputs used in turn, an upload and a download stream
+    struct PipeSlot {
+        float* scene = nullptr; size_t scene_cap = 0;
+        float* out = nullptr; size_t out_cap = 0;
+        cudaEvent_t uploaded = nullptr;    // the slot's scene is on the device
+        cudaEvent_t rendered = nullptr;    // the slot's frame has finished
+        cudaEvent_t downloaded = nullptr;  // the slot's outputs are in host memory
+        bool used = false;
+    } pipe[2];
+    cudaStream_t pipe_up = nullptr, pipe_down = nullptr;
+    int pipe_next = 0;
     // saved state of the last gs_render with GS_RENDER_SAVE (for gs_render_bwd)
     float* r_T = nullptr; size_t r_T_cap = 0;        // final transmittance [H,W]
     int32_t* r_tend = nullptr; size_t r_tend_cap = 0; // per-tile end of the compositing [T]

@@ -29,6 +29,7 @@ PLAN_FEATURES, PLAN_HIDDEN, PLAN_CLASSES = 8, 64, 6
 PLAN_PARAMS = PLAN_HIDDEN * PLAN_FEATURES + PLAN_HIDDEN + PLAN_HIDDEN * PLAN_HIDDEN + PLAN_HIDDEN + \
     PLAN_CLASSES * PLAN_HIDDEN + PLAN_CLASSES
 RENDER_HOST_INPUTS, RENDER_HOST_OUTPUTS, RENDER_NO_SYNC, RENDER_GRAPH, RENDER_SAVE = 1, 2, 4, 8, 16
+RENDER_PIPELINE = 32
 P_XY_AB, P_C_O_Z, P_RGB, P_RECT, P_RADIUS = range(5)
 
 # Every symbol include/tilegs.h declares (checked by the CPU export test).
@@ -43,7 +44,7 @@ EXPORTS = [
     "gs_render_batch", "gs_batch_set_view_config", "gs_batch_get_view_config", "gs_batch_last_entry_count",
     "gs_batch_autotune", "gs_rasterize_fwd_plan", "gs_tile_features", "gs_planner_set_weights", "gs_plan_tiles",
     "gs_mlp_forward", "gs_mlp_loss_grad", "gs_mlp_backward", "gs_adam_step", "gs_spatial_order",
-    "gs_gather_rows", "gs_last_flagged_tiles", "gs_reciprocal",
+    "gs_gather_rows", "gs_last_flagged_tiles", "gs_reciprocal", "gs_render_wait",
 ]
 
 
@@ -131,6 +132,7 @@ def lib():
                                              vp, vp, vp]),
         "gs_grad2d_bytes": (sz, [i64]),
         "gs_render_bwd": (C.c_int, [vp, vp, vp, vp, vp]),
+        "gs_render_wait": (C.c_int, [vp]),
         "gs_render_batch": (C.c_int, [vp, C.POINTER(GsScene), C.POINTER(GsCamera), i32, C.POINTER(C.c_float),
                                       C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i32, vp]),
         "gs_batch_set_view_config": (C.c_int, [vp, i32, C.POINTER(GsConfig)]),
@@ -434,6 +436,11 @@ class Context:
                               int(flags), _stream()), "gs_render")
         self._saved_n = int(sc.n) if flags & RENDER_SAVE else None
         return rgb, alpha, last
+
+    def render_wait(self):
+        """Wait for every render(..., flags=RENDER_PIPELINE | RENDER_HOST_INPUTS
+        | RENDER_HOST_OUTPUTS) made so far: their outputs are in host memory."""
+        check(lib().gs_render_wait(self.h), "gs_render_wait")
 
     def render_bwd(self, dl_drgb, dl_dalpha=None, grad=None):
         """Backward of the last render(..., flags=RENDER_SAVE): the gradient

@@ -412,6 +412,69 @@ def test_render_host_buffers_pageable_and_offset(tiny):
         assert ctx.error() == 0
 
 
+def _pinned_scene(sc):
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory()
+    return G.DeviceScene(pin(sc.means), pin(sc.scales), pin(sc.quats), pin(sc.opacities), pin(sc.sh),
+                         sc.sh_degree)
+
+
+def _pinned_outputs(cam):
+    H, W = cam.height, cam.width
+    return (torch.empty((H, W, 3)).pin_memory(), torch.empty((H, W)).pin_memory(),
+            torch.empty((H, W), dtype=torch.int32).pin_memory())
+
+
+def test_render_pipelined_host_buffers():
+    """Pipelined host-buffer frames: three scene / camera pairs rendered in
+    turn, twice over, each call into outputs of its own, are the oracle's
+    images bit for bit once render_wait returns.  The context's two device
+    slots alternate, so every reuse of a slot (calls i and i + 2, different
+    scenes and image sizes) has to wait for the slot's earlier frame and
+    download."""
+    hin, hout = G.RENDER_HOST_INPUTS, G.RENDER_HOST_OUTPUTS
+    pairs = [(scenes.tiny_scene(), scenes.tiny_camera()),
+             (scenes.tiny_scene(seed=3), scenes.hd_camera(position=(0.3, -0.2, 3.2), width=320, height=200, f=240.0)),
+             (scenes.mixture_scene(20000, 12), scenes.hd_camera(width=480, height=270, f=275.0))]
+    ref = [O.render(sc, cam)[3] for sc, cam in pairs]
+    hs = [_pinned_scene(sc) for sc, _ in pairs]
+    ctx = G.Context("exact")
+    for h, (_, cam) in zip(hs, pairs):  # size the entry capacity
+        ctx.render(h, cam, out=_pinned_outputs(cam), flags=hin | hout)
+    calls = []
+    for _ in range(2):
+        for i, (h, (_, cam)) in enumerate(zip(hs, pairs)):
+            out = _pinned_outputs(cam)
+            ctx.render(h, cam, out=out, flags=G.RENDER_PIPELINE | hin | hout)
+            calls.append((i, out))
+    ctx.render_wait()
+    assert ctx.error() == 0
+    for i, out in calls:
+        rgb_o, a_o, last_o = ref[i]
+        np.testing.assert_array_equal(bits(out[0].numpy()), bits(rgb_o))
+        np.testing.assert_array_equal(out[2].numpy(), last_o)
+        assert np.abs(out[1].numpy() - a_o).max() <= PIX_TOL
+
+
+def test_render_pipelined_flag_rules(tiny):
+    """A pipelined frame needs both host flags and reserved capacity, and
+    takes neither SAVE nor GRAPH; render_wait with nothing pipelined returns
+    at once."""
+    sc, cam = tiny[0], tiny[1]
+    hin, hout, pipe = G.RENDER_HOST_INPUTS, G.RENDER_HOST_OUTPUTS, G.RENDER_PIPELINE
+    hs, out = _pinned_scene(sc), _pinned_outputs(cam)
+    ctx = G.Context("exact")
+    ctx.render_wait()
+    with pytest.raises(G.TileGSError, match="invalid argument"):
+        ctx.render(hs, cam, out=out, flags=pipe | hin | hout)  # no capacity reserved yet
+    ctx.render(hs, cam, out=out, flags=hin | hout)
+    for bad in (pipe | hin, pipe | hout, pipe | hin | hout | G.RENDER_SAVE, pipe | hin | hout | G.RENDER_GRAPH):
+        with pytest.raises(G.TileGSError, match="invalid argument"):
+            ctx.render(hs, cam, out=out, flags=bad)
+    ctx.render(hs, cam, out=out, flags=pipe | hin | hout)
+    ctx.render_wait()
+    np.testing.assert_array_equal(bits(out[0].numpy()), bits(tiny[6][0]))
+
+
 # ------------------------------------------------------------------ edge cases
 
 def test_empty_scene():
