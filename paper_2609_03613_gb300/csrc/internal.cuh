@@ -138,9 +138,12 @@ __device__ __forceinline__ float spec_exp_core(float x)
     p = fmaf(p, r, 1.0f);
     p = fmaf(p, r, 1.0f);
     // bits(k) = bits(kShift) + n for |n| < 2^22, so the exponent field of
-    // 2^n is (bits(k) - bits(kShift) + 127) << 23.
-    const int e = (__float_as_int(k) - 0x4B400000 + 127) << 23;
-    return __fmul_rn(p, __int_as_float(e));
+    // 2^n is (bits(k) - bits(kShift) + 127) << 23 -- formed in unsigned
+    // arithmetic, which wraps, so that x outside the core's range (the
+    // raster evaluates it for every test and uses the value only inside)
+    // gives some float and never an undefined signed overflow.
+    const uint32_t e = (__float_as_uint(k) - 0x4B400000u + 127u) << 23;
+    return __fmul_rn(p, __uint_as_float(e));
 }
 
 // Full-range variant: clamps x to [-87, 88] first.
