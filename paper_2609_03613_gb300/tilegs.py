@@ -419,7 +419,9 @@ class Context:
         return grad
 
     def render(self, sc: DeviceScene, cam, bg=(0.0, 0.0, 0.0), out=None, flags=0):
-        """One frame through gs_render (all intermediates in context scratch)."""
+        """One frame through gs_render (all intermediates in context scratch).
+        With RENDER_PIPELINE (and both host flags) the call returns before its
+        outputs land; render_wait() waits for them."""
         import torch
         H, W = int(cam.height), int(cam.width)
         if out is None:
