@@ -42,6 +42,29 @@ def test_library_exports_every_declared_symbol(G):
     assert sorted(names) == sorted(G.EXPORTS)
 
 
+def header_constants():
+    """Every `GS_NAME = value` enumerator include/tilegs.h declares."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(GS_[A-Z0-9_]+)\s*=\s*(\d+)", src)}
+
+
+def test_binding_constants_match_header(G):
+    """The binding passes flags, modes and status codes as plain integers:
+    each must be the header's value."""
+    h = header_constants()
+    for name in ["RENDER_HOST_INPUTS", "RENDER_HOST_OUTPUTS", "RENDER_NO_SYNC", "RENDER_GRAPH", "RENDER_SAVE",
+                 "RENDER_PIPELINE", "MODE_GLOBAL_SORT", "MODE_BINNED_EXACT", "MODE_BINNED_PAPER",
+                 "MODE_BINNED_NOREPAIR"]:
+        assert getattr(G, name) == h["GS_" + name], name
+    flags = [h[k] for k in h if k.startswith("GS_RENDER_")]
+    assert len(set(flags)) == len(flags) and all(f & (f - 1) == 0 for f in flags)  # distinct single bits
+    assert G.GS_OK == h["GS_OK"]
+    errs = {v: k for k, v in h.items() if k.startswith("GS_ERR_")}
+    assert sorted(G.ERRORS) == sorted(errs)
+    assert G.MODES == {"global": h["GS_MODE_GLOBAL_SORT"], "exact": h["GS_MODE_BINNED_EXACT"],
+                       "paper": h["GS_MODE_BINNED_PAPER"], "norepair": h["GS_MODE_BINNED_NOREPAIR"]}
+
+
 def test_defaults_match_paper_tables(G):
     gold = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_defaults.json")))
     cfg = G.default_config("paper")
